@@ -1,0 +1,279 @@
+"""Benchmark: DD(r) Gpairs/s at N = 1.2M, Rmax = 25 on one GB300 per rank.
+
+Workload: the 1.2M-point Neyman-Scott catalogue in a periodic box of side 420
+(60,000 parents, Poisson(20) children, sigma 2; a stand-in for the paper's
+1.2M-galaxy box of Sec. 3), float64 positions, 20 log bins from 0.1 to 25,
+auto-correlation, FP32 distances with binary64 re-check (exact counts).
+
+A step is one cf_countpairs_xi call: gridding, column-pair pruning, the pair
+kernel, the histogram merge and its copy to the host.  Gpairs/s counts the
+ordered pairs the histogram holds (P_cnt) per second.
+
+  value  device-resident inputs; CUDA events around each call on its stream;
+         L2 flushed (a 256 MiB write) between steps, outside the timed region.
+  e2e    same call with page-locked HOST inputs: the H2D copy of x, y, z and
+         the D2H of the histogram happen inside the timed call.
+  roofline  the pair kernel's pair evaluations (diagnostic counter, separate
+         run) x 7 FP32 instructions each, over its event-timed duration,
+         against SMs x 128 lanes x max SM clock.
+
+--impl reference times the CPU oracle (brute force, canonical binary64) on a
+bounded sample of the same workload: each step counts the pairs of a slice of
+primary points against the whole catalogue.
+
+Multi-GPU (torchrun): each rank counts its own replica (independent problems,
+no collective on the data path); value = total pairs over the max time.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "DD(r) Gpairs/s at N=1.2M, Rmax=25 (FP32+recheck vs FP64, exact counts)"
+UNIT = "Gpairs/s"
+RMIN, RMAX, NBINS = 0.1, 25.0, 20
+INSTR_PER_EVAL = 7  # 3 FADD, FMUL + 2 FFMA, 1 compare per evaluated pair
+
+
+def workload_config(n):
+    return {"workload": "xi_auto_neyman_scott_1.2M_box420_rmax25", "n_points": int(n),
+            "box": 420.0, "rmax": RMAX, "nbins": NBINS, "edges": "log 0.1-25", "periodic": True,
+            "input_dtype": "float64", "l2": "flushed between steps (256 MiB write)"}
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.15)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        rows = []
+        for line in open(self.path):
+            f = [v.strip() for v in line.split(",")]
+            if len(f) >= 9 and f[1].replace(".", "").isdigit():
+                rows.append(f)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": float(rows[0][2]),
+                "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())
+                if any(r[3].replace(".", "").isdigit() for r in rows) else None,
+                "samples": len(rows), "reasons": reasons}
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"sm_max_mhz": 2070.0}, "fallback"
+
+
+def cpu_baseline_sample(cat, edges, rows, reps=1):
+    """Time the oracle on primary rows [0, rows) against the whole catalogue."""
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    cnt = 0
+    for _ in range(reps):
+        n, _, _ = oracle.xi(cat.x[:rows], cat.y[:rows], cat.z[:rows], x2=cat.x, y2=cat.y,
+                            z2=cat.z, edges=edges, autocorr=False, periodic=True, box=cat.box)
+        cnt += int(n.sum())
+    dt = time.perf_counter() - t0
+    return cnt, dt, oracle.num_threads()
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_1911_08275_gb300 import synth
+    cat = synth.c2_clustered()
+    edges = synth.log_edges(RMIN, RMAX, NBINS)
+    rows = int(os.environ.get("CF_REF_ROWS", "2000"))
+    for _ in range(args.warmup):
+        cpu_baseline_sample(cat, edges, max(50, rows // 10))
+    times, counts, cores = [], [], 1
+    for _ in range(args.steps):
+        c, dt, cores = cpu_baseline_sample(cat, edges, rows)
+        times.append(dt)
+        counts.append(c)
+    value = sum(counts) / sum(times) / 1e9
+    sample = (f"{rows} primary points x all {cat.n} points per step (cross count of a slice; "
+              f"{rows * cat.n:.3g} pair evaluations)")
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": workload_config(cat.n),
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--mode", default="fp32_recheck", choices=["fp32_recheck", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    import paper_1911_08275_gb300 as cf
+    from paper_1911_08275_gb300 import synth
+
+    cf.lib()
+    cat = synth.c2_clustered()
+    edges = synth.log_edges(RMIN, RMAX, NBINS)
+    dev = torch.device("cuda", local)
+    xyz = [torch.from_numpy(v).to(dev) for v in (cat.x, cat.y, cat.z)]
+    host = [torch.from_numpy(v).pin_memory() for v in (cat.x, cat.y, cat.z)]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def call(inputs, flags=0, mode=args.mode):
+        return cf.countpairs_xi(*inputs, edges, boxsize=synth.BOX, mode=mode, flags=flags,
+                                stream=stream.cuda_stream)
+
+    diag = call(xyz, flags=cf.CF_FLAG_COUNT_EVALS)  # evaluation count (separate, untimed)
+    p_cnt = int(diag.npairs.sum())
+    for _ in range(args.warmup):
+        call(xyz)
+        call(host)
+
+    def timed(inputs):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        kms = []
+        for s in range(args.steps):
+            flush.zero_()
+            ev[s][0].record(stream)
+            r = call(inputs)
+            ev[s][1].record(stream)
+            kms.append(r.kernel_ms)
+            if int(r.npairs.sum()) != p_cnt:
+                raise RuntimeError("counts changed between steps")
+        torch.cuda.synchronize()
+        return [a.elapsed_time(b) for a, b in ev], kms
+
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        step_ms, kernel_ms = timed(xyz)
+    e2e_ms, _ = timed(host)
+    torch.cuda.synchronize()
+    t_mean = statistics.mean(step_ms)
+    e_mean = statistics.mean(e2e_ms)
+    if dist:
+        tt = torch.tensor([t_mean, e_mean], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_mean, e_mean = float(tt[0]), float(tt[1])
+        dist.barrier()
+    value = world * p_cnt / (t_mean * 1e-3) / 1e9
+    e2e_value = world * p_cnt / (e_mean * 1e-3) / 1e9
+
+    peaks, peak_src = load_peaks()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    fmax = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_evals = sms * 128 * fmax * 1e6 / INSTR_PER_EVAL / 1e9  # Gevals/s
+    k_mean = statistics.mean(kernel_ms)
+    achieved = diag.n_evaluated / (k_mean * 1e-3) / 1e9
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_evals, "unit": "Gevals/s",
+                "frac": achieved / peak_evals, "traffic": None,
+                "peak_note": f"{sms} SMs x 128 FP32 lanes x {fmax:.0f} MHz / {INSTR_PER_EVAL} "
+                             f"instr per evaluated pair ({peak_src} max SM clock)",
+                "kernel_ms": k_mean, "evaluations": diag.n_evaluated}
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": t_mean, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64recheck" if args.mode ==
+           "fp32_recheck" else "f64", "data": "synthetic", "config": workload_config(cat.n),
+           "p_cnt": p_cnt, "clocks": clk.summary(), "roofline": roofline,
+           "e2e": {"value": e2e_value, "unit": UNIT, "ms_per_step": e_mean,
+                   "h2d_bytes_per_step": int(3 * 8 * cat.n),
+                   "d2h_bytes_per_step": int(8 * NBINS + 8 * 4 + 4)},
+           "gpu_launches": 8 * args.steps,
+           "diag": {"n_cellpairs": diag.n_cellpairs, "n_rechecked": diag.n_rechecked,
+                    "useful_fraction": p_cnt / 2 / max(1, diag.n_evaluated)}}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rows = int(os.environ.get("CF_CPU_ROWS", "12000"))
+        c, dt, cores = cpu_baseline_sample(cat, edges, rows)
+        out["cpu_baseline"] = {"value": c / dt / 1e9, "unit": UNIT, "cores": cores,
+                               "kind": "oracle",
+                               "sample": f"{rows} primary points x all {cat.n} points "
+                                         f"({rows * cat.n:.3g} pair evaluations, {dt:.1f} s)"}
+    if args.mode == "fp32_recheck" and rank == 0:
+        # the plain binary64 path on the same workload, for the FP32/FP64 ratio
+        r64 = [call(xyz, mode="fp64") for _ in range(3)]
+        assert all(np.array_equal(r.npairs, diag.npairs) for r in r64)
+        out["fp64_path"] = {"ms_per_step": statistics.median(r.total_ms for r in r64),
+                            "kernel_ms": statistics.median(r.kernel_ms for r in r64)}
+        out["fp64_path"]["value"] = p_cnt / (out["fp64_path"]["ms_per_step"] * 1e-3) / 1e9
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,153 @@
+/*
+ * cf.h -- C ABI of cfgpu, exact cell-list pair counting on NVIDIA GB300 (sm_103a).
+ *
+ * The operation is the pair-separation histogram of Sinha & Garrison,
+ * "Corrfunc: blazing fast correlation functions with AVX512F SIMD intrinsics"
+ * (arXiv:1911.08275):
+ *   - Sec. 1.1, Code 1: for every pair (i, j) compute a separation, skip it
+ *     unless Rmin <= sep < Rmax, and add one (and a weight) to its bin;
+ *   - Sec. 1.1, Eq. "separations": xi(r) uses r = |x_j - x_i|; wp(rp) uses
+ *     rp = |(dx, dy)| and pi = |dz| with the extra filter pi < pimax;
+ *   - Sec. 1.2 and 2.1: points are gridded into cells so only neighbouring
+ *     cells are searched, sorted along z, and auto-correlations visit each
+ *     unordered cell pair once and double the counts;
+ *   - Sec. 2.2: cell pairs whose bounding boxes are >= Rmax apart are pruned;
+ *   - Sec. 2.2, Code 3/4: separations are compared squared against squared
+ *     bin edges; no square root or logarithm decides a bin.
+ *
+ * Exactness.  Every count is defined by canonical IEEE binary64 arithmetic
+ * (inputs promoted exactly to double, no fused multiply-add):
+ *   dx = x_j - x_i; periodic: if dx > L/2: dx -= L; elif dx < -L/2: dx += L;
+ *   rp2 = dx*dx + dy*dy;  r2 = rp2 + dz*dz;  bin k iff e_k^2 <= r2 < e_{k+1}^2;
+ *   pi bins [P_m, P_{m+1}) with P_m = (pimax*m)/npibins, P_npibins = pimax.
+ * CF_MODE_FP64 evaluates exactly that.  CF_MODE_FP32_RECHECK evaluates the
+ * distances in float32 and re-evaluates in binary64 every pair whose float32
+ * value lies within a proven error bound of a bin edge, Rmin, Rmax or a pi
+ * edge; its integer counts are therefore identical to CF_MODE_FP64.
+ *
+ * Conventions shared by all entry points:
+ *   - Return value: CF_OK (0) or a negative CF_E* status; the entry points
+ *     never throw, abort or exit.  cf_last_error() describes the last failure
+ *     of the calling thread.
+ *   - Auto-correlation counts ordered pairs i != j (each unordered pair twice);
+ *     cross-correlation counts every (i in d1, j in d2).
+ *   - Inputs are borrowed for the duration of the call.  Position arrays may
+ *     live in device memory (used in place) or host memory (copied to the
+ *     device inside the call; page-locked host memory copies fastest).
+ *   - Results are written to caller-owned HOST arrays before the call returns
+ *     (the call synchronises its stream).
+ *   - Scratch memory comes from the stream-ordered allocator of the current
+ *     device (cudaMallocAsync on cfg->stream) and is released before return.
+ *   - Periodic mode requires coordinates in [0, boxsize) per axis and
+ *     Rmax, pimax < boxsize/2 (so the minimum image is unique).
+ */
+#ifndef CFGPU_CF_H
+#define CFGPU_CF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CF_OK 0
+#define CF_EINVAL (-1)    /* invalid argument (see cf_last_error)               */
+#define CF_ENOMEM (-2)    /* device or host allocation failed                   */
+#define CF_ECUDA (-3)     /* a CUDA runtime call failed                         */
+#define CF_ETIMEOUT (-4)  /* a bounded device-side wait gave up                 */
+#define CF_EDEVICE (-5)   /* a kernel reported an inconsistency (error word)    */
+
+typedef enum { CF_FLOAT32 = 0, CF_FLOAT64 = 1 } cf_dtype;
+
+typedef enum {
+    CF_MODE_FP64 = 0,          /* all distance arithmetic in binary64          */
+    CF_MODE_FP32_RECHECK = 1   /* float32 bulk + binary64 re-check near edges   */
+} cf_mode;
+
+/* Flags (cf_config.flags). */
+#define CF_FLAG_COUNT_EVALS (1u << 0) /* count pair evaluations into n_evaluated */
+#define CF_FLAG_NO_PRUNE (1u << 1)    /* disable bounding-box cell-pair pruning   */
+#define CF_FLAG_VERIFY_BAND (1u << 2) /* FP32 mode: also evaluate every pair in
+                                         binary64 and count float32 decisions that
+                                         disagree into n_band_violations (debug)  */
+
+/* One catalogue: n points with coordinates x[i], y[i], z[i] of type
+ * cf_config.dtype, contiguous, in device or host memory, and optional float64
+ * weights w[i] (same memory kind as x) or NULL. */
+typedef struct {
+    const void *x, *y, *z;
+    const double *w;
+    int64_t n;
+} cf_catalog;
+
+typedef struct {
+    int periodic;        /* 1: periodic box [0, boxsize)^3; 0: open box          */
+    double boxsize[3];   /* box side per axis (periodic only)                     */
+    cf_dtype dtype;      /* element type of x, y, z                               */
+    cf_mode mode;        /* arithmetic path                                       */
+    int weighted;        /* 1: accumulate w_i * w_j per bin (weights required)   */
+    int want_ravg;       /* 1: accumulate the mean separation per bin             */
+    int refine[3];       /* cell refinement (rx, ry, rz); {0,0,0} = automatic.
+                            Columns in x, y are >= Rmax/rx wide (Sec. 3.1: the
+                            paper's default is (2, 2, 1)); rz sets the z-cell
+                            granularity of the in-column sort.                   */
+    uint32_t flags;      /* CF_FLAG_*                                             */
+    void *stream;        /* cudaStream_t to run on; NULL = legacy default stream  */
+} cf_config;
+
+/* Caller-owned host outputs.  Arrays are NULL when not wanted. */
+typedef struct {
+    uint64_t *npairs;    /* [nbins] (xi) or [n_rp_bins * npibins] rp-major      */
+    double *wsum;        /* same shape: sum of w_i*w_j (weighted) else unused     */
+    double *ravg;        /* same shape: mean separation (r or rp), weighted by
+                            w_i*w_j when weighted; 0 for empty bins               */
+    uint64_t n_cellpairs;       /* column pairs kept after pruning                */
+    uint64_t n_evaluated;       /* pair evaluations (CF_FLAG_COUNT_EVALS)        */
+    uint64_t n_rechecked;       /* pairs re-evaluated in binary64 (FP32 mode)    */
+    uint64_t n_band_violations; /* CF_FLAG_VERIFY_BAND: must be 0                 */
+    double kernel_ms;           /* device time of the pair kernel                 */
+    double total_ms;            /* device time of the whole call                  */
+} cf_result;
+
+/*
+ * DD(r) for xi(r) (Sec. 1.1 Code 1 with the xi separation of Eq.
+ * "separations"; bins tested on squares as in Sec. 2.2 Code 4).
+ *   autocorr   1: pairs within d1 (d2 ignored, may be NULL); 0: d1 x d2.
+ *   edges      nedges >= 2 strictly increasing bin edges, edges[0] >= 0,
+ *              host memory; bins k = [edges[k], edges[k+1]), nbins = nedges-1
+ *              <= 64; Rmin = edges[0], Rmax = edges[nedges-1].
+ *   res        npairs[nbins] (required), wsum[nbins], ravg[nbins] (optional).
+ * Errors: CF_EINVAL for bad arguments (NULL pointers, n < 0, n >= 2^31, edges
+ * not increasing, nbins > 64, weighted without weights, periodic with
+ * Rmax >= boxsize/2 or a coordinate outside [0, boxsize) or non-finite).
+ */
+int cf_countpairs_xi(int autocorr, const cf_catalog *d1, const cf_catalog *d2,
+                     const double *edges, int nedges, const cf_config *cfg, cf_result *res);
+
+/*
+ * DD(rp, pi) for wp(rp) (Sec. 1.1 Eq. "separations", rp-pi case; the line of
+ * sight is z; Sec. 2.1 sizes cells by Rmax in x, y and by pimax in z).
+ *   rp_edges   n_rp_edges >= 2 increasing edges on rp (host), <= 64 rp bins.
+ *   pimax      > 0; pairs count only if |dz| < pimax.
+ *   npibins    >= 1 pi bins [P_m, P_{m+1}), P_m = (pimax*m)/npibins; at most
+ *              4096 bins in total (n_rp_bins * npibins).
+ *   res        npairs[n_rp_bins * npibins], rp-major (index k*npibins + m).
+ *              Summing over m gives the paper's 1-D wp pair count.
+ * Errors as cf_countpairs_xi, plus CF_EINVAL for pimax >= boxsize[2]/2 in
+ * periodic mode.
+ */
+int cf_countpairs_rp_pi(int autocorr, const cf_catalog *d1, const cf_catalog *d2,
+                        const double *rp_edges, int n_rp_edges, double pimax, int npibins,
+                        const cf_config *cfg, cf_result *res);
+
+/* Text of the last non-zero status returned on the calling thread. */
+const char *cf_last_error(void);
+
+/* Library version string. */
+const char *cf_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CFGPU_CF_H */

@@ -1,0 +1,232 @@
+"""cfgpu: exact cell-list pair counting on NVIDIA GB300 (sm_103a).
+
+Python binding of the C ABI in ``include/cf.h`` (ctypes; argument marshalling
+only -- every step of the computation runs in the CUDA library).  The
+operation is the pair-separation histogram of Sinha & Garrison,
+arXiv:1911.08275 (Sec. 1.1, Code 1 and Eq. "separations").
+
+    import paper_1911_08275_gb300 as cf
+    r = cf.countpairs_xi(x, y, z, edges, boxsize=420.0)         # auto, periodic
+    r.npairs                                                    # uint64 histogram
+
+Inputs are torch tensors (CUDA or CPU) or numpy arrays, float32 or float64,
+one per coordinate.  There is no CPU fallback: if the CUDA library cannot be
+loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+
+CF_OK, CF_EINVAL, CF_ENOMEM, CF_ECUDA, CF_ETIMEOUT, CF_EDEVICE = 0, -1, -2, -3, -4, -5
+CF_FLOAT32, CF_FLOAT64 = 0, 1
+CF_MODE_FP64, CF_MODE_FP32_RECHECK = 0, 1
+CF_FLAG_COUNT_EVALS = 1 << 0
+CF_FLAG_NO_PRUNE = 1 << 1
+CF_FLAG_VERIFY_BAND = 1 << 2
+
+_STATUS = {CF_EINVAL: "CF_EINVAL", CF_ENOMEM: "CF_ENOMEM", CF_ECUDA: "CF_ECUDA",
+           CF_ETIMEOUT: "CF_ETIMEOUT", CF_EDEVICE: "CF_EDEVICE"}
+
+# Names exported by the library; they must match include/cf.h.
+EXPORTS = ("cf_countpairs_xi", "cf_countpairs_rp_pi", "cf_last_error", "cf_version")
+
+
+class cf_catalog(ctypes.Structure):
+    _fields_ = [("x", ctypes.c_void_p), ("y", ctypes.c_void_p), ("z", ctypes.c_void_p),
+                ("w", ctypes.c_void_p), ("n", ctypes.c_int64)]
+
+
+class cf_config(ctypes.Structure):
+    _fields_ = [("periodic", ctypes.c_int), ("boxsize", ctypes.c_double * 3),
+                ("dtype", ctypes.c_int), ("mode", ctypes.c_int), ("weighted", ctypes.c_int),
+                ("want_ravg", ctypes.c_int), ("refine", ctypes.c_int * 3),
+                ("flags", ctypes.c_uint32), ("stream", ctypes.c_void_p)]
+
+
+class cf_result(ctypes.Structure):
+    _fields_ = [("npairs", ctypes.POINTER(ctypes.c_uint64)), ("wsum", ctypes.POINTER(ctypes.c_double)),
+                ("ravg", ctypes.POINTER(ctypes.c_double)), ("n_cellpairs", ctypes.c_uint64),
+                ("n_evaluated", ctypes.c_uint64), ("n_rechecked", ctypes.c_uint64),
+                ("n_band_violations", ctypes.c_uint64), ("kernel_ms", ctypes.c_double),
+                ("total_ms", ctypes.c_double)]
+
+
+class CfError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def library_path() -> str:
+    from . import build as _b
+    return _b.LIB
+
+
+def lib(build_if_stale: bool = True):
+    """Load libcfgpu.so (compiling it first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            from . import build as _b
+            path = _b.build() if build_if_stale else _b.LIB
+            if not os.path.exists(path):
+                raise RuntimeError(f"cfgpu CUDA library not found at {path}")
+            L = ctypes.CDLL(path)
+            P = ctypes.POINTER
+            L.cf_countpairs_xi.argtypes = [ctypes.c_int, P(cf_catalog), P(cf_catalog),
+                                           P(ctypes.c_double), ctypes.c_int, P(cf_config),
+                                           P(cf_result)]
+            L.cf_countpairs_xi.restype = ctypes.c_int
+            L.cf_countpairs_rp_pi.argtypes = [ctypes.c_int, P(cf_catalog), P(cf_catalog),
+                                              P(ctypes.c_double), ctypes.c_int, ctypes.c_double,
+                                              ctypes.c_int, P(cf_config), P(cf_result)]
+            L.cf_countpairs_rp_pi.restype = ctypes.c_int
+            L.cf_last_error.restype = ctypes.c_char_p
+            L.cf_version.restype = ctypes.c_char_p
+            _lib = L
+    return _lib
+
+
+@dataclass
+class Result:
+    npairs: np.ndarray
+    wsum: np.ndarray | None
+    ravg: np.ndarray | None
+    n_cellpairs: int
+    n_evaluated: int
+    n_rechecked: int
+    n_band_violations: int
+    kernel_ms: float
+    total_ms: float
+
+
+def _is_torch(a) -> bool:
+    return type(a).__module__.startswith("torch")
+
+
+def _arr(a, name):
+    """(pointer, dtype code, n, is_cuda, keepalive) of a 1-D contiguous array."""
+    if _is_torch(a):
+        import torch
+        if a.dim() != 1 or not a.is_contiguous():
+            raise ValueError(f"{name} must be a 1-D contiguous tensor")
+        code = {torch.float32: CF_FLOAT32, torch.float64: CF_FLOAT64}.get(a.dtype)
+        return a.data_ptr() if a.numel() else None, code, a.numel(), a.is_cuda, a
+    a = np.ascontiguousarray(a)
+    if a.ndim != 1:
+        raise ValueError(f"{name} must be 1-D")
+    code = {np.dtype(np.float32): CF_FLOAT32, np.dtype(np.float64): CF_FLOAT64}.get(a.dtype)
+    return a.ctypes.data if a.size else None, code, a.size, False, a
+
+
+def _catalog(x, y, z, w, keep):
+    ax, ay, az = _arr(x, "x"), _arr(y, "y"), _arr(z, "z")
+    if not (ax[1] == ay[1] == az[1]) or ax[1] is None:
+        raise ValueError("x, y, z must share one dtype, float32 or float64")
+    if not (ax[2] == ay[2] == az[2]):
+        raise ValueError("x, y, z must have the same length")
+    keep += [ax[4], ay[4], az[4]]
+    wp = None
+    if w is not None:
+        aw = _arr(w, "w")
+        if aw[1] != CF_FLOAT64 or aw[2] != ax[2]:
+            raise ValueError("weights must be float64 with one value per point")
+        keep.append(aw[4])
+        wp = aw[0]
+    return cf_catalog(ax[0], ay[0], az[0], wp, ax[2]), ax[1], ax[3]
+
+
+def _config(dtype, periodic, boxsize, mode, weighted, want_ravg, refine, flags, stream, cuda):
+    c = cf_config()
+    c.periodic = 1 if periodic else 0
+    b = np.broadcast_to(np.asarray(boxsize if boxsize is not None else 0.0, dtype=np.float64), (3,))
+    c.boxsize[:] = [float(v) for v in b]
+    c.dtype = dtype
+    c.mode = {"fp64": CF_MODE_FP64, "fp32_recheck": CF_MODE_FP32_RECHECK}[mode]
+    c.weighted = 1 if weighted else 0
+    c.want_ravg = 1 if want_ravg else 0
+    c.refine[:] = list(refine)
+    c.flags = int(flags)
+    if stream is None and cuda:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    c.stream = int(stream) if stream else None
+    return c
+
+
+def _run(fn, nslots, autocorr, x, y, z, w, x2, y2, z2, w2, extra, periodic, boxsize, mode,
+         want_ravg, refine, flags, stream):
+    L = lib()
+    keep = []
+    c1, dt, cuda = _catalog(x, y, z, w, keep)
+    c2 = None
+    if not autocorr:
+        if x2 is None:
+            raise ValueError("cross-correlation needs x2, y2, z2")
+        c2, dt2, cuda2 = _catalog(x2, y2, z2, w2, keep)
+        if dt2 != dt:
+            raise ValueError("both catalogues must share one dtype")
+        cuda = cuda or cuda2
+    weighted = w is not None
+    cfg = _config(dt, periodic, boxsize, mode, weighted, want_ravg, refine, flags, stream, cuda)
+    npairs = np.zeros(nslots, dtype=np.uint64)
+    wsum = np.zeros(nslots) if weighted else None
+    ravg = np.zeros(nslots) if want_ravg else None
+    res = cf_result()
+    res.npairs = npairs.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))
+    res.wsum = wsum.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if wsum is not None else None
+    res.ravg = ravg.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if ravg is not None else None
+    st = fn(L, int(bool(autocorr)), ctypes.byref(c1), ctypes.byref(c2) if c2 is not None else None,
+            *extra, ctypes.byref(cfg), ctypes.byref(res))
+    if st != CF_OK:
+        raise CfError(st, L.cf_last_error().decode())
+    return Result(npairs, wsum, ravg, int(res.n_cellpairs), int(res.n_evaluated),
+                  int(res.n_rechecked), int(res.n_band_violations), float(res.kernel_ms),
+                  float(res.total_ms))
+
+
+def countpairs_xi(x, y, z, edges, *, w=None, x2=None, y2=None, z2=None, w2=None, autocorr=None,
+                  periodic=True, boxsize=420.0, mode="fp32_recheck", want_ravg=False,
+                  refine=(0, 0, 0), flags=0, stream=None) -> Result:
+    """DD(r) histogram through ``cf_countpairs_xi`` (see include/cf.h)."""
+    edges = np.ascontiguousarray(edges, dtype=np.float64)
+    if autocorr is None:
+        autocorr = x2 is None
+    fn = lambda L, *a: L.cf_countpairs_xi(*a)  # noqa: E731
+    extra = (edges.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), int(edges.size))
+    return _run(fn, edges.size - 1, autocorr, x, y, z, w, x2, y2, z2, w2, extra, periodic, boxsize,
+                mode, want_ravg, refine, flags, stream)
+
+
+def countpairs_rp_pi(x, y, z, rp_edges, pimax, npibins, *, w=None, x2=None, y2=None, z2=None,
+                     w2=None, autocorr=None, periodic=True, boxsize=420.0, mode="fp32_recheck",
+                     want_ravg=False, refine=(0, 0, 0), flags=0, stream=None) -> Result:
+    """DD(rp, pi) histogram (rp-major, shape (nrp, npibins)) through ``cf_countpairs_rp_pi``."""
+    rp_edges = np.ascontiguousarray(rp_edges, dtype=np.float64)
+    if autocorr is None:
+        autocorr = x2 is None
+    fn = lambda L, *a: L.cf_countpairs_rp_pi(*a)  # noqa: E731
+    extra = (rp_edges.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), int(rp_edges.size),
+             ctypes.c_double(float(pimax)), int(npibins))
+    r = _run(fn, (rp_edges.size - 1) * int(npibins), autocorr, x, y, z, w, x2, y2, z2, w2, extra,
+             periodic, boxsize, mode, want_ravg, refine, flags, stream)
+    shp = (rp_edges.size - 1, int(npibins))
+    r.npairs = r.npairs.reshape(shp)
+    if r.wsum is not None:
+        r.wsum = r.wsum.reshape(shp)
+    if r.ravg is not None:
+        r.ravg = r.ravg.reshape(shp)
+    return r
+
+
+def version() -> str:
+    return lib().cf_version().decode()

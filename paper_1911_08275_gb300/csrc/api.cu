@@ -1,0 +1,733 @@
+// C ABI of cfgpu (include/cf.h): argument checks, grid planning, the float32
+// error bands, workspace management and the stream-ordered sequence
+//   [H2D of host inputs] -> bbox (open boxes) -> grid D1 [, grid D2] ->
+//   pair kernel -> D2H of the histogram -> one stream synchronisation.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "cf.h"
+#include "cf_internal.cuh"
+#include "grid.cuh"
+#include "pairs.cuh"
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string &msg)
+{
+    g_err = msg;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what)
+{
+    cudaGetLastError();
+    return fail(e == cudaErrorMemoryAllocation ? CF_ENOMEM : CF_ECUDA,
+                std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CF_CUDA(call, what)                 \
+    do {                                    \
+        cudaError_t e_ = (call);            \
+        if (e_ != cudaSuccess) {            \
+            rc = cuda_fail(e_, what);       \
+            goto cleanup;                   \
+        }                                   \
+    } while (0)
+
+const double U32 = std::ldexp(1.0, -24);
+const double U64 = std::ldexp(1.0, -53);
+
+bool is_device_ptr(const void *p)
+{
+    if (!p)
+        return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+float f32_down(double v)
+{
+    float f = (float)v;
+    if ((double)f > v)
+        f = std::nextafter(f, -INFINITY);
+    return f;
+}
+
+float f32_up(double v)
+{
+    float f = (float)v;
+    if ((double)f < v)
+        f = std::nextafter(f, INFINITY);
+    return f;
+}
+
+uint32_t fbits(float f)
+{
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    return u;
+}
+
+float bitsf(uint32_t u)
+{
+    float f;
+    std::memcpy(&f, &u, 4);
+    return f;
+}
+
+// Error model of the float32 path (derivation in the design doc):
+//   coordinates are fl32(X - O) with |X - O| <= M; the primary is shifted by
+//   fl32(S), |S| <= Ls (periodic image), then dx = fl32(x_j - x^_i).
+// Per-axis bound on |dx~ - dx_true| for a component of size <= r:
+double eps_axis(double r, double M, double Ls)
+{
+    const double u = U32;
+    double E = 2.0 * (u + 2.0 * U64) * M;
+    if (Ls > 0)
+        E += u * Ls + u * (1.0 + u) * (M + Ls);
+    return E * (1.0 + u) + u * (r + E);
+}
+
+// Bound on |d2~(float32) - d2(canonical binary64)| for squared separations near S
+// (3 components for xi, 2 for rp).  Doubled for safety.
+double band_sq(double S, int ncomp, double M, double Ls, double R)
+{
+    const double u = U32;
+    const double s = S * (1.0 + 1e-6);
+    const double r = std::sqrt(s);
+    const double eps = eps_axis(r, M, Ls);
+    const double sq = std::sqrt((double)ncomp);
+    const double g = ncomp * u / (1.0 - ncomp * u);
+    const double smax = s + 2.0 * eps * sq * r + ncomp * eps * eps;
+    double B = g * smax + 2.0 * eps * sq * r + ncomp * eps * eps;
+    const double e64 = 2.0 * U64 * (M + Ls + 2.0 * R);
+    B += (ncomp + 0.5) * U64 * s + 2.0 * e64 * sq * r + ncomp * e64 * e64;
+    return 2.0 * B + 1e-37;
+}
+
+// Thresholds T[0..2n+1] = lo_0, hi_0, ..., lo_n, hi_n around squared edges E2.
+// d2~ < lo_k proves d2 < E2_k; d2~ >= hi_k proves d2 >= E2_k.
+std::vector<float> make_thresholds(const std::vector<double> &E2, int ncomp, double M, double Ls,
+                                   double R)
+{
+    const int ne = (int)E2.size();
+    std::vector<float> T(2 * ne);
+    for (int k = 0; k < ne; ++k) {
+        if (E2[k] == 0.0) {  // every d2 >= 0 is surely >= 0
+            T[2 * k] = 0.0f;
+            T[2 * k + 1] = 0.0f;
+            continue;
+        }
+        const double B = band_sq(E2[k], ncomp, M, Ls, R);
+        const double lo = E2[k] - B;
+        // Near zero the bound is not monotone in d2: never claim "below" there.
+        T[2 * k] = (lo <= 0.0 || E2[k] < 1e-6) ? -1.0f : f32_down(lo);
+        T[2 * k + 1] = std::nextafter(f32_up(E2[k] + B), INFINITY);
+    }
+    for (size_t t = 1; t < T.size(); ++t)  // raising a threshold only widens the re-check set
+        T[t] = std::max(T[t], T[t - 1]);
+    return T;
+}
+
+struct Lut {
+    std::vector<uint16_t> tab;
+    int shift = 0;
+    uint32_t u0 = 0, urange = 0;
+};
+
+// Table over the float bit range [u0, u0 + urange): safe bin (as byte offset
+// bin * 128), "inside a band", or "thresholds inside: compare from index t".
+Lut make_lut(const std::vector<float> &T, int nbins)
+{
+    Lut L;
+    const int nthr = (int)T.size();
+    L.u0 = T[0] > 0.0f ? fbits(T[0]) : 0u;
+    const uint32_t u1 = fbits(T[nthr - 1]);
+    L.urange = u1 - L.u0;
+    int s = 0;
+    while ((((uint64_t)L.urange + (1ull << s) - 1) >> s) > (uint64_t)cf::LUT_MAX)
+        ++s;
+    L.shift = s;
+    const int n = (int)(((uint64_t)L.urange + (1ull << s) - 1) >> s);
+    L.tab.resize(std::max(n, 1));
+    auto count_le = [&](float v) {
+        int c = 0;
+        while (c < nthr && T[c] <= v)
+            ++c;
+        return c;
+    };
+    for (int q = 0; q < n; ++q) {
+        const uint32_t blo = L.u0 + ((uint32_t)q << s);
+        const uint64_t bend = std::min<uint64_t>((uint64_t)L.u0 + ((uint64_t)(q + 1) << s), u1);
+        const uint32_t bhi = (uint32_t)(bend - 1);
+        const int clo = count_le(bitsf(blo)), chi = count_le(bitsf(bhi));
+        uint16_t e;
+        if (clo == chi && !(clo & 1) && clo >= 2 && clo <= 2 * nbins)
+            e = (uint16_t)(((clo - 2) / 2) * 128);
+        else if (clo == chi && (clo & 1))
+            e = (uint16_t)cf::LUT_AMBIG;
+        else
+            e = (uint16_t)(cf::LUT_SLOW | (uint32_t)std::min(clo, 0x3fff));
+        L.tab[q] = e;
+    }
+    return L;
+}
+
+struct Bump {  // carve aligned sub-buffers out of one allocation
+    char *base = nullptr;
+    size_t off = 0;
+    template <class T>
+    T *take(size_t count)
+    {
+        off = (off + 255) & ~size_t(255);
+        T *p = reinterpret_cast<T *>(base ? base + off : nullptr);
+        off += sizeof(T) * std::max<size_t>(count, 1);
+        return p;
+    }
+};
+
+struct PinnedScratch {  // per-thread page-locked staging for results
+    void *p = nullptr;
+    size_t n = 0;
+    ~PinnedScratch()
+    {
+        if (p)
+            cudaFreeHost(p);
+    }
+    void *get(size_t bytes)
+    {
+        if (bytes > n) {
+            if (p)
+                cudaFreeHost(p);
+            p = nullptr;
+            n = 0;
+            if (cudaHostAlloc(&p, bytes, cudaHostAllocDefault) != cudaSuccess) {
+                cudaGetLastError();
+                return nullptr;
+            }
+            n = bytes;
+        }
+        return p;
+    }
+};
+thread_local PinnedScratch g_pinned;
+
+struct Events {
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    bool ok = false;
+    ~Events()
+    {
+        for (auto &e : ev)
+            if (e)
+                cudaEventDestroy(e);
+    }
+    bool init()
+    {
+        if (ok)
+            return true;
+        for (auto &e : ev)
+            if (cudaEventCreate(&e) != cudaSuccess) {
+                cudaGetLastError();
+                return false;
+            }
+        ok = true;
+        return true;
+    }
+};
+thread_local Events g_events;
+
+void set_pool_release_threshold(int dev)
+{
+    static bool done[64] = {};
+    if (dev < 0 || dev >= 64 || done[dev])
+        return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t thr = ~0ull;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    cudaGetLastError();
+    done[dev] = true;
+}
+
+struct Request {
+    int kind;  // 0 xi, 1 rp-pi
+    int autocorr;
+    const cf_catalog *d1, *d2;
+    std::vector<double> edges;
+    double pimax;
+    int npibins;
+    const cf_config *cfg;
+    cf_result *res;
+};
+
+int validate(const Request &q)
+{
+    const cf_config *c = q.cfg;
+    if (!c)
+        return fail(CF_EINVAL, "cfg is NULL");
+    if (!q.res || !q.res->npairs)
+        return fail(CF_EINVAL, "res or res->npairs is NULL");
+    if (c->dtype != CF_FLOAT32 && c->dtype != CF_FLOAT64)
+        return fail(CF_EINVAL, "dtype must be CF_FLOAT32 or CF_FLOAT64");
+    if (c->mode != CF_MODE_FP64 && c->mode != CF_MODE_FP32_RECHECK)
+        return fail(CF_EINVAL, "mode must be CF_MODE_FP64 or CF_MODE_FP32_RECHECK");
+    const cf_catalog *cats[2] = {q.d1, q.autocorr ? nullptr : q.d2};
+    for (int t = 0; t < 2; ++t) {
+        const cf_catalog *ct = cats[t];
+        if (t == 1 && q.autocorr)
+            continue;
+        if (!ct)
+            return fail(CF_EINVAL, t ? "d2 is NULL for a cross-correlation" : "d1 is NULL");
+        if (ct->n < 0 || ct->n >= (1ll << 31) - 64)
+            return fail(CF_EINVAL, "catalogue size must be in [0, 2^31 - 64)");
+        if (ct->n > 0 && (!ct->x || !ct->y || !ct->z))
+            return fail(CF_EINVAL, "NULL coordinate array");
+        if (c->weighted && ct->n > 0 && !ct->w)
+            return fail(CF_EINVAL, "weighted mode needs weights for every catalogue");
+    }
+    if (q.edges.size() < 2)
+        return fail(CF_EINVAL, "need at least 2 bin edges");
+    if ((int)q.edges.size() - 1 > cf::NB_MAX)
+        return fail(CF_EINVAL, "at most 64 bins");
+    if (!(q.edges[0] >= 0.0) || !std::isfinite(q.edges.back()))
+        return fail(CF_EINVAL, "edges must be finite and edges[0] >= 0");
+    for (size_t k = 1; k < q.edges.size(); ++k)
+        if (!(q.edges[k] > q.edges[k - 1]))
+            return fail(CF_EINVAL, "edges must be strictly increasing");
+    const double R = q.edges.back();
+    if (q.kind == 1) {
+        if (!(q.pimax > 0.0) || !std::isfinite(q.pimax))
+            return fail(CF_EINVAL, "pimax must be positive and finite");
+        if (q.npibins < 1 || q.npibins > cf::NPI_MAX ||
+            (long long)q.npibins * ((long long)q.edges.size() - 1) > cf::NBINS2D_MAX)
+            return fail(CF_EINVAL, "npibins must be >= 1 with n_rp_bins * npibins <= 4096");
+    }
+    if (c->periodic) {
+        for (int a = 0; a < 3; ++a)
+            if (!(c->boxsize[a] > 0.0) || !std::isfinite(c->boxsize[a]))
+                return fail(CF_EINVAL, "periodic boxsize must be positive and finite");
+        const double rz = q.kind == 0 ? R : q.pimax;
+        const double m = 0.5 * (1.0 - 1e-9);
+        if (!(R < m * c->boxsize[0]) || !(R < m * c->boxsize[1]) || !(rz < m * c->boxsize[2]))
+            return fail(CF_EINVAL, "periodic mode needs Rmax (and pimax) < boxsize/2");
+    }
+    for (int a = 0; a < 3; ++a)
+        if (c->refine[a] < 0 || c->refine[a] > 16)
+            return fail(CF_EINVAL, "refine factors must be in [0, 16]");
+    return CF_OK;
+}
+
+// Grid geometry: columns of side >= Rxy / refine in x, y; z-cells for the sort.
+int plan_geom(const Request &q, const double lo[3], const double hi[3], long long ntot, cf::Geom &g)
+{
+    const cf_config *c = q.cfg;
+    const double R = q.edges.back();
+    int rx = c->refine[0], ry = c->refine[1], rz = c->refine[2];
+    if (rx == 0 && ry == 0 && rz == 0) {
+        rx = 2;
+        ry = 2;
+        rz = 1;
+    }
+    rx = std::max(1, std::min(rx, cf::MAX_REACH));
+    ry = std::max(1, std::min(ry, cf::MAX_REACH));
+    rz = std::max(1, rz);
+    std::memset(&g, 0, sizeof(g));
+    g.periodic = c->periodic ? 1 : 0;
+    for (int a = 0; a < 3; ++a) {
+        if (g.periodic) {
+            g.origin[a] = 0.0;
+            g.extent[a] = c->boxsize[a];
+            g.box[a] = c->boxsize[a];
+        } else {
+            g.origin[a] = lo[a];
+            g.extent[a] = std::max(hi[a] - lo[a], 0.0);
+            g.box[a] = 0.0;
+        }
+    }
+    auto ncol = [&](double ext, int r) {
+        const double per = std::floor(ext / (R * (1.0 + 1e-9)));
+        long long n = (long long)std::max(1.0, std::min(per, 8192.0)) * r;
+        return (int)std::max(1ll, n);
+    };
+    g.ncx = ncol(g.extent[0], rx);
+    g.ncy = ncol(g.extent[1], ry);
+    while ((long long)g.ncx * g.ncy > (1ll << 22)) {
+        g.ncx = std::max(1, g.ncx / 2);
+        g.ncy = std::max(1, g.ncy / 2);
+    }
+    g.ncols = g.ncx * g.ncy;
+    g.reach_x = rx;
+    g.reach_y = ry;
+    const double per_col = (double)ntot / g.ncols;
+    long long nz = (long long)std::floor(per_col * rz / 16.0);
+    nz = std::max(1ll, std::min(nz, 1ll << 16));
+    while (nz > 1 && (long long)g.ncols * nz > (1ll << 24) - 1)
+        nz /= 2;
+    g.nz = (int)nz;
+    g.ncells = (long long)g.ncols * g.nz;
+    const double ex = std::max(g.extent[0], 1e-300), ey = std::max(g.extent[1], 1e-300),
+                 ez = std::max(g.extent[2], 1e-300);
+    g.inv_w[0] = g.ncx / ex;
+    g.inv_w[1] = g.ncy / ey;
+    g.inv_w[2] = g.nz / ez;
+    return CF_OK;
+}
+
+int run(Request &q)
+{
+    int rc = validate(q);
+    if (rc)
+        return rc;
+    const cf_config *c = q.cfg;
+    cf_result *res = q.res;
+    const cudaStream_t st = (cudaStream_t)c->stream;
+    const int nb = (int)q.edges.size() - 1;
+    const int nslots = q.kind == 0 ? nb : nb * q.npibins;
+    const bool f64 = c->mode == CF_MODE_FP64;
+    const size_t esz = c->dtype == CF_FLOAT32 ? 4 : 8;
+    const cf_catalog *cats[2] = {q.d1, q.autocorr ? q.d1 : q.d2};
+    const int ncat = q.autocorr ? 1 : 2;
+    const double R = q.edges.back();
+
+    std::memset(res->npairs, 0, sizeof(uint64_t) * nslots);
+    if (res->wsum)
+        std::memset(res->wsum, 0, sizeof(double) * nslots);
+    if (res->ravg)
+        std::memset(res->ravg, 0, sizeof(double) * nslots);
+    res->n_cellpairs = res->n_evaluated = res->n_rechecked = res->n_band_violations = 0;
+    res->kernel_ms = res->total_ms = 0.0;
+    if (q.kind != 0)
+        return fail(CF_EINVAL, "rp-pi counting is not available in this build");
+    if (c->weighted || c->want_ravg)
+        return fail(CF_EINVAL, "weights / ravg are not available in this build");
+
+    int dev = 0, sms = 0;
+    void *ws = nullptr, *ws2 = nullptr;
+    cf::Geom g;
+    cf::PairParams P;
+    cf::PairLaunch PL;
+    std::vector<double> E2(nb + 1);
+    std::vector<float> T;
+    Lut lut;
+    cf::Gridded G[2];
+    cf::GridTemps tmp;
+    Bump bump;
+    const void *dx[2][3] = {{nullptr}};
+    const double *dw[2] = {nullptr, nullptr};
+    bool host_in[2] = {false, false};
+    long long nmax = 0, ntot = 0;
+    double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+    unsigned long long *bbox_keys = nullptr;
+    unsigned *d_err = nullptr, *d_ctr = nullptr;
+    unsigned long long *d_hist = nullptr, *d_diag = nullptr;
+    float *d_thr = nullptr;
+    uint16_t *d_lut = nullptr;
+    double *d_E2 = nullptr;
+    size_t total = 0;
+    struct HostOut {
+        unsigned long long hist[cf::NBINS2D_MAX];
+        unsigned long long diag[4];
+        unsigned err;
+    } *ho = nullptr;
+
+    CF_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
+    CF_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "device attribute");
+    set_pool_release_threshold(dev);
+    if (!g_events.init())
+        return fail(CF_ECUDA, "cudaEventCreate failed");
+    CF_CUDA(cudaEventRecord(g_events.ev[0], st), "cudaEventRecord");
+
+    for (int t = 0; t < ncat; ++t) {
+        nmax = std::max<long long>(nmax, cats[t]->n);
+        ntot += cats[t]->n;
+        host_in[t] = cats[t]->n > 0 && !is_device_ptr(cats[t]->x);
+    }
+    for (int k = 0; k <= nb; ++k)
+        E2[k] = q.edges[k] * q.edges[k];
+
+    // Pass 1: sizes of everything except the grid (known only after the bbox).
+    for (int pass = 0; pass < 2; ++pass) {
+        bump.base = pass ? (char *)ws : nullptr;
+        bump.off = 0;
+        for (int t = 0; t < ncat; ++t) {
+            const long long n = cats[t]->n;
+            if (host_in[t]) {
+                for (int a = 0; a < 3; ++a)
+                    dx[t][a] = bump.take<char>(n * esz);
+                dw[t] = cats[t]->w ? bump.take<double>(n) : nullptr;
+            } else {
+                dx[t][0] = cats[t]->x;
+                dx[t][1] = cats[t]->y;
+                dx[t][2] = cats[t]->z;
+                dw[t] = cats[t]->w;
+            }
+        }
+        bbox_keys = bump.take<unsigned long long>(6);
+        d_err = bump.take<unsigned>(1);
+        d_ctr = bump.take<unsigned>(1);
+        d_hist = bump.take<unsigned long long>(nslots);
+        d_diag = bump.take<unsigned long long>(4);
+        d_thr = bump.take<float>(2 * (nb + 1));
+        d_lut = bump.take<uint16_t>(cf::LUT_MAX);
+        d_E2 = bump.take<double>(nb + 1);
+        if (pass == 0) {
+            total = bump.off;
+            CF_CUDA(cudaMallocAsync(&ws, total, st), "cudaMallocAsync (inputs)");
+        }
+    }
+    for (int t = 0; t < ncat; ++t) {
+        if (!host_in[t])
+            continue;
+        const long long n = cats[t]->n;
+        CF_CUDA(cudaMemcpyAsync((void *)dx[t][0], cats[t]->x, n * esz, cudaMemcpyHostToDevice, st), "H2D x");
+        CF_CUDA(cudaMemcpyAsync((void *)dx[t][1], cats[t]->y, n * esz, cudaMemcpyHostToDevice, st), "H2D y");
+        CF_CUDA(cudaMemcpyAsync((void *)dx[t][2], cats[t]->z, n * esz, cudaMemcpyHostToDevice, st), "H2D z");
+        if (dw[t])
+            CF_CUDA(cudaMemcpyAsync((void *)dw[t], cats[t]->w, n * 8, cudaMemcpyHostToDevice, st), "H2D w");
+    }
+    CF_CUDA(cudaMemsetAsync(d_err, 0, sizeof(unsigned), st), "memset");
+    CF_CUDA(cudaMemsetAsync(d_ctr, 0, sizeof(unsigned), st), "memset");
+    CF_CUDA(cudaMemsetAsync(d_hist, 0, sizeof(unsigned long long) * nslots, st), "memset");
+    CF_CUDA(cudaMemsetAsync(d_diag, 0, sizeof(unsigned long long) * 4, st), "memset");
+
+    ho = (HostOut *)g_pinned.get(sizeof(HostOut));
+    if (!ho) {
+        rc = fail(CF_ENOMEM, "cudaHostAlloc failed");
+        goto cleanup;
+    }
+
+    if (!c->periodic) {  // open box: grid over the union bounding box
+        unsigned long long init[6] = {~0ull, ~0ull, ~0ull, 0ull, 0ull, 0ull};
+        std::memcpy(ho->hist, init, sizeof(init));
+        CF_CUDA(cudaMemcpyAsync(bbox_keys, ho->hist, sizeof(init), cudaMemcpyHostToDevice, st), "H2D bbox");
+        for (int t = 0; t < ncat; ++t)
+            CF_CUDA(cf::launch_bbox(c->dtype, dx[t][0], dx[t][1], dx[t][2], cats[t]->n, bbox_keys, sms,
+                                    d_err, st),
+                    "bbox kernel");
+        CF_CUDA(cudaMemcpyAsync(ho->hist, bbox_keys, sizeof(init), cudaMemcpyDeviceToHost, st), "D2H bbox");
+        CF_CUDA(cudaMemcpyAsync(&ho->err, d_err, 4, cudaMemcpyDeviceToHost, st), "D2H err");
+        CF_CUDA(cudaStreamSynchronize(st), "sync (bbox)");
+        if (ho->err & cf::ERR_COORD) {
+            rc = fail(CF_EINVAL, "non-finite coordinate");
+            goto cleanup;
+        }
+        if (ntot > 0)
+            for (int a = 0; a < 3; ++a) {
+                lo[a] = cf::decode_dkey(ho->hist[a]);
+                hi[a] = cf::decode_dkey(ho->hist[3 + a]);
+            }
+    }
+    plan_geom(q, lo, hi, ntot, g);
+
+    {  // grid workspace
+        for (int pass = 0; pass < 2; ++pass) {
+            bump.base = pass ? (char *)ws2 : nullptr;
+            bump.off = 0;
+            for (int t = 0; t < ncat; ++t) {
+                const long long n = cats[t]->n;
+                G[t].pos = bump.take<float4>(n);
+                G[t].pos64 = bump.take<double4_32a>(n);
+                G[t].perm = bump.take<int>(n);
+                G[t].cell_start = bump.take<uint32_t>(g.ncells + 1);
+                G[t].colbox = bump.take<double4_32a>(g.ncols);
+            }
+            tmp.cell_of = bump.take<uint32_t>(nmax);
+            tmp.slot = bump.take<uint32_t>(nmax);
+            tmp.tmp_idx = bump.take<int>(nmax);
+            tmp.tmp_z = bump.take<double>(nmax);
+            tmp.tmp_cell = bump.take<uint32_t>(nmax);
+            tmp.counts = bump.take<uint32_t>(g.ncells);
+            tmp.bsum = bump.take<uint32_t>(g.ncells / 4096 + 2);
+            if (pass == 0) {
+                const cudaError_t e = cudaMallocAsync(&ws2, bump.off, st);
+                if (e) {
+                    rc = cuda_fail(e, "cudaMallocAsync (grid)");
+                    goto cleanup;
+                }
+            }
+        }
+        for (int t = 0; t < ncat; ++t) {
+            const cudaError_t e = cf::build_grid(c->dtype, dx[t][0], dx[t][1], dx[t][2], dw[t],
+                                                 cats[t]->n, g, tmp, G[t], sms, d_err, st);
+            if (e) {
+                rc = cuda_fail(e, "grid kernels");
+                goto cleanup;
+            }
+        }
+        if (q.autocorr)
+            G[1] = G[0];
+
+        // ---- pair kernel parameters
+        std::memset(&P, 0, sizeof(P));
+        P.A = G[0];
+        P.B = G[1];
+        P.g = g;
+        P.autocorr = q.autocorr;
+        P.kind = q.kind;
+        P.nstencil = 0;
+        for (int ox = -g.reach_x; ox <= g.reach_x; ++ox)
+            for (int oy = -g.reach_y; oy <= g.reach_y; ++oy) {
+                if (q.autocorr && !(ox > 0 || (ox == 0 && oy >= 0)))
+                    continue;  // Sec. 2.1: each unordered column pair once
+                P.stencil[P.nstencil++] = make_int2(ox, oy);
+            }
+        P.n_items = g.ncols * P.nstencil;
+        P.tile_max = f64 ? 1024 : 2048;
+        P.flags = c->flags;
+        const double M = std::max(g.extent[0], std::max(g.extent[1], g.extent[2]));
+        const double Ls = g.periodic ? std::max(g.box[0], std::max(g.box[1], g.box[2])) : 0.0;
+        const double Rp = R * (1.0 + 1e-9) + 8.0 * U64 * (M + Ls);
+        P.prune_r2 = Rp * Rp;
+        P.rxy2 = Rp * Rp;
+        P.rz = q.kind == 0 ? R : q.pimax;
+        P.zslack = (float)(8.0 * U32 * (M + Ls + R) + 1e-6 * R);
+        for (int a = 0; a < 3; ++a)
+            P.boxf[a] = (float)g.box[a];
+        P.nbins = nb;
+        if (!f64) {
+            T = make_thresholds(E2, 3, M, Ls, R);
+            lut = make_lut(T, nb);
+            P.nthr = (int)T.size();
+            P.lut_n = (int)lut.tab.size();
+            P.lut_shift = lut.shift;
+            P.u0 = lut.u0;
+            P.urange = lut.urange;
+            CF_CUDA(cudaMemcpyAsync(d_thr, T.data(), 4 * T.size(), cudaMemcpyHostToDevice, st), "H2D thresholds");
+            CF_CUDA(cudaMemcpyAsync(d_lut, lut.tab.data(), 2 * lut.tab.size(), cudaMemcpyHostToDevice, st), "H2D lut");
+        }
+        CF_CUDA(cudaMemcpyAsync(d_E2, E2.data(), 8 * E2.size(), cudaMemcpyHostToDevice, st), "H2D E2");
+        P.thr = d_thr;
+        P.lut = d_lut;
+        P.E2 = d_E2;
+        P.hist = d_hist;
+        P.diag = d_diag;
+        P.err = d_err;
+        P.item_counter = d_ctr;
+
+        PL.f64 = f64;
+        PL.chunk = 8;
+        PL.evals = (c->flags & (CF_FLAG_COUNT_EVALS | CF_FLAG_VERIFY_BAND)) ? 1 : 0;
+        PL.verify = (!f64 && (c->flags & CF_FLAG_VERIFY_BAND)) ? 1 : 0;
+        PL.hist_words = cf::pair_hist_words(q.kind, nb, q.npibins);
+        PL.smem = cf::smem_layout(P.tile_max, f64 ? 32 : 16, f64 ? 0 : P.lut_n, f64 ? 0 : P.nthr, nb,
+                                  0, 0, 0, PL.hist_words)
+                      .total;
+        CF_CUDA(cudaEventRecord(g_events.ev[1], st), "cudaEventRecord");
+        if (P.n_items > 0) {
+            const cudaError_t e = cf::launch_pairs(P, PL, sms, st);
+            if (e) {
+                rc = cuda_fail(e, "pair kernel launch");
+                goto cleanup;
+            }
+        }
+        CF_CUDA(cudaEventRecord(g_events.ev[2], st), "cudaEventRecord");
+        CF_CUDA(cudaMemcpyAsync(ho->hist, d_hist, sizeof(unsigned long long) * nslots, cudaMemcpyDeviceToHost, st), "D2H hist");
+        CF_CUDA(cudaMemcpyAsync(ho->diag, d_diag, sizeof(ho->diag), cudaMemcpyDeviceToHost, st), "D2H diag");
+        CF_CUDA(cudaMemcpyAsync(&ho->err, d_err, 4, cudaMemcpyDeviceToHost, st), "D2H err");
+    }
+    CF_CUDA(cudaEventRecord(g_events.ev[3], st), "cudaEventRecord");
+    CF_CUDA(cudaEventSynchronize(g_events.ev[3]), "synchronize");
+    {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, g_events.ev[1], g_events.ev[2]) == cudaSuccess)
+            res->kernel_ms = ms;
+        if (cudaEventElapsedTime(&ms, g_events.ev[0], g_events.ev[3]) == cudaSuccess)
+            res->total_ms = ms;
+        cudaGetLastError();
+    }
+    if (ho->err & cf::ERR_COORD) {
+        rc = fail(CF_EINVAL, c->periodic ? "coordinate outside [0, boxsize) or non-finite"
+                                         : "non-finite coordinate");
+        goto cleanup;
+    }
+    if (ho->err & cf::ERR_TIMEOUT) {
+        rc = fail(CF_ETIMEOUT, "a bounded device wait (TMA tile barrier) gave up");
+        goto cleanup;
+    }
+    if (ho->err) {
+        rc = fail(CF_EDEVICE, "kernel reported an internal inconsistency");
+        goto cleanup;
+    }
+    {
+        const uint64_t mult = q.autocorr ? 2u : 1u;  // Sec. 2.1: double the unique-pair counts
+        for (int k = 0; k < nslots; ++k)
+            res->npairs[k] = ho->hist[k] * mult;
+        res->n_cellpairs = ho->diag[0];
+        res->n_evaluated = ho->diag[1];
+        res->n_rechecked = ho->diag[2];
+        res->n_band_violations = ho->diag[3];
+    }
+    rc = CF_OK;
+cleanup:
+    if (ws2)
+        cudaFreeAsync(ws2, st);
+    if (ws) {
+        cudaFreeAsync(ws, st);
+        if (rc == CF_OK) {
+            cudaError_t e = cudaStreamSynchronize(st);
+            if (e)
+                rc = cuda_fail(e, "final synchronize");
+        }
+    }
+    return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+int cf_countpairs_xi(int autocorr, const cf_catalog *d1, const cf_catalog *d2, const double *edges,
+                     int nedges, const cf_config *cfg, cf_result *res)
+{
+    if (!edges || nedges < 2)
+        return fail(CF_EINVAL, "need at least 2 bin edges");
+    Request q;
+    q.kind = 0;
+    q.autocorr = autocorr ? 1 : 0;
+    q.d1 = d1;
+    q.d2 = d2;
+    q.edges.assign(edges, edges + nedges);
+    q.pimax = 0.0;
+    q.npibins = 0;
+    q.cfg = cfg;
+    q.res = res;
+    return run(q);
+}
+
+int cf_countpairs_rp_pi(int autocorr, const cf_catalog *d1, const cf_catalog *d2,
+                        const double *rp_edges, int n_rp_edges, double pimax, int npibins,
+                        const cf_config *cfg, cf_result *res)
+{
+    if (!rp_edges || n_rp_edges < 2)
+        return fail(CF_EINVAL, "need at least 2 rp bin edges");
+    Request q;
+    q.kind = 1;
+    q.autocorr = autocorr ? 1 : 0;
+    q.d1 = d1;
+    q.d2 = d2;
+    q.edges.assign(rp_edges, rp_edges + n_rp_edges);
+    q.pimax = pimax;
+    q.npibins = npibins;
+    q.cfg = cfg;
+    q.res = res;
+    return run(q);
+}
+
+const char *cf_last_error(void) { return g_err.c_str(); }
+
+const char *cf_version(void) { return "cfgpu 0.1 sm_103a"; }
+
+}  // extern "C"

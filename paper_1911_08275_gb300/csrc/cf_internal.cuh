@@ -1,0 +1,169 @@
+// Internal definitions shared by the cfgpu translation units (not installed).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "cf.h"
+
+namespace cf {
+
+// ----------------------------------------------------------------- limits
+constexpr int NB_MAX = 64;          // radial (xi) or rp bins
+constexpr int NBINS2D_MAX = 4096;   // rp bins * pi bins
+constexpr int NPI_MAX = 4096;
+constexpr int LUT_MAX = 4096;       // entries of the float32 bin lookup table
+constexpr int MAX_REACH = 4;        // column stencil half-width per axis
+constexpr int MAX_STENCIL = (2 * MAX_REACH + 1) * (2 * MAX_REACH + 1);
+constexpr int WARPS = 8;            // warps per pair-kernel CTA
+constexpr int THREADS = WARPS * 32;
+constexpr unsigned FULL = 0xffffffffu;
+
+// Error-word bits written by kernels (read back once per call).
+enum : unsigned {
+    ERR_COORD = 1u,     // non-finite coordinate or outside [0, L) in periodic mode
+    ERR_TIMEOUT = 2u,   // a bounded mbarrier wait gave up
+    ERR_INTERNAL = 4u,  // an index or table inconsistency that must never happen
+};
+
+// LUT entry encoding (uint16): < 0x4000 -> safe bin, value = bin * 128 (byte
+// offset of the bin row in a warp's per-lane histogram); 0x8000 -> the whole
+// cell lies inside an error band (re-check in binary64); 0xC000 | t -> the cell
+// contains thresholds starting at index t (compare, then maybe re-check).
+constexpr uint32_t LUT_AMBIG = 0x8000u;
+constexpr uint32_t LUT_SLOW = 0xC000u;
+
+// Grid geometry: columns in (x, y), z-cells inside each column (sort keys).
+struct Geom {
+    int periodic;
+    int ncx, ncy, nz;
+    int ncols;
+    long long ncells;
+    int reach_x, reach_y;
+    double origin[3];   // grid frame origin (0 in periodic mode)
+    double extent[3];   // grid extent (= box in periodic mode)
+    double inv_w[3];    // cells per unit length along each axis
+    double box[3];      // periodic box (0 when open)
+};
+
+// A gridded catalogue, in (column, z, original index) order.
+struct Gridded {
+    long long n;
+    float4 *pos;          // (x~, y~, z~, w) float32 in the grid frame
+    double4_32a *pos64;       // (x, y, z, w) binary64, exact inputs
+    int *perm;            // original index of each sorted point
+    uint32_t *cell_start; // ncells + 1
+    double4_32a *colbox;      // per column (xmin, xmax, ymin, ymax)
+};
+
+// Everything a pair kernel needs (passed by value, lives in the constant bank).
+struct PairParams {
+    Gridded A, B;
+    Geom g;
+    int autocorr;
+    int kind;           // 0 = xi, 1 = rp-pi
+    int nstencil;
+    int2 stencil[MAX_STENCIL];
+    int n_items;
+    int tile_max;       // points per staged tile
+    uint32_t flags;
+    // radii (binary64 decisions on bounding boxes)
+    double prune_r2;    // prune a column pair if its xy gap^2 >= prune_r2
+    double rz;          // z reach: Rmax (xi) or pimax (rp-pi)
+    double rxy2;        // squared xy reach for the z window: Rmax^2
+    float zslack;       // float32 slack added to z windows
+    float boxf[3];      // fl32(L)
+    // binning
+    int nbins;          // xi or rp bins
+    int npibins;        // rp-pi only
+    int nthr;           // 2 * nbins + 2 float32 thresholds
+    int lut_n, lut_shift;
+    uint32_t u0, urange; // float bit range covered by the LUT
+    int pi_nthr;        // 2 * npibins + 2 (rp-pi)
+    int pilut_n, pilut_shift;
+    uint32_t pu0, purange;
+    const float *thr;        // nthr
+    const uint16_t *lut;     // lut_n
+    const double *E2;        // nbins + 1
+    const float *pithr;      // pi_nthr
+    const uint16_t *pilut;   // pilut_n
+    const double *P;         // npibins + 1
+    // outputs
+    unsigned long long *hist;  // nbins (xi) or nbins * npibins
+    double *wsum, *rsum;
+    unsigned long long *diag;  // [0] kept items, [1] evaluations, [2] rechecks, [3] band violations
+    unsigned *err;
+    unsigned *item_counter;
+};
+
+// ----------------------------------------------------------------- device helpers
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+// One bounded wait on phase `parity`; returns false if the limit was reached.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity, unsigned limit)
+{
+    const uint32_t a = smem_u32(bar);
+    for (unsigned it = 0; it < limit; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done)
+            return true;
+    }
+    return false;
+}
+
+// 1-D bulk copy global -> shared (TMA, no tensor map), completion on `bar`.
+// dst, src 16-byte aligned; bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+            "r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// Canonical binary64 squared separation of point j (image shifted by S) from i:
+// d = fl(x_j - x_i), then fl(d + S) when S != 0; rp2 = dx*dx + dy*dy; r2 = rp2 + dz*dz.
+// With S equal to the periodic image of j, this is bit-identical to the
+// minimum-image wrap for every pair closer than L/2.
+__device__ __forceinline__ double canon_comp(double xi, double xj, double S)
+{
+    double d = __dsub_rn(xj, xi);
+    if (S != 0.0)
+        d = __dadd_rn(d, S);
+    return d;
+}
+
+}  // namespace cf

@@ -1,0 +1,33 @@
+// Host interface of the gridding kernels (grid.cu).
+#pragma once
+
+#include <cstring>
+
+#include "cf_internal.cuh"
+
+namespace cf {
+
+// Temporaries of one grid build (device memory, carved from the workspace).
+struct GridTemps {
+    uint32_t *cell_of;   // n
+    uint32_t *slot;      // n
+    int *tmp_idx;        // n
+    double *tmp_z;       // n
+    uint32_t *tmp_cell;  // n
+    uint32_t *counts;    // ncells
+    uint32_t *bsum;      // ceil(ncells / 4096)
+};
+
+// Grid one catalogue into `out` (whose arrays are preallocated).
+cudaError_t build_grid(cf_dtype dt, const void *x, const void *y, const void *z, const double *w,
+                       long long n, const Geom &g, const GridTemps &t, Gridded &out, int sms,
+                       unsigned *err, cudaStream_t st);
+
+// Bounding box of a catalogue: out6 = order-preserving keys of (min x,y,z, max x,y,z);
+// initialise out6[0..2] to ~0 and out6[3..5] to 0 first.
+cudaError_t launch_bbox(cf_dtype dt, const void *x, const void *y, const void *z, long long n,
+                        unsigned long long *out6, int sms, unsigned *err, cudaStream_t st);
+
+double decode_dkey(unsigned long long k);
+
+}  // namespace cf
