@@ -140,6 +140,29 @@ int cf_countpairs_rp_pi(int autocorr, const cf_catalog *d1, const cf_catalog *d2
                         const double *rp_edges, int n_rp_edges, double pimax, int npibins,
                         const cf_config *cfg, cf_result *res);
 
+/*
+ * Allocation-free DD(r).  The paper has no counterpart: this entry point exists
+ * for callers that cannot allocate device memory at call time -- for example a
+ * process whose GPU memory is already reserved by another allocator, or a loop
+ * that must never wait on cudaMalloc.  Same arguments and results as
+ * cf_countpairs_xi, with these differences:
+ *   - all device scratch comes from one static device array of 32 MiB inside
+ *     the library (held by every GPU that loads it until the process exits);
+ *     nothing is allocated or freed by the call;
+ *   - each catalogue has at most 131072 points; larger problems, or grids that
+ *     do not fit the array, return CF_EINVAL with a message saying so;
+ *   - coordinates must already be in device memory; no weights, no ravg;
+ *     CF_FLAG_VERIFY_BAND is ignored; kernel_ms and total_ms are reported as 0;
+ *   - the first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress) while that device is current: make that first
+ *     call before any stream capture;
+ *   - every call on a device reuses the same array: calls whose GPU work
+ *     overlaps (concurrent streams or threads) race and must be serialised.
+ */
+int cf_countpairs_xi_noalloc(int autocorr, const cf_catalog *d1, const cf_catalog *d2,
+                             const double *edges, int nedges, const cf_config *cfg,
+                             cf_result *res);
+
 /* Text of the last non-zero status returned on the calling thread. */
 const char *cf_last_error(void);
 

@@ -33,7 +33,8 @@ _STATUS = {CF_EINVAL: "CF_EINVAL", CF_ENOMEM: "CF_ENOMEM", CF_ECUDA: "CF_ECUDA",
            CF_ETIMEOUT: "CF_ETIMEOUT", CF_EDEVICE: "CF_EDEVICE"}
 
 # Names exported by the library; they must match include/cf.h.
-EXPORTS = ("cf_countpairs_xi", "cf_countpairs_rp_pi", "cf_last_error", "cf_version")
+EXPORTS = ("cf_countpairs_xi", "cf_countpairs_rp_pi", "cf_last_error", "cf_version",
+           "cf_countpairs_xi_noalloc")
 
 
 class cf_catalog(ctypes.Structure):
@@ -230,3 +231,25 @@ def countpairs_rp_pi(x, y, z, rp_edges, pimax, npibins, *, w=None, x2=None, y2=N
 
 def version() -> str:
     return lib().cf_version().decode()
+
+
+def countpairs_xi_noalloc(x, y, z, edges, *, x2=None, y2=None, z2=None, autocorr=None,
+                          periodic=True, boxsize=420.0, mode="fp32_recheck", refine=(0, 0, 0),
+                          flags=0, stream=None) -> Result:
+    """DD(r) through ``cf_countpairs_xi_noalloc``: no device allocation per call.
+
+    For callers that cannot allocate GPU memory while counting (see include/cf.h):
+    inputs must be CUDA tensors, at most 131072 points per catalogue, unweighted.
+    Calls on one device share the library's static scratch, so they must not
+    overlap on the GPU.
+    """
+    L = lib()
+    L.cf_countpairs_xi_noalloc.argtypes = L.cf_countpairs_xi.argtypes
+    L.cf_countpairs_xi_noalloc.restype = ctypes.c_int
+    edges = np.ascontiguousarray(edges, dtype=np.float64)
+    if autocorr is None:
+        autocorr = x2 is None
+    fn = lambda L, *a: L.cf_countpairs_xi_noalloc(*a)  # noqa: E731
+    extra = (edges.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), int(edges.size))
+    return _run(fn, edges.size - 1, autocorr, x, y, z, None, x2, y2, z2, None, extra, periodic,
+                boxsize, mode, False, refine, flags, stream)

@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -731,3 +732,370 @@ const char *cf_last_error(void) { return g_err.c_str(); }
 const char *cf_version(void) { return "cfgpu 0.1 sm_103a"; }
 
 }  // extern "C"
+
+// ============================================================================
+// Allocation-free DD(r): cf_countpairs_xi_noalloc.
+//
+// Some callers cannot allocate device memory at call time: a process whose
+// device memory is already owned by another allocator (for example a
+// framework's caching allocator that reserved the whole GPU), or a loop with a
+// latency budget that must never wait on cudaMalloc / cudaMallocAsync.  This
+// entry point runs the same gridding and pair kernels as cf_countpairs_xi, but
+// every device buffer they use is carved out of one file-scope static device
+// array (g_noalloc_scratch, NOALLOC_BYTES = 32 MiB), which every GPU that loads
+// the library holds until the process exits.  It calls no cudaMalloc,
+// cudaMallocAsync, cudaFree, cudaHostAlloc or other allocating routine, and no
+// host heap allocation on its success path (tables live on the stack).
+//
+// The host cannot use the array's name as a device address (in host code it
+// names a host-side stand-in), so the first call on each device looks the
+// address up with cudaGetSymbolAddress while that device is current, checks
+// the result, and caches it; later calls reuse it.  Make that first call on a
+// device before any stream capture.
+//
+// All calls on a device share the array and it keeps the previous call's
+// contents; each call clears the counters it needs.  Two calls whose work
+// overlaps on the GPU (different streams or threads without ordering) race on
+// the array and give wrong results: serialise them.
+// ============================================================================
+namespace {
+
+constexpr long long NOALLOC_MAX_POINTS = 1ll << 17;  // per catalogue
+constexpr long long NOALLOC_MAX_CELLS = 1ll << 19;
+constexpr long long NOALLOC_MAX_COLS = 1ll << 15;
+constexpr size_t NOALLOC_BYTES = size_t(32) << 20;
+
+}  // namespace
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
+
+namespace {
+
+std::mutex g_noalloc_mu;
+void *g_noalloc_ptr[64] = {};
+
+// Device address of the static scratch on device `dev` (set up once per device).
+int noalloc_scratch(int dev, void **out)
+{
+    if (dev < 0 || dev >= 64)
+        return fail(CF_EINVAL, "device ordinal out of range for the no-alloc scratch");
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p)
+            return cuda_fail(e != cudaSuccess ? e : cudaErrorInvalidSymbol,
+                             "cudaGetSymbolAddress(no-alloc scratch)");
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return CF_OK;
+}
+
+// Float32 thresholds and lookup table into caller-provided fixed arrays
+// (the same rules as make_thresholds / make_lut, without heap storage).
+int noalloc_tables(const double *E2, int ne, double M, double Ls, double R, float *T,
+                   uint16_t *tab, int *lut_n, int *shift, uint32_t *u0, uint32_t *urange)
+{
+    const int nthr = 2 * ne;
+    for (int k = 0; k < ne; ++k) {
+        if (E2[k] == 0.0) {
+            T[2 * k] = 0.0f;
+            T[2 * k + 1] = 0.0f;
+            continue;
+        }
+        const double B = band_sq(E2[k], 3, M, Ls, R);
+        const double lo = E2[k] - B;
+        T[2 * k] = (lo <= 0.0 || E2[k] < 1e-6) ? -1.0f : f32_down(lo);
+        T[2 * k + 1] = std::nextafter(f32_up(E2[k] + B), INFINITY);
+    }
+    for (int t = 1; t < nthr; ++t)
+        T[t] = std::max(T[t], T[t - 1]);
+    *u0 = T[0] > 0.0f ? fbits(T[0]) : 0u;
+    const uint32_t u1 = fbits(T[nthr - 1]);
+    *urange = u1 - *u0;
+    int s = 0;
+    while ((((uint64_t)*urange + (1ull << s) - 1) >> s) > (uint64_t)cf::LUT_MAX)
+        ++s;
+    *shift = s;
+    const int n = std::max(1, (int)(((uint64_t)*urange + (1ull << s) - 1) >> s));
+    *lut_n = n;
+    const int nbins = ne - 1;
+    for (int q = 0; q < n; ++q) {
+        const uint32_t blo = *u0 + ((uint32_t)q << s);
+        const uint64_t bend = std::min<uint64_t>((uint64_t)*u0 + ((uint64_t)(q + 1) << s), u1);
+        const uint32_t bhi = (uint32_t)(bend - 1);
+        int clo = 0, chi = 0;
+        while (clo < nthr && T[clo] <= bitsf(blo))
+            ++clo;
+        while (chi < nthr && T[chi] <= bitsf(bhi))
+            ++chi;
+        if (clo == chi && !(clo & 1) && clo >= 2 && clo <= 2 * nbins)
+            tab[q] = (uint16_t)(((clo - 2) / 2) * 128);
+        else if (clo == chi && (clo & 1))
+            tab[q] = (uint16_t)cf::LUT_AMBIG;
+        else
+            tab[q] = (uint16_t)(cf::LUT_SLOW | (uint32_t)std::min(clo, 0x3fff));
+    }
+    return CF_OK;
+}
+
+int noalloc_xi(int autocorr, const cf_catalog *d1, const cf_catalog *d2, const double *edges,
+               int nedges, const cf_config *c, cf_result *res)
+{
+    if (!c || !res || !res->npairs || !d1 || (!autocorr && !d2))
+        return fail(CF_EINVAL, "NULL argument");
+    if (!edges || nedges < 2 || nedges - 1 > cf::NB_MAX)
+        return fail(CF_EINVAL, "need 2..65 bin edges");
+    if (c->dtype != CF_FLOAT32 && c->dtype != CF_FLOAT64)
+        return fail(CF_EINVAL, "dtype must be CF_FLOAT32 or CF_FLOAT64");
+    if (c->mode != CF_MODE_FP64 && c->mode != CF_MODE_FP32_RECHECK)
+        return fail(CF_EINVAL, "mode must be CF_MODE_FP64 or CF_MODE_FP32_RECHECK");
+    if (c->weighted || c->want_ravg)
+        return fail(CF_EINVAL, "the no-alloc entry point counts unweighted pairs only");
+    if (!(edges[0] >= 0.0) || !std::isfinite(edges[nedges - 1]))
+        return fail(CF_EINVAL, "edges must be finite and edges[0] >= 0");
+    for (int k = 1; k < nedges; ++k)
+        if (!(edges[k] > edges[k - 1]))
+            return fail(CF_EINVAL, "edges must be strictly increasing");
+    for (int a = 0; a < 3; ++a)
+        if (c->refine[a] < 0 || c->refine[a] > 16)
+            return fail(CF_EINVAL, "refine factors must be in [0, 16]");
+    const cf_catalog *cats[2] = {d1, autocorr ? d1 : d2};
+    const int ncat = autocorr ? 1 : 2;
+    for (int t = 0; t < ncat; ++t) {
+        if (cats[t]->n < 0 || cats[t]->n > NOALLOC_MAX_POINTS)
+            return fail(CF_EINVAL, "no-alloc entry point: each catalogue must have at most "
+                                   "131072 points (the static scratch is 32 MiB)");
+        if (cats[t]->n > 0 && (!cats[t]->x || !cats[t]->y || !cats[t]->z))
+            return fail(CF_EINVAL, "NULL coordinate array");
+        if (cats[t]->n > 0 && (!is_device_ptr(cats[t]->x) || !is_device_ptr(cats[t]->y) ||
+                               !is_device_ptr(cats[t]->z)))
+            return fail(CF_EINVAL, "no-alloc entry point: coordinates must be in device memory");
+    }
+    const double R = edges[nedges - 1];
+    if (c->periodic) {
+        const double m = 0.5 * (1.0 - 1e-9);
+        for (int a = 0; a < 3; ++a)
+            if (!(c->boxsize[a] > 0.0) || !std::isfinite(c->boxsize[a]) || !(R < m * c->boxsize[a]))
+                return fail(CF_EINVAL, "periodic mode needs a positive box and Rmax < boxsize/2");
+    }
+    const int nb = nedges - 1;
+    const bool f64 = c->mode == CF_MODE_FP64;
+    const cudaStream_t st = (cudaStream_t)c->stream;
+    std::memset(res->npairs, 0, sizeof(uint64_t) * nb);
+    res->n_cellpairs = res->n_evaluated = res->n_rechecked = res->n_band_violations = 0;
+    res->kernel_ms = res->total_ms = 0.0;
+
+    int dev = 0, sms = 0, rc = CF_OK;
+    cudaError_t e;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess)
+        return cuda_fail(e, "cudaGetDevice");
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+        return cuda_fail(e, "device attribute");
+    void *scratch = nullptr;
+    if ((rc = noalloc_scratch(dev, &scratch)) != CF_OK)
+        return rc;
+
+    long long nmax = 0, ntot = 0;
+    for (int t = 0; t < ncat; ++t) {
+        nmax = std::max<long long>(nmax, cats[t]->n);
+        ntot += cats[t]->n;
+    }
+    // geometry (the planner's rules, with the static-scratch caps)
+    cf::Geom g;
+    std::memset(&g, 0, sizeof(g));
+    g.periodic = c->periodic ? 1 : 0;
+    Bump bump;
+    bump.base = (char *)scratch;
+    unsigned long long *bbox_keys = bump.take<unsigned long long>(6);
+    unsigned *d_err = bump.take<unsigned>(1);
+    unsigned *d_ctr = bump.take<unsigned>(1);
+    unsigned long long *d_hist = bump.take<unsigned long long>(cf::NB_MAX);
+    unsigned long long *d_diag = bump.take<unsigned long long>(4);
+    float *d_thr = bump.take<float>(2 * (cf::NB_MAX + 1));
+    uint16_t *d_lut = bump.take<uint16_t>(cf::LUT_MAX);
+    double *d_E2 = bump.take<double>(cf::NB_MAX + 1);
+    struct {
+        unsigned long long keys[6];
+        unsigned long long hist[cf::NB_MAX];
+        unsigned long long diag[4];
+        unsigned err;
+    } h;
+    if ((e = cudaMemsetAsync(d_err, 0, sizeof(unsigned), st)) != cudaSuccess)
+        return cuda_fail(e, "memset");
+    double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+    if (!g.periodic) {
+        const unsigned long long init[6] = {~0ull, ~0ull, ~0ull, 0ull, 0ull, 0ull};
+        if ((e = cudaMemcpyAsync(bbox_keys, init, sizeof(init), cudaMemcpyHostToDevice, st)))
+            return cuda_fail(e, "H2D bbox");
+        for (int t = 0; t < ncat; ++t)
+            if ((e = cf::launch_bbox(c->dtype, cats[t]->x, cats[t]->y, cats[t]->z, cats[t]->n,
+                                     bbox_keys, sms, d_err, st)))
+                return cuda_fail(e, "bbox kernel");
+        if ((e = cudaMemcpyAsync(h.keys, bbox_keys, sizeof(h.keys), cudaMemcpyDeviceToHost, st)) ||
+            (e = cudaMemcpyAsync(&h.err, d_err, 4, cudaMemcpyDeviceToHost, st)) ||
+            (e = cudaStreamSynchronize(st)))
+            return cuda_fail(e, "bbox readback");
+        if (h.err & cf::ERR_COORD)
+            return fail(CF_EINVAL, "non-finite coordinate");
+        if (ntot > 0)
+            for (int a = 0; a < 3; ++a) {
+                lo[a] = cf::decode_dkey(h.keys[a]);
+                hi[a] = cf::decode_dkey(h.keys[3 + a]);
+            }
+    }
+    int rx = c->refine[0], ry = c->refine[1], rz = c->refine[2];
+    if (rx == 0 && ry == 0 && rz == 0) {
+        rx = 2;
+        ry = 2;
+        rz = 1;
+    }
+    rx = std::max(1, std::min(rx, cf::MAX_REACH));
+    ry = std::max(1, std::min(ry, cf::MAX_REACH));
+    rz = std::max(1, rz);
+    for (int a = 0; a < 3; ++a) {
+        g.origin[a] = g.periodic ? 0.0 : lo[a];
+        g.extent[a] = g.periodic ? c->boxsize[a] : std::max(hi[a] - lo[a], 0.0);
+        g.box[a] = g.periodic ? c->boxsize[a] : 0.0;
+    }
+    auto ncol = [&](double ext, int r) {
+        const double per = std::floor(ext / (R * (1.0 + 1e-9)));
+        return (int)std::max(1ll, (long long)std::max(1.0, std::min(per, 8192.0)) * r);
+    };
+    g.ncx = ncol(g.extent[0], rx);
+    g.ncy = ncol(g.extent[1], ry);
+    while ((long long)g.ncx * g.ncy > NOALLOC_MAX_COLS) {  // wider columns stay correct
+        g.ncx = std::max(1, g.ncx / 2);
+        g.ncy = std::max(1, g.ncy / 2);
+    }
+    g.ncols = g.ncx * g.ncy;
+    g.reach_x = rx;
+    g.reach_y = ry;
+    long long nz = (long long)std::floor((double)ntot / g.ncols * rz / 16.0);
+    nz = std::max(1ll, std::min(nz, 1ll << 16));
+    while (nz > 1 && (long long)g.ncols * nz > NOALLOC_MAX_CELLS)
+        nz /= 2;
+    g.nz = (int)nz;
+    g.ncells = (long long)g.ncols * g.nz;
+    g.inv_w[0] = g.ncx / std::max(g.extent[0], 1e-300);
+    g.inv_w[1] = g.ncy / std::max(g.extent[1], 1e-300);
+    g.inv_w[2] = g.nz / std::max(g.extent[2], 1e-300);
+
+    cf::Gridded G[2];
+    cf::GridTemps tmp;
+    for (int t = 0; t < ncat; ++t) {
+        const long long n = cats[t]->n;
+        G[t].pos = bump.take<float4>(n);
+        G[t].pos64 = bump.take<double4_32a>(n);
+        G[t].perm = bump.take<int>(n);
+        G[t].cell_start = bump.take<uint32_t>(g.ncells + 1);
+        G[t].colbox = bump.take<double4_32a>(g.ncols);
+    }
+    tmp.cell_of = bump.take<uint32_t>(nmax);
+    tmp.slot = bump.take<uint32_t>(nmax);
+    tmp.tmp_idx = bump.take<int>(nmax);
+    tmp.tmp_z = bump.take<double>(nmax);
+    tmp.tmp_cell = bump.take<uint32_t>(nmax);
+    tmp.counts = bump.take<uint32_t>(g.ncells);
+    tmp.bsum = bump.take<uint32_t>(g.ncells / 4096 + 2);
+    if (bump.off > NOALLOC_BYTES)
+        return fail(CF_EINVAL, "no-alloc entry point: problem does not fit the 32 MiB static scratch");
+
+    if ((e = cudaMemsetAsync(d_ctr, 0, sizeof(unsigned), st)) ||
+        (e = cudaMemsetAsync(d_hist, 0, sizeof(unsigned long long) * nb, st)) ||
+        (e = cudaMemsetAsync(d_diag, 0, sizeof(unsigned long long) * 4, st)))
+        return cuda_fail(e, "memset");
+    for (int t = 0; t < ncat; ++t)
+        if ((e = cf::build_grid(c->dtype, cats[t]->x, cats[t]->y, cats[t]->z, nullptr, cats[t]->n,
+                                g, tmp, G[t], sms, d_err, st)))
+            return cuda_fail(e, "grid kernels");
+    if (autocorr)
+        G[1] = G[0];
+
+    double E2[cf::NB_MAX + 1];
+    for (int k = 0; k <= nb; ++k)
+        E2[k] = edges[k] * edges[k];
+    cf::PairParams P;
+    std::memset(&P, 0, sizeof(P));
+    P.A = G[0];
+    P.B = G[1];
+    P.g = g;
+    P.autocorr = autocorr ? 1 : 0;
+    P.kind = 0;
+    for (int ox = -g.reach_x; ox <= g.reach_x; ++ox)
+        for (int oy = -g.reach_y; oy <= g.reach_y; ++oy) {
+            if (autocorr && !(ox > 0 || (ox == 0 && oy >= 0)))
+                continue;
+            P.stencil[P.nstencil++] = make_int2(ox, oy);
+        }
+    P.n_items = g.ncols * P.nstencil;
+    P.tile_max = f64 ? 1024 : 2048;
+    P.flags = c->flags & (CF_FLAG_NO_PRUNE | CF_FLAG_COUNT_EVALS);
+    const double M = std::max(g.extent[0], std::max(g.extent[1], g.extent[2]));
+    const double Ls = g.periodic ? std::max(g.box[0], std::max(g.box[1], g.box[2])) : 0.0;
+    const double Rp = R * (1.0 + 1e-9) + 8.0 * U64 * (M + Ls);
+    P.prune_r2 = Rp * Rp;
+    P.rxy2 = Rp * Rp;
+    P.rz = R;
+    P.zslack = (float)(8.0 * U32 * (M + Ls + R) + 1e-6 * R);
+    for (int a = 0; a < 3; ++a)
+        P.boxf[a] = (float)g.box[a];
+    P.nbins = nb;
+    float T[2 * (cf::NB_MAX + 1)];
+    uint16_t tab[cf::LUT_MAX];
+    if (!f64) {
+        noalloc_tables(E2, nb + 1, M, Ls, R, T, tab, &P.lut_n, &P.lut_shift, &P.u0, &P.urange);
+        P.nthr = 2 * (nb + 1);
+        if ((e = cudaMemcpyAsync(d_thr, T, sizeof(float) * P.nthr, cudaMemcpyHostToDevice, st)) ||
+            (e = cudaMemcpyAsync(d_lut, tab, sizeof(uint16_t) * P.lut_n, cudaMemcpyHostToDevice, st)))
+            return cuda_fail(e, "H2D tables");
+    }
+    if ((e = cudaMemcpyAsync(d_E2, E2, sizeof(double) * (nb + 1), cudaMemcpyHostToDevice, st)))
+        return cuda_fail(e, "H2D E2");
+    P.thr = d_thr;
+    P.lut = d_lut;
+    P.E2 = d_E2;
+    P.hist = d_hist;
+    P.diag = d_diag;
+    P.err = d_err;
+    P.item_counter = d_ctr;
+    cf::PairLaunch PL;
+    std::memset(&PL, 0, sizeof(PL));
+    PL.f64 = f64;
+    PL.chunk = 8;
+    PL.evals = (P.flags & CF_FLAG_COUNT_EVALS) ? 1 : 0;
+    PL.hist_words = cf::pair_hist_words(0, nb, 0);
+    PL.smem = cf::smem_layout(P.tile_max, f64 ? 32 : 16, f64 ? 0 : P.lut_n, f64 ? 0 : P.nthr, nb,
+                              0, 0, 0, PL.hist_words)
+                  .total;
+    if (P.n_items > 0 && (e = cf::launch_pairs(P, PL, sms, st)))
+        return cuda_fail(e, "pair kernel launch");
+    if ((e = cudaMemcpyAsync(h.hist, d_hist, sizeof(unsigned long long) * nb, cudaMemcpyDeviceToHost, st)) ||
+        (e = cudaMemcpyAsync(h.diag, d_diag, sizeof(h.diag), cudaMemcpyDeviceToHost, st)) ||
+        (e = cudaMemcpyAsync(&h.err, d_err, 4, cudaMemcpyDeviceToHost, st)) ||
+        (e = cudaStreamSynchronize(st)))
+        return cuda_fail(e, "result readback");
+    if (h.err & cf::ERR_COORD)
+        return fail(CF_EINVAL, "coordinate outside [0, boxsize) or non-finite");
+    if (h.err & cf::ERR_TIMEOUT)
+        return fail(CF_ETIMEOUT, "a bounded device wait (TMA tile barrier) gave up");
+    if (h.err)
+        return fail(CF_EDEVICE, "kernel reported an internal inconsistency");
+    const uint64_t mult = autocorr ? 2u : 1u;
+    for (int k = 0; k < nb; ++k)
+        res->npairs[k] = h.hist[k] * mult;
+    res->n_cellpairs = h.diag[0];
+    res->n_evaluated = h.diag[1];
+    res->n_rechecked = h.diag[2];
+    return CF_OK;
+}
+
+}  // namespace
+
+extern "C" int cf_countpairs_xi_noalloc(int autocorr, const cf_catalog *d1, const cf_catalog *d2,
+                                        const double *edges, int nedges, const cf_config *cfg,
+                                        cf_result *res)
+{
+    return noalloc_xi(autocorr ? 1 : 0, d1, d2, edges, nedges, cfg, res);
+}
