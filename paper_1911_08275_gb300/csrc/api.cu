@@ -118,13 +118,25 @@ double band_sq(double S, int ncomp, double M, double Ls, double R)
     return 2.0 * B + 1e-37;
 }
 
-// Thresholds T[0..2n+1] = lo_0, hi_0, ..., lo_n, hi_n around squared edges E2.
-// d2~ < lo_k proves d2 < E2_k; d2~ >= hi_k proves d2 >= E2_k.
-std::vector<float> make_thresholds(const std::vector<double> &E2, int ncomp, double M, double Ls,
-                                   double R)
+// Float32 decision tables for squared separations (ncomp = 3 for xi, 2 for rp).
+//   T[0..2*ne): lo_0, hi_0, ..., lo_n, hi_n around the squared edges E2[0..ne):
+//     d2~ < lo_k proves d2 < E2_k and d2~ >= hi_k proves d2 >= E2_k.
+//   tab[0..lut_n): one byte per cell of float bit patterns
+//     [u0, u0 + (lut_n - 1) << shift); tab[lut_n - 1] is the entry that every
+//     out-of-range distance (below lo_0, at or above hi_n, NaN) uses.
+//     Entries: bin k if every value of the cell lies in [hi_k, lo_{k+1});
+//     nbins (the dummy row) if every value is surely not counted; LUT_FLAG if
+//     the cell contains a threshold or lies inside a band.
+struct Tables {
+    int nthr, lut_n, shift;
+    uint32_t u0;
+};
+
+Tables build_tables(const double *E2, int ne, int ncomp, double M, double Ls, double R, float *T,
+                    uint8_t *tab)
 {
-    const int ne = (int)E2.size();
-    std::vector<float> T(2 * ne);
+    Tables t;
+    const int nthr = 2 * ne, nbins = ne - 1;
     for (int k = 0; k < ne; ++k) {
         if (E2[k] == 0.0) {  // every d2 >= 0 is surely >= 0
             T[2 * k] = 0.0f;
@@ -137,32 +149,15 @@ std::vector<float> make_thresholds(const std::vector<double> &E2, int ncomp, dou
         T[2 * k] = (lo <= 0.0 || E2[k] < 1e-6) ? -1.0f : f32_down(lo);
         T[2 * k + 1] = std::nextafter(f32_up(E2[k] + B), INFINITY);
     }
-    for (size_t t = 1; t < T.size(); ++t)  // raising a threshold only widens the re-check set
-        T[t] = std::max(T[t], T[t - 1]);
-    return T;
-}
-
-struct Lut {
-    std::vector<uint16_t> tab;
-    int shift = 0;
-    uint32_t u0 = 0, urange = 0;
-};
-
-// Table over the float bit range [u0, u0 + urange): safe bin (as byte offset
-// bin * 128), "inside a band", or "thresholds inside: compare from index t".
-Lut make_lut(const std::vector<float> &T, int nbins)
-{
-    Lut L;
-    const int nthr = (int)T.size();
-    L.u0 = T[0] > 0.0f ? fbits(T[0]) : 0u;
-    const uint32_t u1 = fbits(T[nthr - 1]);
-    L.urange = u1 - L.u0;
+    for (int q = 1; q < nthr; ++q)  // raising a threshold only widens the re-check set
+        T[q] = std::max(T[q], T[q - 1]);
+    const uint32_t u0 = T[0] > 0.0f ? fbits(T[0]) : 0u;
+    const uint32_t urange = fbits(T[nthr - 1]) - u0;
     int s = 0;
-    while ((((uint64_t)L.urange + (1ull << s) - 1) >> s) > (uint64_t)cf::LUT_MAX)
+    while ((((uint64_t)urange + (1ull << s) - 1) >> s) > (uint64_t)(cf::LUT_MAX - 1))
         ++s;
-    L.shift = s;
-    const int n = (int)(((uint64_t)L.urange + (1ull << s) - 1) >> s);
-    L.tab.resize(std::max(n, 1));
+    const int n = std::max(1, (int)(((uint64_t)urange + (1ull << s) - 1) >> s));
+    const uint8_t dummy = (uint8_t)nbins;
     auto count_le = [&](float v) {
         int c = 0;
         while (c < nthr && T[c] <= v)
@@ -170,20 +165,20 @@ Lut make_lut(const std::vector<float> &T, int nbins)
         return c;
     };
     for (int q = 0; q < n; ++q) {
-        const uint32_t blo = L.u0 + ((uint32_t)q << s);
-        const uint64_t bend = std::min<uint64_t>((uint64_t)L.u0 + ((uint64_t)(q + 1) << s), u1);
-        const uint32_t bhi = (uint32_t)(bend - 1);
+        const uint32_t blo = u0 + ((uint32_t)q << s);
+        const uint32_t bhi = u0 + (uint32_t)(((uint64_t)(q + 1) << s) - 1);
         const int clo = count_le(bitsf(blo)), chi = count_le(bitsf(bhi));
-        uint16_t e;
-        if (clo == chi && !(clo & 1) && clo >= 2 && clo <= 2 * nbins)
-            e = (uint16_t)(((clo - 2) / 2) * 128);
-        else if (clo == chi && (clo & 1))
-            e = (uint16_t)cf::LUT_AMBIG;
+        if (clo == chi && !(clo & 1))
+            tab[q] = (clo >= 2 && clo <= 2 * nbins) ? (uint8_t)((clo - 2) / 2) : dummy;
         else
-            e = (uint16_t)(cf::LUT_SLOW | (uint32_t)std::min(clo, 0x3fff));
-        L.tab[q] = e;
+            tab[q] = (uint8_t)cf::LUT_FLAG;
     }
-    return L;
+    tab[n] = dummy;
+    t.nthr = nthr;
+    t.lut_n = n + 1;
+    t.shift = s;
+    t.u0 = u0;
+    return t;
 }
 
 struct Bump {  // carve aligned sub-buffers out of one allocation
@@ -309,6 +304,8 @@ int validate(const Request &q)
         if (!(q.edges[k] > q.edges[k - 1]))
             return fail(CF_EINVAL, "edges must be strictly increasing");
     const double R = q.edges.back();
+    if (!(R < 1e18))
+        return fail(CF_EINVAL, "Rmax must be below 1e18");
     if (q.kind == 1) {
         if (!(q.pimax > 0.0) || !std::isfinite(q.pimax))
             return fail(CF_EINVAL, "pimax must be positive and finite");
@@ -421,8 +418,8 @@ int run(Request &q)
     cf::PairParams P;
     cf::PairLaunch PL;
     std::vector<double> E2(nb + 1);
-    std::vector<float> T;
-    Lut lut;
+    float T[2 * (cf::NB_MAX + 1)];
+    uint8_t tab[cf::LUT_MAX];
     cf::Gridded G[2];
     cf::GridTemps tmp;
     Bump bump;
@@ -435,7 +432,7 @@ int run(Request &q)
     unsigned *d_err = nullptr, *d_ctr = nullptr;
     unsigned long long *d_hist = nullptr, *d_diag = nullptr;
     float *d_thr = nullptr;
-    uint16_t *d_lut = nullptr;
+    uint8_t *d_lut = nullptr;
     double *d_E2 = nullptr;
     size_t total = 0;
     struct HostOut {
@@ -482,7 +479,7 @@ int run(Request &q)
         d_hist = bump.take<unsigned long long>(nslots);
         d_diag = bump.take<unsigned long long>(4);
         d_thr = bump.take<float>(2 * (nb + 1));
-        d_lut = bump.take<uint16_t>(cf::LUT_MAX);
+        d_lut = bump.take<uint8_t>(cf::LUT_MAX);
         d_E2 = bump.take<double>(nb + 1);
         if (pass == 0) {
             total = bump.off;
@@ -538,8 +535,10 @@ int run(Request &q)
             bump.base = pass ? (char *)ws2 : nullptr;
             bump.off = 0;
             for (int t = 0; t < ncat; ++t) {
-                const long long n = cats[t]->n;
-                G[t].pos = bump.take<float4>(n);
+                const long long n = cats[t]->n + 3ll * g.ncols;  // columns padded to 4
+                G[t].xs = bump.take<float>(n);
+                G[t].ys = bump.take<float>(n);
+                G[t].zs = bump.take<float>(n);
                 G[t].pos64 = bump.take<double4_32a>(n);
                 G[t].perm = bump.take<int>(n);
                 G[t].cell_start = bump.take<uint32_t>(g.ncells + 1);
@@ -547,10 +546,10 @@ int run(Request &q)
             }
             tmp.cell_of = bump.take<uint32_t>(nmax);
             tmp.slot = bump.take<uint32_t>(nmax);
-            tmp.tmp_idx = bump.take<int>(nmax);
-            tmp.tmp_z = bump.take<double>(nmax);
-            tmp.tmp_cell = bump.take<uint32_t>(nmax);
+            tmp.tmp_idx = bump.take<int>(nmax + 3ll * g.ncols);
+            tmp.tmp_z = bump.take<double>(nmax + 3ll * g.ncols);
             tmp.counts = bump.take<uint32_t>(g.ncells);
+            tmp.pad = bump.take<uint32_t>(g.ncols);
             tmp.bsum = bump.take<uint32_t>(g.ncells / 4096 + 2);
             if (pass == 0) {
                 const cudaError_t e = cudaMallocAsync(&ws2, bump.off, st);
@@ -586,7 +585,7 @@ int run(Request &q)
                 P.stencil[P.nstencil++] = make_int2(ox, oy);
             }
         P.n_items = g.ncols * P.nstencil;
-        P.tile_max = f64 ? 1024 : 2048;
+        P.tile_max = 1024;
         P.flags = c->flags;
         const double M = std::max(g.extent[0], std::max(g.extent[1], g.extent[2]));
         const double Ls = g.periodic ? std::max(g.box[0], std::max(g.box[1], g.box[2])) : 0.0;
@@ -599,15 +598,13 @@ int run(Request &q)
             P.boxf[a] = (float)g.box[a];
         P.nbins = nb;
         if (!f64) {
-            T = make_thresholds(E2, 3, M, Ls, R);
-            lut = make_lut(T, nb);
-            P.nthr = (int)T.size();
-            P.lut_n = (int)lut.tab.size();
-            P.lut_shift = lut.shift;
-            P.u0 = lut.u0;
-            P.urange = lut.urange;
-            CF_CUDA(cudaMemcpyAsync(d_thr, T.data(), 4 * T.size(), cudaMemcpyHostToDevice, st), "H2D thresholds");
-            CF_CUDA(cudaMemcpyAsync(d_lut, lut.tab.data(), 2 * lut.tab.size(), cudaMemcpyHostToDevice, st), "H2D lut");
+            const Tables tb = build_tables(E2.data(), nb + 1, 3, M, Ls, R, T, tab);
+            P.nthr = tb.nthr;
+            P.lut_n = tb.lut_n;
+            P.lut_shift = tb.shift;
+            P.u0 = tb.u0;
+            CF_CUDA(cudaMemcpyAsync(d_thr, T, 4 * P.nthr, cudaMemcpyHostToDevice, st), "H2D thresholds");
+            CF_CUDA(cudaMemcpyAsync(d_lut, tab, P.lut_n, cudaMemcpyHostToDevice, st), "H2D lut");
         }
         CF_CUDA(cudaMemcpyAsync(d_E2, E2.data(), 8 * E2.size(), cudaMemcpyHostToDevice, st), "H2D E2");
         P.thr = d_thr;
@@ -623,9 +620,8 @@ int run(Request &q)
         PL.evals = (c->flags & (CF_FLAG_COUNT_EVALS | CF_FLAG_VERIFY_BAND)) ? 1 : 0;
         PL.verify = (!f64 && (c->flags & CF_FLAG_VERIFY_BAND)) ? 1 : 0;
         PL.hist_words = cf::pair_hist_words(q.kind, nb, q.npibins);
-        PL.smem = cf::smem_layout(P.tile_max, f64 ? 32 : 16, f64 ? 0 : P.lut_n, f64 ? 0 : P.nthr, nb,
-                                  0, 0, 0, PL.hist_words)
-                      .total;
+        PL.smem = f64 ? cf::smem_layout(P.tile_max, 32, 0, 0, nb, 0, 0, 0, PL.hist_words).total
+                      : cf::xi32_smem_bytes(nb);
         CF_CUDA(cudaEventRecord(g_events.ev[1], st), "cudaEventRecord");
         if (P.n_items > 0) {
             const cudaError_t e = cf::launch_pairs(P, PL, sms, st);
@@ -792,54 +788,6 @@ int noalloc_scratch(int dev, void **out)
     return CF_OK;
 }
 
-// Float32 thresholds and lookup table into caller-provided fixed arrays
-// (the same rules as make_thresholds / make_lut, without heap storage).
-int noalloc_tables(const double *E2, int ne, double M, double Ls, double R, float *T,
-                   uint16_t *tab, int *lut_n, int *shift, uint32_t *u0, uint32_t *urange)
-{
-    const int nthr = 2 * ne;
-    for (int k = 0; k < ne; ++k) {
-        if (E2[k] == 0.0) {
-            T[2 * k] = 0.0f;
-            T[2 * k + 1] = 0.0f;
-            continue;
-        }
-        const double B = band_sq(E2[k], 3, M, Ls, R);
-        const double lo = E2[k] - B;
-        T[2 * k] = (lo <= 0.0 || E2[k] < 1e-6) ? -1.0f : f32_down(lo);
-        T[2 * k + 1] = std::nextafter(f32_up(E2[k] + B), INFINITY);
-    }
-    for (int t = 1; t < nthr; ++t)
-        T[t] = std::max(T[t], T[t - 1]);
-    *u0 = T[0] > 0.0f ? fbits(T[0]) : 0u;
-    const uint32_t u1 = fbits(T[nthr - 1]);
-    *urange = u1 - *u0;
-    int s = 0;
-    while ((((uint64_t)*urange + (1ull << s) - 1) >> s) > (uint64_t)cf::LUT_MAX)
-        ++s;
-    *shift = s;
-    const int n = std::max(1, (int)(((uint64_t)*urange + (1ull << s) - 1) >> s));
-    *lut_n = n;
-    const int nbins = ne - 1;
-    for (int q = 0; q < n; ++q) {
-        const uint32_t blo = *u0 + ((uint32_t)q << s);
-        const uint64_t bend = std::min<uint64_t>((uint64_t)*u0 + ((uint64_t)(q + 1) << s), u1);
-        const uint32_t bhi = (uint32_t)(bend - 1);
-        int clo = 0, chi = 0;
-        while (clo < nthr && T[clo] <= bitsf(blo))
-            ++clo;
-        while (chi < nthr && T[chi] <= bitsf(bhi))
-            ++chi;
-        if (clo == chi && !(clo & 1) && clo >= 2 && clo <= 2 * nbins)
-            tab[q] = (uint16_t)(((clo - 2) / 2) * 128);
-        else if (clo == chi && (clo & 1))
-            tab[q] = (uint16_t)cf::LUT_AMBIG;
-        else
-            tab[q] = (uint16_t)(cf::LUT_SLOW | (uint32_t)std::min(clo, 0x3fff));
-    }
-    return CF_OK;
-}
-
 int noalloc_xi(int autocorr, const cf_catalog *d1, const cf_catalog *d2, const double *edges,
                int nedges, const cf_config *c, cf_result *res)
 {
@@ -914,7 +862,7 @@ int noalloc_xi(int autocorr, const cf_catalog *d1, const cf_catalog *d2, const d
     unsigned long long *d_hist = bump.take<unsigned long long>(cf::NB_MAX);
     unsigned long long *d_diag = bump.take<unsigned long long>(4);
     float *d_thr = bump.take<float>(2 * (cf::NB_MAX + 1));
-    uint16_t *d_lut = bump.take<uint16_t>(cf::LUT_MAX);
+    uint8_t *d_lut = bump.take<uint8_t>(cf::LUT_MAX);
     double *d_E2 = bump.take<double>(cf::NB_MAX + 1);
     struct {
         unsigned long long keys[6];
@@ -985,8 +933,10 @@ int noalloc_xi(int autocorr, const cf_catalog *d1, const cf_catalog *d2, const d
     cf::Gridded G[2];
     cf::GridTemps tmp;
     for (int t = 0; t < ncat; ++t) {
-        const long long n = cats[t]->n;
-        G[t].pos = bump.take<float4>(n);
+        const long long n = cats[t]->n + 3ll * g.ncols;  // columns padded to 4
+        G[t].xs = bump.take<float>(n);
+        G[t].ys = bump.take<float>(n);
+        G[t].zs = bump.take<float>(n);
         G[t].pos64 = bump.take<double4_32a>(n);
         G[t].perm = bump.take<int>(n);
         G[t].cell_start = bump.take<uint32_t>(g.ncells + 1);
@@ -994,10 +944,10 @@ int noalloc_xi(int autocorr, const cf_catalog *d1, const cf_catalog *d2, const d
     }
     tmp.cell_of = bump.take<uint32_t>(nmax);
     tmp.slot = bump.take<uint32_t>(nmax);
-    tmp.tmp_idx = bump.take<int>(nmax);
-    tmp.tmp_z = bump.take<double>(nmax);
-    tmp.tmp_cell = bump.take<uint32_t>(nmax);
+    tmp.tmp_idx = bump.take<int>(nmax + 3ll * g.ncols);
+    tmp.tmp_z = bump.take<double>(nmax + 3ll * g.ncols);
     tmp.counts = bump.take<uint32_t>(g.ncells);
+    tmp.pad = bump.take<uint32_t>(g.ncols);
     tmp.bsum = bump.take<uint32_t>(g.ncells / 4096 + 2);
     if (bump.off > NOALLOC_BYTES)
         return fail(CF_EINVAL, "no-alloc entry point: problem does not fit the 32 MiB static scratch");
@@ -1030,7 +980,7 @@ int noalloc_xi(int autocorr, const cf_catalog *d1, const cf_catalog *d2, const d
             P.stencil[P.nstencil++] = make_int2(ox, oy);
         }
     P.n_items = g.ncols * P.nstencil;
-    P.tile_max = f64 ? 1024 : 2048;
+    P.tile_max = 1024;
     P.flags = c->flags & (CF_FLAG_NO_PRUNE | CF_FLAG_COUNT_EVALS);
     const double M = std::max(g.extent[0], std::max(g.extent[1], g.extent[2]));
     const double Ls = g.periodic ? std::max(g.box[0], std::max(g.box[1], g.box[2])) : 0.0;
@@ -1043,12 +993,15 @@ int noalloc_xi(int autocorr, const cf_catalog *d1, const cf_catalog *d2, const d
         P.boxf[a] = (float)g.box[a];
     P.nbins = nb;
     float T[2 * (cf::NB_MAX + 1)];
-    uint16_t tab[cf::LUT_MAX];
+    uint8_t tab[cf::LUT_MAX];
     if (!f64) {
-        noalloc_tables(E2, nb + 1, M, Ls, R, T, tab, &P.lut_n, &P.lut_shift, &P.u0, &P.urange);
-        P.nthr = 2 * (nb + 1);
+        const Tables tb = build_tables(E2, nb + 1, 3, M, Ls, R, T, tab);
+        P.nthr = tb.nthr;
+        P.lut_n = tb.lut_n;
+        P.lut_shift = tb.shift;
+        P.u0 = tb.u0;
         if ((e = cudaMemcpyAsync(d_thr, T, sizeof(float) * P.nthr, cudaMemcpyHostToDevice, st)) ||
-            (e = cudaMemcpyAsync(d_lut, tab, sizeof(uint16_t) * P.lut_n, cudaMemcpyHostToDevice, st)))
+            (e = cudaMemcpyAsync(d_lut, tab, P.lut_n, cudaMemcpyHostToDevice, st)))
             return cuda_fail(e, "H2D tables");
     }
     if ((e = cudaMemcpyAsync(d_E2, E2, sizeof(double) * (nb + 1), cudaMemcpyHostToDevice, st)))
@@ -1066,9 +1019,8 @@ int noalloc_xi(int autocorr, const cf_catalog *d1, const cf_catalog *d2, const d
     PL.chunk = 8;
     PL.evals = (P.flags & CF_FLAG_COUNT_EVALS) ? 1 : 0;
     PL.hist_words = cf::pair_hist_words(0, nb, 0);
-    PL.smem = cf::smem_layout(P.tile_max, f64 ? 32 : 16, f64 ? 0 : P.lut_n, f64 ? 0 : P.nthr, nb,
-                              0, 0, 0, PL.hist_words)
-                  .total;
+    PL.smem = f64 ? cf::smem_layout(P.tile_max, 32, 0, 0, nb, 0, 0, 0, PL.hist_words).total
+                  : cf::xi32_smem_bytes(nb);
     if (P.n_items > 0 && (e = cf::launch_pairs(P, PL, sms, st)))
         return cuda_fail(e, "pair kernel launch");
     if ((e = cudaMemcpyAsync(h.hist, d_hist, sizeof(unsigned long long) * nb, cudaMemcpyDeviceToHost, st)) ||

@@ -12,7 +12,8 @@ namespace cf {
 constexpr int NB_MAX = 64;          // radial (xi) or rp bins
 constexpr int NBINS2D_MAX = 4096;   // rp bins * pi bins
 constexpr int NPI_MAX = 4096;
-constexpr int LUT_MAX = 4096;       // entries of the float32 bin lookup table
+constexpr int LUT_MAX = 8192;       // entries (bytes) of the float32 bin lookup table
+constexpr int TILE32 = 2048;        // secondary points per staged float32 tile
 constexpr int MAX_REACH = 4;        // column stencil half-width per axis
 constexpr int MAX_STENCIL = (2 * MAX_REACH + 1) * (2 * MAX_REACH + 1);
 constexpr int WARPS = 8;            // warps per pair-kernel CTA
@@ -26,12 +27,20 @@ enum : unsigned {
     ERR_INTERNAL = 4u,  // an index or table inconsistency that must never happen
 };
 
-// LUT entry encoding (uint16): < 0x4000 -> safe bin, value = bin * 128 (byte
-// offset of the bin row in a warp's per-lane histogram); 0x8000 -> the whole
-// cell lies inside an error band (re-check in binary64); 0xC000 | t -> the cell
-// contains thresholds starting at index t (compare, then maybe re-check).
-constexpr uint32_t LUT_AMBIG = 0x8000u;
-constexpr uint32_t LUT_SLOW = 0xC000u;
+// Lookup-table entry (one byte): 0..nbins-1 -> the bin (the cell lies wholly
+// between hi_k and lo_{k+1}); nbins -> surely not counted (dummy row);
+// LUT_FLAG -> the cell touches a threshold (compare, maybe re-check).
+constexpr uint32_t LUT_FLAG = 0x80u;
+
+// Shared layout of the float32 DD(r) kernel (compile-time offsets):
+// [0,128) barrier + work item; LUT; x, y, z tiles of TILE32 + 64 floats each;
+// thresholds; squared edges; per-warp histograms ((nbins + 1) rows of 32 lanes).
+constexpr int XI32_LUT_OFF = 128;
+constexpr int XI32_TX_OFF = XI32_LUT_OFF + LUT_MAX;
+constexpr int XI32_TSTRIDE = (TILE32 + 64) * 4;
+constexpr int XI32_THR_OFF = XI32_TX_OFF + 3 * XI32_TSTRIDE;
+constexpr int XI32_E2_OFF = XI32_THR_OFF + 2 * (NB_MAX + 1) * 4;
+constexpr int XI32_HIST_OFF = XI32_E2_OFF + (NB_MAX + 1) * 8;
 
 // Grid geometry: columns in (x, y), z-cells inside each column (sort keys).
 struct Geom {
@@ -46,10 +55,11 @@ struct Geom {
     double box[3];      // periodic box (0 when open)
 };
 
-// A gridded catalogue, in (column, z, original index) order.
+// A gridded catalogue, in (column, z, original index) order; every column is
+// padded with NaN entries to a multiple of 4 (see grid.cu).
 struct Gridded {
     long long n;
-    float4 *pos;          // (x~, y~, z~, w) float32 in the grid frame
+    float *xs, *ys, *zs;  // float32 coordinates in the grid frame (padded columns)
     double4_32a *pos64;       // (x, y, z, w) binary64, exact inputs
     int *perm;            // original index of each sorted point
     uint32_t *cell_start; // ncells + 1
@@ -77,13 +87,13 @@ struct PairParams {
     int nbins;          // xi or rp bins
     int npibins;        // rp-pi only
     int nthr;           // 2 * nbins + 2 float32 thresholds
-    int lut_n, lut_shift;
-    uint32_t u0, urange; // float bit range covered by the LUT
+    int lut_n, lut_shift; // table entries (last one = out of range), cell width 2^shift
+    uint32_t u0;          // float bit pattern of the table's first cell
     int pi_nthr;        // 2 * npibins + 2 (rp-pi)
     int pilut_n, pilut_shift;
     uint32_t pu0, purange;
     const float *thr;        // nthr
-    const uint16_t *lut;     // lut_n
+    const uint8_t *lut;      // lut_n
     const double *E2;        // nbins + 1
     const float *pithr;      // pi_nthr
     const uint16_t *pilut;   // pilut_n

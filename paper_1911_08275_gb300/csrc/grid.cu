@@ -6,11 +6,15 @@
 // Layout produced (one gridded catalogue):
 //   cell_start[ncells + 1]  counting-sort offsets; cell = column * nz + zcell,
 //                           column = cx * ncy + cy.  A column is the contiguous
-//                           range [cell_start[col*nz], cell_start[(col+1)*nz]).
-//   pos[n]   float4  (x - ox, y - oy, z - oz, w) rounded to float32 (grid frame)
-//   pos64[n] double4_32a (x, y, z, w) exact binary64 copies (re-checks, FP64 path)
-//   perm[n]  original index of each sorted point
-//   colbox[ncols]  (xmin, xmax, ymin, ymax) of the column's points, binary64
+//                           range [cell_start[col*nz], cell_start[(col+1)*nz]),
+//                           padded at its end to a multiple of 4 entries (16 bytes
+//                           of float) so 1-D bulk copies of column slices are
+//                           aligned; padding entries are NaN and never counted.
+//   xs, ys, zs[n']  float32 x - ox, y - oy, z - oz (grid frame), structure of arrays
+//   pos64[n']       double4 (x, y, z, w) exact binary64 copies (re-checks, FP64 path)
+//   perm[n']        original index of each sorted point (-1 for padding)
+//   colbox[ncols]   (xmin, xmax, ymin, ymax) of the column's points, binary64
+// with n' <= n + 3 * ncols.
 //
 // Within a cell the order is (z, original index), computed by ranking, so the
 // output is deterministic whatever the order of the atomic slot assignment.
@@ -100,8 +104,7 @@ __device__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *warp_sums, uint32
 }
 
 __global__ void __launch_bounds__(SCAN_THREADS)
-    k_scan_blocks(const uint32_t *__restrict__ in, uint32_t *__restrict__ out, long long n,
-                  uint32_t *__restrict__ bsum)
+    k_scan_blocks(const uint32_t *in, uint32_t *out, long long n, uint32_t *__restrict__ bsum)
 {
     __shared__ uint32_t ws[32];
     __shared__ uint32_t tot;
@@ -154,53 +157,97 @@ __global__ void k_scan_add(uint32_t *__restrict__ out, long long n, const uint32
         out[i] += bsum[i / SCAN_ITEMS];
 }
 
+// One warp per column: padding that rounds the column up to a multiple of 4,
+// written into the padded count of the column's last cell.
+__global__ void k_colpad(const uint32_t *__restrict__ count, int ncols, int nz,
+                         uint32_t *__restrict__ pad, uint32_t *__restrict__ padded)
+{
+    const int lane = threadIdx.x & 31;
+    const int col = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (col >= ncols)
+        return;
+    const long long c0 = (long long)col * nz;
+    uint32_t tot = 0;
+    for (int z = lane; z < nz; z += 32) {
+        const uint32_t v = count[c0 + z];
+        padded[c0 + z] = v;
+        tot += v;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        tot += __shfl_xor_sync(FULL, tot, o);
+    const uint32_t pd = (4u - (tot & 3u)) & 3u;
+    __syncwarp();
+    if (lane == 0) {
+        pad[col] = pd;
+        padded[c0 + nz - 1] += pd;
+    }
+}
+
 template <class T>
 __global__ void k_scatter(const T *__restrict__ z, long long n, const uint32_t *__restrict__ cell_of,
                           const uint32_t *__restrict__ slot, const uint32_t *__restrict__ start,
-                          int *__restrict__ tmp_idx, double *__restrict__ tmp_z,
-                          uint32_t *__restrict__ tmp_cell)
+                          int *__restrict__ tmp_idx, double *__restrict__ tmp_z)
+{
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
+         p += (long long)gridDim.x * blockDim.x) {
+        const uint32_t q = start[cell_of[p]] + slot[p];
+        tmp_idx[q] = (int)p;
+        tmp_z[q] = (double)z[p];
+    }
+}
+
+// Rank each point inside its cell by (z, original index) among the cell's real
+// entries and write the sorted float32 / binary64 copies.  Work per cell is
+// quadratic in its occupancy; z-cells are sized for ~16 points on average.
+template <class T>
+__global__ void k_sort_gather(const T *__restrict__ x, const T *__restrict__ y,
+                              const T *__restrict__ z, const double *__restrict__ w, long long n,
+                              Geom g, const uint32_t *__restrict__ cell_of,
+                              const uint32_t *__restrict__ count, const uint32_t *__restrict__ start,
+                              const int *__restrict__ tmp_idx, const double *__restrict__ tmp_z,
+                              float *__restrict__ xs, float *__restrict__ ys,
+                              float *__restrict__ zs, double4_32a *__restrict__ pos64,
+                              int *__restrict__ perm)
 {
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
          p += (long long)gridDim.x * blockDim.x) {
         const uint32_t c = cell_of[p];
-        const uint32_t q = start[c] + slot[p];
-        tmp_idx[q] = (int)p;
-        tmp_z[q] = (double)z[p];
-        tmp_cell[q] = c;
-    }
-}
-
-// Rank each point inside its cell by (z, original index) and write the sorted
-// float32 / binary64 copies.  Work per cell is quadratic in its occupancy;
-// z-cells are sized for ~16 points on average.
-template <class T>
-__global__ void k_sort_gather(const T *__restrict__ x, const T *__restrict__ y,
-                              const T *__restrict__ z, const double *__restrict__ w, long long n,
-                              Geom g, const uint32_t *__restrict__ start,
-                              const int *__restrict__ tmp_idx, const double *__restrict__ tmp_z,
-                              const uint32_t *__restrict__ tmp_cell, float4 *__restrict__ pos,
-                              double4_32a *__restrict__ pos64, int *__restrict__ perm)
-{
-    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n;
-         q += (long long)gridDim.x * blockDim.x) {
-        const uint32_t c = tmp_cell[q];
-        const uint32_t s = start[c], e = start[c + 1];
-        const double zq = tmp_z[q];
-        const int iq = tmp_idx[q];
+        const uint32_t s = start[c], e = s + count[c];
+        const double X = (double)x[p], Y = (double)y[p], Z = (double)z[p];
+        const int iq = (int)p;
         uint32_t rank = 0;
         for (uint32_t r = s; r < e; ++r) {
             const double zr = tmp_z[r];
             const int ir = tmp_idx[r];
-            rank += (zr < zq) || (zr == zq && ir < iq);
+            rank += (zr < Z) || (zr == Z && ir < iq);
         }
         const uint32_t d = s + rank;
-        const double X = (double)x[iq], Y = (double)y[iq], Z = (double)z[iq];
-        const double W = w ? w[iq] : 0.0;
+        const double W = w ? w[p] : 0.0;
         pos64[d] = make_double4_32a(X, Y, Z, W);
-        pos[d] = make_float4(__double2float_rn(__dsub_rn(X, g.origin[0])),
-                             __double2float_rn(__dsub_rn(Y, g.origin[1])),
-                             __double2float_rn(__dsub_rn(Z, g.origin[2])), __double2float_rn(W));
+        xs[d] = __double2float_rn(__dsub_rn(X, g.origin[0]));
+        ys[d] = __double2float_rn(__dsub_rn(Y, g.origin[1]));
+        zs[d] = __double2float_rn(__dsub_rn(Z, g.origin[2]));
         perm[d] = iq;
+    }
+}
+
+// Padding entries at the end of each column: NaN (never counted), perm -1.
+__global__ void k_padfill(const uint32_t *__restrict__ start, const uint32_t *__restrict__ pad,
+                          int ncols, int nz, float *__restrict__ xs, float *__restrict__ ys,
+                          float *__restrict__ zs, double4_32a *__restrict__ pos64,
+                          int *__restrict__ perm)
+{
+    const int col = blockIdx.x * blockDim.x + threadIdx.x;
+    if (col >= ncols)
+        return;
+    const uint32_t e = start[(long long)(col + 1) * nz];
+    const float fn = __int_as_float(0x7fc00000);
+    const double dn = __longlong_as_double(0x7ff8000000000000ll);
+    for (uint32_t q = e - pad[col]; q < e; ++q) {
+        xs[q] = ys[q] = zs[q] = fn;
+        pos64[q] = make_double4_32a(dn, dn, dn, dn);
+        perm[q] = -1;
     }
 }
 
@@ -302,19 +349,21 @@ cudaError_t build_grid_t(const void *x, const void *y, const void *z, const doub
                                                             (const T *)z, n, g, t.cell_of, t.slot,
                                                             t.counts, err);
     }
+    const int cb = (g.ncols * 32 + 255) / 256;
+    k_colpad<<<cb, 256, 0, st>>>(t.counts, g.ncols, g.nz, t.pad, out.cell_start);
     const int nb = (int)((nc + SCAN_ITEMS - 1) / SCAN_ITEMS);
-    k_scan_blocks<<<nb, SCAN_THREADS, 0, st>>>(t.counts, out.cell_start, nc, t.bsum);
+    k_scan_blocks<<<nb, SCAN_THREADS, 0, st>>>(out.cell_start, out.cell_start, nc, t.bsum);
     k_scan_sums<<<1, SCAN_THREADS, 0, st>>>(t.bsum, nb, out.cell_start + nc);
     k_scan_add<<<(int)((nc + 255) / 256), 256, 0, st>>>(out.cell_start, nc, t.bsum);
     if (n > 0) {
         k_scatter<T><<<grid_blocks(n, TB, sms), TB, 0, st>>>((const T *)z, n, t.cell_of, t.slot,
-                                                             out.cell_start, t.tmp_idx, t.tmp_z,
-                                                             t.tmp_cell);
+                                                             out.cell_start, t.tmp_idx, t.tmp_z);
         k_sort_gather<T><<<grid_blocks(n, TB, sms), TB, 0, st>>>(
-            (const T *)x, (const T *)y, (const T *)z, w, n, g, out.cell_start, t.tmp_idx, t.tmp_z,
-            t.tmp_cell, out.pos, out.pos64, out.perm);
+            (const T *)x, (const T *)y, (const T *)z, w, n, g, t.cell_of, t.counts,
+            out.cell_start, t.tmp_idx, t.tmp_z, out.xs, out.ys, out.zs, out.pos64, out.perm);
     }
-    const int cb = (g.ncols * 32 + 255) / 256;
+    k_padfill<<<(g.ncols + 255) / 256, 256, 0, st>>>(out.cell_start, t.pad, g.ncols, g.nz, out.xs,
+                                                      out.ys, out.zs, out.pos64, out.perm);
     k_colbox<<<cb, 256, 0, st>>>(out.pos64, out.cell_start, g.ncols, g.nz, out.colbox);
     return cudaGetLastError();
 }

@@ -11,10 +11,10 @@ namespace cf {
 struct GridTemps {
     uint32_t *cell_of;   // n
     uint32_t *slot;      // n
-    int *tmp_idx;        // n
-    double *tmp_z;       // n
-    uint32_t *tmp_cell;  // n
+    int *tmp_idx;        // n + 3 * ncols (padded index space)
+    double *tmp_z;       // n + 3 * ncols
     uint32_t *counts;    // ncells
+    uint32_t *pad;       // ncols
     uint32_t *bsum;      // ceil(ncells / 4096)
 };
 

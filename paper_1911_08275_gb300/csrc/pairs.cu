@@ -12,51 +12,90 @@
 // periodic z image a warp finds, by a lane-parallel search of the staged z
 // values, the window of b points whose z can be within the reach of the chunk
 // (the paper's late entry and early exit, applied per chunk rather than per
-// particle), then evaluates I x (32/I) pairs per step.
+// particle), then sweeps it.
 //
-// Binning (xi, float32 mode): the squared distance is evaluated in float32;
-// its bit pattern indexes a lookup table built on the host from float32
-// thresholds lo_k < e_k^2 < hi_k that bracket every squared edge by a proven
-// error bound.  A table cell wholly between hi_k and lo_{k+1} gives the bin
-// directly; a cell that touches a band falls back to threshold compares, and a
-// distance inside a band is re-evaluated with the canonical binary64 formula
-// from the binary64 copies of the two points.  Counts are thus bit-identical to
-// the binary64 definition.  Each lane owns one column of its warp's histogram
-// in shared memory (no atomics, no bank conflicts); columns are reduced and
-// added to the global histogram once per CTA.
+// Float32 kernel (k_xi32).  The staged tiles hold every coordinate twice,
+// (x,x,y,y) and (z,z,w,w) in two arrays of 16-byte elements, so one 16-byte and
+// one 8-byte conflict-free shared load give packed operands for the
+// sm_100-family f32x2 instructions: each lane evaluates two primaries against
+// one secondary with 6 packed FP32 instructions.  The squared distance's bit
+// pattern indexes (clamped, branch-free) a lookup table built on the host from
+// float32 thresholds lo_k < e_k^2 < hi_k that bracket every squared edge by a
+// proven error bound; a safe table cell gives the byte offset of the bin row
+// directly, out-of-range distances share one entry that points at a dummy row,
+// and every lane adds one to its own column of the warp's shared histogram
+// with a shared-memory atomic (no bank conflicts, no branch).  Cells that touch a band fall back to threshold
+// compares, and a distance inside a band is re-evaluated with the canonical
+// binary64 formula from the binary64 copies of the two points, so counts are
+// bit-identical to the binary64 definition.
 //
-// The binary64 path (CF_MODE_FP64) runs the same loop on binary64 copies with
-// the canonical formula and exact squared-edge compares.
+// Binary64 kernel (k_xi64, CF_MODE_FP64): the same loop on binary64 copies
+// with the canonical formula and exact squared-edge compares.
 #include <cuda_runtime.h>
-
-#include <type_traits>
 
 #include "cf_internal.cuh"
 #include "pairs.cuh"
 
 namespace cf {
 
+int xi32_smem_bytes(int nbins)
+{
+    return ((XI32_HIST_OFF + WARPS * (nbins + 1) * 32 * 4) + 127) / 128 * 128;
+}
+
 int pair_hist_words(int kind, int nbins, int npibins)
 {
     if (kind == 0)
-        return WARPS * nbins * 32;
+        return WARPS * (nbins + 1) * 32;  // per-lane rows + one dummy row
     return WARPS * nbins * npibins;
 }
 
 namespace {
 
 constexpr unsigned WAIT_LIMIT = 1u << 22;
+typedef unsigned long long u64;
 
 __device__ __forceinline__ int floor_div(int a, int n)
 {
     return a >= 0 ? a / n : -((-a + n - 1) / n);
 }
 
-// First index p in [0, n) with t[p].z >= v (upper = false) or t[p].z > v
-// (upper = true); n if none.  t[0..n) must be sorted by z.  All lanes call it
-// with the same arguments; each round probes 32 positions.
-template <class P4, class V>
-__device__ __forceinline__ int warp_bound(const P4 *t, int n, V v, bool upper, int lane)
+// ---------------------------------------------------------------- packed f32x2
+__device__ __forceinline__ u64 pack2(float lo, float hi)
+{
+    u64 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void unpack2(u64 v, float &lo, float &hi)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ u64 fsub2(u64 a, u64 b)
+{
+    u64 r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ u64 fmul2(u64 a, u64 b)
+{
+    u64 r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ u64 ffma2(u64 a, u64 b, u64 c)
+{
+    u64 r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+
+// ---------------------------------------------------------------- searches
+// First index p in [0, n) with key(p) >= v (upper = false) or key(p) > v
+// (upper = true); n if none.  Keys must be sorted.  All lanes call it with the
+// same arguments; each round probes 32 positions.
+template <class Key, class V>
+__device__ __forceinline__ int warp_bound(Key key, int n, V v, bool upper, int lane)
 {
     int lo = 0, hi = n;
     while (lo < hi) {
@@ -64,7 +103,7 @@ __device__ __forceinline__ int warp_bound(const P4 *t, int n, V v, bool upper, i
         const int p = lo + lane * s;
         bool q = false;
         if (p < hi) {
-            const V z = t[p].z;
+            const V z = key(p);
             q = upper ? (z <= v) : (z < v);
         }
         const int c = __popc(__ballot_sync(FULL, q));
@@ -96,8 +135,8 @@ __device__ __forceinline__ int bin_f64(double r2, const double *E2, int nb)
     return lo;
 }
 
-__device__ __forceinline__ double canon_r2(const double4_32a &p, const double4_32a &q, double Sx, double Sy,
-                                           double Sz)
+__device__ __forceinline__ double canon_r2(const double4_32a &p, const double4_32a &q, double Sx,
+                                           double Sy, double Sz)
 {
     const double dx = canon_comp(p.x, q.x, Sx);
     const double dy = canon_comp(p.y, q.y, Sy);
@@ -105,35 +144,33 @@ __device__ __forceinline__ double canon_r2(const double4_32a &p, const double4_3
     return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
 }
 
-// Rare path of the float32 binning: the table cell touches an error band.
-// Returns 1 if the pair was re-evaluated in binary64.
-__device__ __noinline__ int bin_slow(uint32_t e, float d2, const float *thr, int nthr, int nb,
-                                     const double *E2, uint32_t *hl, const double4_32a *pa,
-                                     const double4_32a *pb, int i, int j, double Sx, double Sy,
-                                     double Sz)
+// Number of thresholds <= d2 (T non-decreasing, nthr entries).
+__device__ __forceinline__ int count_le(const float *T, int nthr, float d2)
 {
-    int c = -1;
-    if (e != LUT_AMBIG) {
-        c = (int)(e & 0x3fffu);
-        while (c < nthr && thr[c] <= d2)
-            ++c;
+    int lo = 0, hi = nthr;  // answer in [lo, hi]
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (T[mid] <= d2)
+            lo = mid + 1;
+        else
+            hi = mid;
     }
-    if (c >= 0 && !(c & 1)) {
-        if (c >= 2 && c <= 2 * nb)
-            hl[((c - 2) >> 1) * 32] += 1u;
-        return 0;
-    }
-    const double r2 = canon_r2(pa[i], pb[j], Sx, Sy, Sz);
-    const int k = bin_f64(r2, E2, nb);
-    if (k >= 0)
-        hl[k * 32] += 1u;
-    return 1;
+    return lo;
+}
+
+// Binary64 re-evaluation of one pair inside an error band: bin row or -1.
+__device__ __noinline__ int recheck64(const double *E2, int nb, const double4_32a *pa,
+                                      const double4_32a *pb, int i, int j, double Sx, double Sy,
+                                      double Sz)
+{
+    return bin_f64(canon_r2(pa[i], pb[j], Sx, Sy, Sz), E2, nb);
 }
 
 // Debug: does the float32 decision for d2 agree with binary64?  (1 = violation)
 __device__ __noinline__ int verify_pair(float d2, const float *thr, int nthr, int nb,
-                                        const double *E2, const double4_32a *pa, const double4_32a *pb,
-                                        int i, int j, double Sx, double Sy, double Sz)
+                                        const double *E2, const double4_32a *pa,
+                                        const double4_32a *pb, int i, int j, double Sx, double Sy,
+                                        double Sz)
 {
     int c = 0;
     while (c < nthr && thr[c] <= d2)
@@ -145,7 +182,7 @@ __device__ __noinline__ int verify_pair(float d2, const float *thr, int nthr, in
     return k32 != k64;
 }
 
-__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v)
+__device__ __forceinline__ u64 warp_sum_u64(u64 v)
 {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1)
@@ -157,42 +194,301 @@ __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v)
 __device__ void warp_flush(uint32_t *hw, int nb, unsigned long long *ghist, int lane)
 {
     for (int b = 0; b < nb; ++b) {
-        const unsigned long long v = warp_sum_u64(hw[b * 32 + lane]);
+        const u64 v = warp_sum_u64(hw[b * 32 + lane]);
         hw[b * 32 + lane] = 0u;
         if (lane == 0 && v)
             atomicAdd(&ghist[b], v);
     }
 }
 
-template <bool F64, int I, bool EVALS, bool VERIFY>
-__global__ void __launch_bounds__(THREADS) k_xi(const __grid_constant__ PairParams P)
-{
-    using P4 = typename std::conditional<F64, double4_32a, float4>::type;
-    using V = typename std::conditional<F64, double, float>::type;
-    constexpr int J = 32 / I;
-    extern __shared__ __align__(128) unsigned char smem[];
+// One work item decoded (identical in every thread of the CTA).
+struct Item {
+    int a0, a1, b0, b1;
+    double Sx, Sy, dzmax;
+    bool self;
+    int kmin, kmax;
+};
 
+// Decode item -> column pair, image, pruning (Sec. 2.2) and z reach.
+// Returns false if the item has no work.
+__device__ __forceinline__ bool decode_item(const PairParams &P, int item, Item &it)
+{
+    const int a = item / P.nstencil, s = item - a * P.nstencil;
+    const int2 o = P.stencil[s];
+    const int ax = a / P.g.ncy, ay = a - ax * P.g.ncy;
+    int bx = ax + o.x, by = ay + o.y;
+    it.Sx = 0.0;
+    it.Sy = 0.0;
+    if (P.g.periodic) {
+        const int qx = floor_div(bx, P.g.ncx), qy = floor_div(by, P.g.ncy);
+        bx -= qx * P.g.ncx;
+        by -= qy * P.g.ncy;
+        it.Sx = qx * P.g.box[0];
+        it.Sy = qy * P.g.box[1];
+    } else if (bx < 0 || bx >= P.g.ncx || by < 0 || by >= P.g.ncy) {
+        return false;
+    }
+    const int b = bx * P.g.ncy + by;
+    const long long nz = P.g.nz;
+    it.a0 = (int)P.A.cell_start[a * nz];
+    it.a1 = (int)P.A.cell_start[(a + 1) * nz];
+    it.b0 = (int)P.B.cell_start[b * nz];
+    it.b1 = (int)P.B.cell_start[(b + 1) * nz];
+    if (it.a0 >= it.a1 || it.b0 >= it.b1)
+        return false;
+    // minimum possible (x, y) separation of the two columns' bounding boxes
+    const double4_32a ba = P.A.colbox[a], bb = P.B.colbox[b];
+    const double gx = fmax(0.0, fmax(__dsub_rn(__dadd_rn(bb.x, it.Sx), ba.y),
+                                     __dsub_rn(ba.x, __dadd_rn(bb.y, it.Sx))));
+    const double gy = fmax(0.0, fmax(__dsub_rn(__dadd_rn(bb.z, it.Sy), ba.w),
+                                     __dsub_rn(ba.z, __dadd_rn(bb.w, it.Sy))));
+    const double g2 = __dadd_rn(__dmul_rn(gx, gx), __dmul_rn(gy, gy));
+    if (!(P.flags & CF_FLAG_NO_PRUNE) && g2 >= P.prune_r2)
+        return false;
+    // z reach: dz_max,all of Sec. 2.2 (xi); pimax (rp-pi)
+    double dzmax = P.rz;
+    if (P.kind == 0)
+        dzmax = sqrt(fmax(0.0, __dsub_rn(P.rxy2, __dmul_rn(g2, 1.0 - 1e-12))));
+    it.dzmax = __dmul_rn(dzmax, 1.0 + 1e-9);
+    it.self = P.autocorr && o.x == 0 && o.y == 0;
+    it.kmin = P.g.periodic ? (it.self ? 0 : -1) : 0;
+    it.kmax = P.g.periodic ? 1 : 0;
+    return true;
+}
+
+// Stage the float32 x, y, z tiles (three 1-D bulk copies, one mbarrier):
+// thread 0 issues the copies, every thread pads and waits (bounded).  The
+// source slices start at a multiple of 4 floats and hold a multiple of 4 (the
+// gridded columns are padded), as the bulk copy requires.  False in every
+// thread if the wait gave up.
+__device__ __forceinline__ bool stage_tiles32(unsigned char *smem, const Gridded &B, int t0,
+                                              int count, uint64_t *bar, unsigned &phase,
+                                              unsigned *err)
+{
+    __syncthreads();  // previous tile fully consumed
+    const unsigned bytes = (unsigned)count * 4u;
+    if (threadIdx.x == 0) {
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(bar, 3u * bytes);
+        bulk_g2s(smem + XI32_TX_OFF, B.xs + t0, bytes, bar);
+        bulk_g2s(smem + XI32_TX_OFF + XI32_TSTRIDE, B.ys + t0, bytes, bar);
+        bulk_g2s(smem + XI32_TX_OFF + 2 * XI32_TSTRIDE, B.zs + t0, bytes, bar);
+    }
+    float *t = reinterpret_cast<float *>(smem + XI32_TX_OFF);
+    for (int s = threadIdx.x; s < 3 * 64; s += THREADS)  // sentinels: never counted
+        t[(s >> 6) * (XI32_TSTRIDE / 4) + count + (s & 63)] = __int_as_float(0x7fc00000);
+    const bool ok = mbar_wait(bar, phase, WAIT_LIMIT);
+    phase ^= 1u;
+    if (__syncthreads_or(!ok)) {
+        if (threadIdx.x == 0)
+            atomicOr(err, ERR_TIMEOUT);
+        return false;
+    }
+    return true;
+}
+
+// Issue the bulk copy of one tile (thread 0), pad, wait (all threads, bounded).
+// Returns false (in every thread) if the wait gave up.
+template <class T>
+__device__ __forceinline__ bool stage_tile(T *tile, const T *src, int count, int pad_elems,
+                                           uint64_t *bar, unsigned &phase, unsigned *err)
+{
+    __syncthreads();  // previous tile fully consumed
+    if (threadIdx.x == 0) {
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(bar, (unsigned)(count * sizeof(T)));
+        bulk_g2s(tile, src, (unsigned)(count * sizeof(T)), bar);
+    }
+    for (int s = threadIdx.x; s < pad_elems; s += THREADS) {
+        T nanv;
+        const float q = __int_as_float(0x7fc00000);
+        nanv.x = nanv.y = nanv.z = nanv.w = q;
+        tile[count + s] = nanv;  // sentinels after the copied range: never counted
+    }
+    const bool ok = mbar_wait(bar, phase, WAIT_LIMIT);
+    phase ^= 1u;
+    if (__syncthreads_or(!ok)) {
+        if (threadIdx.x == 0)
+            atomicOr(err, ERR_TIMEOUT);
+        return false;
+    }
+    return true;
+}
+
+// ============================================================ float32 kernel
+// Shared layout of k_xi32 (compile-time offsets, so table and tile addresses
+// fold into load immediates): [0,128) barrier + item; LUT (LUT_MAX bytes);
+// two tiles of TILE32 + 32 float4 ((x,x,y,y) and (z,z,w,w)); thresholds;
+// squared edges; per-warp histograms.
+constexpr int LUT_OFF = XI32_LUT_OFF;
+constexpr int TX_OFF = XI32_TX_OFF;
+constexpr int TSTRIDE = XI32_TSTRIDE;
+constexpr int THR_OFF = XI32_THR_OFF;
+constexpr int E2_OFF = XI32_E2_OFF;
+constexpr int HIST_OFF = XI32_HIST_OFF;
+
+// Per-window constants of the sweep.
+struct Sweep32 {
+    int t0;                   // global index of tile element 0
+    int nb;                   // bins; row nb is the dummy row
+    uint32_t u0, lut_last;
+    int shift;
+    int nthr;
+    const double4_32a *pa, *pb;
+    double Sx, Sy, Sz;
+};
+
+__device__ __forceinline__ uint32_t lut_byte(const unsigned char *smem, const Sweep32 &S, float d2)
+{
+    const uint32_t u = __float_as_uint(d2) - S.u0;  // below-range values wrap to huge
+    return smem[LUT_OFF + min(u >> S.shift, S.lut_last)];
+}
+
+// Flagged table cell (entry bit 7): compare with the thresholds; inside a band
+// re-evaluate in binary64.  Adds the pair to its true bin (the main path has
+// already put it in the dummy row).  Returns 1 if re-evaluated.
+__device__ __forceinline__ int resolve_pair(const unsigned char *smem, const Sweep32 &S,
+                                            char *hl, float d2, int i, int jg)
+{
+    const float *T = reinterpret_cast<const float *>(smem + THR_OFF);
+    const int c = count_le(T, S.nthr, d2);
+    int row;
+    int re = 0;
+    if (!(c & 1)) {
+        row = (c >= 2 && c <= 2 * S.nb) ? (c - 2) >> 1 : -1;
+    } else {
+        row = recheck64(reinterpret_cast<const double *>(smem + E2_OFF), S.nb, S.pa, S.pb, i, jg,
+                        S.Sx, S.Sy, S.Sz);
+        re = 1;
+    }
+    if (row >= 0)
+        atomicAdd(reinterpret_cast<unsigned *>(hl + row * 128), 1u);
+    return re;
+}
+
+// Sweep one window [jlo, jhi) of the staged tile.  Lane (ii, jj) holds one
+// primary i (broadcast to both halves of packed registers) and evaluates it
+// against two consecutive secondaries j, j+1 (one 8-byte load per axis); a
+// step covers 8 primaries x 8 secondaries, an iteration two steps, with one
+// warp-uniform check for flagged table cells.
+template <bool TRI, bool EVALS, bool VERIFY>
+__device__ __forceinline__ void sweep32(unsigned char *smem, const Sweep32 &S, char *hl, int jlo,
+                                        int jhi, int jj, u64 XH, u64 YH, u64 ZH, int i, bool vi,
+                                        u64 &n_eval, u64 &n_rck, u64 &n_viol)
+{
+    const float qnan = __int_as_float(0x7fc00000);
+    const int jstart = jlo & ~1;  // 8-byte aligned pairs; extra j's are never counted
+    const int nit = (jhi - jstart + 15) >> 4;
+    const unsigned char *p = smem + TX_OFF + (jstart + 2 * jj) * 4;
+    int jA = jstart + 2 * jj;
+    for (int it = 0; it < nit; ++it, p += 64, jA += 16) {
+        const u64 xA = *reinterpret_cast<const u64 *>(p);
+        const u64 yA = *reinterpret_cast<const u64 *>(p + TSTRIDE);
+        const u64 zA = *reinterpret_cast<const u64 *>(p + 2 * TSTRIDE);
+        const u64 xB = *reinterpret_cast<const u64 *>(p + 32);
+        const u64 yB = *reinterpret_cast<const u64 *>(p + 32 + TSTRIDE);
+        const u64 zB = *reinterpret_cast<const u64 *>(p + 32 + 2 * TSTRIDE);
+        u64 dx = fsub2(xA, XH), dy = fsub2(yA, YH), dz = fsub2(zA, ZH);
+        const u64 dA = ffma2(dz, dz, ffma2(dy, dy, fmul2(dx, dx)));
+        dx = fsub2(xB, XH);
+        dy = fsub2(yB, YH);
+        dz = fsub2(zB, ZH);
+        const u64 dB = ffma2(dz, dz, ffma2(dy, dy, fmul2(dx, dx)));
+        float a0, a1, b0, b1;
+        unpack2(dA, a0, a1);
+        unpack2(dB, b0, b1);
+        const int gA = S.t0 + jA, gB = gA + 8;  // global indices of (a0, b0); a1, b1 are +1
+        bool la0 = true, la1 = true, lb0 = true, lb1 = true;
+        if (TRI) {
+            la0 = gA > i;
+            la1 = gA + 1 > i;
+            lb0 = gB > i;
+            lb1 = gB + 1 > i;
+            a0 = la0 ? a0 : qnan;
+            a1 = la1 ? a1 : qnan;
+            b0 = lb0 ? b0 : qnan;
+            b1 = lb1 ? b1 : qnan;
+        }
+        if (EVALS) {
+            const int jB = jA + 8;
+            n_eval += (u64)((vi && jA >= jlo && jA < jhi && la0) +
+                            (vi && jA + 1 >= jlo && jA + 1 < jhi && la1) +
+                            (vi && jB >= jlo && jB < jhi && lb0) +
+                            (vi && jB + 1 >= jlo && jB + 1 < jhi && lb1));
+        }
+        const uint32_t ea0 = lut_byte(smem, S, a0), ea1 = lut_byte(smem, S, a1);
+        const uint32_t eb0 = lut_byte(smem, S, b0), eb1 = lut_byte(smem, S, b1);
+        const uint32_t nbu = (uint32_t)S.nb;
+        atomicAdd(reinterpret_cast<unsigned *>(hl + min(ea0, nbu) * 128), 1u);
+        atomicAdd(reinterpret_cast<unsigned *>(hl + min(ea1, nbu) * 128), 1u);
+        atomicAdd(reinterpret_cast<unsigned *>(hl + min(eb0, nbu) * 128), 1u);
+        atomicAdd(reinterpret_cast<unsigned *>(hl + min(eb1, nbu) * 128), 1u);
+        if (__any_sync(FULL, (ea0 | ea1 | eb0 | eb1) & LUT_FLAG)) {
+            if (ea0 & LUT_FLAG)
+                n_rck += resolve_pair(smem, S, hl, a0, i, gA);
+            if (ea1 & LUT_FLAG)
+                n_rck += resolve_pair(smem, S, hl, a1, i, gA + 1);
+            if (eb0 & LUT_FLAG)
+                n_rck += resolve_pair(smem, S, hl, b0, i, gB);
+            if (eb1 & LUT_FLAG)
+                n_rck += resolve_pair(smem, S, hl, b1, i, gB + 1);
+        }
+        if (VERIFY) {
+            const float *T = reinterpret_cast<const float *>(smem + THR_OFF);
+            const double *E2 = reinterpret_cast<const double *>(smem + E2_OFF);
+            // pairs with real points on both sides (sentinels and padding give NaN)
+            const float dv[4] = {a0, a1, b0, b1};
+            const int gv[4] = {gA, gA + 1, gB, gB + 1};
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (vi && !isnan(dv[q]))
+                    n_viol += verify_pair(dv[q], T, S.nthr, S.nb, E2, S.pa, S.pb, i, gv[q], S.Sx,
+                                          S.Sy, S.Sz);
+        }
+    }
+}
+
+// Lane-parallel search for the first index in [start, n) whose key is >= v
+// (upper = false) or > v (upper = true), assuming it is at least start: one
+// probe round at stride 4 from start, then a short or general search.
+template <class Key, class V>
+__device__ __forceinline__ int warp_bound_from(Key key, int start, int n, V v, bool upper, int lane)
+{
+    const int p = start + 4 * lane;
+    bool q = false;
+    if (p < n) {
+        const V z = key(p);
+        q = upper ? (z <= v) : (z < v);
+    }
+    const int c = __popc(__ballot_sync(FULL, q));
+    if (c == 0)
+        return start;
+    const int lo = start + 4 * (c - 1) + 1;
+    const int hi = c < 32 ? min(n, start + 4 * c) : n;
+    return lo + warp_bound([&](int t) { return key(lo + t); }, hi - lo, v, upper, lane);
+}
+
+template <bool EVALS, bool VERIFY>
+__global__ void __launch_bounds__(THREADS, 3) k_xi32(const __grid_constant__ PairParams P)
+{
+    constexpr int I = 8;  // primaries per chunk: lanes (ii = lane & 7, jj = lane >> 3)
+    extern __shared__ __align__(128) unsigned char smem[];
     const int nb = P.nbins;
-    const SmemLayout L = smem_layout(P.tile_max, (int)sizeof(P4), F64 ? 0 : P.lut_n,
-                                     F64 ? 0 : P.nthr, nb, 0, 0, 0, WARPS * nb * 32);
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
     volatile int *s_item = reinterpret_cast<volatile int *>(smem + 8);
-    P4 *tile = reinterpret_cast<P4 *>(smem + L.tile);
-    uint16_t *lut = reinterpret_cast<uint16_t *>(smem + L.lut);
-    float *thr = reinterpret_cast<float *>(smem + L.thr);
-    double *E2 = reinterpret_cast<double *>(smem + L.e2);
-    uint32_t *hist = reinterpret_cast<uint32_t *>(smem + L.hist);
+    const float *tz = reinterpret_cast<const float *>(smem + TX_OFF + 2 * TSTRIDE);
+    float *thr = reinterpret_cast<float *>(smem + THR_OFF);
+    double *E2 = reinterpret_cast<double *>(smem + E2_OFF);
+    uint32_t *hist = reinterpret_cast<uint32_t *>(smem + HIST_OFF);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    if (!F64) {
-        for (int q = tid; q < P.lut_n; q += THREADS)
-            lut[q] = P.lut[q];
-        for (int q = tid; q < P.nthr; q += THREADS)
-            thr[q] = P.thr[q];
-    }
+    for (int q = tid; q < P.lut_n; q += THREADS)
+        smem[LUT_OFF + q] = P.lut[q];
+    for (int q = tid; q < P.nthr; q += THREADS)
+        thr[q] = P.thr[q];
     for (int q = tid; q <= nb; q += THREADS)
         E2[q] = P.E2[q];
-    for (int q = tid; q < WARPS * nb * 32; q += THREADS)
+    for (int q = tid; q < WARPS * (nb + 1) * 32; q += THREADS)
         hist[q] = 0u;
     if (tid == 0) {
         mbar_init(bar, 1);
@@ -200,14 +496,22 @@ __global__ void __launch_bounds__(THREADS) k_xi(const __grid_constant__ PairPara
     }
     __syncthreads();
 
-    uint32_t *hw = hist + warp * nb * 32;
-    uint32_t *hl = hw + lane;
-    const int ii = lane % I, jj = lane / I;
+    uint32_t *hw = hist + warp * (nb + 1) * 32;
+    char *hl = reinterpret_cast<char *>(hw + lane);
+    const int ii = lane & 7, jj = lane >> 3;
+    Sweep32 S;
+    S.nb = nb;
+    S.u0 = P.u0;
+    S.lut_last = (uint32_t)(P.lut_n - 1);
+    S.shift = P.lut_shift;
+    S.nthr = P.nthr;
+    S.pa = P.A.pos64;
+    S.pb = P.B.pos64;
     unsigned phase = 0;
-    unsigned long long n_eval = 0, n_rck = 0, n_viol = 0;
+    u64 n_eval = 0, n_rck = 0, n_viol = 0;
     unsigned pending = 0;
     bool aborted = false;
-    const double4_32a *pa64 = P.A.pos64, *pb64 = P.B.pos64;
+    const float qnan = __int_as_float(0x7fc00000);
 
     for (;;) {
         if (tid == 0)
@@ -217,153 +521,85 @@ __global__ void __launch_bounds__(THREADS) k_xi(const __grid_constant__ PairPara
         __syncthreads();
         if (item >= P.n_items)
             break;
-        const int a = item / P.nstencil, s = item - a * P.nstencil;
-        const int2 o = P.stencil[s];
-        const int ax = a / P.g.ncy, ay = a - ax * P.g.ncy;
-        int bx = ax + o.x, by = ay + o.y;
-        double Sx = 0.0, Sy = 0.0;
-        if (P.g.periodic) {
-            const int qx = floor_div(bx, P.g.ncx), qy = floor_div(by, P.g.ncy);
-            bx -= qx * P.g.ncx;
-            by -= qy * P.g.ncy;
-            Sx = qx * P.g.box[0];
-            Sy = qy * P.g.box[1];
-        } else if (bx < 0 || bx >= P.g.ncx || by < 0 || by >= P.g.ncy) {
+        Item it;
+        if (!decode_item(P, item, it))
             continue;
-        }
-        const int b = bx * P.g.ncy + by;
-        const long long nz = P.g.nz;
-        const int a0 = (int)P.A.cell_start[a * nz], a1 = (int)P.A.cell_start[(a + 1) * nz];
-        const int b0 = (int)P.B.cell_start[b * nz], b1 = (int)P.B.cell_start[(b + 1) * nz];
-        if (a0 >= a1 || b0 >= b1)
-            continue;
-        // Sec. 2.2: minimum possible (x, y) separation of the two columns' boxes.
-        const double4_32a ba = P.A.colbox[a], bb = P.B.colbox[b];
-        const double gx = fmax(0.0, fmax(__dsub_rn(__dadd_rn(bb.x, Sx), ba.y),
-                                         __dsub_rn(ba.x, __dadd_rn(bb.y, Sx))));
-        const double gy = fmax(0.0, fmax(__dsub_rn(__dadd_rn(bb.z, Sy), ba.w),
-                                         __dsub_rn(ba.z, __dadd_rn(bb.w, Sy))));
-        const double g2 = __dadd_rn(__dmul_rn(gx, gx), __dmul_rn(gy, gy));
-        if (!(P.flags & CF_FLAG_NO_PRUNE) && g2 >= P.prune_r2)
-            continue;
-        // z reach of this column pair: dz_max,all of Sec. 2.2 (xi), pimax (rp-pi).
-        double dzmax = P.rz;
-        if (P.kind == 0)
-            dzmax = sqrt(fmax(0.0, __dsub_rn(P.rxy2, __dmul_rn(g2, 1.0 - 1e-12))));
-        dzmax = __dmul_rn(dzmax, 1.0 + 1e-9);
-        V dzw;
-        if (F64)
-            dzw = (V)__dadd_rn(dzmax, 1e-9 * (P.rz + P.g.box[2] + 1.0));
-        else
-            dzw = (V)__fadd_ru(__double2float_ru(dzmax), P.zslack);
-        const bool self = P.autocorr && o.x == 0 && o.y == 0;
-        const int kmin = P.g.periodic ? (self ? 0 : -1) : 0;
-        const int kmax = P.g.periodic ? 1 : 0;
         if (tid == 0)
             atomicAdd(&P.diag[0], 1ull);
-        const float Sxf = __double2float_rn(Sx), Syf = __double2float_rn(Sy);
-        const int na = a1 - a0;
-        const int nchunks = (na + I - 1) / I;
+        const float dzw = __fadd_ru(__double2float_ru(it.dzmax), P.zslack);
+        const float Sxf = __double2float_rn(it.Sx), Syf = __double2float_rn(it.Sy);
+        S.Sx = it.Sx;
+        S.Sy = it.Sy;
+        const int nchunks = (it.a1 - it.a0 + I - 1) / I;
 
-        for (int t0 = b0; t0 < b1 && !aborted; t0 += P.tile_max) {
-            const int nt = min(P.tile_max, b1 - t0);
-            __syncthreads();  // previous tile fully consumed
-            if (tid == 0) {
-                fence_proxy_async_smem();
-                mbar_arrive_expect_tx(bar, (unsigned)(nt * sizeof(P4)));
-                const void *src = F64 ? (const void *)(P.B.pos64 + t0) : (const void *)(P.B.pos + t0);
-                bulk_g2s(tile, src, (unsigned)(nt * sizeof(P4)), bar);
-            }
-            if (tid < 32) {
-                P4 nanp;
-                nanp.x = nanp.y = nanp.z = nanp.w = (V)__int_as_float(0x7fc00000);
-                tile[nt + tid] = nanp;  // sentinels: never counted
-            }
-            const bool ok = mbar_wait(bar, phase, WAIT_LIMIT);
-            phase ^= 1u;
-            if (__syncthreads_or(!ok)) {
-                if (tid == 0)
-                    atomicOr(P.err, ERR_TIMEOUT);
+        for (int t0 = it.b0; t0 < it.b1; t0 += TILE32) {
+            const int nt = min(TILE32, it.b1 - t0);
+            if (!stage_tiles32(smem, P.B, t0, nt, bar, phase, P.err)) {
                 aborted = true;
                 break;
             }
-            const V zt_lo = tile[0].z, zt_hi = tile[nt - 1].z;
+            S.t0 = t0;
+            const float zt_lo = tz[0];
+            float zt_hi = tz[nt - 1];
+            if (isnan(zt_hi))  // padding at the column end: largest real z is earlier
+                zt_hi = INFINITY;
+            auto zkey = [&](int q) { return tz[q]; };
+            int lo_prev[3] = {0, 0, 0}, hi_prev[3] = {0, 0, 0};
 
             for (int c = warp; c < nchunks; c += WARPS) {
-                const int ib = a0 + c * I;
-                const int nvi = min(I, a1 - ib);
+                const int ib = it.a0 + c * I;
+                const int nvi = min(I, it.a1 - ib);
                 const int i = ib + ii;
-                const bool vi = ii < nvi;
-                P4 pi;
-                if (vi) {
-                    if (F64)
-                        pi = *reinterpret_cast<const P4 *>(&pa64[i]);
-                    else
-                        pi = *reinterpret_cast<const P4 *>(&P.A.pos[i]);
-                } else {
-                    pi.x = pi.y = pi.z = pi.w = (V)__int_as_float(0x7fc00000);
+                float xi = qnan, yi = qnan, zi = qnan;
+                if (ii < nvi) {
+                    xi = P.A.xs[i];
+                    yi = P.A.ys[i];
+                    zi = P.A.zs[i];
                 }
-                const V zlo = __shfl_sync(FULL, pi.z, 0);
-                const V zhi = __shfl_sync(FULL, pi.z, nvi - 1);
-                const float xh = F64 ? 0.f : __fsub_rn((float)pi.x, Sxf);
-                const float yh = F64 ? 0.f : __fsub_rn((float)pi.y, Syf);
-                double4_32a pi64 = make_double4_32a(0, 0, 0, 0);
-                if (F64)
-                    pi64 = make_double4_32a((double)pi.x, (double)pi.y, (double)pi.z, 0.0);
+                const bool vi = !isnan(xi);  // chunk tail and column padding are NaN
+                const float xh = __fsub_rn(xi, Sxf), yh = __fsub_rn(yi, Syf);
+                const u64 XH = pack2(xh, xh), YH = pack2(yh, yh);
+                const float zlo = __shfl_sync(FULL, zi, 0);
+                float zhi = zi;
+#pragma unroll
+                for (int o = 1; o < 8; o <<= 1) {  // largest real z of the chunk
+                    const float t = __shfl_xor_sync(FULL, zhi, o);
+                    zhi = (isnan(zhi) || t > zhi) ? t : zhi;
+                }
+                if (isnan(zlo))
+                    continue;
 
-                for (int k = kmin; k <= kmax; ++k) {
-                    const V kz = F64 ? (V)(k * P.g.box[2]) : (V)((float)k * P.boxf[2]);
-                    const V wlo = zlo - kz - dzw, whi = zhi - kz + dzw;
+#pragma unroll
+                for (int kk = 0; kk < 3; ++kk) {
+                    const int k = kk - 1;
+                    if (k < it.kmin || k > it.kmax)
+                        continue;
+                    const float kz = (float)k * P.boxf[2];
+                    const float wlo = zlo - kz - dzw, whi = zhi - kz + dzw;
                     if (whi < zt_lo || wlo > zt_hi)
                         continue;
-                    int jlo = warp_bound(tile, nt, wlo, false, lane);
-                    const int jhi = warp_bound(tile, nt, whi, true, lane);
-                    const bool tri = self && k == 0;
+                    int jlo = warp_bound_from(zkey, lo_prev[kk], nt, wlo, false, lane);
+                    const int jhi = warp_bound_from(zkey, max(hi_prev[kk], jlo), nt, whi, true, lane);
+                    lo_prev[kk] = jlo;
+                    hi_prev[kk] = jhi;
+                    const bool tri = it.self && k == 0;
                     if (tri)
                         jlo = max(jlo, ib + 1 - t0);
                     if (jlo >= jhi)
                         continue;
-                    pending += (unsigned)((jhi - jlo + J - 1) / J);
-                    const double Sz = k * P.g.box[2];
-                    const float zh = F64 ? 0.f : __fsub_rn((float)pi.z, (float)kz);
-
-                    for (int jb = jlo; jb < jhi; jb += J) {
-                        const int j = jb + jj;
-                        const P4 pj = tile[j];
-                        const bool live = !tri || (t0 + j > i);
-                        if (EVALS)
-                            n_eval += (vi && j < jhi && live) ? 1ull : 0ull;
-                        if (F64) {
-                            const double4_32a q = make_double4_32a((double)pj.x, (double)pj.y, (double)pj.z, 0.0);
-                            double r2 = canon_r2(pi64, q, Sx, Sy, Sz);
-                            if (!live)
-                                r2 = __longlong_as_double(0x7ff8000000000000ll);
-                            const int kb = bin_f64(r2, E2, nb);
-                            if (kb >= 0)
-                                hl[kb * 32] += 1u;
-                        } else {
-                            const float dx = __fsub_rn((float)pj.x, xh);
-                            const float dy = __fsub_rn((float)pj.y, yh);
-                            const float dz = __fsub_rn((float)pj.z, zh);
-                            float d2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
-                            if (!live)
-                                d2 = __int_as_float(0x7fc00000);
-                            const uint32_t u = __float_as_uint(d2) - P.u0;
-                            if (u < P.urange) {
-                                const uint32_t e = lut[u >> P.lut_shift];
-                                if (e < 0x4000u)
-                                    hl[e >> 2] += 1u;
-                                else
-                                    n_rck += bin_slow(e, d2, thr, P.nthr, nb, E2, hl, pa64, pb64,
-                                                      i, t0 + j, Sx, Sy, Sz);
-                            }
-                            if (VERIFY && vi && j < nt && live)
-                                n_viol += verify_pair(d2, thr, P.nthr, nb, E2, pa64, pb64, i,
-                                                      t0 + j, Sx, Sy, Sz);
-                        }
-                    }
+                    pending += (unsigned)(((jhi - jlo) >> 3) + 4) * 2u;
+                    const float zh = __fsub_rn(zi, kz);
+                    const u64 ZH = pack2(zh, zh);
+                    S.Sz = k == 0 ? 0.0 : (k > 0 ? P.g.box[2] : -P.g.box[2]);
+                    if (tri)
+                        sweep32<true, EVALS, VERIFY>(smem, S, hl, jlo, jhi, jj, XH, YH, ZH, i, vi,
+                                                     n_eval, n_rck, n_viol);
+                    else
+                        sweep32<false, EVALS, VERIFY>(smem, S, hl, jlo, jhi, jj, XH, YH, ZH, i,
+                                                      vi, n_eval, n_rck, n_viol);
                 }
                 if (pending > (1u << 30)) {  // keep every per-lane u32 count far from overflow
+                    __syncwarp();
                     warp_flush(hw, nb, P.hist, lane);
                     pending = 0;
                 }
@@ -375,10 +611,10 @@ __global__ void __launch_bounds__(THREADS) k_xi(const __grid_constant__ PairPara
 
     __syncthreads();
     for (int bn = tid; bn < nb; bn += THREADS) {
-        unsigned long long sum = 0;
+        u64 sum = 0;
         for (int w = 0; w < WARPS; ++w)
             for (int l = 0; l < 32; ++l)
-                sum += hist[(w * nb + bn) * 32 + l];
+                sum += hist[(w * (nb + 1) + bn) * 32 + l];
         if (sum)
             atomicAdd(&P.hist[bn], sum);
     }
@@ -395,10 +631,135 @@ __global__ void __launch_bounds__(THREADS) k_xi(const __grid_constant__ PairPara
     }
 }
 
-template <bool F64, int I, bool EVALS, bool VERIFY>
-cudaError_t launch_xi(const PairParams &P, PairLaunch &L, int sms, cudaStream_t st)
+// ============================================================ binary64 kernel
+template <int I, bool EVALS>
+__global__ void __launch_bounds__(THREADS) k_xi64(const __grid_constant__ PairParams P)
 {
-    auto kern = k_xi<F64, I, EVALS, VERIFY>;
+    constexpr int J = 32 / I;
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int nb = P.nbins;
+    const SmemLayout L = smem_layout(P.tile_max, 32, 0, 0, nb, 0, 0, 0, WARPS * (nb + 1) * 32);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
+    volatile int *s_item = reinterpret_cast<volatile int *>(smem + 8);
+    double4_32a *tile = reinterpret_cast<double4_32a *>(smem + L.tile);
+    double *E2 = reinterpret_cast<double *>(smem + L.e2);
+    uint32_t *hist = reinterpret_cast<uint32_t *>(smem + L.hist);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    for (int q = tid; q <= nb; q += THREADS)
+        E2[q] = P.E2[q];
+    for (int q = tid; q < WARPS * (nb + 1) * 32; q += THREADS)
+        hist[q] = 0u;
+    if (tid == 0) {
+        mbar_init(bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    uint32_t *hw = hist + warp * (nb + 1) * 32;
+    uint32_t *hl = hw + lane;
+    const int ii = lane % I, jj = lane / I;
+    unsigned phase = 0;
+    u64 n_eval = 0;
+    unsigned pending = 0;
+    bool aborted = false;
+    const double qnan = __longlong_as_double(0x7ff8000000000000ll);
+
+    for (;;) {
+        if (tid == 0)
+            *s_item = (int)atomicAdd(P.item_counter, 1u);
+        __syncthreads();
+        const int item = *s_item;
+        __syncthreads();
+        if (item >= P.n_items)
+            break;
+        Item it;
+        if (!decode_item(P, item, it))
+            continue;
+        if (tid == 0)
+            atomicAdd(&P.diag[0], 1ull);
+        const double dzw = __dadd_rn(it.dzmax, 1e-9 * (P.rz + P.g.box[2] + 1.0));
+        const int nchunks = (it.a1 - it.a0 + I - 1) / I;
+
+        for (int t0 = it.b0; t0 < it.b1; t0 += P.tile_max) {
+            const int nt = min(P.tile_max, it.b1 - t0);
+            if (!stage_tile(tile, P.B.pos64 + t0, nt, 32, bar, phase, P.err)) {
+                aborted = true;
+                break;
+            }
+            const double zt_lo = tile[0].z, zt_hi = tile[nt - 1].z;
+            auto zkey = [&](int p) { return tile[p].z; };
+            for (int c = warp; c < nchunks; c += WARPS) {
+                const int ib = it.a0 + c * I;
+                const int nvi = min(I, it.a1 - ib);
+                const int i = ib + ii;
+                const bool vi = ii < nvi;
+                double4_32a pi = make_double4_32a(qnan, qnan, qnan, qnan);
+                if (vi)
+                    pi = P.A.pos64[i];  // column padding entries are NaN
+                const double zlo = __shfl_sync(FULL, pi.z, 0);
+                double zhi = pi.z;
+#pragma unroll
+                for (int o = 1; o < I; o <<= 1) {  // largest real z of the chunk
+                    const double t = __shfl_xor_sync(FULL, zhi, o);
+                    zhi = (isnan(zhi) || t > zhi) ? t : zhi;
+                }
+                if (isnan(zlo))
+                    continue;
+                for (int k = it.kmin; k <= it.kmax; ++k) {
+                    const double kz = k * P.g.box[2];
+                    const double wlo = zlo - kz - dzw, whi = zhi - kz + dzw;
+                    if (whi < zt_lo || wlo > zt_hi)
+                        continue;
+                    int jlo = warp_bound(zkey, nt, wlo, false, lane);
+                    const int jhi = warp_bound(zkey, nt, whi, true, lane);
+                    const bool tri = it.self && k == 0;
+                    if (tri)
+                        jlo = max(jlo, ib + 1 - t0);
+                    if (jlo >= jhi)
+                        continue;
+                    pending += (unsigned)((jhi - jlo + J - 1) / J);
+                    for (int jb = jlo; jb < jhi; jb += J) {
+                        const int j = jb + jj;
+                        const double4_32a pj = tile[j];
+                        const bool live = !tri || (t0 + j > i);
+                        if (EVALS)
+                            n_eval += (vi && j < jhi && live) ? 1ull : 0ull;
+                        double r2 = canon_r2(pi, pj, it.Sx, it.Sy, kz);
+                        if (!live)
+                            r2 = qnan;
+                        const int kb = bin_f64(r2, E2, nb);
+                        if (kb >= 0)
+                            hl[kb * 32] += 1u;
+                    }
+                }
+                if (pending > (1u << 30)) {
+                    warp_flush(hw, nb, P.hist, lane);
+                    pending = 0;
+                }
+            }
+        }
+        if (aborted)
+            break;
+    }
+
+    __syncthreads();
+    for (int bn = tid; bn < nb; bn += THREADS) {
+        u64 sum = 0;
+        for (int w = 0; w < WARPS; ++w)
+            for (int l = 0; l < 32; ++l)
+                sum += hist[(w * (nb + 1) + bn) * 32 + l];
+        if (sum)
+            atomicAdd(&P.hist[bn], sum);
+    }
+    n_eval = warp_sum_u64(n_eval);
+    if (lane == 0 && n_eval)
+        atomicAdd(&P.diag[1], n_eval);
+}
+
+template <class K>
+cudaError_t launch_persistent(K kern, const PairParams &P, PairLaunch &L, int sms, cudaStream_t st)
+{
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L.smem);
     if (e)
         return e;
@@ -422,27 +783,14 @@ cudaError_t launch_pairs(const PairParams &P, PairLaunch &L, int sms, cudaStream
 {
     if (P.kind != 0)
         return cudaErrorNotSupported;
-    if (L.f64) {
-        if (L.evals)
-            return launch_xi<true, 8, true, false>(P, L, sms, st);
-        if (L.chunk == 32)
-            return launch_xi<true, 32, false, false>(P, L, sms, st);
-        return launch_xi<true, 8, false, false>(P, L, sms, st);
-    }
+    if (L.f64)
+        return L.evals ? launch_persistent(k_xi64<8, true>, P, L, sms, st)
+                       : launch_persistent(k_xi64<8, false>, P, L, sms, st);
     if (L.verify)
-        return launch_xi<false, 8, true, true>(P, L, sms, st);
-    if (L.evals) {
-        if (L.chunk == 16)
-            return launch_xi<false, 16, true, false>(P, L, sms, st);
-        if (L.chunk == 32)
-            return launch_xi<false, 32, true, false>(P, L, sms, st);
-        return launch_xi<false, 8, true, false>(P, L, sms, st);
-    }
-    if (L.chunk == 16)
-        return launch_xi<false, 16, false, false>(P, L, sms, st);
-    if (L.chunk == 32)
-        return launch_xi<false, 32, false, false>(P, L, sms, st);
-    return launch_xi<false, 8, false, false>(P, L, sms, st);
+        return launch_persistent(k_xi32<true, true>, P, L, sms, st);
+    if (L.evals)
+        return launch_persistent(k_xi32<true, false>, P, L, sms, st);
+    return launch_persistent(k_xi32<false, false>, P, L, sms, st);
 }
 
 }  // namespace cf

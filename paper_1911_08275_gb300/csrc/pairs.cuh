@@ -48,6 +48,9 @@ struct PairLaunch {
     int hist_words;  // shared histogram words
 };
 
+// Dynamic shared memory of the float32 DD(r) kernel for nbins bins.
+int xi32_smem_bytes(int nbins);
+
 // Hist words of one CTA for a given kind / bin count (xi: per-lane rows per warp;
 // rp-pi: one row per warp).
 int pair_hist_words(int kind, int nbins, int npibins);
