@@ -5,8 +5,10 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -125,8 +127,9 @@ double band_sq(double S, int ncomp, double M, double Ls, double R)
 //     [u0, u0 + (lut_n - 1) << shift); tab[lut_n - 1] is the entry that every
 //     out-of-range distance (below lo_0, at or above hi_n, NaN) uses.
 //     Entries: bin k if every value of the cell lies in [hi_k, lo_{k+1});
-//     nbins (the dummy row) if every value is surely not counted; LUT_FLAG if
-//     the cell contains a threshold or lies inside a band.
+//     nbins (the dummy row) if every value is surely not counted; otherwise
+//     (the cell contains a threshold or lies inside a band) LUT_FLAG | h with
+//     2h <= the number of thresholds below the cell.
 struct Tables {
     int nthr, lut_n, shift;
     uint32_t u0;
@@ -158,20 +161,22 @@ Tables build_tables(const double *E2, int ne, int ncomp, double M, double Ls, do
         ++s;
     const int n = std::max(1, (int)(((uint64_t)urange + (1ull << s) - 1) >> s));
     const uint8_t dummy = (uint8_t)nbins;
-    auto count_le = [&](float v) {
-        int c = 0;
-        while (c < nthr && T[c] <= v)
-            ++c;
-        return c;
-    };
+    // Cells are visited in increasing value, so the threshold counts at the cell
+    // ends only move forward: one sweep over cells and thresholds.
+    int clo = 0, chi = 0;
     for (int q = 0; q < n; ++q) {
         const uint32_t blo = u0 + ((uint32_t)q << s);
         const uint32_t bhi = u0 + (uint32_t)(((uint64_t)(q + 1) << s) - 1);
-        const int clo = count_le(bitsf(blo)), chi = count_le(bitsf(bhi));
+        const float vlo = bitsf(blo), vhi = bitsf(bhi);
+        while (clo < nthr && T[clo] <= vlo)
+            ++clo;
+        chi = std::max(chi, clo);
+        while (chi < nthr && T[chi] <= vhi)
+            ++chi;
         if (clo == chi && !(clo & 1))
             tab[q] = (clo >= 2 && clo <= 2 * nbins) ? (uint8_t)((clo - 2) / 2) : dummy;
         else
-            tab[q] = (uint8_t)cf::LUT_FLAG;
+            tab[q] = (uint8_t)(cf::LUT_FLAG | (uint32_t)(clo >> 1));
     }
     tab[n] = dummy;
     t.nthr = nthr;
@@ -179,6 +184,43 @@ Tables build_tables(const double *E2, int ne, int ncomp, double M, double Ls, do
     t.shift = s;
     t.u0 = u0;
     return t;
+}
+
+// The last tables built on this thread, reused when the inputs repeat (a
+// benchmark or an MCMC chain calls with the same bins and box every time).
+struct TableCache {
+    bool valid = false;
+    double key[cf::NB_MAX + 1 + 5];
+    int nkey = 0;
+    Tables t;
+    float T[2 * (cf::NB_MAX + 1)];
+    uint8_t tab[cf::LUT_MAX];
+};
+thread_local TableCache g_tables;
+
+Tables cached_tables(const double *E2, int ne, int ncomp, double M, double Ls, double R, float *T,
+                     uint8_t *tab)
+{
+    TableCache &c = g_tables;
+    const int nk = ne + 5;
+    bool hit = c.valid && c.nkey == nk;
+    const double extra[5] = {(double)ne, (double)ncomp, M, Ls, R};
+    for (int k = 0; hit && k < ne; ++k)
+        hit = c.key[k] == E2[k];
+    for (int k = 0; hit && k < 5; ++k)
+        hit = c.key[ne + k] == extra[k];
+    if (!hit) {
+        c.t = build_tables(E2, ne, ncomp, M, Ls, R, c.T, c.tab);
+        for (int k = 0; k < ne; ++k)
+            c.key[k] = E2[k];
+        for (int k = 0; k < 5; ++k)
+            c.key[ne + k] = extra[k];
+        c.nkey = nk;
+        c.valid = true;
+    }
+    std::memcpy(T, c.T, sizeof(float) * c.t.nthr);
+    std::memcpy(tab, c.tab, c.t.lut_n);
+    return c.t;
 }
 
 struct Bump {  // carve aligned sub-buffers out of one allocation
@@ -221,7 +263,7 @@ struct PinnedScratch {  // per-thread page-locked staging for results
 thread_local PinnedScratch g_pinned;
 
 struct Events {
-    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t ev[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     bool ok = false;
     ~Events()
     {
@@ -257,6 +299,30 @@ void set_pool_release_threshold(int dev)
     cudaGetLastError();
     done[dev] = true;
 }
+
+// Opt-in phase trace (environment CF_TRACE=1, diagnosis only): synchronise the
+// stream at each phase boundary and print the wall time of the phase to stderr.
+struct Trace {
+    bool on;
+    cudaStream_t st;
+    double t0;
+    explicit Trace(cudaStream_t s) : on(std::getenv("CF_TRACE") != nullptr), st(s), t0(now_us()) {}
+    static double now_us()
+    {
+        return std::chrono::duration<double, std::micro>(
+                   std::chrono::steady_clock::now().time_since_epoch())
+            .count();
+    }
+    void point(const char *what)
+    {
+        if (!on)
+            return;
+        cudaStreamSynchronize(st);
+        const double t = now_us();
+        std::fprintf(stderr, "cf_trace %-12s %9.1f us\n", what, t - t0);
+        t0 = t;
+    }
+};
 
 struct Request {
     int kind;  // 0 xi, 1 rp-pi
@@ -328,6 +394,18 @@ int validate(const Request &q)
     return CF_OK;
 }
 
+// Float32 fields of the geometry used by the gridding kernels.
+void finish_geom(cf::Geom &g)
+{
+    for (int a = 0; a < 3; ++a) {
+        g.inv_wf[a] = (float)g.inv_w[a];
+        long long bits = 0;
+        std::memcpy(&bits, &g.box[a], 8);
+        g.box_bits[a] = bits;
+        g.box_bits32[a] = (int)fbits(f32_up(g.box[a]));
+    }
+}
+
 // Grid geometry: columns of side >= Rxy / refine in x, y; z-cells for the sort.
 int plan_geom(const Request &q, const double lo[3], const double hi[3], long long ntot, cf::Geom &g)
 {
@@ -356,7 +434,12 @@ int plan_geom(const Request &q, const double lo[3], const double hi[3], long lon
         }
     }
     auto ncol = [&](double ext, int r) {
-        const double per = std::floor(ext / (R * (1.0 + 1e-9)));
+        // Cell indices are computed in float32 (relative error <= 4 u32 per index
+        // coordinate t in [0, n)): widen cells by delta >= 16 u32 n so two points
+        // closer than Rmax never land more than r columns apart.
+        const double nmax = std::max(1.0, std::floor(ext / R)) * r;
+        const double delta = 16.0 * U32 * nmax + 1e-9;
+        const double per = std::floor(ext / (R * (1.0 + delta)));
         long long n = (long long)std::max(1.0, std::min(per, 8192.0)) * r;
         return (int)std::max(1ll, n);
     };
@@ -381,6 +464,7 @@ int plan_geom(const Request &q, const double lo[3], const double hi[3], long lon
     g.inv_w[0] = g.ncx / ex;
     g.inv_w[1] = g.ncy / ey;
     g.inv_w[2] = g.nz / ez;
+    finish_geom(g);
     return CF_OK;
 }
 
@@ -392,6 +476,7 @@ int run(Request &q)
     const cf_config *c = q.cfg;
     cf_result *res = q.res;
     const cudaStream_t st = (cudaStream_t)c->stream;
+    Trace trace(st);
     const int nb = (int)q.edges.size() - 1;
     const int nslots = q.kind == 0 ? nb : nb * q.npibins;
     const bool f64 = c->mode == CF_MODE_FP64;
@@ -436,9 +521,12 @@ int run(Request &q)
     double *d_E2 = nullptr;
     size_t total = 0;
     struct HostOut {
-        unsigned long long hist[cf::NBINS2D_MAX];
-        unsigned long long diag[4];
+        unsigned long long hist[cf::NBINS2D_MAX + 5];  // hist | diag(4) | err, counter
+        unsigned long long *diag;
         unsigned err;
+        float thr[2 * (cf::NB_MAX + 1)];  // page-locked staging of the tables
+        double e2[cf::NB_MAX + 1];
+        uint8_t lut[cf::LUT_MAX];
     } *ho = nullptr;
 
     CF_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
@@ -447,6 +535,7 @@ int run(Request &q)
     if (!g_events.init())
         return fail(CF_ECUDA, "cudaEventCreate failed");
     CF_CUDA(cudaEventRecord(g_events.ev[0], st), "cudaEventRecord");
+    trace.t0 = Trace::now_us();
 
     for (int t = 0; t < ncat; ++t) {
         nmax = std::max<long long>(nmax, cats[t]->n);
@@ -474,10 +563,11 @@ int run(Request &q)
             }
         }
         bbox_keys = bump.take<unsigned long long>(6);
-        d_err = bump.take<unsigned>(1);
-        d_ctr = bump.take<unsigned>(1);
-        d_hist = bump.take<unsigned long long>(nslots);
-        d_diag = bump.take<unsigned long long>(4);
+        // one block, one memset, one copy back: [hist | diag(4) | err, counter]
+        d_hist = bump.take<unsigned long long>(nslots + 5);
+        d_diag = d_hist + nslots;
+        d_err = reinterpret_cast<unsigned *>(d_hist + nslots + 4);
+        d_ctr = d_err + 1;
         d_thr = bump.take<float>(2 * (nb + 1));
         d_lut = bump.take<uint8_t>(cf::LUT_MAX);
         d_E2 = bump.take<double>(nb + 1);
@@ -496,10 +586,7 @@ int run(Request &q)
         if (dw[t])
             CF_CUDA(cudaMemcpyAsync((void *)dw[t], cats[t]->w, n * 8, cudaMemcpyHostToDevice, st), "H2D w");
     }
-    CF_CUDA(cudaMemsetAsync(d_err, 0, sizeof(unsigned), st), "memset");
-    CF_CUDA(cudaMemsetAsync(d_ctr, 0, sizeof(unsigned), st), "memset");
-    CF_CUDA(cudaMemsetAsync(d_hist, 0, sizeof(unsigned long long) * nslots, st), "memset");
-    CF_CUDA(cudaMemsetAsync(d_diag, 0, sizeof(unsigned long long) * 4, st), "memset");
+    CF_CUDA(cudaMemsetAsync(d_hist, 0, sizeof(unsigned long long) * (nslots + 5), st), "memset");
 
     ho = (HostOut *)g_pinned.get(sizeof(HostOut));
     if (!ho) {
@@ -528,6 +615,7 @@ int run(Request &q)
                 hi[a] = cf::decode_dkey(ho->hist[3 + a]);
             }
     }
+    trace.point("setup");
     plan_geom(q, lo, hi, ntot, g);
 
     {  // grid workspace
@@ -547,7 +635,7 @@ int run(Request &q)
             tmp.cell_of = bump.take<uint32_t>(nmax);
             tmp.slot = bump.take<uint32_t>(nmax);
             tmp.tmp_idx = bump.take<int>(nmax + 3ll * g.ncols);
-            tmp.tmp_z = bump.take<double>(nmax + 3ll * g.ncols);
+            tmp.tmp_key = bump.take<unsigned long long>(nmax + 3ll * g.ncols);
             tmp.counts = bump.take<uint32_t>(g.ncells);
             tmp.pad = bump.take<uint32_t>(g.ncols);
             tmp.bsum = bump.take<uint32_t>(g.ncells / 4096 + 2);
@@ -569,6 +657,7 @@ int run(Request &q)
         }
         if (q.autocorr)
             G[1] = G[0];
+        trace.point("gridding");
 
         // ---- pair kernel parameters
         std::memset(&P, 0, sizeof(P));
@@ -598,15 +687,18 @@ int run(Request &q)
             P.boxf[a] = (float)g.box[a];
         P.nbins = nb;
         if (!f64) {
-            const Tables tb = build_tables(E2.data(), nb + 1, 3, M, Ls, R, T, tab);
+            const Tables tb = cached_tables(E2.data(), nb + 1, 3, M, Ls, R, T, tab);
             P.nthr = tb.nthr;
             P.lut_n = tb.lut_n;
             P.lut_shift = tb.shift;
             P.u0 = tb.u0;
-            CF_CUDA(cudaMemcpyAsync(d_thr, T, 4 * P.nthr, cudaMemcpyHostToDevice, st), "H2D thresholds");
-            CF_CUDA(cudaMemcpyAsync(d_lut, tab, P.lut_n, cudaMemcpyHostToDevice, st), "H2D lut");
+            std::memcpy(ho->thr, T, 4 * P.nthr);
+            std::memcpy(ho->lut, tab, P.lut_n);
+            CF_CUDA(cudaMemcpyAsync(d_thr, ho->thr, 4 * P.nthr, cudaMemcpyHostToDevice, st), "H2D thresholds");
+            CF_CUDA(cudaMemcpyAsync(d_lut, ho->lut, P.lut_n, cudaMemcpyHostToDevice, st), "H2D lut");
         }
-        CF_CUDA(cudaMemcpyAsync(d_E2, E2.data(), 8 * E2.size(), cudaMemcpyHostToDevice, st), "H2D E2");
+        std::memcpy(ho->e2, E2.data(), 8 * E2.size());
+        CF_CUDA(cudaMemcpyAsync(d_E2, ho->e2, 8 * E2.size(), cudaMemcpyHostToDevice, st), "H2D E2");
         P.thr = d_thr;
         P.lut = d_lut;
         P.E2 = d_E2;
@@ -616,12 +708,18 @@ int run(Request &q)
         P.item_counter = d_ctr;
 
         PL.f64 = f64;
-        PL.chunk = 8;
+        PL.chunk = 16;
+        if (const char *ev = std::getenv("CF_PAIR_CHUNK")) {  // tuning experiments
+            const int c = std::atoi(ev);
+            if (c == 8 || c == 16 || c == 32)
+                PL.chunk = c;
+        }
         PL.evals = (c->flags & (CF_FLAG_COUNT_EVALS | CF_FLAG_VERIFY_BAND)) ? 1 : 0;
         PL.verify = (!f64 && (c->flags & CF_FLAG_VERIFY_BAND)) ? 1 : 0;
         PL.hist_words = cf::pair_hist_words(q.kind, nb, q.npibins);
         PL.smem = f64 ? cf::smem_layout(P.tile_max, 32, 0, 0, nb, 0, 0, 0, PL.hist_words).total
                       : cf::xi32_smem_bytes(nb);
+        trace.point("tables");
         CF_CUDA(cudaEventRecord(g_events.ev[1], st), "cudaEventRecord");
         if (P.n_items > 0) {
             const cudaError_t e = cf::launch_pairs(P, PL, sms, st);
@@ -631,12 +729,14 @@ int run(Request &q)
             }
         }
         CF_CUDA(cudaEventRecord(g_events.ev[2], st), "cudaEventRecord");
-        CF_CUDA(cudaMemcpyAsync(ho->hist, d_hist, sizeof(unsigned long long) * nslots, cudaMemcpyDeviceToHost, st), "D2H hist");
-        CF_CUDA(cudaMemcpyAsync(ho->diag, d_diag, sizeof(ho->diag), cudaMemcpyDeviceToHost, st), "D2H diag");
-        CF_CUDA(cudaMemcpyAsync(&ho->err, d_err, 4, cudaMemcpyDeviceToHost, st), "D2H err");
+        trace.point("pair kernel");
+        CF_CUDA(cudaMemcpyAsync(ho->hist, d_hist, sizeof(unsigned long long) * (nslots + 5),
+                                cudaMemcpyDeviceToHost, st),
+                "D2H results");
     }
     CF_CUDA(cudaEventRecord(g_events.ev[3], st), "cudaEventRecord");
     CF_CUDA(cudaEventSynchronize(g_events.ev[3]), "synchronize");
+    trace.point("readback");
     {
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, g_events.ev[1], g_events.ev[2]) == cudaSuccess)
@@ -645,6 +745,8 @@ int run(Request &q)
             res->total_ms = ms;
         cudaGetLastError();
     }
+    ho->diag = ho->hist + nslots;
+    std::memcpy(&ho->err, ho->hist + nslots + 4, sizeof(unsigned));
     if (ho->err & cf::ERR_COORD) {
         rc = fail(CF_EINVAL, c->periodic ? "coordinate outside [0, boxsize) or non-finite"
                                          : "non-finite coordinate");
@@ -907,8 +1009,10 @@ int noalloc_xi(int autocorr, const cf_catalog *d1, const cf_catalog *d2, const d
         g.extent[a] = g.periodic ? c->boxsize[a] : std::max(hi[a] - lo[a], 0.0);
         g.box[a] = g.periodic ? c->boxsize[a] : 0.0;
     }
-    auto ncol = [&](double ext, int r) {
-        const double per = std::floor(ext / (R * (1.0 + 1e-9)));
+    auto ncol = [&](double ext, int r) {  // same rule as plan_geom
+        const double nmax = std::max(1.0, std::floor(ext / R)) * r;
+        const double delta = 16.0 * U32 * nmax + 1e-9;
+        const double per = std::floor(ext / (R * (1.0 + delta)));
         return (int)std::max(1ll, (long long)std::max(1.0, std::min(per, 8192.0)) * r);
     };
     g.ncx = ncol(g.extent[0], rx);
@@ -929,6 +1033,7 @@ int noalloc_xi(int autocorr, const cf_catalog *d1, const cf_catalog *d2, const d
     g.inv_w[0] = g.ncx / std::max(g.extent[0], 1e-300);
     g.inv_w[1] = g.ncy / std::max(g.extent[1], 1e-300);
     g.inv_w[2] = g.nz / std::max(g.extent[2], 1e-300);
+    finish_geom(g);
 
     cf::Gridded G[2];
     cf::GridTemps tmp;
@@ -945,7 +1050,7 @@ int noalloc_xi(int autocorr, const cf_catalog *d1, const cf_catalog *d2, const d
     tmp.cell_of = bump.take<uint32_t>(nmax);
     tmp.slot = bump.take<uint32_t>(nmax);
     tmp.tmp_idx = bump.take<int>(nmax + 3ll * g.ncols);
-    tmp.tmp_z = bump.take<double>(nmax + 3ll * g.ncols);
+    tmp.tmp_key = bump.take<unsigned long long>(nmax + 3ll * g.ncols);
     tmp.counts = bump.take<uint32_t>(g.ncells);
     tmp.pad = bump.take<uint32_t>(g.ncols);
     tmp.bsum = bump.take<uint32_t>(g.ncells / 4096 + 2);
@@ -995,7 +1100,7 @@ int noalloc_xi(int autocorr, const cf_catalog *d1, const cf_catalog *d2, const d
     float T[2 * (cf::NB_MAX + 1)];
     uint8_t tab[cf::LUT_MAX];
     if (!f64) {
-        const Tables tb = build_tables(E2, nb + 1, 3, M, Ls, R, T, tab);
+        const Tables tb = cached_tables(E2, nb + 1, 3, M, Ls, R, T, tab);
         P.nthr = tb.nthr;
         P.lut_n = tb.lut_n;
         P.lut_shift = tb.shift;
@@ -1016,7 +1121,7 @@ int noalloc_xi(int autocorr, const cf_catalog *d1, const cf_catalog *d2, const d
     cf::PairLaunch PL;
     std::memset(&PL, 0, sizeof(PL));
     PL.f64 = f64;
-    PL.chunk = 8;
+    PL.chunk = 16;
     PL.evals = (P.flags & CF_FLAG_COUNT_EVALS) ? 1 : 0;
     PL.hist_words = cf::pair_hist_words(0, nb, 0);
     PL.smem = f64 ? cf::smem_layout(P.tile_max, 32, 0, 0, nb, 0, 0, 0, PL.hist_words).total

@@ -12,7 +12,7 @@ namespace cf {
 constexpr int NB_MAX = 64;          // radial (xi) or rp bins
 constexpr int NBINS2D_MAX = 4096;   // rp bins * pi bins
 constexpr int NPI_MAX = 4096;
-constexpr int LUT_MAX = 8192;       // entries (bytes) of the float32 bin lookup table
+constexpr int LUT_MAX = 16384;      // entries (bytes) of the float32 bin lookup table
 constexpr int TILE32 = 2048;        // secondary points per staged float32 tile
 constexpr int MAX_REACH = 4;        // column stencil half-width per axis
 constexpr int MAX_STENCIL = (2 * MAX_REACH + 1) * (2 * MAX_REACH + 1);
@@ -29,7 +29,8 @@ enum : unsigned {
 
 // Lookup-table entry (one byte): 0..nbins-1 -> the bin (the cell lies wholly
 // between hi_k and lo_{k+1}); nbins -> surely not counted (dummy row);
-// LUT_FLAG -> the cell touches a threshold (compare, maybe re-check).
+// LUT_FLAG | h -> the cell touches a threshold: the thresholds below index 2h
+// are all below the cell, so counting from 2h settles it (maybe re-check).
 constexpr uint32_t LUT_FLAG = 0x80u;
 
 // Shared layout of the float32 DD(r) kernel (compile-time offsets):
@@ -53,6 +54,9 @@ struct Geom {
     double extent[3];   // grid extent (= box in periodic mode)
     double inv_w[3];    // cells per unit length along each axis
     double box[3];      // periodic box (0 when open)
+    float inv_wf[3];    // fl32(inv_w): cell indices are computed in float32
+    long long box_bits[3];  // bit pattern of box (binary64 inputs: 0 <= x < box)
+    int box_bits32[3];      // bits of the smallest float >= box (float32 inputs)
 };
 
 // A gridded catalogue, in (column, z, original index) order; every column is

@@ -21,6 +21,8 @@
 #include <cuda_runtime.h>
 #include <float.h>
 
+#include <algorithm>
+
 #include "cf_internal.cuh"
 #include "grid.cuh"
 
@@ -28,11 +30,47 @@ namespace cf {
 
 namespace {
 
-__device__ __forceinline__ int cell_index_1d(double v, double origin, double inv_w, int n)
+// Order-preserving map of a binary64 bit pattern onto uint64 (and back).
+__device__ __forceinline__ unsigned long long order_key(long long b)
 {
-    double t = floor(__dmul_rn(__dsub_rn(v, origin), inv_w));
-    t = fmin(fmax(t, 0.0), (double)(n - 1));
-    return (int)t;
+    const unsigned long long u = (unsigned long long)b;
+    return (b < 0) ? ~u : (u | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double key_value(unsigned long long k)
+{
+    const unsigned long long b = (k >> 63) ? (k & 0x7fffffffffffffffull) : ~k;
+    return __longlong_as_double((long long)b);
+}
+
+// Cell index along one axis from a float32 frame coordinate (monotone in it).
+__device__ __forceinline__ int cell_index_f(float t, float inv_w, int n)
+{
+    const float c = floorf(__fmul_rn(t, inv_w));
+    return (int)fminf(fmaxf(c, 0.0f), (float)(n - 1));
+}
+
+// Validity and float32 frame coordinate of one input coordinate, without
+// binary64 arithmetic (the binary64 pipe of this GPU is narrow): range tests on
+// bit patterns, one conversion.
+__device__ __forceinline__ bool coord(double v, int a, const Geom &g, float &f)
+{
+    const long long b = __double_as_longlong(v);
+    if (g.periodic) {
+        f = __double2float_rn(v);  // frame origin is 0
+        return (b >= 0 && b < g.box_bits[a]) || b == (long long)0x8000000000000000ull;
+    }
+    f = __double2float_rn(__dsub_rn(v, g.origin[a]));
+    return (b & 0x7ff0000000000000ll) != 0x7ff0000000000000ll;
+}
+__device__ __forceinline__ bool coord(float v, int a, const Geom &g, float &f)
+{
+    const int b = __float_as_int(v);
+    if (g.periodic) {
+        f = v;
+        return (b >= 0 && b < g.box_bits32[a]) || b == (int)0x80000000u;
+    }
+    f = __double2float_rn(__dsub_rn((double)v, g.origin[a]));
+    return (b & 0x7f800000) != 0x7f800000;
 }
 
 template <class T>
@@ -41,25 +79,37 @@ __global__ void k_assign(const T *__restrict__ x, const T *__restrict__ y, const
                          uint32_t *__restrict__ slot, uint32_t *__restrict__ count,
                          unsigned *__restrict__ err)
 {
-    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
-         p += (long long)gridDim.x * blockDim.x) {
-        double X = (double)x[p], Y = (double)y[p], Z = (double)z[p];
-        bool ok = isfinite(X) && isfinite(Y) && isfinite(Z);
-        if (g.periodic)
-            ok = ok && X >= 0.0 && X < g.box[0] && Y >= 0.0 && Y < g.box[1] && Z >= 0.0 &&
-                 Z < g.box[2];
-        if (!ok) {
-            atomicOr(err, ERR_COORD);
-            X = g.origin[0];
-            Y = g.origin[1];
-            Z = g.origin[2];
+    const int lane = threadIdx.x & 31;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    // every lane of a warp runs the same number of iterations (warp-wide match)
+    const long long first = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31);
+    for (long long base = first; base < n; base += stride) {
+        const long long p = base + lane;
+        const bool live = p < n;
+        uint32_t cell = 0xffffffffu;
+        if (live) {
+            float fx, fy, fz;
+            const bool ok = coord(x[p], 0, g, fx) & coord(y[p], 1, g, fy) & coord(z[p], 2, g, fz);
+            if (!ok) {
+                atomicOr(err, ERR_COORD);
+                fx = fy = fz = 0.0f;
+            }
+            const int cx = cell_index_f(fx, g.inv_wf[0], g.ncx);
+            const int cy = cell_index_f(fy, g.inv_wf[1], g.ncy);
+            const int cz = cell_index_f(fz, g.inv_wf[2], g.nz);
+            cell = (uint32_t)(((long long)(cx * g.ncy + cy)) * g.nz + cz);
         }
-        const int cx = cell_index_1d(X, g.origin[0], g.inv_w[0], g.ncx);
-        const int cy = cell_index_1d(Y, g.origin[1], g.inv_w[1], g.ncy);
-        const int cz = cell_index_1d(Z, g.origin[2], g.inv_w[2], g.nz);
-        const uint32_t cell = (uint32_t)(((long long)(cx * g.ncy + cy)) * g.nz + cz);
-        cell_of[p] = cell;
-        slot[p] = atomicAdd(&count[cell], 1u);
+        // clustered inputs put runs of points into one cell: one atomic per group
+        const unsigned same = __match_any_sync(FULL, cell);
+        const int leader = __ffs(same) - 1;
+        uint32_t b0 = 0;
+        if (live && lane == leader)
+            b0 = atomicAdd(&count[cell], (uint32_t)__popc(same));
+        b0 = __shfl_sync(FULL, b0, leader);
+        if (live) {
+            cell_of[p] = cell;
+            slot[p] = b0 + (uint32_t)__popc(same & ((1u << lane) - 1u));
+        }
     }
 }
 
@@ -187,48 +237,73 @@ __global__ void k_colpad(const uint32_t *__restrict__ count, int ncols, int nz,
 template <class T>
 __global__ void k_scatter(const T *__restrict__ z, long long n, const uint32_t *__restrict__ cell_of,
                           const uint32_t *__restrict__ slot, const uint32_t *__restrict__ start,
-                          int *__restrict__ tmp_idx, double *__restrict__ tmp_z)
+                          int *__restrict__ tmp_idx, unsigned long long *__restrict__ tmp_key)
 {
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
          p += (long long)gridDim.x * blockDim.x) {
         const uint32_t q = start[cell_of[p]] + slot[p];
         tmp_idx[q] = (int)p;
-        tmp_z[q] = (double)z[p];
+        tmp_key[q] = order_key(__double_as_longlong((double)z[p]));
     }
 }
 
-// Rank each point inside its cell by (z, original index) among the cell's real
-// entries and write the sorted float32 / binary64 copies.  Work per cell is
-// quadratic in its occupancy; z-cells are sized for ~16 points on average.
+// One warp per cell: rank the cell's real entries by (z, original index) and
+// write the sorted float32 / binary64 copies.  Cells of up to 32 entries are
+// ranked in registers with shuffles; larger cells compare against all of the
+// cell's entries in L1-resident global memory (quadratic in the occupancy;
+// z-cells are sized for ~16 points on average).
 template <class T>
-__global__ void k_sort_gather(const T *__restrict__ x, const T *__restrict__ y,
-                              const T *__restrict__ z, const double *__restrict__ w, long long n,
-                              Geom g, const uint32_t *__restrict__ cell_of,
-                              const uint32_t *__restrict__ count, const uint32_t *__restrict__ start,
-                              const int *__restrict__ tmp_idx, const double *__restrict__ tmp_z,
-                              float *__restrict__ xs, float *__restrict__ ys,
-                              float *__restrict__ zs, double4_32a *__restrict__ pos64,
-                              int *__restrict__ perm)
+__global__ void k_sort_cells(const T *__restrict__ x, const T *__restrict__ y,
+                             const double *__restrict__ w, long long ncells, Geom g,
+                             const uint32_t *__restrict__ count, const uint32_t *__restrict__ start,
+                             const int *__restrict__ tmp_idx,
+                             const unsigned long long *__restrict__ tmp_key,
+                             float *__restrict__ xs, float *__restrict__ ys,
+                             float *__restrict__ zs, double4_32a *__restrict__ pos64,
+                             int *__restrict__ perm)
 {
-    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
-         p += (long long)gridDim.x * blockDim.x) {
-        const uint32_t c = cell_of[p];
-        const uint32_t s = start[c], e = s + count[c];
-        const double X = (double)x[p], Y = (double)y[p], Z = (double)z[p];
-        const int iq = (int)p;
-        uint32_t rank = 0;
-        for (uint32_t r = s; r < e; ++r) {
-            const double zr = tmp_z[r];
-            const int ir = tmp_idx[r];
-            rank += (zr < Z) || (zr == Z && ir < iq);
+    const int lane = threadIdx.x & 31;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long c = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < ncells;
+         c += nwarps) {
+        const uint32_t cnt = count[c];
+        if (cnt == 0)
+            continue;
+        const uint32_t s = start[c];
+        for (uint32_t e0 = 0; e0 < cnt; e0 += 32) {
+            const uint32_t e = e0 + lane;
+            const bool mine = e < cnt;
+            const unsigned long long kq = mine ? tmp_key[s + e] : ~0ull;
+            const int iq = mine ? tmp_idx[s + e] : 0x7fffffff;
+            uint32_t rank = 0;
+            if (cnt <= 32) {
+                for (uint32_t m = 0; m < cnt; ++m) {
+                    const unsigned long long km = __shfl_sync(FULL, kq, (int)m);
+                    const int im = __shfl_sync(FULL, iq, (int)m);
+                    rank += (km < kq) || (km == kq && im < iq);
+                }
+            } else {
+                for (uint32_t m = 0; m < cnt; ++m) {
+                    const unsigned long long km = tmp_key[s + m];
+                    const int im = tmp_idx[s + m];
+                    rank += (km < kq) || (km == kq && im < iq);
+                }
+            }
+            if (mine) {
+                const uint32_t d = s + rank;
+                const double X = (double)x[iq], Y = (double)y[iq], Z = key_value(kq);
+                const double W = w ? w[iq] : 0.0;
+                pos64[d] = make_double4_32a(X, Y, Z, W);
+                float fx, fy, fz;
+                coord(X, 0, g, fx);
+                coord(Y, 1, g, fy);
+                coord(Z, 2, g, fz);
+                xs[d] = fx;
+                ys[d] = fy;
+                zs[d] = fz;
+                perm[d] = iq;
+            }
         }
-        const uint32_t d = s + rank;
-        const double W = w ? w[p] : 0.0;
-        pos64[d] = make_double4_32a(X, Y, Z, W);
-        xs[d] = __double2float_rn(__dsub_rn(X, g.origin[0]));
-        ys[d] = __double2float_rn(__dsub_rn(Y, g.origin[1]));
-        zs[d] = __double2float_rn(__dsub_rn(Z, g.origin[2]));
-        perm[d] = iq;
     }
 }
 
@@ -251,32 +326,56 @@ __global__ void k_padfill(const uint32_t *__restrict__ start, const uint32_t *__
     }
 }
 
-// One warp per column: (xmin, xmax, ymin, ymax) of its points.
-__global__ void k_colbox(const double4_32a *__restrict__ pos64, const uint32_t *__restrict__ start,
-                         int ncols, int nz, double4_32a *__restrict__ colbox)
+// One block per column: (xmin, xmax, ymin, ymax) of its points, with min / max
+// taken on order-preserving integer keys (padding entries, NaN, are skipped).
+__global__ void __launch_bounds__(256) k_colbox(const double4_32a *__restrict__ pos64,
+                                                const uint32_t *__restrict__ start, int ncols,
+                                                int nz, double4_32a *__restrict__ colbox)
 {
-    const int lane = threadIdx.x & 31;
-    const int col = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (col >= ncols)
-        return;
-    const uint32_t s = start[(long long)col * nz], e = start[(long long)(col + 1) * nz];
-    double x0 = DBL_MAX, x1 = -DBL_MAX, y0 = DBL_MAX, y1 = -DBL_MAX;
-    for (uint32_t r = s + lane; r < e; r += 32) {
-        const double4_32a p = pos64[r];
-        x0 = fmin(x0, p.x);
-        x1 = fmax(x1, p.x);
-        y0 = fmin(y0, p.y);
-        y1 = fmax(y1, p.y);
-    }
+    __shared__ unsigned long long red[4][8];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int col = blockIdx.x; col < ncols; col += gridDim.x) {
+        const uint32_t s = start[(long long)col * nz], e = start[(long long)(col + 1) * nz];
+        unsigned long long x0 = ~0ull, x1 = 0ull, y0 = ~0ull, y1 = 0ull;
+        for (uint32_t r = s + threadIdx.x; r < e; r += blockDim.x) {
+            const long long bx = __double_as_longlong(pos64[r].x);
+            const long long by = __double_as_longlong(pos64[r].y);
+            if ((bx & 0x7ff0000000000000ll) == 0x7ff0000000000000ll)
+                continue;  // padding
+            const unsigned long long kx = order_key(bx), ky = order_key(by);
+            x0 = min(x0, kx);
+            x1 = max(x1, kx);
+            y0 = min(y0, ky);
+            y1 = max(y1, ky);
+        }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        x0 = fmin(x0, __shfl_xor_sync(FULL, x0, o));
-        x1 = fmax(x1, __shfl_xor_sync(FULL, x1, o));
-        y0 = fmin(y0, __shfl_xor_sync(FULL, y0, o));
-        y1 = fmax(y1, __shfl_xor_sync(FULL, y1, o));
+        for (int o = 16; o > 0; o >>= 1) {
+            x0 = min(x0, __shfl_xor_sync(FULL, x0, o));
+            x1 = max(x1, __shfl_xor_sync(FULL, x1, o));
+            y0 = min(y0, __shfl_xor_sync(FULL, y0, o));
+            y1 = max(y1, __shfl_xor_sync(FULL, y1, o));
+        }
+        if (lane == 0) {
+            red[0][wid] = x0;
+            red[1][wid] = x1;
+            red[2][wid] = y0;
+            red[3][wid] = y1;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int q = 1; q < (int)(blockDim.x >> 5); ++q) {
+                x0 = min(x0, red[0][q]);
+                x1 = max(x1, red[1][q]);
+                y0 = min(y0, red[2][q]);
+                y1 = max(y1, red[3][q]);
+            }
+            // empty column: keys keep their start values; mark the box empty
+            colbox[col] = x1 == 0ull ? make_double4_32a(DBL_MAX, -DBL_MAX, DBL_MAX, -DBL_MAX)
+                                     : make_double4_32a(key_value(x0), key_value(x1),
+                                                        key_value(y0), key_value(y1));
+        }
+        __syncthreads();
     }
-    if (lane == 0)
-        colbox[col] = make_double4_32a(x0, x1, y0, y1);
 }
 
 // Order-preserving map of a double onto uint64 (for atomic min / max).
@@ -357,14 +456,16 @@ cudaError_t build_grid_t(const void *x, const void *y, const void *z, const doub
     k_scan_add<<<(int)((nc + 255) / 256), 256, 0, st>>>(out.cell_start, nc, t.bsum);
     if (n > 0) {
         k_scatter<T><<<grid_blocks(n, TB, sms), TB, 0, st>>>((const T *)z, n, t.cell_of, t.slot,
-                                                             out.cell_start, t.tmp_idx, t.tmp_z);
-        k_sort_gather<T><<<grid_blocks(n, TB, sms), TB, 0, st>>>(
-            (const T *)x, (const T *)y, (const T *)z, w, n, g, t.cell_of, t.counts,
-            out.cell_start, t.tmp_idx, t.tmp_z, out.xs, out.ys, out.zs, out.pos64, out.perm);
+                                                             out.cell_start, t.tmp_idx, t.tmp_key);
+        const long long cwarps = std::min<long long>(nc, (long long)sms * 64);
+        k_sort_cells<T><<<(int)((cwarps * 32 + 255) / 256), 256, 0, st>>>(
+            (const T *)x, (const T *)y, w, nc, g, t.counts, out.cell_start, t.tmp_idx, t.tmp_key,
+            out.xs, out.ys, out.zs, out.pos64, out.perm);
     }
     k_padfill<<<(g.ncols + 255) / 256, 256, 0, st>>>(out.cell_start, t.pad, g.ncols, g.nz, out.xs,
                                                       out.ys, out.zs, out.pos64, out.perm);
-    k_colbox<<<cb, 256, 0, st>>>(out.pos64, out.cell_start, g.ncols, g.nz, out.colbox);
+    k_colbox<<<std::min(g.ncols, sms * 8), 256, 0, st>>>(out.pos64, out.cell_start, g.ncols, g.nz,
+                                                          out.colbox);
     return cudaGetLastError();
 }
 

@@ -12,7 +12,7 @@ struct GridTemps {
     uint32_t *cell_of;   // n
     uint32_t *slot;      // n
     int *tmp_idx;        // n + 3 * ncols (padded index space)
-    double *tmp_z;       // n + 3 * ncols
+    unsigned long long *tmp_key;  // n + 3 * ncols: order-preserving keys of z
     uint32_t *counts;    // ncells
     uint32_t *pad;       // ncols
     uint32_t *bsum;      // ceil(ncells / 4096)

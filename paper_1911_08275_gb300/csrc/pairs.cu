@@ -33,6 +33,8 @@
 // with the canonical formula and exact squared-edge compares.
 #include <cuda_runtime.h>
 
+#include <mutex>
+
 #include "cf_internal.cuh"
 #include "pairs.cuh"
 
@@ -142,20 +144,6 @@ __device__ __forceinline__ double canon_r2(const double4_32a &p, const double4_3
     const double dy = canon_comp(p.y, q.y, Sy);
     const double dz = canon_comp(p.z, q.z, Sz);
     return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
-}
-
-// Number of thresholds <= d2 (T non-decreasing, nthr entries).
-__device__ __forceinline__ int count_le(const float *T, int nthr, float d2)
-{
-    int lo = 0, hi = nthr;  // answer in [lo, hi]
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (T[mid] <= d2)
-            lo = mid + 1;
-        else
-            hi = mid;
-    }
-    return lo;
 }
 
 // Binary64 re-evaluation of one pair inside an error band: bin row or -1.
@@ -344,14 +332,22 @@ __device__ __forceinline__ uint32_t lut_byte(const unsigned char *smem, const Sw
     return smem[LUT_OFF + min(u >> S.shift, S.lut_last)];
 }
 
-// Flagged table cell (entry bit 7): compare with the thresholds; inside a band
-// re-evaluate in binary64.  Adds the pair to its true bin (the main path has
-// already put it in the dummy row).  Returns 1 if re-evaluated.
+__device__ __forceinline__ void red_shared1(uint32_t addr)
+{
+    asm volatile("red.shared.add.u32 [%0], 1;" ::"r"(addr));
+}
+
+// Flagged table cell (entry = LUT_FLAG | h): count the thresholds <= d2 from
+// index 2h (all earlier ones lie below the cell); inside a band re-evaluate in
+// binary64.  Adds the pair to its true bin (the main path has already put it in
+// the dummy row).  Returns 1 if re-evaluated.
 __device__ __forceinline__ int resolve_pair(const unsigned char *smem, const Sweep32 &S,
-                                            char *hl, float d2, int i, int jg)
+                                            uint32_t hl, uint32_t e, float d2, int i, int jg)
 {
     const float *T = reinterpret_cast<const float *>(smem + THR_OFF);
-    const int c = count_le(T, S.nthr, d2);
+    int c = (int)(e & 0x7fu) * 2;
+    while (c < S.nthr && T[c] <= d2)
+        ++c;
     int row;
     int re = 0;
     if (!(c & 1)) {
@@ -362,32 +358,33 @@ __device__ __forceinline__ int resolve_pair(const unsigned char *smem, const Swe
         re = 1;
     }
     if (row >= 0)
-        atomicAdd(reinterpret_cast<unsigned *>(hl + row * 128), 1u);
+        red_shared1(hl + (uint32_t)row * 128u);
     return re;
 }
 
 // Sweep one window [jlo, jhi) of the staged tile.  Lane (ii, jj) holds one
 // primary i (broadcast to both halves of packed registers) and evaluates it
 // against two consecutive secondaries j, j+1 (one 8-byte load per axis); a
-// step covers 8 primaries x 8 secondaries, an iteration two steps, with one
+// step covers I primaries x 64/I secondaries, an iteration two steps, with one
 // warp-uniform check for flagged table cells.
-template <bool TRI, bool EVALS, bool VERIFY>
-__device__ __forceinline__ void sweep32(unsigned char *smem, const Sweep32 &S, char *hl, int jlo,
+template <int I, bool TRI, bool EVALS, bool VERIFY>
+__device__ __forceinline__ void sweep32(unsigned char *smem, const Sweep32 &S, uint32_t hl, int jlo,
                                         int jhi, int jj, u64 XH, u64 YH, u64 ZH, int i, bool vi,
                                         u64 &n_eval, u64 &n_rck, u64 &n_viol)
 {
     const float qnan = __int_as_float(0x7fc00000);
     const int jstart = jlo & ~1;  // 8-byte aligned pairs; extra j's are never counted
-    const int nit = (jhi - jstart + 15) >> 4;
+    constexpr int JS = 64 / I;  // secondaries per step
+    const int nit = (jhi - jstart + 2 * JS - 1) / (2 * JS);
     const unsigned char *p = smem + TX_OFF + (jstart + 2 * jj) * 4;
     int jA = jstart + 2 * jj;
-    for (int it = 0; it < nit; ++it, p += 64, jA += 16) {
+    for (int it = 0; it < nit; ++it, p += 8 * JS, jA += 2 * JS) {
         const u64 xA = *reinterpret_cast<const u64 *>(p);
         const u64 yA = *reinterpret_cast<const u64 *>(p + TSTRIDE);
         const u64 zA = *reinterpret_cast<const u64 *>(p + 2 * TSTRIDE);
-        const u64 xB = *reinterpret_cast<const u64 *>(p + 32);
-        const u64 yB = *reinterpret_cast<const u64 *>(p + 32 + TSTRIDE);
-        const u64 zB = *reinterpret_cast<const u64 *>(p + 32 + 2 * TSTRIDE);
+        const u64 xB = *reinterpret_cast<const u64 *>(p + 4 * JS);
+        const u64 yB = *reinterpret_cast<const u64 *>(p + 4 * JS + TSTRIDE);
+        const u64 zB = *reinterpret_cast<const u64 *>(p + 4 * JS + 2 * TSTRIDE);
         u64 dx = fsub2(xA, XH), dy = fsub2(yA, YH), dz = fsub2(zA, ZH);
         const u64 dA = ffma2(dz, dz, ffma2(dy, dy, fmul2(dx, dx)));
         dx = fsub2(xB, XH);
@@ -397,7 +394,7 @@ __device__ __forceinline__ void sweep32(unsigned char *smem, const Sweep32 &S, c
         float a0, a1, b0, b1;
         unpack2(dA, a0, a1);
         unpack2(dB, b0, b1);
-        const int gA = S.t0 + jA, gB = gA + 8;  // global indices of (a0, b0); a1, b1 are +1
+        const int gA = S.t0 + jA, gB = gA + JS;  // global indices of (a0, b0); a1, b1 are +1
         bool la0 = true, la1 = true, lb0 = true, lb1 = true;
         if (TRI) {
             la0 = gA > i;
@@ -410,7 +407,7 @@ __device__ __forceinline__ void sweep32(unsigned char *smem, const Sweep32 &S, c
             b1 = lb1 ? b1 : qnan;
         }
         if (EVALS) {
-            const int jB = jA + 8;
+            const int jB = jA + JS;
             n_eval += (u64)((vi && jA >= jlo && jA < jhi && la0) +
                             (vi && jA + 1 >= jlo && jA + 1 < jhi && la1) +
                             (vi && jB >= jlo && jB < jhi && lb0) +
@@ -419,19 +416,19 @@ __device__ __forceinline__ void sweep32(unsigned char *smem, const Sweep32 &S, c
         const uint32_t ea0 = lut_byte(smem, S, a0), ea1 = lut_byte(smem, S, a1);
         const uint32_t eb0 = lut_byte(smem, S, b0), eb1 = lut_byte(smem, S, b1);
         const uint32_t nbu = (uint32_t)S.nb;
-        atomicAdd(reinterpret_cast<unsigned *>(hl + min(ea0, nbu) * 128), 1u);
-        atomicAdd(reinterpret_cast<unsigned *>(hl + min(ea1, nbu) * 128), 1u);
-        atomicAdd(reinterpret_cast<unsigned *>(hl + min(eb0, nbu) * 128), 1u);
-        atomicAdd(reinterpret_cast<unsigned *>(hl + min(eb1, nbu) * 128), 1u);
+        red_shared1(hl + min(ea0, nbu) * 128u);  // flagged entries -> dummy row here
+        red_shared1(hl + min(ea1, nbu) * 128u);
+        red_shared1(hl + min(eb0, nbu) * 128u);
+        red_shared1(hl + min(eb1, nbu) * 128u);
         if (__any_sync(FULL, (ea0 | ea1 | eb0 | eb1) & LUT_FLAG)) {
             if (ea0 & LUT_FLAG)
-                n_rck += resolve_pair(smem, S, hl, a0, i, gA);
+                n_rck += resolve_pair(smem, S, hl, ea0, a0, i, gA);
             if (ea1 & LUT_FLAG)
-                n_rck += resolve_pair(smem, S, hl, a1, i, gA + 1);
+                n_rck += resolve_pair(smem, S, hl, ea1, a1, i, gA + 1);
             if (eb0 & LUT_FLAG)
-                n_rck += resolve_pair(smem, S, hl, b0, i, gB);
+                n_rck += resolve_pair(smem, S, hl, eb0, b0, i, gB);
             if (eb1 & LUT_FLAG)
-                n_rck += resolve_pair(smem, S, hl, b1, i, gB + 1);
+                n_rck += resolve_pair(smem, S, hl, eb1, b1, i, gB + 1);
         }
         if (VERIFY) {
             const float *T = reinterpret_cast<const float *>(smem + THR_OFF);
@@ -468,10 +465,11 @@ __device__ __forceinline__ int warp_bound_from(Key key, int start, int n, V v, b
     return lo + warp_bound([&](int t) { return key(lo + t); }, hi - lo, v, upper, lane);
 }
 
-template <bool EVALS, bool VERIFY>
+template <int I, bool EVALS, bool VERIFY>
 __global__ void __launch_bounds__(THREADS, 3) k_xi32(const __grid_constant__ PairParams P)
 {
-    constexpr int I = 8;  // primaries per chunk: lanes (ii = lane & 7, jj = lane >> 3)
+    // I primaries per chunk (one per lane ii = lane % I); jj = lane / I picks the
+    // pair of secondaries.
     extern __shared__ __align__(128) unsigned char smem[];
     const int nb = P.nbins;
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
@@ -497,8 +495,8 @@ __global__ void __launch_bounds__(THREADS, 3) k_xi32(const __grid_constant__ Pai
     __syncthreads();
 
     uint32_t *hw = hist + warp * (nb + 1) * 32;
-    char *hl = reinterpret_cast<char *>(hw + lane);
-    const int ii = lane & 7, jj = lane >> 3;
+    const uint32_t hl = smem_u32(hw + lane);  // this lane's histogram column (shared address)
+    const int ii = lane % I, jj = lane / I;
     Sweep32 S;
     S.nb = nb;
     S.u0 = P.u0;
@@ -562,7 +560,7 @@ __global__ void __launch_bounds__(THREADS, 3) k_xi32(const __grid_constant__ Pai
                 const float zlo = __shfl_sync(FULL, zi, 0);
                 float zhi = zi;
 #pragma unroll
-                for (int o = 1; o < 8; o <<= 1) {  // largest real z of the chunk
+                for (int o = 1; o < I; o <<= 1) {  // largest real z of the chunk
                     const float t = __shfl_xor_sync(FULL, zhi, o);
                     zhi = (isnan(zhi) || t > zhi) ? t : zhi;
                 }
@@ -587,15 +585,15 @@ __global__ void __launch_bounds__(THREADS, 3) k_xi32(const __grid_constant__ Pai
                         jlo = max(jlo, ib + 1 - t0);
                     if (jlo >= jhi)
                         continue;
-                    pending += (unsigned)(((jhi - jlo) >> 3) + 4) * 2u;
+                    pending += (unsigned)((jhi - jlo) / (64 / I) + 4) * 2u;
                     const float zh = __fsub_rn(zi, kz);
                     const u64 ZH = pack2(zh, zh);
                     S.Sz = k == 0 ? 0.0 : (k > 0 ? P.g.box[2] : -P.g.box[2]);
                     if (tri)
-                        sweep32<true, EVALS, VERIFY>(smem, S, hl, jlo, jhi, jj, XH, YH, ZH, i, vi,
+                        sweep32<I, true, EVALS, VERIFY>(smem, S, hl, jlo, jhi, jj, XH, YH, ZH, i, vi,
                                                      n_eval, n_rck, n_viol);
                     else
-                        sweep32<false, EVALS, VERIFY>(smem, S, hl, jlo, jhi, jj, XH, YH, ZH, i,
+                        sweep32<I, false, EVALS, VERIFY>(smem, S, hl, jlo, jhi, jj, XH, YH, ZH, i,
                                                       vi, n_eval, n_rck, n_viol);
                 }
                 if (pending > (1u << 30)) {  // keep every per-lane u32 count far from overflow
@@ -757,14 +755,60 @@ __global__ void __launch_bounds__(THREADS) k_xi64(const __grid_constant__ PairPa
         atomicAdd(&P.diag[1], n_eval);
 }
 
+// Per (kernel, device): the dynamic shared-memory limit set so far (only ever
+// raised) and the occupancy per shared-memory size, queried once.
+struct OccCache {
+    const void *kern;
+    int dev, smem, occ;
+};
+struct AttrCache {
+    const void *kern;
+    int dev, limit;
+};
+OccCache g_occ[128];
+AttrCache g_attr[32];
+int g_nocc = 0, g_nattr = 0;
+std::mutex g_occ_mu;
+
+template <class K>
+cudaError_t occupancy(K kern, int smem, int &occ)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e)
+        return e;
+    std::lock_guard<std::mutex> lock(g_occ_mu);
+    AttrCache *a = nullptr;
+    for (int q = 0; q < g_nattr; ++q)
+        if (g_attr[q].kern == (const void *)kern && g_attr[q].dev == dev)
+            a = &g_attr[q];
+    if (!a || a->limit < smem) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e)
+            return e;
+        if (!a && g_nattr < 32)
+            a = &g_attr[g_nattr++];
+        if (a)
+            *a = AttrCache{(const void *)kern, dev, smem};
+    }
+    for (int q = 0; q < g_nocc; ++q)
+        if (g_occ[q].kern == (const void *)kern && g_occ[q].dev == dev && g_occ[q].smem == smem) {
+            occ = g_occ[q].occ;
+            return cudaSuccess;
+        }
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, THREADS, smem);
+    if (e)
+        return e;
+    if (g_nocc < 128)
+        g_occ[g_nocc++] = OccCache{(const void *)kern, dev, smem, occ};
+    return cudaSuccess;
+}
+
 template <class K>
 cudaError_t launch_persistent(K kern, const PairParams &P, PairLaunch &L, int sms, cudaStream_t st)
 {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L.smem);
-    if (e)
-        return e;
     int occ = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, THREADS, L.smem);
+    cudaError_t e = occupancy(kern, L.smem, occ);
     if (e)
         return e;
     if (occ < 1)
@@ -787,10 +831,18 @@ cudaError_t launch_pairs(const PairParams &P, PairLaunch &L, int sms, cudaStream
         return L.evals ? launch_persistent(k_xi64<8, true>, P, L, sms, st)
                        : launch_persistent(k_xi64<8, false>, P, L, sms, st);
     if (L.verify)
-        return launch_persistent(k_xi32<true, true>, P, L, sms, st);
-    if (L.evals)
-        return launch_persistent(k_xi32<true, false>, P, L, sms, st);
-    return launch_persistent(k_xi32<false, false>, P, L, sms, st);
+        return launch_persistent(k_xi32<8, true, true>, P, L, sms, st);
+    switch (L.chunk) {
+    case 16:
+        return L.evals ? launch_persistent(k_xi32<16, true, false>, P, L, sms, st)
+                       : launch_persistent(k_xi32<16, false, false>, P, L, sms, st);
+    case 32:
+        return L.evals ? launch_persistent(k_xi32<32, true, false>, P, L, sms, st)
+                       : launch_persistent(k_xi32<32, false, false>, P, L, sms, st);
+    default:
+        return L.evals ? launch_persistent(k_xi32<8, true, false>, P, L, sms, st)
+                       : launch_persistent(k_xi32<8, false, false>, P, L, sms, st);
+    }
 }
 
 }  // namespace cf
