@@ -492,8 +492,6 @@ int run(Request &q)
         std::memset(res->ravg, 0, sizeof(double) * nslots);
     res->n_cellpairs = res->n_evaluated = res->n_rechecked = res->n_band_violations = 0;
     res->kernel_ms = res->total_ms = 0.0;
-    if (q.kind != 0)
-        return fail(CF_EINVAL, "rp-pi counting is not available in this build");
     if (c->weighted || c->want_ravg)
         return fail(CF_EINVAL, "weights / ravg are not available in this build");
 
@@ -503,6 +501,7 @@ int run(Request &q)
     cf::PairParams P;
     cf::PairLaunch PL;
     std::vector<double> E2(nb + 1);
+    std::vector<double> Pe(q.kind == 1 ? q.npibins + 1 : 0);
     float T[2 * (cf::NB_MAX + 1)];
     uint8_t tab[cf::LUT_MAX];
     cf::Gridded G[2];
@@ -518,7 +517,7 @@ int run(Request &q)
     unsigned long long *d_hist = nullptr, *d_diag = nullptr;
     float *d_thr = nullptr;
     uint8_t *d_lut = nullptr;
-    double *d_E2 = nullptr;
+    double *d_E2 = nullptr, *d_P = nullptr;
     size_t total = 0;
     struct HostOut {
         unsigned long long hist[cf::NBINS2D_MAX + 5];  // hist | diag(4) | err, counter
@@ -526,6 +525,7 @@ int run(Request &q)
         unsigned err;
         float thr[2 * (cf::NB_MAX + 1)];  // page-locked staging of the tables
         double e2[cf::NB_MAX + 1];
+        double pe[cf::NPI_MAX + 1];
         uint8_t lut[cf::LUT_MAX];
     } *ho = nullptr;
 
@@ -544,6 +544,11 @@ int run(Request &q)
     }
     for (int k = 0; k <= nb; ++k)
         E2[k] = q.edges[k] * q.edges[k];
+    if (q.kind == 1) {  // pi edges P_m = (pimax * m) / npibins, P_npibins = pimax
+        for (int m = 0; m < q.npibins; ++m)
+            Pe[m] = (q.pimax * (double)m) / (double)q.npibins;
+        Pe[q.npibins] = q.pimax;
+    }
 
     // Pass 1: sizes of everything except the grid (known only after the bbox).
     for (int pass = 0; pass < 2; ++pass) {
@@ -571,6 +576,7 @@ int run(Request &q)
         d_thr = bump.take<float>(2 * (nb + 1));
         d_lut = bump.take<uint8_t>(cf::LUT_MAX);
         d_E2 = bump.take<double>(nb + 1);
+        d_P = bump.take<double>(Pe.size());
         if (pass == 0) {
             total = bump.off;
             CF_CUDA(cudaMallocAsync(&ws, total, st), "cudaMallocAsync (inputs)");
@@ -682,12 +688,27 @@ int run(Request &q)
         P.prune_r2 = Rp * Rp;
         P.rxy2 = Rp * Rp;
         P.rz = q.kind == 0 ? R : q.pimax;
-        P.zslack = (float)(8.0 * U32 * (M + Ls + R) + 1e-6 * R);
+        const double Rz = std::max(R, P.rz);
+        P.zslack = (float)(8.0 * U32 * (M + Ls + Rz) + 1e-6 * Rz);
         for (int a = 0; a < 3; ++a)
             P.boxf[a] = (float)g.box[a];
         P.nbins = nb;
+        if (q.kind == 1) {
+            P.npibins = q.npibins;
+            const double s = (double)q.npibins / q.pimax;
+            P.pscale = (float)s;
+            // t = |dz| * s: float32 error in t (dz error, the scale's and the fma's
+            // roundings, the binary64 edges' own rounding), doubled for safety.
+            const double tmax = q.npibins + 1.0;
+            const double eps_z = eps_axis(q.pimax * (1.0 + 1e-6), M, Ls) + 2.0 * U64 * (M + Ls + 2.0 * q.pimax);
+            const double beta = 2.0 * (eps_z * s * (1.0 + 1e-6) + (2.0 * tmax + 2.0) * U32 +
+                                       4.0 * tmax * U64) + 1e-30;
+            P.pband = 0.5 - beta > 0.0 ? f32_down(0.5 - beta) : -1.0f;  // -1: every pair re-checked
+            std::memcpy(ho->pe, Pe.data(), 8 * Pe.size());
+            CF_CUDA(cudaMemcpyAsync(d_P, ho->pe, 8 * Pe.size(), cudaMemcpyHostToDevice, st), "H2D pi edges");
+        }
         if (!f64) {
-            const Tables tb = cached_tables(E2.data(), nb + 1, 3, M, Ls, R, T, tab);
+            const Tables tb = cached_tables(E2.data(), nb + 1, q.kind == 0 ? 3 : 2, M, Ls, R, T, tab);
             P.nthr = tb.nthr;
             P.lut_n = tb.lut_n;
             P.lut_shift = tb.shift;
@@ -702,6 +723,7 @@ int run(Request &q)
         P.thr = d_thr;
         P.lut = d_lut;
         P.E2 = d_E2;
+        P.P = d_P;
         P.hist = d_hist;
         P.diag = d_diag;
         P.err = d_err;
@@ -716,9 +738,7 @@ int run(Request &q)
         }
         PL.evals = (c->flags & (CF_FLAG_COUNT_EVALS | CF_FLAG_VERIFY_BAND)) ? 1 : 0;
         PL.verify = (!f64 && (c->flags & CF_FLAG_VERIFY_BAND)) ? 1 : 0;
-        PL.hist_words = cf::pair_hist_words(q.kind, nb, q.npibins);
-        PL.smem = f64 ? cf::smem_layout(P.tile_max, 32, 0, 0, nb, 0, 0, 0, PL.hist_words).total
-                      : cf::xi32_smem_bytes(nb);
+        cf::plan_pairs(P, PL);
         trace.point("tables");
         CF_CUDA(cudaEventRecord(g_events.ev[1], st), "cudaEventRecord");
         if (P.n_items > 0) {
@@ -1123,9 +1143,7 @@ int noalloc_xi(int autocorr, const cf_catalog *d1, const cf_catalog *d2, const d
     PL.f64 = f64;
     PL.chunk = 16;
     PL.evals = (P.flags & CF_FLAG_COUNT_EVALS) ? 1 : 0;
-    PL.hist_words = cf::pair_hist_words(0, nb, 0);
-    PL.smem = f64 ? cf::smem_layout(P.tile_max, 32, 0, 0, nb, 0, 0, 0, PL.hist_words).total
-                  : cf::xi32_smem_bytes(nb);
+    cf::plan_pairs(P, PL);
     if (P.n_items > 0 && (e = cf::launch_pairs(P, PL, sms, st)))
         return cuda_fail(e, "pair kernel launch");
     if ((e = cudaMemcpyAsync(h.hist, d_hist, sizeof(unsigned long long) * nb, cudaMemcpyDeviceToHost, st)) ||

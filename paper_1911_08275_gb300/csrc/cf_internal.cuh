@@ -43,6 +43,12 @@ constexpr int XI32_THR_OFF = XI32_TX_OFF + 3 * XI32_TSTRIDE;
 constexpr int XI32_E2_OFF = XI32_THR_OFF + 2 * (NB_MAX + 1) * 4;
 constexpr int XI32_HIST_OFF = XI32_E2_OFF + (NB_MAX + 1) * 8;
 
+// The float32 DD(rp, pi) kernel uses the DD(r) layout up to the thresholds and
+// squared rp edges, then the pi edges (binary64) and, from a run-time offset,
+// its histograms: hcopies copies of (nbins + 1) rows of (npibins + 1) words
+// (row nbins and column npibins collect pairs that are not counted).
+constexpr int RPPI_P_OFF = XI32_HIST_OFF;
+
 // Grid geometry: columns in (x, y), z-cells inside each column (sort keys).
 struct Geom {
     int periodic;
@@ -93,15 +99,14 @@ struct PairParams {
     int nthr;           // 2 * nbins + 2 float32 thresholds
     int lut_n, lut_shift; // table entries (last one = out of range), cell width 2^shift
     uint32_t u0;          // float bit pattern of the table's first cell
-    int pi_nthr;        // 2 * npibins + 2 (rp-pi)
-    int pilut_n, pilut_shift;
-    uint32_t pu0, purange;
+    float pscale;       // rp-pi: fl32(npibins / pimax), pi edges at integer t = |dz| * pscale
+    float pband;        // rp-pi: |t - 1/2 - round(t - 1/2)| > pband means t is near an edge
+    int hcopies;        // rp-pi: shared histogram copies per CTA (warp w uses w % hcopies)
+    int hist_off;       // byte offset of the shared histograms (rp-pi kernels)
     const float *thr;        // nthr
     const uint8_t *lut;      // lut_n
     const double *E2;        // nbins + 1
-    const float *pithr;      // pi_nthr
-    const uint16_t *pilut;   // pilut_n
-    const double *P;         // npibins + 1
+    const double *P;         // npibins + 1 pi edges (rp-pi)
     // outputs
     unsigned long long *hist;  // nbins (xi) or nbins * npibins
     double *wsum, *rsum;

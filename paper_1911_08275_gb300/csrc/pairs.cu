@@ -40,16 +40,32 @@
 
 namespace cf {
 
-int xi32_smem_bytes(int nbins)
+void plan_pairs(PairParams &P, PairLaunch &L)
 {
-    return ((XI32_HIST_OFF + WARPS * (nbins + 1) * 32 * 4) + 127) / 128 * 128;
-}
-
-int pair_hist_words(int kind, int nbins, int npibins)
-{
-    if (kind == 0)
-        return WARPS * (nbins + 1) * 32;  // per-lane rows + one dummy row
-    return WARPS * nbins * npibins;
+    const int nb = P.nbins;
+    if (P.kind == 0) {
+        L.hist_words = WARPS * (nb + 1) * 32;  // per-lane rows + one dummy row per warp
+        L.smem = L.f64 ? smem64_layout(P.tile_max, nb, 0, L.hist_words).total
+                       : align_up(XI32_HIST_OFF + L.hist_words * 4, 128);
+        P.hcopies = WARPS;
+        P.hist_off = L.f64 ? smem64_layout(P.tile_max, nb, 0, L.hist_words).hist : XI32_HIST_OFF;
+        return;
+    }
+    // rp-pi: one histogram copy per warp while the CTA stays small enough for
+    // three CTAs per SM, else fewer copies shared by several warps.
+    const int copy = (nb + 1) * (P.npibins + 1);
+    const int base = L.f64 ? smem64_layout(P.tile_max, nb, P.npibins, 0).hist
+                           : align_up(RPPI_P_OFF + (P.npibins + 1) * 8, 128);
+    int hc = 1;
+    for (int c = WARPS; c >= 1; c >>= 1)
+        if (base + c * copy * 4 <= 75 * 1024) {
+            hc = c;
+            break;
+        }
+    P.hcopies = hc;
+    P.hist_off = base;
+    L.hist_words = hc * copy;
+    L.smem = align_up(base + L.hist_words * 4, 128);
 }
 
 namespace {
@@ -326,10 +342,11 @@ struct Sweep32 {
     double Sx, Sy, Sz;
 };
 
-__device__ __forceinline__ uint32_t lut_byte(const unsigned char *smem, const Sweep32 &S, float d2)
+__device__ __forceinline__ uint32_t lut_byte(const unsigned char *smem, uint32_t u0, int shift,
+                                             uint32_t last, float d2)
 {
-    const uint32_t u = __float_as_uint(d2) - S.u0;  // below-range values wrap to huge
-    return smem[LUT_OFF + min(u >> S.shift, S.lut_last)];
+    const uint32_t u = __float_as_uint(d2) - u0;  // below-range values wrap to huge
+    return smem[LUT_OFF + min(u >> shift, last)];
 }
 
 __device__ __forceinline__ void red_shared1(uint32_t addr)
@@ -413,8 +430,8 @@ __device__ __forceinline__ void sweep32(unsigned char *smem, const Sweep32 &S, u
                             (vi && jB >= jlo && jB < jhi && lb0) +
                             (vi && jB + 1 >= jlo && jB + 1 < jhi && lb1));
         }
-        const uint32_t ea0 = lut_byte(smem, S, a0), ea1 = lut_byte(smem, S, a1);
-        const uint32_t eb0 = lut_byte(smem, S, b0), eb1 = lut_byte(smem, S, b1);
+        const uint32_t ea0 = lut_byte(smem, S.u0, S.shift, S.lut_last, a0), ea1 = lut_byte(smem, S.u0, S.shift, S.lut_last, a1);
+        const uint32_t eb0 = lut_byte(smem, S.u0, S.shift, S.lut_last, b0), eb1 = lut_byte(smem, S.u0, S.shift, S.lut_last, b1);
         const uint32_t nbu = (uint32_t)S.nb;
         red_shared1(hl + min(ea0, nbu) * 128u);  // flagged entries -> dummy row here
         red_shared1(hl + min(ea1, nbu) * 128u);
@@ -636,7 +653,7 @@ __global__ void __launch_bounds__(THREADS) k_xi64(const __grid_constant__ PairPa
     constexpr int J = 32 / I;
     extern __shared__ __align__(128) unsigned char smem[];
     const int nb = P.nbins;
-    const SmemLayout L = smem_layout(P.tile_max, 32, 0, 0, nb, 0, 0, 0, WARPS * (nb + 1) * 32);
+    const Smem64 L = smem64_layout(P.tile_max, nb, 0, WARPS * (nb + 1) * 32);
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
     volatile int *s_item = reinterpret_cast<volatile int *>(smem + 8);
     double4_32a *tile = reinterpret_cast<double4_32a *>(smem + L.tile);
@@ -755,6 +772,549 @@ __global__ void __launch_bounds__(THREADS) k_xi64(const __grid_constant__ PairPa
         atomicAdd(&P.diag[1], n_eval);
 }
 
+// ============================================================ DD(rp, pi) kernels
+// rp^2 = dx^2 + dy^2 is binned like r^2 (bits-indexed table of float32
+// thresholds with 2-component error bands).  pi = |dz| is binned by
+// arithmetic, since its edges are uniform: t = |dz| * npibins / pimax has the
+// pi edges at the integers.  With t' = t - 1/2 (one fma), adding 1.5 * 2^23
+// rounds t' to the nearest integer m, which the sum's low mantissa bits hold;
+// m = floor(t) unless t is within rounding of an integer, and the exact
+// remainder d = t' - m tells that case apart (|d| close to 1/2).
+constexpr float PI_MAGIC = 12582912.0f;        // 1.5 * 2^23: spacing 1 in [2^23, 2^24)
+constexpr uint32_t PI_MAGIC_BITS = 0x4b400000u;  // its bit pattern
+
+__device__ __forceinline__ u64 fadd2(u64 a, u64 b)
+{
+    u64 r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+
+__device__ __forceinline__ u64 fabs2(u64 a) { return a & 0x7fffffff7fffffffull; }
+
+__device__ __forceinline__ void red_shared(uint32_t addr, uint32_t v)
+{
+    asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(addr), "r"(v));
+}
+
+// Canonical binary64 rp^2 of one pair inside an rp band: rp bin or -1.
+__device__ __noinline__ int recheck_rp64(const double *E2, int nb, const double4_32a *pa,
+                                         const double4_32a *pb, int i, int j, double Sx, double Sy)
+{
+    const double dx = canon_comp(pa[i].x, pb[j].x, Sx);
+    const double dy = canon_comp(pa[i].y, pb[j].y, Sy);
+    return bin_f64(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), E2, nb);
+}
+
+// Canonical binary64 pi = |dz| of one pair near a pi edge: pi bin or -1.
+__device__ __noinline__ int recheck_pi64(const double *Pe, int npi, const double4_32a *pa,
+                                         const double4_32a *pb, int i, int j, double Sz)
+{
+    return bin_f64(fabs(canon_comp(pa[i].z, pb[j].z, Sz)), Pe, npi);
+}
+
+// Debug: do the float32 decisions (rp from thresholds, pi from the rounding)
+// agree with binary64?  No claim inside a band.  (1 = violation)
+__device__ __noinline__ int verify_rppi(float rp2, uint32_t m32, bool pflag, const float *thr,
+                                        int nthr, int nb, int npi, const double *E2,
+                                        const double *Pe, const double4_32a *pa,
+                                        const double4_32a *pb, int i, int j, double Sx, double Sy,
+                                        double Sz)
+{
+    int c = 0;
+    while (c < nthr && thr[c] <= rp2)
+        ++c;
+    if ((c & 1) || pflag)
+        return 0;
+    const int k32 = (c >= 2 && c <= 2 * nb) ? (c - 2) >> 1 : -1;
+    const int mm = m32 < (uint32_t)npi ? (int)m32 : -1;
+    const int k64 = recheck_rp64(E2, nb, pa, pb, i, j, Sx, Sy);
+    const int m64 = recheck_pi64(Pe, npi, pa, pb, i, j, Sz);
+    const bool c32 = k32 >= 0 && mm >= 0, c64 = k64 >= 0 && m64 >= 0;
+    return c32 != c64 || (c32 && (k32 != k64 || mm != m64));
+}
+
+// Per-window constants of the rp-pi sweep.
+struct SweepRP {
+    int t0, nb, npi;
+    uint32_t u0, lut_last;
+    int shift, nthr;
+    uint32_t hbase, rowb;  // shared address of this warp's histogram copy; bytes per rp row
+    float pband;
+    const double4_32a *pa, *pb;
+    double Sx, Sy, Sz;
+};
+
+// A pair whose rp table cell is flagged or whose t is near a pi edge: settle
+// both decisions exactly, undo the main path's increment (at addr_main) and
+// add the pair to its true slot.  Returns 1 if binary64 was needed.
+__device__ __forceinline__ int resolve_rppi(const unsigned char *smem, const SweepRP &S, uint32_t e,
+                                            float rp2, uint32_t m_main, bool pflag,
+                                            uint32_t addr_main, int i, int jg)
+{
+    int k, re = 0;
+    if (e & LUT_FLAG) {
+        const float *T = reinterpret_cast<const float *>(smem + THR_OFF);
+        int c = (int)(e & 0x7fu) * 2;
+        while (c < S.nthr && T[c] <= rp2)
+            ++c;
+        if (c & 1) {
+            k = recheck_rp64(reinterpret_cast<const double *>(smem + E2_OFF), S.nb, S.pa, S.pb, i,
+                             jg, S.Sx, S.Sy);
+            re = 1;
+        } else {
+            k = (c >= 2 && c <= 2 * S.nb) ? (c - 2) >> 1 : -1;
+        }
+    } else {
+        k = e < (uint32_t)S.nb ? (int)e : -1;
+    }
+    if (k < 0)  // the main path used the dummy row
+        return re;
+    int m;
+    if (pflag) {
+        m = recheck_pi64(reinterpret_cast<const double *>(smem + RPPI_P_OFF), S.npi, S.pa, S.pb, i,
+                         jg, S.Sz);
+        re = 1;
+    } else {
+        m = m_main < (uint32_t)S.npi ? (int)m_main : -1;
+    }
+    red_shared(addr_main, 0xffffffffu);
+    if (m >= 0)
+        red_shared(S.hbase + (uint32_t)k * S.rowb + (uint32_t)m * 4u, 1u);
+    return re;
+}
+
+// Sweep one window of the staged tile (lane layout as in sweep32): per pair
+// rp^2 and t' = |dz| * s - 1/2 in packed float32, the rp table byte, the pi
+// index from the rounding, one shared atomic into the warp's 2-D histogram
+// copy; one warp-uniform check for flagged pairs per iteration.
+template <int I, bool TRI, bool EVALS, bool VERIFY>
+__device__ __forceinline__ void sweep_rppi32(unsigned char *smem, const SweepRP &S, int jlo, int jhi,
+                                             int jj, u64 XH, u64 YH, u64 ZH, u64 SC, int i, bool vi,
+                                             u64 &n_eval, u64 &n_rck, u64 &n_viol)
+{
+    const float qnan = __int_as_float(0x7fc00000);
+    const u64 MH = pack2(-0.5f, -0.5f), MG = pack2(PI_MAGIC, PI_MAGIC);
+    const uint32_t npiu = (uint32_t)S.npi, nbu = (uint32_t)S.nb;
+    const int jstart = jlo & ~1;
+    constexpr int JS = 64 / I;
+    const int nit = (jhi - jstart + 2 * JS - 1) / (2 * JS);
+    const unsigned char *p = smem + TX_OFF + (jstart + 2 * jj) * 4;
+    int jA = jstart + 2 * jj;
+    for (int it = 0; it < nit; ++it, p += 8 * JS, jA += 2 * JS) {
+        const u64 xA = *reinterpret_cast<const u64 *>(p);
+        const u64 yA = *reinterpret_cast<const u64 *>(p + TSTRIDE);
+        const u64 zA = *reinterpret_cast<const u64 *>(p + 2 * TSTRIDE);
+        const u64 xB = *reinterpret_cast<const u64 *>(p + 4 * JS);
+        const u64 yB = *reinterpret_cast<const u64 *>(p + 4 * JS + TSTRIDE);
+        const u64 zB = *reinterpret_cast<const u64 *>(p + 4 * JS + 2 * TSTRIDE);
+        u64 dx = fsub2(xA, XH), dy = fsub2(yA, YH);
+        const u64 rA = ffma2(dy, dy, fmul2(dx, dx));
+        const u64 tA = ffma2(fabs2(fsub2(zA, ZH)), SC, MH);
+        dx = fsub2(xB, XH);
+        dy = fsub2(yB, YH);
+        const u64 rB = ffma2(dy, dy, fmul2(dx, dx));
+        const u64 tB = ffma2(fabs2(fsub2(zB, ZH)), SC, MH);
+        const u64 qA = fadd2(tA, MG), qB = fadd2(tB, MG);
+        const u64 fA = fsub2(tA, fsub2(qA, MG)), fB = fsub2(tB, fsub2(qB, MG));
+        float a0, a1, b0, b1, fa0, fa1, fb0, fb1, qa0, qa1, qb0, qb1;
+        unpack2(rA, a0, a1);
+        unpack2(rB, b0, b1);
+        unpack2(fA, fa0, fa1);
+        unpack2(fB, fb0, fb1);
+        unpack2(qA, qa0, qa1);
+        unpack2(qB, qb0, qb1);
+        const int gA = S.t0 + jA, gB = gA + JS;
+        bool la0 = true, la1 = true, lb0 = true, lb1 = true;
+        if (TRI) {
+            la0 = gA > i;
+            la1 = gA + 1 > i;
+            lb0 = gB > i;
+            lb1 = gB + 1 > i;
+            a0 = la0 ? a0 : qnan;
+            a1 = la1 ? a1 : qnan;
+            b0 = lb0 ? b0 : qnan;
+            b1 = lb1 ? b1 : qnan;
+        }
+        if (EVALS) {
+            const int jB = jA + JS;
+            n_eval += (u64)((vi && jA >= jlo && jA < jhi && la0) +
+                            (vi && jA + 1 >= jlo && jA + 1 < jhi && la1) +
+                            (vi && jB >= jlo && jB < jhi && lb0) +
+                            (vi && jB + 1 >= jlo && jB + 1 < jhi && lb1));
+        }
+        const uint32_t ea0 = lut_byte(smem, S.u0, S.shift, S.lut_last, a0);
+        const uint32_t ea1 = lut_byte(smem, S.u0, S.shift, S.lut_last, a1);
+        const uint32_t eb0 = lut_byte(smem, S.u0, S.shift, S.lut_last, b0);
+        const uint32_t eb1 = lut_byte(smem, S.u0, S.shift, S.lut_last, b1);
+        const uint32_t ma0 = min(__float_as_uint(qa0) - PI_MAGIC_BITS, npiu);
+        const uint32_t ma1 = min(__float_as_uint(qa1) - PI_MAGIC_BITS, npiu);
+        const uint32_t mb0 = min(__float_as_uint(qb0) - PI_MAGIC_BITS, npiu);
+        const uint32_t mb1 = min(__float_as_uint(qb1) - PI_MAGIC_BITS, npiu);
+        const uint32_t ha0 = S.hbase + min(ea0, nbu) * S.rowb + ma0 * 4u;
+        const uint32_t ha1 = S.hbase + min(ea1, nbu) * S.rowb + ma1 * 4u;
+        const uint32_t hb0 = S.hbase + min(eb0, nbu) * S.rowb + mb0 * 4u;
+        const uint32_t hb1 = S.hbase + min(eb1, nbu) * S.rowb + mb1 * 4u;
+        red_shared(ha0, 1u);
+        red_shared(ha1, 1u);
+        red_shared(hb0, 1u);
+        red_shared(hb1, 1u);
+        const bool pa0 = fabsf(fa0) > S.pband, pa1 = fabsf(fa1) > S.pband;
+        const bool pb0 = fabsf(fb0) > S.pband, pb1 = fabsf(fb1) > S.pband;
+        if (__any_sync(FULL, ((ea0 | ea1 | eb0 | eb1) & LUT_FLAG) || pa0 || pa1 || pb0 || pb1)) {
+            if ((ea0 & LUT_FLAG) || pa0)
+                n_rck += resolve_rppi(smem, S, ea0, a0, ma0, pa0, ha0, i, gA);
+            if ((ea1 & LUT_FLAG) || pa1)
+                n_rck += resolve_rppi(smem, S, ea1, a1, ma1, pa1, ha1, i, gA + 1);
+            if ((eb0 & LUT_FLAG) || pb0)
+                n_rck += resolve_rppi(smem, S, eb0, b0, mb0, pb0, hb0, i, gB);
+            if ((eb1 & LUT_FLAG) || pb1)
+                n_rck += resolve_rppi(smem, S, eb1, b1, mb1, pb1, hb1, i, gB + 1);
+        }
+        if (VERIFY) {
+            const float *T = reinterpret_cast<const float *>(smem + THR_OFF);
+            const double *E2 = reinterpret_cast<const double *>(smem + E2_OFF);
+            const double *Pe = reinterpret_cast<const double *>(smem + RPPI_P_OFF);
+            const float dv[4] = {a0, a1, b0, b1};
+            const uint32_t mv[4] = {ma0, ma1, mb0, mb1};
+            const bool pv[4] = {pa0, pa1, pb0, pb1};
+            const int gv[4] = {gA, gA + 1, gB, gB + 1};
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (vi && !isnan(dv[q]))
+                    n_viol += verify_rppi(dv[q], mv[q], pv[q], T, S.nthr, S.nb, S.npi, E2, Pe, S.pa,
+                                          S.pb, i, gv[q], S.Sx, S.Sy, S.Sz);
+        }
+    }
+}
+
+// Move one histogram copy to the global histogram.  Counts are read as
+// signed 32-bit values: a warp may undo an increment (resolve_rppi) after
+// another warp sharing the copy has flushed it.
+__device__ void flush_rppi(uint32_t *hc, int nb, int npi, unsigned long long *ghist, int lane)
+{
+    const int row = npi + 1;
+    for (int s = lane; s < nb * row; s += 32) {
+        const int k = s / row, m = s - k * row;
+        if (m == npi)
+            continue;
+        const int v = (int)atomicExch(&hc[s], 0u);
+        if (v)
+            atomicAdd(&ghist[k * npi + m], (u64)(long long)v);
+    }
+}
+
+// All copies of the CTA's histograms -> global (after the last __syncthreads).
+__device__ void merge_rppi(const uint32_t *hist, int hcopies, int nb, int npi,
+                           unsigned long long *ghist)
+{
+    const int row = npi + 1, copy = (nb + 1) * row;
+    for (int s = threadIdx.x; s < nb * npi; s += THREADS) {
+        const int k = s / npi, m = s - k * npi;
+        long long sum = 0;
+        for (int c = 0; c < hcopies; ++c)
+            sum += (int)hist[c * copy + k * row + m];
+        if (sum)
+            atomicAdd(&ghist[s], (u64)sum);
+    }
+}
+
+template <int I, bool EVALS, bool VERIFY>
+__global__ void __launch_bounds__(THREADS, 3) k_rppi32(const __grid_constant__ PairParams P)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int nb = P.nbins, npi = P.npibins;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
+    volatile int *s_item = reinterpret_cast<volatile int *>(smem + 8);
+    const float *tz = reinterpret_cast<const float *>(smem + TX_OFF + 2 * TSTRIDE);
+    float *thr = reinterpret_cast<float *>(smem + THR_OFF);
+    double *E2 = reinterpret_cast<double *>(smem + E2_OFF);
+    double *Pe = reinterpret_cast<double *>(smem + RPPI_P_OFF);
+    uint32_t *hist = reinterpret_cast<uint32_t *>(smem + P.hist_off);
+    const int copy = (nb + 1) * (npi + 1);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    for (int q = tid; q < P.lut_n; q += THREADS)
+        smem[LUT_OFF + q] = P.lut[q];
+    for (int q = tid; q < P.nthr; q += THREADS)
+        thr[q] = P.thr[q];
+    for (int q = tid; q <= nb; q += THREADS)
+        E2[q] = P.E2[q];
+    for (int q = tid; q <= npi; q += THREADS)
+        Pe[q] = P.P[q];
+    for (int q = tid; q < P.hcopies * copy; q += THREADS)
+        hist[q] = 0u;
+    if (tid == 0) {
+        mbar_init(bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    uint32_t *hc = hist + (warp % P.hcopies) * copy;
+    const int ii = lane % I, jj = lane / I;
+    SweepRP S;
+    S.nb = nb;
+    S.npi = npi;
+    S.u0 = P.u0;
+    S.lut_last = (uint32_t)(P.lut_n - 1);
+    S.shift = P.lut_shift;
+    S.nthr = P.nthr;
+    S.hbase = smem_u32(hc);
+    S.rowb = (uint32_t)(npi + 1) * 4u;
+    S.pband = P.pband;
+    S.pa = P.A.pos64;
+    S.pb = P.B.pos64;
+    const u64 SC = pack2(P.pscale, P.pscale);
+    const unsigned flush_at = (1u << 30) / (unsigned)(WARPS / P.hcopies);
+    unsigned phase = 0;
+    u64 n_eval = 0, n_rck = 0, n_viol = 0;
+    unsigned pending = 0;
+    bool aborted = false;
+    const float qnan = __int_as_float(0x7fc00000);
+
+    for (;;) {
+        if (tid == 0)
+            *s_item = (int)atomicAdd(P.item_counter, 1u);
+        __syncthreads();
+        const int item = *s_item;
+        __syncthreads();
+        if (item >= P.n_items)
+            break;
+        Item it;
+        if (!decode_item(P, item, it))
+            continue;
+        if (tid == 0)
+            atomicAdd(&P.diag[0], 1ull);
+        const float dzw = __fadd_ru(__double2float_ru(it.dzmax), P.zslack);
+        const float Sxf = __double2float_rn(it.Sx), Syf = __double2float_rn(it.Sy);
+        S.Sx = it.Sx;
+        S.Sy = it.Sy;
+        const int nchunks = (it.a1 - it.a0 + I - 1) / I;
+
+        for (int t0 = it.b0; t0 < it.b1; t0 += TILE32) {
+            const int nt = min(TILE32, it.b1 - t0);
+            if (!stage_tiles32(smem, P.B, t0, nt, bar, phase, P.err)) {
+                aborted = true;
+                break;
+            }
+            S.t0 = t0;
+            const float zt_lo = tz[0];
+            float zt_hi = tz[nt - 1];
+            if (isnan(zt_hi))
+                zt_hi = INFINITY;
+            auto zkey = [&](int q) { return tz[q]; };
+            int lo_prev[3] = {0, 0, 0}, hi_prev[3] = {0, 0, 0};
+
+            for (int c = warp; c < nchunks; c += WARPS) {
+                const int ib = it.a0 + c * I;
+                const int nvi = min(I, it.a1 - ib);
+                const int i = ib + ii;
+                float xi = qnan, yi = qnan, zi = qnan;
+                if (ii < nvi) {
+                    xi = P.A.xs[i];
+                    yi = P.A.ys[i];
+                    zi = P.A.zs[i];
+                }
+                const bool vi = !isnan(xi);
+                const float xh = __fsub_rn(xi, Sxf), yh = __fsub_rn(yi, Syf);
+                const u64 XH = pack2(xh, xh), YH = pack2(yh, yh);
+                const float zlo = __shfl_sync(FULL, zi, 0);
+                float zhi = zi;
+#pragma unroll
+                for (int o = 1; o < I; o <<= 1) {
+                    const float t = __shfl_xor_sync(FULL, zhi, o);
+                    zhi = (isnan(zhi) || t > zhi) ? t : zhi;
+                }
+                if (isnan(zlo))
+                    continue;
+
+#pragma unroll
+                for (int kk = 0; kk < 3; ++kk) {
+                    const int k = kk - 1;
+                    if (k < it.kmin || k > it.kmax)
+                        continue;
+                    const float kz = (float)k * P.boxf[2];
+                    const float wlo = zlo - kz - dzw, whi = zhi - kz + dzw;
+                    if (whi < zt_lo || wlo > zt_hi)
+                        continue;
+                    int jlo = warp_bound_from(zkey, lo_prev[kk], nt, wlo, false, lane);
+                    const int jhi = warp_bound_from(zkey, max(hi_prev[kk], jlo), nt, whi, true, lane);
+                    lo_prev[kk] = jlo;
+                    hi_prev[kk] = jhi;
+                    const bool tri = it.self && k == 0;
+                    if (tri)
+                        jlo = max(jlo, ib + 1 - t0);
+                    if (jlo >= jhi)
+                        continue;
+                    pending += (unsigned)((jhi - jlo) / (64 / I) + 4) * 64u;
+                    const float zh = __fsub_rn(zi, kz);
+                    const u64 ZH = pack2(zh, zh);
+                    S.Sz = k == 0 ? 0.0 : (k > 0 ? P.g.box[2] : -P.g.box[2]);
+                    if (tri)
+                        sweep_rppi32<I, true, EVALS, VERIFY>(smem, S, jlo, jhi, jj, XH, YH, ZH, SC, i,
+                                                          vi, n_eval, n_rck, n_viol);
+                    else
+                        sweep_rppi32<I, false, EVALS, VERIFY>(smem, S, jlo, jhi, jj, XH, YH, ZH, SC,
+                                                           i, vi, n_eval, n_rck, n_viol);
+                }
+                if (pending > flush_at) {  // keep every shared u32 count far from overflow
+                    __syncwarp();
+                    flush_rppi(hc, nb, npi, P.hist, lane);
+                    pending = 0;
+                }
+            }
+        }
+        if (aborted)
+            break;
+    }
+
+    __syncthreads();
+    merge_rppi(hist, P.hcopies, nb, npi, P.hist);
+    n_eval = warp_sum_u64(n_eval);
+    n_rck = warp_sum_u64(n_rck);
+    n_viol = warp_sum_u64(n_viol);
+    if (lane == 0) {
+        if (n_eval)
+            atomicAdd(&P.diag[1], n_eval);
+        if (n_rck)
+            atomicAdd(&P.diag[2], n_rck);
+        if (n_viol)
+            atomicAdd(&P.diag[3], n_viol);
+    }
+}
+
+// Binary64 DD(rp, pi): canonical rp^2 and |dz|, exact edge compares.
+template <int I, bool EVALS>
+__global__ void __launch_bounds__(THREADS) k_rppi64(const __grid_constant__ PairParams P)
+{
+    constexpr int J = 32 / I;
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int nb = P.nbins, npi = P.npibins, row = npi + 1, copy = (nb + 1) * row;
+    const Smem64 L = smem64_layout(P.tile_max, nb, npi, 0);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
+    volatile int *s_item = reinterpret_cast<volatile int *>(smem + 8);
+    double4_32a *tile = reinterpret_cast<double4_32a *>(smem + L.tile);
+    double *E2 = reinterpret_cast<double *>(smem + L.e2);
+    double *Pe = reinterpret_cast<double *>(smem + L.p);
+    uint32_t *hist = reinterpret_cast<uint32_t *>(smem + P.hist_off);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    for (int q = tid; q <= nb; q += THREADS)
+        E2[q] = P.E2[q];
+    for (int q = tid; q <= npi; q += THREADS)
+        Pe[q] = P.P[q];
+    for (int q = tid; q < P.hcopies * copy; q += THREADS)
+        hist[q] = 0u;
+    if (tid == 0) {
+        mbar_init(bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    uint32_t *hc = hist + (warp % P.hcopies) * copy;
+    const unsigned flush_at = (1u << 30) / (unsigned)(WARPS / P.hcopies);
+    const int ii = lane % I, jj = lane / I;
+    unsigned phase = 0;
+    u64 n_eval = 0;
+    unsigned pending = 0;
+    bool aborted = false;
+    const double qnan = __longlong_as_double(0x7ff8000000000000ll);
+
+    for (;;) {
+        if (tid == 0)
+            *s_item = (int)atomicAdd(P.item_counter, 1u);
+        __syncthreads();
+        const int item = *s_item;
+        __syncthreads();
+        if (item >= P.n_items)
+            break;
+        Item it;
+        if (!decode_item(P, item, it))
+            continue;
+        if (tid == 0)
+            atomicAdd(&P.diag[0], 1ull);
+        const double dzw = __dadd_rn(it.dzmax, 1e-9 * (P.rz + P.g.box[2] + 1.0));
+        const int nchunks = (it.a1 - it.a0 + I - 1) / I;
+
+        for (int t0 = it.b0; t0 < it.b1; t0 += P.tile_max) {
+            const int nt = min(P.tile_max, it.b1 - t0);
+            if (!stage_tile(tile, P.B.pos64 + t0, nt, 32, bar, phase, P.err)) {
+                aborted = true;
+                break;
+            }
+            double zt_hi = tile[nt - 1].z;
+            if (isnan(zt_hi))
+                zt_hi = INFINITY;
+            const double zt_lo = tile[0].z;
+            auto zkey = [&](int p) { return tile[p].z; };
+            for (int c = warp; c < nchunks; c += WARPS) {
+                const int ib = it.a0 + c * I;
+                const int nvi = min(I, it.a1 - ib);
+                const int i = ib + ii;
+                const bool vi = ii < nvi;
+                double4_32a pi = make_double4_32a(qnan, qnan, qnan, qnan);
+                if (vi)
+                    pi = P.A.pos64[i];
+                const double zlo = __shfl_sync(FULL, pi.z, 0);
+                double zhi = pi.z;
+#pragma unroll
+                for (int o = 1; o < I; o <<= 1) {
+                    const double t = __shfl_xor_sync(FULL, zhi, o);
+                    zhi = (isnan(zhi) || t > zhi) ? t : zhi;
+                }
+                if (isnan(zlo))
+                    continue;
+                for (int k = it.kmin; k <= it.kmax; ++k) {
+                    const double kz = k * P.g.box[2];
+                    const double wlo = zlo - kz - dzw, whi = zhi - kz + dzw;
+                    if (whi < zt_lo || wlo > zt_hi)
+                        continue;
+                    int jlo = warp_bound(zkey, nt, wlo, false, lane);
+                    const int jhi = warp_bound(zkey, nt, whi, true, lane);
+                    const bool tri = it.self && k == 0;
+                    if (tri)
+                        jlo = max(jlo, ib + 1 - t0);
+                    if (jlo >= jhi)
+                        continue;
+                    pending += (unsigned)((jhi - jlo + J - 1) / J) * 32u;
+                    for (int jb = jlo; jb < jhi; jb += J) {
+                        const int j = jb + jj;
+                        const double4_32a pj = tile[j];
+                        const bool live = !tri || (t0 + j > i);
+                        if (EVALS)
+                            n_eval += (vi && j < jhi && live) ? 1ull : 0ull;
+                        const double dx = canon_comp(pi.x, pj.x, it.Sx);
+                        const double dy = canon_comp(pi.y, pj.y, it.Sy);
+                        const double dz = canon_comp(pi.z, pj.z, kz);
+                        double rp2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
+                        if (!live)
+                            rp2 = qnan;
+                        const int kb = bin_f64(rp2, E2, nb);
+                        if (kb >= 0) {
+                            const int m = bin_f64(fabs(dz), Pe, npi);
+                            if (m >= 0)
+                                atomicAdd(&hc[kb * row + m], 1u);
+                        }
+                    }
+                }
+                if (pending > flush_at) {
+                    __syncwarp();
+                    flush_rppi(hc, nb, npi, P.hist, lane);
+                    pending = 0;
+                }
+            }
+        }
+        if (aborted)
+            break;
+    }
+
+    __syncthreads();
+    merge_rppi(hist, P.hcopies, nb, npi, P.hist);
+    n_eval = warp_sum_u64(n_eval);
+    if (lane == 0 && n_eval)
+        atomicAdd(&P.diag[1], n_eval);
+}
+
 // Per (kernel, device): the dynamic shared-memory limit set so far (only ever
 // raised) and the occupancy per shared-memory size, queried once.
 struct OccCache {
@@ -825,6 +1385,24 @@ cudaError_t launch_persistent(K kern, const PairParams &P, PairLaunch &L, int sm
 
 cudaError_t launch_pairs(const PairParams &P, PairLaunch &L, int sms, cudaStream_t st)
 {
+    if (P.kind == 1) {
+        if (L.f64)
+            return L.evals ? launch_persistent(k_rppi64<8, true>, P, L, sms, st)
+                           : launch_persistent(k_rppi64<8, false>, P, L, sms, st);
+        if (L.verify)
+            return launch_persistent(k_rppi32<8, true, true>, P, L, sms, st);
+        switch (L.chunk) {
+        case 16:
+            return L.evals ? launch_persistent(k_rppi32<16, true, false>, P, L, sms, st)
+                           : launch_persistent(k_rppi32<16, false, false>, P, L, sms, st);
+        case 32:
+            return L.evals ? launch_persistent(k_rppi32<32, true, false>, P, L, sms, st)
+                           : launch_persistent(k_rppi32<32, false, false>, P, L, sms, st);
+        default:
+            return L.evals ? launch_persistent(k_rppi32<8, true, false>, P, L, sms, st)
+                           : launch_persistent(k_rppi32<8, false, false>, P, L, sms, st);
+        }
+    }
     if (P.kind != 0)
         return cudaErrorNotSupported;
     if (L.f64)

@@ -5,34 +5,26 @@
 
 namespace cf {
 
-// Shared-memory layout of a pair-kernel CTA (identical on host and device).
-struct SmemLayout {
-    int tile, lut, thr, e2, pilut, pithr, p, hist, total;
-};
-
 __host__ __device__ inline int align_up(int v, int a) { return (v + a - 1) / a * a; }
 
-__host__ __device__ inline SmemLayout smem_layout(int tile_max, int pt_bytes, int lut_n, int nthr,
-                                                  int nbins, int pilut_n, int pi_nthr, int npibins,
-                                                  int hist_words)
+// Shared-memory layout of the binary64 kernels (identical on host and device):
+// [0, 128) barrier + work item; tile of tile_max + 32 points (x, y, z, w);
+// squared edges; pi edges (rp-pi); histograms.
+struct Smem64 {
+    int tile, e2, p, hist, total;
+};
+
+__host__ __device__ inline Smem64 smem64_layout(int tile_max, int nbins, int npibins, int hist_words)
 {
-    SmemLayout L;
-    int off = 128;  // [0, 128): mbarrier, work item, flags
+    Smem64 L;
+    int off = 128;
     L.tile = off;
-    off += (tile_max + 32) * pt_bytes;
-    L.lut = off = align_up(off, 16);
-    off += lut_n * 2;
-    L.thr = off = align_up(off, 16);
-    off += nthr * 4;
+    off += (tile_max + 32) * 32;
     L.e2 = off = align_up(off, 16);
     off += (nbins + 1) * 8;
-    L.pilut = off = align_up(off, 16);
-    off += pilut_n * 2;
-    L.pithr = off = align_up(off, 16);
-    off += pi_nthr * 4;
     L.p = off = align_up(off, 16);
     off += (npibins > 0 ? npibins + 1 : 0) * 8;
-    L.hist = off = align_up(off, 16);
+    L.hist = off = align_up(off, 128);
     off += hist_words * 4;
     L.total = align_up(off, 128);
     return L;
@@ -48,12 +40,10 @@ struct PairLaunch {
     int hist_words;  // shared histogram words
 };
 
-// Dynamic shared memory of the float32 DD(r) kernel for nbins bins.
-int xi32_smem_bytes(int nbins);
-
-// Hist words of one CTA for a given kind / bin count (xi: per-lane rows per warp;
-// rp-pi: one row per warp).
-int pair_hist_words(int kind, int nbins, int npibins);
+// Fill the shared-memory plan of a launch: L.smem, L.hist_words and, for
+// rp-pi, P.hcopies and P.hist_off.  Needs P.kind, P.nbins, P.npibins,
+// P.tile_max and L.f64.
+void plan_pairs(PairParams &P, PairLaunch &L);
 
 // Configure (max dynamic smem), pick the occupancy-based grid and launch.
 cudaError_t launch_pairs(const PairParams &P, PairLaunch &L, int sms, cudaStream_t st);

@@ -53,6 +53,17 @@ def test_xi_full_size_matches_stored_oracle(cuda_device, c2, path, mode):
     assert r.npairs.tolist() == g["npairs"]
 
 
+@pytest.mark.parametrize("mode", ["fp32_recheck", "fp64"])
+def test_rppi_full_size_matches_stored_oracle(cuda_device, c2, mode):
+    g = _load(os.path.join(GOLDEN, "c3_rppi_f32.json"))
+    cat = _cat(c2, g["workload"]["cat"][1])
+    assert cat.digest() == g["catalog_digest"], "catalogue differs from the stored one"
+    edges = np.array([float.fromhex(h) for h in g["edges_hex"]])
+    w = g["workload"]
+    r = cf.countpairs_rp_pi(*_dev(cat), edges, w["pimax"], w["npibins"], boxsize=g["box"], mode=mode)
+    assert r.npairs.tolist() == g["npairs"]
+
+
 def test_full_size_properties(cuda_device, c2):
     edges = synth.log_edges(0.1, 25.0, 20)
     xyz = _dev(c2)
