@@ -480,6 +480,8 @@ int run(Request &q)
     const int nb = (int)q.edges.size() - 1;
     const int nslots = q.kind == 0 ? nb : nb * q.npibins;
     const bool f64 = c->mode == CF_MODE_FP64;
+    const bool wacc = c->weighted || c->want_ravg;
+    const int nacc = wacc ? 2 * nslots : 0;  // binary64 wsum | rsum after the counts
     const size_t esz = c->dtype == CF_FLOAT32 ? 4 : 8;
     const cf_catalog *cats[2] = {q.d1, q.autocorr ? q.d1 : q.d2};
     const int ncat = q.autocorr ? 1 : 2;
@@ -492,8 +494,6 @@ int run(Request &q)
         std::memset(res->ravg, 0, sizeof(double) * nslots);
     res->n_cellpairs = res->n_evaluated = res->n_rechecked = res->n_band_violations = 0;
     res->kernel_ms = res->total_ms = 0.0;
-    if (c->weighted || c->want_ravg)
-        return fail(CF_EINVAL, "weights / ravg are not available in this build");
 
     int dev = 0, sms = 0;
     void *ws = nullptr, *ws2 = nullptr;
@@ -504,8 +504,8 @@ int run(Request &q)
     std::vector<double> Pe(q.kind == 1 ? q.npibins + 1 : 0);
     float T[2 * (cf::NB_MAX + 1)];
     uint8_t tab[cf::LUT_MAX];
-    cf::Gridded G[2];
-    cf::GridTemps tmp;
+    cf::Gridded G[2] = {};
+    cf::GridTemps tmp = {};
     Bump bump;
     const void *dx[2][3] = {{nullptr}};
     const double *dw[2] = {nullptr, nullptr};
@@ -520,7 +520,7 @@ int run(Request &q)
     double *d_E2 = nullptr, *d_P = nullptr;
     size_t total = 0;
     struct HostOut {
-        unsigned long long hist[cf::NBINS2D_MAX + 5];  // hist | diag(4) | err, counter
+        unsigned long long hist[3 * cf::NBINS2D_MAX + 5];  // hist | diag(4) | err, counter | wsum | rsum
         unsigned long long *diag;
         unsigned err;
         float thr[2 * (cf::NB_MAX + 1)];  // page-locked staging of the tables
@@ -568,8 +568,8 @@ int run(Request &q)
             }
         }
         bbox_keys = bump.take<unsigned long long>(6);
-        // one block, one memset, one copy back: [hist | diag(4) | err, counter]
-        d_hist = bump.take<unsigned long long>(nslots + 5);
+        // one block, one memset, one copy back: [hist | diag(4) | err, counter | wsum | rsum]
+        d_hist = bump.take<unsigned long long>(nslots + 5 + nacc);
         d_diag = d_hist + nslots;
         d_err = reinterpret_cast<unsigned *>(d_hist + nslots + 4);
         d_ctr = d_err + 1;
@@ -592,7 +592,7 @@ int run(Request &q)
         if (dw[t])
             CF_CUDA(cudaMemcpyAsync((void *)dw[t], cats[t]->w, n * 8, cudaMemcpyHostToDevice, st), "H2D w");
     }
-    CF_CUDA(cudaMemsetAsync(d_hist, 0, sizeof(unsigned long long) * (nslots + 5), st), "memset");
+    CF_CUDA(cudaMemsetAsync(d_hist, 0, sizeof(unsigned long long) * (nslots + 5 + nacc), st), "memset");
 
     ho = (HostOut *)g_pinned.get(sizeof(HostOut));
     if (!ho) {
@@ -633,6 +633,7 @@ int run(Request &q)
                 G[t].xs = bump.take<float>(n);
                 G[t].ys = bump.take<float>(n);
                 G[t].zs = bump.take<float>(n);
+                G[t].ws = c->weighted ? bump.take<float>(n) : nullptr;
                 G[t].pos64 = bump.take<double4_32a>(n);
                 G[t].perm = bump.take<int>(n);
                 G[t].cell_start = bump.take<uint32_t>(g.ncells + 1);
@@ -725,6 +726,11 @@ int run(Request &q)
         P.E2 = d_E2;
         P.P = d_P;
         P.hist = d_hist;
+        P.weighted = c->weighted ? 1 : 0;
+        P.want_r = c->want_ravg ? 1 : 0;
+        P.wacc = wacc ? 1 : 0;
+        P.wsum = wacc ? reinterpret_cast<double *>(d_hist + nslots + 5) : nullptr;
+        P.rsum = wacc ? P.wsum + nslots : nullptr;
         P.diag = d_diag;
         P.err = d_err;
         P.item_counter = d_ctr;
@@ -750,7 +756,7 @@ int run(Request &q)
         }
         CF_CUDA(cudaEventRecord(g_events.ev[2], st), "cudaEventRecord");
         trace.point("pair kernel");
-        CF_CUDA(cudaMemcpyAsync(ho->hist, d_hist, sizeof(unsigned long long) * (nslots + 5),
+        CF_CUDA(cudaMemcpyAsync(ho->hist, d_hist, sizeof(unsigned long long) * (nslots + 5 + nacc),
                                 cudaMemcpyDeviceToHost, st),
                 "D2H results");
     }
@@ -784,6 +790,19 @@ int run(Request &q)
         const uint64_t mult = q.autocorr ? 2u : 1u;  // Sec. 2.1: double the unique-pair counts
         for (int k = 0; k < nslots; ++k)
             res->npairs[k] = ho->hist[k] * mult;
+        if (wacc) {
+            const double *ws = reinterpret_cast<const double *>(ho->hist + nslots + 5);
+            const double *rs = ws + nslots;
+            for (int k = 0; k < nslots; ++k) {
+                const double wk = ws[k] * (double)mult, rk = rs[k] * (double)mult;
+                if (res->wsum && c->weighted)
+                    res->wsum[k] = wk;
+                if (res->ravg) {  // mean separation, weighted by w_i * w_j when weighted
+                    const double den = c->weighted ? wk : (double)res->npairs[k];
+                    res->ravg[k] = den != 0.0 ? rk / den : 0.0;
+                }
+            }
+        }
         res->n_cellpairs = ho->diag[0];
         res->n_evaluated = ho->diag[1];
         res->n_rechecked = ho->diag[2];
@@ -1055,8 +1074,8 @@ int noalloc_xi(int autocorr, const cf_catalog *d1, const cf_catalog *d2, const d
     g.inv_w[2] = g.nz / std::max(g.extent[2], 1e-300);
     finish_geom(g);
 
-    cf::Gridded G[2];
-    cf::GridTemps tmp;
+    cf::Gridded G[2] = {};
+    cf::GridTemps tmp = {};
     for (int t = 0; t < ncat; ++t) {
         const long long n = cats[t]->n + 3ll * g.ncols;  // columns padded to 4
         G[t].xs = bump.take<float>(n);

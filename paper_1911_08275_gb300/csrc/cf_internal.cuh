@@ -43,11 +43,21 @@ constexpr int XI32_THR_OFF = XI32_TX_OFF + 3 * XI32_TSTRIDE;
 constexpr int XI32_E2_OFF = XI32_THR_OFF + 2 * (NB_MAX + 1) * 4;
 constexpr int XI32_HIST_OFF = XI32_E2_OFF + (NB_MAX + 1) * 8;
 
+// The weighted / mean-separation float32 DD(r) kernel adds, after the DD(r)
+// layout's squared edges: a weight tile; per warp and bin the binary64
+// accumulators {count (u64), sum w, sum r w}; per warp, bin and lane a byte
+// count and two float32 partial sums that hold at most 63 terms each.
+constexpr int XIW_W_OFF = XI32_HIST_OFF;
+constexpr int XIW_ACC_OFF = XIW_W_OFF + XI32_TSTRIDE;
+constexpr unsigned XIW_FLUSH = 64;  // terms per float32 partial before it moves to binary64
+static_assert(XIW_W_OFF % 16 == 0 && XIW_ACC_OFF % 16 == 0, "bulk-copy destinations need 16 B");
+
 // The float32 DD(rp, pi) kernel uses the DD(r) layout up to the thresholds and
-// squared rp edges, then the pi edges (binary64) and, from a run-time offset,
-// its histograms: hcopies copies of (nbins + 1) rows of (npibins + 1) words
-// (row nbins and column npibins collect pairs that are not counted).
-constexpr int RPPI_P_OFF = XI32_HIST_OFF;
+// squared rp edges, then a weight tile (as above), the pi edges (binary64) and,
+// from a run-time offset, its histograms: hcopies copies of (nbins + 1) rows
+// of (npibins + 1) words (row nbins and column npibins collect pairs that are
+// not counted), then for weighted sums binary64 [copy][slot][w, r w].
+constexpr int RPPI_P_OFF = XIW_W_OFF + XI32_TSTRIDE;
 
 // Grid geometry: columns in (x, y), z-cells inside each column (sort keys).
 struct Geom {
@@ -70,6 +80,7 @@ struct Geom {
 struct Gridded {
     long long n;
     float *xs, *ys, *zs;  // float32 coordinates in the grid frame (padded columns)
+    float *ws;            // float32 weights (padded columns; NULL without weights)
     double4_32a *pos64;       // (x, y, z, w) binary64, exact inputs
     int *perm;            // original index of each sorted point
     uint32_t *cell_start; // ncells + 1
@@ -103,13 +114,19 @@ struct PairParams {
     float pband;        // rp-pi: |t - 1/2 - round(t - 1/2)| > pband means t is near an edge
     int hcopies;        // rp-pi: shared histogram copies per CTA (warp w uses w % hcopies)
     int hist_off;       // byte offset of the shared histograms (rp-pi kernels)
+    // weighted sums (Code 1's weight per bin) and mean separation
+    int weighted;       // pair weight w_i * w_j (else 1)
+    int want_r;         // accumulate r (xi) or rp (rp-pi) times the pair weight
+    int wacc;           // weighted || want_r
+    int acc_off;        // byte offset of the binary64 accumulators in shared memory
+    int rows_off;       // float32 DD(r) kernel: byte offset of the per-lane partial rows
     const float *thr;        // nthr
     const uint8_t *lut;      // lut_n
     const double *E2;        // nbins + 1
     const double *P;         // npibins + 1 pi edges (rp-pi)
     // outputs
     unsigned long long *hist;  // nbins (xi) or nbins * npibins
-    double *wsum, *rsum;
+    double *wsum, *rsum;       // same shape (accumulated only when wacc)
     unsigned long long *diag;  // [0] kept items, [1] evaluations, [2] rechecks, [3] band violations
     unsigned *err;
     unsigned *item_counter;

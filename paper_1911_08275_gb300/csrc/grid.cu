@@ -259,8 +259,8 @@ __global__ void k_sort_cells(const T *__restrict__ x, const T *__restrict__ y,
                              const int *__restrict__ tmp_idx,
                              const unsigned long long *__restrict__ tmp_key,
                              float *__restrict__ xs, float *__restrict__ ys,
-                             float *__restrict__ zs, double4_32a *__restrict__ pos64,
-                             int *__restrict__ perm)
+                             float *__restrict__ zs, float *__restrict__ ws,
+                             double4_32a *__restrict__ pos64, int *__restrict__ perm)
 {
     const int lane = threadIdx.x & 31;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -301,6 +301,8 @@ __global__ void k_sort_cells(const T *__restrict__ x, const T *__restrict__ y,
                 xs[d] = fx;
                 ys[d] = fy;
                 zs[d] = fz;
+                if (ws)
+                    ws[d] = (float)W;
                 perm[d] = iq;
             }
         }
@@ -310,8 +312,8 @@ __global__ void k_sort_cells(const T *__restrict__ x, const T *__restrict__ y,
 // Padding entries at the end of each column: NaN (never counted), perm -1.
 __global__ void k_padfill(const uint32_t *__restrict__ start, const uint32_t *__restrict__ pad,
                           int ncols, int nz, float *__restrict__ xs, float *__restrict__ ys,
-                          float *__restrict__ zs, double4_32a *__restrict__ pos64,
-                          int *__restrict__ perm)
+                          float *__restrict__ zs, float *__restrict__ ws,
+                          double4_32a *__restrict__ pos64, int *__restrict__ perm)
 {
     const int col = blockIdx.x * blockDim.x + threadIdx.x;
     if (col >= ncols)
@@ -321,6 +323,8 @@ __global__ void k_padfill(const uint32_t *__restrict__ start, const uint32_t *__
     const double dn = __longlong_as_double(0x7ff8000000000000ll);
     for (uint32_t q = e - pad[col]; q < e; ++q) {
         xs[q] = ys[q] = zs[q] = fn;
+        if (ws)
+            ws[q] = 0.0f;
         pos64[q] = make_double4_32a(dn, dn, dn, dn);
         perm[q] = -1;
     }
@@ -460,10 +464,10 @@ cudaError_t build_grid_t(const void *x, const void *y, const void *z, const doub
         const long long cwarps = std::min<long long>(nc, (long long)sms * 64);
         k_sort_cells<T><<<(int)((cwarps * 32 + 255) / 256), 256, 0, st>>>(
             (const T *)x, (const T *)y, w, nc, g, t.counts, out.cell_start, t.tmp_idx, t.tmp_key,
-            out.xs, out.ys, out.zs, out.pos64, out.perm);
+            out.xs, out.ys, out.zs, out.ws, out.pos64, out.perm);
     }
     k_padfill<<<(g.ncols + 255) / 256, 256, 0, st>>>(out.cell_start, t.pad, g.ncols, g.nz, out.xs,
-                                                      out.ys, out.zs, out.pos64, out.perm);
+                                                      out.ys, out.zs, out.ws, out.pos64, out.perm);
     k_colbox<<<std::min(g.ncols, sms * 8), 256, 0, st>>>(out.pos64, out.cell_start, g.ncols, g.nz,
                                                           out.colbox);
     return cudaGetLastError();

@@ -42,30 +42,47 @@ namespace cf {
 
 void plan_pairs(PairParams &P, PairLaunch &L)
 {
-    const int nb = P.nbins;
+    const int nb = P.nbins, nr = nb + 1;
+    P.acc_off = P.rows_off = 0;
     if (P.kind == 0) {
-        L.hist_words = WARPS * (nb + 1) * 32;  // per-lane rows + one dummy row per warp
-        L.smem = L.f64 ? smem64_layout(P.tile_max, nb, 0, L.hist_words).total
-                       : align_up(XI32_HIST_OFF + L.hist_words * 4, 128);
+        L.hist_words = WARPS * nr * 32;  // per-lane rows + one dummy row per warp
         P.hcopies = WARPS;
-        P.hist_off = L.f64 ? smem64_layout(P.tile_max, nb, 0, L.hist_words).hist : XI32_HIST_OFF;
+        if (L.f64) {
+            const Smem64 S = smem64_layout(P.tile_max, nb, 0, L.hist_words);
+            P.hist_off = S.hist;
+            P.acc_off = S.total;  // [warp][bin][w, r w] binary64 when weighted
+            L.smem = P.wacc ? align_up(S.total + WARPS * nb * 16, 128) : S.total;
+        } else if (P.wacc) {
+            // [warp][bin] {u64, f64, f64}; byte-count plane; two float32 planes
+            P.hist_off = XIW_ACC_OFF;
+            P.acc_off = XIW_ACC_OFF;
+            P.rows_off = align_up(XIW_ACC_OFF + WARPS * nr * 24, 128);
+            L.hist_words = 0;
+            L.smem = align_up(P.rows_off + align_up(WARPS * nr * 32, 128) + 2 * WARPS * nr * 32 * 4,
+                              128);
+        } else {
+            P.hist_off = XI32_HIST_OFF;
+            L.smem = align_up(XI32_HIST_OFF + L.hist_words * 4, 128);
+        }
         return;
     }
     // rp-pi: one histogram copy per warp while the CTA stays small enough for
     // three CTAs per SM, else fewer copies shared by several warps.
-    const int copy = (nb + 1) * (P.npibins + 1);
+    const int copy = nr * (P.npibins + 1);
     const int base = L.f64 ? smem64_layout(P.tile_max, nb, P.npibins, 0).hist
                            : align_up(RPPI_P_OFF + (P.npibins + 1) * 8, 128);
+    const int per = copy * 4 + (P.wacc ? copy * 16 + 16 : 0);
     int hc = 1;
     for (int c = WARPS; c >= 1; c >>= 1)
-        if (base + c * copy * 4 <= 75 * 1024) {
+        if (base + c * per <= 75 * 1024) {
             hc = c;
             break;
         }
     P.hcopies = hc;
     P.hist_off = base;
     L.hist_words = hc * copy;
-    L.smem = align_up(base + L.hist_words * 4, 128);
+    P.acc_off = align_up(base + L.hist_words * 4, 16);
+    L.smem = align_up(P.wacc ? P.acc_off + hc * copy * 16 : base + L.hist_words * 4, 128);
 }
 
 namespace {
@@ -267,20 +284,25 @@ __device__ __forceinline__ bool decode_item(const PairParams &P, int item, Item 
 // thread if the wait gave up.
 __device__ __forceinline__ bool stage_tiles32(unsigned char *smem, const Gridded &B, int t0,
                                               int count, uint64_t *bar, unsigned &phase,
-                                              unsigned *err)
+                                              unsigned *err, bool with_w = false)
 {
     __syncthreads();  // previous tile fully consumed
     const unsigned bytes = (unsigned)count * 4u;
     if (threadIdx.x == 0) {
         fence_proxy_async_smem();
-        mbar_arrive_expect_tx(bar, 3u * bytes);
+        mbar_arrive_expect_tx(bar, (with_w ? 4u : 3u) * bytes);
         bulk_g2s(smem + XI32_TX_OFF, B.xs + t0, bytes, bar);
         bulk_g2s(smem + XI32_TX_OFF + XI32_TSTRIDE, B.ys + t0, bytes, bar);
         bulk_g2s(smem + XI32_TX_OFF + 2 * XI32_TSTRIDE, B.zs + t0, bytes, bar);
+        if (with_w)
+            bulk_g2s(smem + XIW_W_OFF, B.ws + t0, bytes, bar);
     }
     float *t = reinterpret_cast<float *>(smem + XI32_TX_OFF);
     for (int s = threadIdx.x; s < 3 * 64; s += THREADS)  // sentinels: never counted
         t[(s >> 6) * (XI32_TSTRIDE / 4) + count + (s & 63)] = __int_as_float(0x7fc00000);
+    if (with_w)
+        for (int s = threadIdx.x; s < 64; s += THREADS)
+            reinterpret_cast<float *>(smem + XIW_W_OFF)[count + s] = 0.0f;
     const bool ok = mbar_wait(bar, phase, WAIT_LIMIT);
     phase ^= 1u;
     if (__syncthreads_or(!ok)) {
@@ -646,8 +668,337 @@ __global__ void __launch_bounds__(THREADS, 3) k_xi32(const __grid_constant__ Pai
     }
 }
 
-// ============================================================ binary64 kernel
+// ============================================ float32 DD(r) with weights / ravg
+// Code 1 adds a weight per counted pair; here the pair weight is w_i * w_j
+// (float32 product of the float32 weights, or 1) and the mean separation sums
+// r * weight with r = sqrt(d2) in float32.  Sums are binary64: each lane keeps,
+// per bin, a byte count and float32 partial sums of at most 63 terms (so each
+// partial's relative rounding error stays below 63 u32 for same-sign terms);
+// the 64th term moves the partials to the warp's binary64 accumulators.
+struct AccW {
+    unsigned char *cnt;  // this warp's byte-count plane + lane (stride 32 per bin)
+    float *wp, *rp;      // float32 partial planes + lane (stride 32 per bin)
+    double *acc;         // this warp's binary64 accumulators: [bin][count(u64), w, r w]
+    bool want_r;
+};
+
+__device__ __forceinline__ float sqrt_approx(float v)
+{
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+    return r;
+}
+
+__device__ __forceinline__ void acc_pair(const AccW &A, uint32_t row, float pw, float rw)
+{
+    unsigned char *cp = A.cnt + row * 32u;
+    float *wp = A.wp + row * 32u;
+    const unsigned c = (unsigned)*cp + 1u;
+    const float ws = *wp + pw;
+    if (c == XIW_FLUSH) {
+        atomicAdd(reinterpret_cast<unsigned long long *>(A.acc + row * 3u), (u64)XIW_FLUSH);
+        atomicAdd(A.acc + row * 3u + 1u, (double)ws);
+        if (A.want_r) {
+            float *rp = A.rp + row * 32u;
+            atomicAdd(A.acc + row * 3u + 2u, (double)(*rp + rw));
+            *rp = 0.0f;
+        }
+        *cp = 0;
+        *wp = 0.0f;
+    } else {
+        *cp = (unsigned char)c;
+        *wp = ws;
+        if (A.want_r) {
+            float *rp = A.rp + row * 32u;
+            *rp += rw;
+        }
+    }
+}
+
+// Flagged table cell, weighted kernel: as resolve_pair, but the pair's weight
+// and r * weight go with it to its true bin.
+__device__ __forceinline__ int resolve_pair_w(const unsigned char *smem, const Sweep32 &S,
+                                              const AccW &A, uint32_t e, float d2, float pw, int i,
+                                              int jg)
+{
+    const float *T = reinterpret_cast<const float *>(smem + THR_OFF);
+    int c = (int)(e & 0x7fu) * 2;
+    while (c < S.nthr && T[c] <= d2)
+        ++c;
+    int row;
+    int re = 0;
+    if (!(c & 1)) {
+        row = (c >= 2 && c <= 2 * S.nb) ? (c - 2) >> 1 : -1;
+    } else {
+        row = recheck64(reinterpret_cast<const double *>(smem + E2_OFF), S.nb, S.pa, S.pb, i, jg,
+                        S.Sx, S.Sy, S.Sz);
+        re = 1;
+    }
+    if (row >= 0)
+        acc_pair(A, (uint32_t)row, pw, sqrt_approx(d2) * pw);
+    return re;
+}
+
+template <int I, bool TRI, bool EVALS>
+__device__ __forceinline__ void sweep32w(unsigned char *smem, const Sweep32 &S, const AccW &A,
+                                         bool weighted, int jlo, int jhi, int jj, u64 XH, u64 YH,
+                                         u64 ZH, u64 WH, int i, bool vi, u64 &n_eval, u64 &n_rck)
+{
+    const float qnan = __int_as_float(0x7fc00000);
+    const int jstart = jlo & ~1;
+    constexpr int JS = 64 / I;
+    const int nit = (jhi - jstart + 2 * JS - 1) / (2 * JS);
+    const unsigned char *p = smem + TX_OFF + (jstart + 2 * jj) * 4;
+    const unsigned char *pw8 = smem + XIW_W_OFF + (jstart + 2 * jj) * 4;
+    const uint32_t nbu = (uint32_t)S.nb;
+    int jA = jstart + 2 * jj;
+    for (int it = 0; it < nit; ++it, p += 8 * JS, pw8 += 8 * JS, jA += 2 * JS) {
+        const u64 xA = *reinterpret_cast<const u64 *>(p);
+        const u64 yA = *reinterpret_cast<const u64 *>(p + TSTRIDE);
+        const u64 zA = *reinterpret_cast<const u64 *>(p + 2 * TSTRIDE);
+        const u64 xB = *reinterpret_cast<const u64 *>(p + 4 * JS);
+        const u64 yB = *reinterpret_cast<const u64 *>(p + 4 * JS + TSTRIDE);
+        const u64 zB = *reinterpret_cast<const u64 *>(p + 4 * JS + 2 * TSTRIDE);
+        u64 dx = fsub2(xA, XH), dy = fsub2(yA, YH), dz = fsub2(zA, ZH);
+        const u64 dA = ffma2(dz, dz, ffma2(dy, dy, fmul2(dx, dx)));
+        dx = fsub2(xB, XH);
+        dy = fsub2(yB, YH);
+        dz = fsub2(zB, ZH);
+        const u64 dB = ffma2(dz, dz, ffma2(dy, dy, fmul2(dx, dx)));
+        float pa0 = 1.0f, pa1 = 1.0f, pb0 = 1.0f, pb1 = 1.0f;
+        if (weighted) {
+            const u64 wA = fmul2(*reinterpret_cast<const u64 *>(pw8), WH);
+            const u64 wB = fmul2(*reinterpret_cast<const u64 *>(pw8 + 4 * JS), WH);
+            unpack2(wA, pa0, pa1);
+            unpack2(wB, pb0, pb1);
+        }
+        float a0, a1, b0, b1;
+        unpack2(dA, a0, a1);
+        unpack2(dB, b0, b1);
+        const int gA = S.t0 + jA, gB = gA + JS;
+        bool la0 = true, la1 = true, lb0 = true, lb1 = true;
+        if (TRI) {
+            la0 = gA > i;
+            la1 = gA + 1 > i;
+            lb0 = gB > i;
+            lb1 = gB + 1 > i;
+            a0 = la0 ? a0 : qnan;
+            a1 = la1 ? a1 : qnan;
+            b0 = lb0 ? b0 : qnan;
+            b1 = lb1 ? b1 : qnan;
+        }
+        if (EVALS) {
+            const int jB = jA + JS;
+            n_eval += (u64)((vi && jA >= jlo && jA < jhi && la0) +
+                            (vi && jA + 1 >= jlo && jA + 1 < jhi && la1) +
+                            (vi && jB >= jlo && jB < jhi && lb0) +
+                            (vi && jB + 1 >= jlo && jB + 1 < jhi && lb1));
+        }
+        const uint32_t ea0 = lut_byte(smem, S.u0, S.shift, S.lut_last, a0);
+        const uint32_t ea1 = lut_byte(smem, S.u0, S.shift, S.lut_last, a1);
+        const uint32_t eb0 = lut_byte(smem, S.u0, S.shift, S.lut_last, b0);
+        const uint32_t eb1 = lut_byte(smem, S.u0, S.shift, S.lut_last, b1);
+        // flagged entries -> dummy row here, settled below
+        acc_pair(A, min(ea0, nbu), pa0, sqrt_approx(a0) * pa0);
+        acc_pair(A, min(ea1, nbu), pa1, sqrt_approx(a1) * pa1);
+        acc_pair(A, min(eb0, nbu), pb0, sqrt_approx(b0) * pb0);
+        acc_pair(A, min(eb1, nbu), pb1, sqrt_approx(b1) * pb1);
+        if (__any_sync(FULL, (ea0 | ea1 | eb0 | eb1) & LUT_FLAG)) {
+            if (ea0 & LUT_FLAG)
+                n_rck += resolve_pair_w(smem, S, A, ea0, a0, pa0, i, gA);
+            if (ea1 & LUT_FLAG)
+                n_rck += resolve_pair_w(smem, S, A, ea1, a1, pa1, i, gA + 1);
+            if (eb0 & LUT_FLAG)
+                n_rck += resolve_pair_w(smem, S, A, eb0, b0, pb0, i, gB);
+            if (eb1 & LUT_FLAG)
+                n_rck += resolve_pair_w(smem, S, A, eb1, b1, pb1, i, gB + 1);
+        }
+    }
+}
+
 template <int I, bool EVALS>
+__global__ void __launch_bounds__(THREADS, 2) k_xi32w(const __grid_constant__ PairParams P)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int nb = P.nbins, nr = nb + 1;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
+    volatile int *s_item = reinterpret_cast<volatile int *>(smem + 8);
+    const float *tz = reinterpret_cast<const float *>(smem + TX_OFF + 2 * TSTRIDE);
+    float *thr = reinterpret_cast<float *>(smem + THR_OFF);
+    double *E2 = reinterpret_cast<double *>(smem + E2_OFF);
+    double *acc = reinterpret_cast<double *>(smem + XIW_ACC_OFF);  // [warp][bin][3]
+    unsigned char *cplane = smem + P.rows_off;                      // [warp][bin][lane] bytes
+    const int cbytes = align_up(WARPS * nr * 32, 128);
+    float *wplane = reinterpret_cast<float *>(smem + P.rows_off + cbytes);  // [warp][bin][lane]
+    float *rplane = wplane + WARPS * nr * 32;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    for (int q = tid; q < P.lut_n; q += THREADS)
+        smem[LUT_OFF + q] = P.lut[q];
+    for (int q = tid; q < P.nthr; q += THREADS)
+        thr[q] = P.thr[q];
+    for (int q = tid; q <= nb; q += THREADS)
+        E2[q] = P.E2[q];
+    for (int q = tid; q < WARPS * nr * 3; q += THREADS)
+        acc[q] = 0.0;  // the count words' bit pattern 0 is also the u64 zero
+    for (int q = tid; q < WARPS * nr * 32; q += THREADS) {
+        cplane[q] = 0;
+        wplane[q] = 0.0f;
+        rplane[q] = 0.0f;
+    }
+    if (tid == 0) {
+        mbar_init(bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    AccW A;
+    A.cnt = cplane + warp * nr * 32 + lane;
+    A.wp = wplane + warp * nr * 32 + lane;
+    A.rp = rplane + warp * nr * 32 + lane;
+    A.acc = acc + warp * nr * 3;
+    A.want_r = P.want_r != 0;
+    const bool weighted = P.weighted != 0;
+    const int ii = lane % I, jj = lane / I;
+    Sweep32 S;
+    S.nb = nb;
+    S.u0 = P.u0;
+    S.lut_last = (uint32_t)(P.lut_n - 1);
+    S.shift = P.lut_shift;
+    S.nthr = P.nthr;
+    S.pa = P.A.pos64;
+    S.pb = P.B.pos64;
+    unsigned phase = 0;
+    u64 n_eval = 0, n_rck = 0;
+    bool aborted = false;
+    const float qnan = __int_as_float(0x7fc00000);
+
+    for (;;) {
+        if (tid == 0)
+            *s_item = (int)atomicAdd(P.item_counter, 1u);
+        __syncthreads();
+        const int item = *s_item;
+        __syncthreads();
+        if (item >= P.n_items)
+            break;
+        Item it;
+        if (!decode_item(P, item, it))
+            continue;
+        if (tid == 0)
+            atomicAdd(&P.diag[0], 1ull);
+        const float dzw = __fadd_ru(__double2float_ru(it.dzmax), P.zslack);
+        const float Sxf = __double2float_rn(it.Sx), Syf = __double2float_rn(it.Sy);
+        S.Sx = it.Sx;
+        S.Sy = it.Sy;
+        const int nchunks = (it.a1 - it.a0 + I - 1) / I;
+
+        for (int t0 = it.b0; t0 < it.b1; t0 += TILE32) {
+            const int nt = min(TILE32, it.b1 - t0);
+            if (!stage_tiles32(smem, P.B, t0, nt, bar, phase, P.err, weighted)) {
+                aborted = true;
+                break;
+            }
+            S.t0 = t0;
+            const float zt_lo = tz[0];
+            float zt_hi = tz[nt - 1];
+            if (isnan(zt_hi))
+                zt_hi = INFINITY;
+            auto zkey = [&](int q) { return tz[q]; };
+            int lo_prev[3] = {0, 0, 0}, hi_prev[3] = {0, 0, 0};
+
+            for (int c = warp; c < nchunks; c += WARPS) {
+                const int ib = it.a0 + c * I;
+                const int nvi = min(I, it.a1 - ib);
+                const int i = ib + ii;
+                float xi = qnan, yi = qnan, zi = qnan, wi = 1.0f;
+                if (ii < nvi) {
+                    xi = P.A.xs[i];
+                    yi = P.A.ys[i];
+                    zi = P.A.zs[i];
+                    if (weighted)
+                        wi = P.A.ws[i];
+                }
+                const bool vi = !isnan(xi);
+                const float xh = __fsub_rn(xi, Sxf), yh = __fsub_rn(yi, Syf);
+                const u64 XH = pack2(xh, xh), YH = pack2(yh, yh), WH = pack2(wi, wi);
+                const float zlo = __shfl_sync(FULL, zi, 0);
+                float zhi = zi;
+#pragma unroll
+                for (int o = 1; o < I; o <<= 1) {
+                    const float t = __shfl_xor_sync(FULL, zhi, o);
+                    zhi = (isnan(zhi) || t > zhi) ? t : zhi;
+                }
+                if (isnan(zlo))
+                    continue;
+#pragma unroll
+                for (int kk = 0; kk < 3; ++kk) {
+                    const int k = kk - 1;
+                    if (k < it.kmin || k > it.kmax)
+                        continue;
+                    const float kz = (float)k * P.boxf[2];
+                    const float wlo = zlo - kz - dzw, whi = zhi - kz + dzw;
+                    if (whi < zt_lo || wlo > zt_hi)
+                        continue;
+                    int jlo = warp_bound_from(zkey, lo_prev[kk], nt, wlo, false, lane);
+                    const int jhi = warp_bound_from(zkey, max(hi_prev[kk], jlo), nt, whi, true, lane);
+                    lo_prev[kk] = jlo;
+                    hi_prev[kk] = jhi;
+                    const bool tri = it.self && k == 0;
+                    if (tri)
+                        jlo = max(jlo, ib + 1 - t0);
+                    if (jlo >= jhi)
+                        continue;
+                    const float zh = __fsub_rn(zi, kz);
+                    const u64 ZH = pack2(zh, zh);
+                    S.Sz = k == 0 ? 0.0 : (k > 0 ? P.g.box[2] : -P.g.box[2]);
+                    if (tri)
+                        sweep32w<I, true, EVALS>(smem, S, A, weighted, jlo, jhi, jj, XH, YH, ZH, WH,
+                                                 i, vi, n_eval, n_rck);
+                    else
+                        sweep32w<I, false, EVALS>(smem, S, A, weighted, jlo, jhi, jj, XH, YH, ZH,
+                                                  WH, i, vi, n_eval, n_rck);
+                }
+            }
+        }
+        if (aborted)
+            break;
+    }
+
+    __syncthreads();
+    for (int bn = tid; bn < nb; bn += THREADS) {
+        u64 cnt = 0;
+        double ws = 0.0, rs = 0.0;
+        for (int w = 0; w < WARPS; ++w) {
+            const double *aw = acc + (w * nr + bn) * 3;
+            cnt += *reinterpret_cast<const u64 *>(aw);
+            ws += aw[1];
+            rs += aw[2];
+            const int base = (w * nr + bn) * 32;
+            for (int l = 0; l < 32; ++l) {
+                cnt += cplane[base + l];
+                ws += (double)wplane[base + l];
+                rs += (double)rplane[base + l];
+            }
+        }
+        if (cnt) {
+            atomicAdd(&P.hist[bn], cnt);
+            atomicAdd(&P.wsum[bn], ws);
+            if (P.want_r)
+                atomicAdd(&P.rsum[bn], rs);
+        }
+    }
+    n_eval = warp_sum_u64(n_eval);
+    n_rck = warp_sum_u64(n_rck);
+    if (lane == 0) {
+        if (n_eval)
+            atomicAdd(&P.diag[1], n_eval);
+        if (n_rck)
+            atomicAdd(&P.diag[2], n_rck);
+    }
+}
+
+// ============================================================ binary64 kernel
+template <int I, bool EVALS, bool WACC>
 __global__ void __launch_bounds__(THREADS) k_xi64(const __grid_constant__ PairParams P)
 {
     constexpr int J = 32 / I;
@@ -659,12 +1010,16 @@ __global__ void __launch_bounds__(THREADS) k_xi64(const __grid_constant__ PairPa
     double4_32a *tile = reinterpret_cast<double4_32a *>(smem + L.tile);
     double *E2 = reinterpret_cast<double *>(smem + L.e2);
     uint32_t *hist = reinterpret_cast<uint32_t *>(smem + L.hist);
+    double *acc = WACC ? reinterpret_cast<double *>(smem + P.acc_off) : nullptr;  // [warp][bin][2]
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     for (int q = tid; q <= nb; q += THREADS)
         E2[q] = P.E2[q];
     for (int q = tid; q < WARPS * (nb + 1) * 32; q += THREADS)
         hist[q] = 0u;
+    if (WACC)
+        for (int q = tid; q < WARPS * nb * 2; q += THREADS)
+            acc[q] = 0.0;
     if (tid == 0) {
         mbar_init(bar, 1);
         fence_mbar_init();
@@ -744,8 +1099,16 @@ __global__ void __launch_bounds__(THREADS) k_xi64(const __grid_constant__ PairPa
                         if (!live)
                             r2 = qnan;
                         const int kb = bin_f64(r2, E2, nb);
-                        if (kb >= 0)
+                        if (kb >= 0) {
                             hl[kb * 32] += 1u;
+                            if (WACC) {  // Code 1's weight; the oracle's product and sqrt
+                                double *aw = acc + (warp * nb + kb) * 2;
+                                const double pw = P.weighted ? __dmul_rn(pi.w, pj.w) : 1.0;
+                                atomicAdd(aw, pw);
+                                if (P.want_r)
+                                    atomicAdd(aw + 1, __dmul_rn(__dsqrt_rn(r2), pw));
+                            }
+                        }
                     }
                 }
                 if (pending > (1u << 30)) {
@@ -761,11 +1124,23 @@ __global__ void __launch_bounds__(THREADS) k_xi64(const __grid_constant__ PairPa
     __syncthreads();
     for (int bn = tid; bn < nb; bn += THREADS) {
         u64 sum = 0;
-        for (int w = 0; w < WARPS; ++w)
+        double ws = 0.0, rs = 0.0;
+        for (int w = 0; w < WARPS; ++w) {
             for (int l = 0; l < 32; ++l)
                 sum += hist[(w * (nb + 1) + bn) * 32 + l];
-        if (sum)
+            if (WACC) {
+                ws += acc[(w * nb + bn) * 2];
+                rs += acc[(w * nb + bn) * 2 + 1];
+            }
+        }
+        if (sum) {
             atomicAdd(&P.hist[bn], sum);
+            if (WACC) {
+                atomicAdd(&P.wsum[bn], ws);
+                if (P.want_r)
+                    atomicAdd(&P.rsum[bn], rs);
+            }
+        }
     }
     n_eval = warp_sum_u64(n_eval);
     if (lane == 0 && n_eval)
@@ -841,6 +1216,8 @@ struct SweepRP {
     int shift, nthr;
     uint32_t hbase, rowb;  // shared address of this warp's histogram copy; bytes per rp row
     float pband;
+    double *acc;           // weighted sums: this copy's binary64 [slot][w, r w] (or NULL)
+    bool weighted, want_r;
     const double4_32a *pa, *pb;
     double Sx, Sy, Sz;
 };
@@ -848,9 +1225,18 @@ struct SweepRP {
 // A pair whose rp table cell is flagged or whose t is near a pi edge: settle
 // both decisions exactly, undo the main path's increment (at addr_main) and
 // add the pair to its true slot.  Returns 1 if binary64 was needed.
+// Binary64 accumulation of one counted pair's weight and rp * weight.
+__device__ __forceinline__ void acc_rppi(const SweepRP &S, int slot, float pw, float rp2)
+{
+    atomicAdd(S.acc + 2 * slot, (double)pw);
+    if (S.want_r)
+        atomicAdd(S.acc + 2 * slot + 1, (double)(sqrt_approx(rp2) * pw));
+}
+
+template <bool WACC>
 __device__ __forceinline__ int resolve_rppi(const unsigned char *smem, const SweepRP &S, uint32_t e,
                                             float rp2, uint32_t m_main, bool pflag,
-                                            uint32_t addr_main, int i, int jg)
+                                            uint32_t addr_main, int i, int jg, float pw)
 {
     int k, re = 0;
     if (e & LUT_FLAG) {
@@ -879,8 +1265,11 @@ __device__ __forceinline__ int resolve_rppi(const unsigned char *smem, const Swe
         m = m_main < (uint32_t)S.npi ? (int)m_main : -1;
     }
     red_shared(addr_main, 0xffffffffu);
-    if (m >= 0)
+    if (m >= 0) {
         red_shared(S.hbase + (uint32_t)k * S.rowb + (uint32_t)m * 4u, 1u);
+        if (WACC)
+            acc_rppi(S, k * (S.npi + 1) + m, pw, rp2);
+    }
     return re;
 }
 
@@ -888,10 +1277,10 @@ __device__ __forceinline__ int resolve_rppi(const unsigned char *smem, const Swe
 // rp^2 and t' = |dz| * s - 1/2 in packed float32, the rp table byte, the pi
 // index from the rounding, one shared atomic into the warp's 2-D histogram
 // copy; one warp-uniform check for flagged pairs per iteration.
-template <int I, bool TRI, bool EVALS, bool VERIFY>
+template <int I, bool TRI, bool EVALS, bool VERIFY, bool WACC>
 __device__ __forceinline__ void sweep_rppi32(unsigned char *smem, const SweepRP &S, int jlo, int jhi,
-                                             int jj, u64 XH, u64 YH, u64 ZH, u64 SC, int i, bool vi,
-                                             u64 &n_eval, u64 &n_rck, u64 &n_viol)
+                                             int jj, u64 XH, u64 YH, u64 ZH, u64 SC, u64 WH, int i,
+                                             bool vi, u64 &n_eval, u64 &n_rck, u64 &n_viol)
 {
     const float qnan = __int_as_float(0x7fc00000);
     const u64 MH = pack2(-0.5f, -0.5f), MG = pack2(PI_MAGIC, PI_MAGIC);
@@ -961,15 +1350,32 @@ __device__ __forceinline__ void sweep_rppi32(unsigned char *smem, const SweepRP 
         red_shared(hb1, 1u);
         const bool pa0 = fabsf(fa0) > S.pband, pa1 = fabsf(fa1) > S.pband;
         const bool pb0 = fabsf(fb0) > S.pband, pb1 = fabsf(fb1) > S.pband;
+        float wa0 = 1.0f, wa1 = 1.0f, wb0 = 1.0f, wb1 = 1.0f;
+        if (WACC) {
+            if (S.weighted) {
+                const unsigned char *pw8 = smem + XIW_W_OFF + (p - (smem + TX_OFF));
+                unpack2(fmul2(*reinterpret_cast<const u64 *>(pw8), WH), wa0, wa1);
+                unpack2(fmul2(*reinterpret_cast<const u64 *>(pw8 + 4 * JS), WH), wb0, wb1);
+            }
+            // pairs settled by the float32 path; flagged ones are added when resolved
+            if (!(ea0 & LUT_FLAG) && !pa0 && ea0 < nbu && ma0 < npiu)
+                acc_rppi(S, (int)(ea0 * (npiu + 1) + ma0), wa0, a0);
+            if (!(ea1 & LUT_FLAG) && !pa1 && ea1 < nbu && ma1 < npiu)
+                acc_rppi(S, (int)(ea1 * (npiu + 1) + ma1), wa1, a1);
+            if (!(eb0 & LUT_FLAG) && !pb0 && eb0 < nbu && mb0 < npiu)
+                acc_rppi(S, (int)(eb0 * (npiu + 1) + mb0), wb0, b0);
+            if (!(eb1 & LUT_FLAG) && !pb1 && eb1 < nbu && mb1 < npiu)
+                acc_rppi(S, (int)(eb1 * (npiu + 1) + mb1), wb1, b1);
+        }
         if (__any_sync(FULL, ((ea0 | ea1 | eb0 | eb1) & LUT_FLAG) || pa0 || pa1 || pb0 || pb1)) {
             if ((ea0 & LUT_FLAG) || pa0)
-                n_rck += resolve_rppi(smem, S, ea0, a0, ma0, pa0, ha0, i, gA);
+                n_rck += resolve_rppi<WACC>(smem, S, ea0, a0, ma0, pa0, ha0, i, gA, wa0);
             if ((ea1 & LUT_FLAG) || pa1)
-                n_rck += resolve_rppi(smem, S, ea1, a1, ma1, pa1, ha1, i, gA + 1);
+                n_rck += resolve_rppi<WACC>(smem, S, ea1, a1, ma1, pa1, ha1, i, gA + 1, wa1);
             if ((eb0 & LUT_FLAG) || pb0)
-                n_rck += resolve_rppi(smem, S, eb0, b0, mb0, pb0, hb0, i, gB);
+                n_rck += resolve_rppi<WACC>(smem, S, eb0, b0, mb0, pb0, hb0, i, gB, wb0);
             if ((eb1 & LUT_FLAG) || pb1)
-                n_rck += resolve_rppi(smem, S, eb1, b1, mb1, pb1, hb1, i, gB + 1);
+                n_rck += resolve_rppi<WACC>(smem, S, eb1, b1, mb1, pb1, hb1, i, gB + 1, wb1);
         }
         if (VERIFY) {
             const float *T = reinterpret_cast<const float *>(smem + THR_OFF);
@@ -1004,22 +1410,35 @@ __device__ void flush_rppi(uint32_t *hc, int nb, int npi, unsigned long long *gh
     }
 }
 
-// All copies of the CTA's histograms -> global (after the last __syncthreads).
-__device__ void merge_rppi(const uint32_t *hist, int hcopies, int nb, int npi,
-                           unsigned long long *ghist)
+// All copies of the CTA's histograms (and binary64 sums, if acc) -> global
+// (after the last __syncthreads).
+__device__ void merge_rppi(const PairParams &P, const uint32_t *hist, const double *acc)
 {
-    const int row = npi + 1, copy = (nb + 1) * row;
+    const int nb = P.nbins, npi = P.npibins, row = npi + 1, copy = (nb + 1) * row;
     for (int s = threadIdx.x; s < nb * npi; s += THREADS) {
         const int k = s / npi, m = s - k * npi;
         long long sum = 0;
-        for (int c = 0; c < hcopies; ++c)
-            sum += (int)hist[c * copy + k * row + m];
-        if (sum)
-            atomicAdd(&ghist[s], (u64)sum);
+        double ws = 0.0, rs = 0.0;
+        for (int c = 0; c < P.hcopies; ++c) {
+            const int q = c * copy + k * row + m;
+            sum += (int)hist[q];
+            if (acc) {
+                ws += acc[2 * q];
+                rs += acc[2 * q + 1];
+            }
+        }
+        if (sum) {
+            atomicAdd(&P.hist[s], (u64)sum);
+            if (acc) {
+                atomicAdd(&P.wsum[s], ws);
+                if (P.want_r)
+                    atomicAdd(&P.rsum[s], rs);
+            }
+        }
     }
 }
 
-template <int I, bool EVALS, bool VERIFY>
+template <int I, bool EVALS, bool VERIFY, bool WACC>
 __global__ void __launch_bounds__(THREADS, 3) k_rppi32(const __grid_constant__ PairParams P)
 {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -1031,6 +1450,7 @@ __global__ void __launch_bounds__(THREADS, 3) k_rppi32(const __grid_constant__ P
     double *E2 = reinterpret_cast<double *>(smem + E2_OFF);
     double *Pe = reinterpret_cast<double *>(smem + RPPI_P_OFF);
     uint32_t *hist = reinterpret_cast<uint32_t *>(smem + P.hist_off);
+    double *acc = WACC ? reinterpret_cast<double *>(smem + P.acc_off) : nullptr;
     const int copy = (nb + 1) * (npi + 1);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -1044,6 +1464,9 @@ __global__ void __launch_bounds__(THREADS, 3) k_rppi32(const __grid_constant__ P
         Pe[q] = P.P[q];
     for (int q = tid; q < P.hcopies * copy; q += THREADS)
         hist[q] = 0u;
+    if (WACC)
+        for (int q = tid; q < 2 * P.hcopies * copy; q += THREADS)
+            acc[q] = 0.0;
     if (tid == 0) {
         mbar_init(bar, 1);
         fence_mbar_init();
@@ -1064,6 +1487,9 @@ __global__ void __launch_bounds__(THREADS, 3) k_rppi32(const __grid_constant__ P
     S.pband = P.pband;
     S.pa = P.A.pos64;
     S.pb = P.B.pos64;
+    S.acc = WACC ? acc + 2 * (warp % P.hcopies) * copy : nullptr;
+    S.weighted = WACC && P.weighted;
+    S.want_r = WACC && P.want_r;
     const u64 SC = pack2(P.pscale, P.pscale);
     const unsigned flush_at = (1u << 30) / (unsigned)(WARPS / P.hcopies);
     unsigned phase = 0;
@@ -1093,7 +1519,7 @@ __global__ void __launch_bounds__(THREADS, 3) k_rppi32(const __grid_constant__ P
 
         for (int t0 = it.b0; t0 < it.b1; t0 += TILE32) {
             const int nt = min(TILE32, it.b1 - t0);
-            if (!stage_tiles32(smem, P.B, t0, nt, bar, phase, P.err)) {
+            if (!stage_tiles32(smem, P.B, t0, nt, bar, phase, P.err, S.weighted)) {
                 aborted = true;
                 break;
             }
@@ -1109,15 +1535,17 @@ __global__ void __launch_bounds__(THREADS, 3) k_rppi32(const __grid_constant__ P
                 const int ib = it.a0 + c * I;
                 const int nvi = min(I, it.a1 - ib);
                 const int i = ib + ii;
-                float xi = qnan, yi = qnan, zi = qnan;
+                float xi = qnan, yi = qnan, zi = qnan, wi = 1.0f;
                 if (ii < nvi) {
                     xi = P.A.xs[i];
                     yi = P.A.ys[i];
                     zi = P.A.zs[i];
+                    if (S.weighted)
+                        wi = P.A.ws[i];
                 }
                 const bool vi = !isnan(xi);
                 const float xh = __fsub_rn(xi, Sxf), yh = __fsub_rn(yi, Syf);
-                const u64 XH = pack2(xh, xh), YH = pack2(yh, yh);
+                const u64 XH = pack2(xh, xh), YH = pack2(yh, yh), WH = pack2(wi, wi);
                 const float zlo = __shfl_sync(FULL, zi, 0);
                 float zhi = zi;
 #pragma unroll
@@ -1151,11 +1579,12 @@ __global__ void __launch_bounds__(THREADS, 3) k_rppi32(const __grid_constant__ P
                     const u64 ZH = pack2(zh, zh);
                     S.Sz = k == 0 ? 0.0 : (k > 0 ? P.g.box[2] : -P.g.box[2]);
                     if (tri)
-                        sweep_rppi32<I, true, EVALS, VERIFY>(smem, S, jlo, jhi, jj, XH, YH, ZH, SC, i,
-                                                          vi, n_eval, n_rck, n_viol);
+                        sweep_rppi32<I, true, EVALS, VERIFY, WACC>(smem, S, jlo, jhi, jj, XH, YH, ZH,
+                                                                SC, WH, i, vi, n_eval, n_rck, n_viol);
                     else
-                        sweep_rppi32<I, false, EVALS, VERIFY>(smem, S, jlo, jhi, jj, XH, YH, ZH, SC,
-                                                           i, vi, n_eval, n_rck, n_viol);
+                        sweep_rppi32<I, false, EVALS, VERIFY, WACC>(smem, S, jlo, jhi, jj, XH, YH, ZH,
+                                                                 SC, WH, i, vi, n_eval, n_rck,
+                                                                 n_viol);
                 }
                 if (pending > flush_at) {  // keep every shared u32 count far from overflow
                     __syncwarp();
@@ -1169,7 +1598,7 @@ __global__ void __launch_bounds__(THREADS, 3) k_rppi32(const __grid_constant__ P
     }
 
     __syncthreads();
-    merge_rppi(hist, P.hcopies, nb, npi, P.hist);
+    merge_rppi(P, hist, acc);
     n_eval = warp_sum_u64(n_eval);
     n_rck = warp_sum_u64(n_rck);
     n_viol = warp_sum_u64(n_viol);
@@ -1184,7 +1613,7 @@ __global__ void __launch_bounds__(THREADS, 3) k_rppi32(const __grid_constant__ P
 }
 
 // Binary64 DD(rp, pi): canonical rp^2 and |dz|, exact edge compares.
-template <int I, bool EVALS>
+template <int I, bool EVALS, bool WACC>
 __global__ void __launch_bounds__(THREADS) k_rppi64(const __grid_constant__ PairParams P)
 {
     constexpr int J = 32 / I;
@@ -1197,6 +1626,7 @@ __global__ void __launch_bounds__(THREADS) k_rppi64(const __grid_constant__ Pair
     double *E2 = reinterpret_cast<double *>(smem + L.e2);
     double *Pe = reinterpret_cast<double *>(smem + L.p);
     uint32_t *hist = reinterpret_cast<uint32_t *>(smem + P.hist_off);
+    double *acc = WACC ? reinterpret_cast<double *>(smem + P.acc_off) : nullptr;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     for (int q = tid; q <= nb; q += THREADS)
@@ -1205,6 +1635,9 @@ __global__ void __launch_bounds__(THREADS) k_rppi64(const __grid_constant__ Pair
         Pe[q] = P.P[q];
     for (int q = tid; q < P.hcopies * copy; q += THREADS)
         hist[q] = 0u;
+    if (WACC)
+        for (int q = tid; q < 2 * P.hcopies * copy; q += THREADS)
+            acc[q] = 0.0;
     if (tid == 0) {
         mbar_init(bar, 1);
         fence_mbar_init();
@@ -1212,6 +1645,7 @@ __global__ void __launch_bounds__(THREADS) k_rppi64(const __grid_constant__ Pair
     __syncthreads();
 
     uint32_t *hc = hist + (warp % P.hcopies) * copy;
+    double *ac = WACC ? acc + 2 * (warp % P.hcopies) * copy : nullptr;
     const unsigned flush_at = (1u << 30) / (unsigned)(WARPS / P.hcopies);
     const int ii = lane % I, jj = lane / I;
     unsigned phase = 0;
@@ -1292,8 +1726,16 @@ __global__ void __launch_bounds__(THREADS) k_rppi64(const __grid_constant__ Pair
                         const int kb = bin_f64(rp2, E2, nb);
                         if (kb >= 0) {
                             const int m = bin_f64(fabs(dz), Pe, npi);
-                            if (m >= 0)
+                            if (m >= 0) {
                                 atomicAdd(&hc[kb * row + m], 1u);
+                                if (WACC) {  // Code 1's weight; the oracle's product and sqrt
+                                    const double pw = P.weighted ? __dmul_rn(pi.w, pj.w) : 1.0;
+                                    atomicAdd(ac + 2 * (kb * row + m), pw);
+                                    if (P.want_r)
+                                        atomicAdd(ac + 2 * (kb * row + m) + 1,
+                                                  __dmul_rn(__dsqrt_rn(rp2), pw));
+                                }
+                            }
                         }
                     }
                 }
@@ -1309,7 +1751,7 @@ __global__ void __launch_bounds__(THREADS) k_rppi64(const __grid_constant__ Pair
     }
 
     __syncthreads();
-    merge_rppi(hist, P.hcopies, nb, npi, P.hist);
+    merge_rppi(P, hist, acc);
     n_eval = warp_sum_u64(n_eval);
     if (lane == 0 && n_eval)
         atomicAdd(&P.diag[1], n_eval);
@@ -1386,28 +1828,42 @@ cudaError_t launch_persistent(K kern, const PairParams &P, PairLaunch &L, int sm
 cudaError_t launch_pairs(const PairParams &P, PairLaunch &L, int sms, cudaStream_t st)
 {
     if (P.kind == 1) {
-        if (L.f64)
-            return L.evals ? launch_persistent(k_rppi64<8, true>, P, L, sms, st)
-                           : launch_persistent(k_rppi64<8, false>, P, L, sms, st);
+        if (L.f64) {
+            if (P.wacc)
+                return L.evals ? launch_persistent(k_rppi64<8, true, true>, P, L, sms, st)
+                               : launch_persistent(k_rppi64<8, false, true>, P, L, sms, st);
+            return L.evals ? launch_persistent(k_rppi64<8, true, false>, P, L, sms, st)
+                           : launch_persistent(k_rppi64<8, false, false>, P, L, sms, st);
+        }
+        if (P.wacc)
+            return L.evals ? launch_persistent(k_rppi32<16, true, false, true>, P, L, sms, st)
+                           : launch_persistent(k_rppi32<16, false, false, true>, P, L, sms, st);
         if (L.verify)
-            return launch_persistent(k_rppi32<8, true, true>, P, L, sms, st);
+            return launch_persistent(k_rppi32<8, true, true, false>, P, L, sms, st);
         switch (L.chunk) {
         case 16:
-            return L.evals ? launch_persistent(k_rppi32<16, true, false>, P, L, sms, st)
-                           : launch_persistent(k_rppi32<16, false, false>, P, L, sms, st);
+            return L.evals ? launch_persistent(k_rppi32<16, true, false, false>, P, L, sms, st)
+                           : launch_persistent(k_rppi32<16, false, false, false>, P, L, sms, st);
         case 32:
-            return L.evals ? launch_persistent(k_rppi32<32, true, false>, P, L, sms, st)
-                           : launch_persistent(k_rppi32<32, false, false>, P, L, sms, st);
+            return L.evals ? launch_persistent(k_rppi32<32, true, false, false>, P, L, sms, st)
+                           : launch_persistent(k_rppi32<32, false, false, false>, P, L, sms, st);
         default:
-            return L.evals ? launch_persistent(k_rppi32<8, true, false>, P, L, sms, st)
-                           : launch_persistent(k_rppi32<8, false, false>, P, L, sms, st);
+            return L.evals ? launch_persistent(k_rppi32<8, true, false, false>, P, L, sms, st)
+                           : launch_persistent(k_rppi32<8, false, false, false>, P, L, sms, st);
         }
     }
     if (P.kind != 0)
         return cudaErrorNotSupported;
-    if (L.f64)
-        return L.evals ? launch_persistent(k_xi64<8, true>, P, L, sms, st)
-                       : launch_persistent(k_xi64<8, false>, P, L, sms, st);
+    if (L.f64) {
+        if (P.wacc)
+            return L.evals ? launch_persistent(k_xi64<8, true, true>, P, L, sms, st)
+                           : launch_persistent(k_xi64<8, false, true>, P, L, sms, st);
+        return L.evals ? launch_persistent(k_xi64<8, true, false>, P, L, sms, st)
+                       : launch_persistent(k_xi64<8, false, false>, P, L, sms, st);
+    }
+    if (P.wacc)
+        return L.evals ? launch_persistent(k_xi32w<16, true>, P, L, sms, st)
+                       : launch_persistent(k_xi32w<16, false>, P, L, sms, st);
     if (L.verify)
         return launch_persistent(k_xi32<8, true, true>, P, L, sms, st);
     switch (L.chunk) {
