@@ -15,7 +15,10 @@ ordered pairs the histogram holds (P_cnt) per second.
          the D2H of the histogram happen inside the timed call.
   roofline  the pair kernel's pair evaluations (diagnostic counter, separate
          run) x 7 FP32 instructions each, over its event-timed duration,
-         against SMs x 128 lanes x max SM clock.
+         against SMs x 128 lanes x max SM clock; traffic = DRAM bytes per launch
+         from the committed ncu summary while the kernel sources are unchanged.
+  other_workloads  a few calls each of DD(r) at Rmax 10 and 50, DD(rp, pi)
+         14 x 40, and the weighted DR count with ravg (1.2M x 12M, open box).
 
 --impl reference times the CPU oracle (brute force, canonical binary64) on a
 bounded sample of the same workload: each step counts the pairs of a slice of
@@ -112,6 +115,32 @@ def load_peaks():
     return {"sm_max_mhz": 2070.0}, "fallback"
 
 
+PROFILE = os.path.join(ROOT, "profiles", "k_xi32_xi_auto_1.2M_rmax25.md")
+KERNEL_SOURCES = [os.path.join(ROOT, "paper_1911_08275_gb300", "csrc", f)
+                  for f in ("pairs.cu", "cf_internal.cuh")]
+
+
+def profile_traffic():
+    """DRAM bytes per launch of the pair kernel from the committed ncu summary,
+    or None when the kernel sources changed since that capture."""
+    import hashlib
+    if not os.path.exists(PROFILE):
+        return None, "no profile"
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    fields = {}
+    for line in open(PROFILE):
+        if ":" in line and line.split(":")[0].strip() in ("kernel_source_sha256_16",
+                                                          "traffic_bytes_per_launch"):
+            k, v = line.split(":", 1)
+            fields[k.strip()] = v.split()[0]
+    if fields.get("kernel_source_sha256_16") != h.hexdigest()[:16]:
+        return None, "kernel changed since the ncu capture"
+    return int(fields["traffic_bytes_per_launch"]), "ncu capture " + os.path.basename(PROFILE)
+
+
 def cpu_baseline_sample(cat, edges, rows, reps=1):
     """Time the oracle on primary rows [0, rows) against the whole catalogue."""
     import oracle
@@ -154,6 +183,54 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def _median_call(fn, flush, reps=3):
+    """Median library-reported device time (ms) of reps calls, L2 flushed before each."""
+    res = []
+    for _ in range(reps):
+        flush.zero_()
+        res.append(fn())
+    ms = statistics.median(r.total_ms for r in res)
+    kms = statistics.median(r.kernel_ms for r in res)
+    return res[-1], ms, kms
+
+
+def other_workloads(cf, synth, torch, cat, xyz, dev, stream, flush):
+    """Secondary measurements (a few calls each; not the headline)."""
+    out = {}
+    st = stream.cuda_stream
+    for rmax in (10.0, 50.0):
+        e = synth.log_edges(RMIN, rmax, NBINS)
+        row = {}
+        for mode in ("fp32_recheck", "fp64"):
+            r, ms, kms = _median_call(lambda: cf.countpairs_xi(*xyz, e, boxsize=synth.BOX, mode=mode,
+                                                               stream=st), flush)
+            row[mode] = {"ms": ms, "kernel_ms": kms,
+                         "Gpairs_s": float(r.npairs.sum()) / (ms * 1e-3) / 1e9}
+        out[f"xi_auto_rmax{rmax:g}"] = row
+    e = synth.log_edges(RMIN, RMAX, 14)
+    row = {}
+    for mode in ("fp32_recheck", "fp64"):
+        r, ms, kms = _median_call(lambda: cf.countpairs_rp_pi(*xyz, e, 40.0, 40, boxsize=synth.BOX,
+                                                              mode=mode, stream=st), flush)
+        row[mode] = {"ms": ms, "kernel_ms": kms,
+                     "Gpairs_s": float(r.npairs.sum()) / (ms * 1e-3) / 1e9}
+    out["rppi_auto_14x40_pimax40"] = row
+    # weighted DR with ravg: 1.2M clustered data x 12M uniform randoms, open box
+    wd = synth.uniform_weights(cat.n, 0.5, 1.5, seed=4)
+    rnd = synth.c4_randoms()
+    wr = synth.uniform_weights(rnd.n, 0.5, 1.5, seed=5)
+    a_w = torch.from_numpy(wd).to(dev)
+    b = [torch.from_numpy(v).to(dev) for v in (rnd.x, rnd.y, rnd.z, wr)]
+    r, ms, kms = _median_call(lambda: cf.countpairs_xi(
+        *xyz, synth.log_edges(RMIN, RMAX, NBINS), w=a_w, x2=b[0], y2=b[1], z2=b[2], w2=b[3],
+        periodic=False, mode="fp32_recheck", want_ravg=True, stream=st), flush)
+    out["dr_weighted_ravg_1.2Mx12M_open"] = {
+        "fp32_recheck": {"ms": ms, "kernel_ms": kms,
+                         "Gpairs_s": float(r.npairs.sum()) / (ms * 1e-3) / 1e9}}
+    del b, a_w
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -162,6 +239,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--mode", default="fp32_recheck", choices=["fp32_recheck", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the secondary workloads (Rmax sweep, DD(rp,pi), weighted DR)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -200,10 +279,13 @@ def main():
         call(xyz)
         call(host)
 
+    launches = [0]
+
     def timed(inputs):
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
               for _ in range(args.steps)]
         kms, tms = [], []
+        launches[0] = 0
         for s in range(args.steps):
             flush.zero_()
             ev[s][0].record(stream)
@@ -211,6 +293,7 @@ def main():
             ev[s][1].record(stream)
             kms.append(r.kernel_ms)
             tms.append(r.total_ms)
+            launches[0] += r.n_kernels
             if int(r.npairs.sum()) != p_cnt:
                 raise RuntimeError("counts changed between steps")
         torch.cuda.synchronize()
@@ -221,6 +304,7 @@ def main():
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
         step_ms, kernel_ms, lib_ms = timed(xyz)
+    n_launches = launches[0]
     e2e_ms, _, _ = timed(host)
     torch.cuda.synchronize()
     t_mean = statistics.mean(step_ms)
@@ -239,8 +323,9 @@ def main():
     peak_evals = sms * 128 * fmax * 1e6 / INSTR_PER_EVAL / 1e9  # Gevals/s
     k_mean = statistics.mean(kernel_ms)
     achieved = diag.n_evaluated / (k_mean * 1e-3) / 1e9
+    traffic, traffic_src = profile_traffic()
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak_evals, "unit": "Gevals/s",
-                "frac": achieved / peak_evals, "traffic": None,
+                "frac": achieved / peak_evals, "traffic": traffic, "traffic_source": traffic_src,
                 "peak_note": f"{sms} SMs x 128 FP32 lanes x {fmax:.0f} MHz / {INSTR_PER_EVAL} "
                              f"instr per evaluated pair ({peak_src} max SM clock)",
                 "kernel_ms": k_mean, "evaluations": diag.n_evaluated,
@@ -254,7 +339,7 @@ def main():
            "e2e": {"value": e2e_value, "unit": UNIT, "ms_per_step": e_mean,
                    "h2d_bytes_per_step": int(3 * 8 * cat.n),
                    "d2h_bytes_per_step": int(8 * NBINS + 8 * 4 + 4)},
-           "gpu_launches": 8 * args.steps,
+           "gpu_launches": n_launches,
            "diag": {"n_cellpairs": diag.n_cellpairs, "n_rechecked": diag.n_rechecked,
                     "useful_fraction": p_cnt / 2 / max(1, diag.n_evaluated)}}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -271,6 +356,9 @@ def main():
         out["fp64_path"] = {"ms_per_step": statistics.median(r.total_ms for r in r64),
                             "kernel_ms": statistics.median(r.kernel_ms for r in r64)}
         out["fp64_path"]["value"] = p_cnt / (out["fp64_path"]["ms_per_step"] * 1e-3) / 1e9
+        out["fp32_over_fp64"] = out["fp64_path"]["ms_per_step"] / t_mean
+    if rank == 0 and world == 1 and not args.no_extra:
+        out["other_workloads"] = other_workloads(cf, synth, torch, cat, xyz, dev, stream, flush)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if dist:

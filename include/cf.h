@@ -107,6 +107,8 @@ typedef struct {
     uint64_t n_band_violations; /* CF_FLAG_VERIFY_BAND: must be 0                 */
     double kernel_ms;           /* device time of the pair kernel                 */
     double total_ms;            /* device time of the whole call                  */
+    uint64_t n_kernels;         /* kernels the call launched (gridding, bounding
+                                   box, pair kernel; copies and memsets excluded) */
 } cf_result;
 
 /*

@@ -54,7 +54,7 @@ class cf_result(ctypes.Structure):
                 ("ravg", ctypes.POINTER(ctypes.c_double)), ("n_cellpairs", ctypes.c_uint64),
                 ("n_evaluated", ctypes.c_uint64), ("n_rechecked", ctypes.c_uint64),
                 ("n_band_violations", ctypes.c_uint64), ("kernel_ms", ctypes.c_double),
-                ("total_ms", ctypes.c_double)]
+                ("total_ms", ctypes.c_double), ("n_kernels", ctypes.c_uint64)]
 
 
 class CfError(RuntimeError):
@@ -108,6 +108,7 @@ class Result:
     n_band_violations: int
     kernel_ms: float
     total_ms: float
+    n_kernels: int = 0
 
 
 def _is_torch(a) -> bool:
@@ -192,7 +193,7 @@ def _run(fn, nslots, autocorr, x, y, z, w, x2, y2, z2, w2, extra, periodic, boxs
         raise CfError(st, L.cf_last_error().decode())
     return Result(npairs, wsum, ravg, int(res.n_cellpairs), int(res.n_evaluated),
                   int(res.n_rechecked), int(res.n_band_violations), float(res.kernel_ms),
-                  float(res.total_ms))
+                  float(res.total_ms), int(res.n_kernels))
 
 
 def countpairs_xi(x, y, z, edges, *, w=None, x2=None, y2=None, z2=None, w2=None, autocorr=None,

@@ -494,6 +494,7 @@ int run(Request &q)
         std::memset(res->ravg, 0, sizeof(double) * nslots);
     res->n_cellpairs = res->n_evaluated = res->n_rechecked = res->n_band_violations = 0;
     res->kernel_ms = res->total_ms = 0.0;
+    res->n_kernels = 0;
 
     int dev = 0, sms = 0;
     void *ws = nullptr, *ws2 = nullptr;
@@ -807,6 +808,10 @@ int run(Request &q)
         res->n_evaluated = ho->diag[1];
         res->n_rechecked = ho->diag[2];
         res->n_band_violations = ho->diag[3];
+        for (int t = 0; t < ncat; ++t)
+            res->n_kernels += cf::grid_kernels(cats[t]->n) +
+                              (c->periodic ? 0 : cf::bbox_kernels(cats[t]->n));
+        res->n_kernels += P.n_items > 0 ? 1 : 0;
     }
     rc = CF_OK;
 cleanup:
@@ -975,6 +980,7 @@ int noalloc_xi(int autocorr, const cf_catalog *d1, const cf_catalog *d2, const d
     std::memset(res->npairs, 0, sizeof(uint64_t) * nb);
     res->n_cellpairs = res->n_evaluated = res->n_rechecked = res->n_band_violations = 0;
     res->kernel_ms = res->total_ms = 0.0;
+    res->n_kernels = 0;
 
     int dev = 0, sms = 0, rc = CF_OK;
     cudaError_t e;
@@ -1182,6 +1188,9 @@ int noalloc_xi(int autocorr, const cf_catalog *d1, const cf_catalog *d2, const d
     res->n_cellpairs = h.diag[0];
     res->n_evaluated = h.diag[1];
     res->n_rechecked = h.diag[2];
+    for (int t = 0; t < ncat; ++t)
+        res->n_kernels += cf::grid_kernels(cats[t]->n) + (c->periodic ? 0 : cf::bbox_kernels(cats[t]->n));
+    res->n_kernels += P.n_items > 0 ? 1 : 0;
     return CF_OK;
 }
 
