@@ -123,16 +123,15 @@ double band_sq(double S, int ncomp, double M, double Ls, double R)
 // Float32 decision tables for squared separations (ncomp = 3 for xi, 2 for rp).
 //   T[0..2*ne): lo_0, hi_0, ..., lo_n, hi_n around the squared edges E2[0..ne):
 //     d2~ < lo_k proves d2 < E2_k and d2~ >= hi_k proves d2 >= E2_k.
-//   tab[0..lut_n): one byte per cell of float bit patterns
-//     [u0, u0 + (lut_n - 1) << shift); tab[lut_n - 1] is the entry that every
-//     out-of-range distance (below lo_0, at or above hi_n, NaN) uses.
+//   tab[0..lut_n): one byte per cell of float bit patterns; cell q holds the
+//     patterns u with (u >> shift) == u0s + q; tab[lut_n - 1] is the entry that
+//     every out-of-range distance (below lo_0, at or above hi_n, NaN) uses.
 //     Entries: bin k if every value of the cell lies in [hi_k, lo_{k+1});
-//     nbins (the dummy row) if every value is surely not counted; otherwise
-//     (the cell contains a threshold or lies inside a band) LUT_FLAG | h with
-//     2h <= the number of thresholds below the cell.
+//     nbins if every value is surely not counted; nbins + 1 otherwise (the
+//     cell contains a threshold or lies inside a band).
 struct Tables {
     int nthr, lut_n, shift;
-    uint32_t u0;
+    uint32_t u0s;  // first cell's bit pattern >> shift
 };
 
 Tables build_tables(const double *E2, int ne, int ncomp, double M, double Ls, double R, float *T,
@@ -155,18 +154,21 @@ Tables build_tables(const double *E2, int ne, int ncomp, double M, double Ls, do
     for (int q = 1; q < nthr; ++q)  // raising a threshold only widens the re-check set
         T[q] = std::max(T[q], T[q - 1]);
     const uint32_t u0 = T[0] > 0.0f ? fbits(T[0]) : 0u;
-    const uint32_t urange = fbits(T[nthr - 1]) - u0;
+    const uint32_t uhi = fbits(T[nthr - 1]);
+    // cells are aligned to multiples of 2^s, so a kernel finds a value's cell as
+    // (bits >> s) - u0s; the last cell holds T[nthr - 1]
     int s = 0;
-    while ((((uint64_t)urange + (1ull << s) - 1) >> s) > (uint64_t)(cf::LUT_MAX - 1))
+    while (((uhi >> s) - (u0 >> s)) + 1 > (uint32_t)(cf::LUT_MAX - 1))
         ++s;
-    const int n = std::max(1, (int)(((uint64_t)urange + (1ull << s) - 1) >> s));
-    const uint8_t dummy = (uint8_t)nbins;
+    const uint32_t u0s = u0 >> s;
+    const int n = (int)((uhi >> s) - u0s) + 1;
+    const uint8_t dummy = (uint8_t)nbins, flagged = (uint8_t)(nbins + 1);
     // Cells are visited in increasing value, so the threshold counts at the cell
     // ends only move forward: one sweep over cells and thresholds.
     int clo = 0, chi = 0;
     for (int q = 0; q < n; ++q) {
-        const uint32_t blo = u0 + ((uint32_t)q << s);
-        const uint32_t bhi = u0 + (uint32_t)(((uint64_t)(q + 1) << s) - 1);
+        const uint32_t blo = (u0s + (uint32_t)q) << s;
+        const uint32_t bhi = blo + (uint32_t)((1ull << s) - 1);
         const float vlo = bitsf(blo), vhi = bitsf(bhi);
         while (clo < nthr && T[clo] <= vlo)
             ++clo;
@@ -176,13 +178,13 @@ Tables build_tables(const double *E2, int ne, int ncomp, double M, double Ls, do
         if (clo == chi && !(clo & 1))
             tab[q] = (clo >= 2 && clo <= 2 * nbins) ? (uint8_t)((clo - 2) / 2) : dummy;
         else
-            tab[q] = (uint8_t)(cf::LUT_FLAG | (uint32_t)(clo >> 1));
+            tab[q] = flagged;
     }
     tab[n] = dummy;
     t.nthr = nthr;
     t.lut_n = n + 1;
     t.shift = s;
-    t.u0 = u0;
+    t.u0s = u0s;
     return t;
 }
 
@@ -514,14 +516,15 @@ int run(Request &q)
     long long nmax = 0, ntot = 0;
     double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
     unsigned long long *bbox_keys = nullptr;
-    unsigned *d_err = nullptr, *d_ctr = nullptr;
+    unsigned *d_err = nullptr, *d_ctr = nullptr, *d_wcount = nullptr;
+    cf::WorkItem *work = nullptr;
     unsigned long long *d_hist = nullptr, *d_diag = nullptr;
     float *d_thr = nullptr;
     uint8_t *d_lut = nullptr;
     double *d_E2 = nullptr, *d_P = nullptr;
     size_t total = 0;
     struct HostOut {
-        unsigned long long hist[3 * cf::NBINS2D_MAX + 5];  // hist | diag(4) | err, counter | wsum | rsum
+        unsigned long long hist[3 * cf::NBINS2D_MAX + 6];  // hist | diag(4) | err, counter | kept | wsum | rsum
         unsigned long long *diag;
         unsigned err;
         float thr[2 * (cf::NB_MAX + 1)];  // page-locked staging of the tables
@@ -570,10 +573,11 @@ int run(Request &q)
         }
         bbox_keys = bump.take<unsigned long long>(6);
         // one block, one memset, one copy back: [hist | diag(4) | err, counter | wsum | rsum]
-        d_hist = bump.take<unsigned long long>(nslots + 5 + nacc);
+        d_hist = bump.take<unsigned long long>(nslots + 6 + nacc);
         d_diag = d_hist + nslots;
         d_err = reinterpret_cast<unsigned *>(d_hist + nslots + 4);
         d_ctr = d_err + 1;
+        d_wcount = d_err + 2;
         d_thr = bump.take<float>(2 * (nb + 1));
         d_lut = bump.take<uint8_t>(cf::LUT_MAX);
         d_E2 = bump.take<double>(nb + 1);
@@ -593,7 +597,7 @@ int run(Request &q)
         if (dw[t])
             CF_CUDA(cudaMemcpyAsync((void *)dw[t], cats[t]->w, n * 8, cudaMemcpyHostToDevice, st), "H2D w");
     }
-    CF_CUDA(cudaMemsetAsync(d_hist, 0, sizeof(unsigned long long) * (nslots + 5 + nacc), st), "memset");
+    CF_CUDA(cudaMemsetAsync(d_hist, 0, sizeof(unsigned long long) * (nslots + 6 + nacc), st), "memset");
 
     ho = (HostOut *)g_pinned.get(sizeof(HostOut));
     if (!ho) {
@@ -647,6 +651,7 @@ int run(Request &q)
             tmp.counts = bump.take<uint32_t>(g.ncells);
             tmp.pad = bump.take<uint32_t>(g.ncols);
             tmp.bsum = bump.take<uint32_t>(g.ncells / 4096 + 2);
+            work = bump.take<cf::WorkItem>((size_t)g.ncols * cf::MAX_STENCIL);
             if (pass == 0) {
                 const cudaError_t e = cudaMallocAsync(&ws2, bump.off, st);
                 if (e) {
@@ -682,6 +687,7 @@ int run(Request &q)
                 P.stencil[P.nstencil++] = make_int2(ox, oy);
             }
         P.n_items = g.ncols * P.nstencil;
+        P.work = work;
         P.tile_max = 1024;
         P.flags = c->flags;
         const double M = std::max(g.extent[0], std::max(g.extent[1], g.extent[2]));
@@ -714,7 +720,7 @@ int run(Request &q)
             P.nthr = tb.nthr;
             P.lut_n = tb.lut_n;
             P.lut_shift = tb.shift;
-            P.u0 = tb.u0;
+            P.u0 = tb.u0s;
             std::memcpy(ho->thr, T, 4 * P.nthr);
             std::memcpy(ho->lut, tab, P.lut_n);
             CF_CUDA(cudaMemcpyAsync(d_thr, ho->thr, 4 * P.nthr, cudaMemcpyHostToDevice, st), "H2D thresholds");
@@ -730,18 +736,25 @@ int run(Request &q)
         P.weighted = c->weighted ? 1 : 0;
         P.want_r = c->want_ravg ? 1 : 0;
         P.wacc = wacc ? 1 : 0;
-        P.wsum = wacc ? reinterpret_cast<double *>(d_hist + nslots + 5) : nullptr;
+        P.wsum = wacc ? reinterpret_cast<double *>(d_hist + nslots + 6) : nullptr;
         P.rsum = wacc ? P.wsum + nslots : nullptr;
         P.diag = d_diag;
         P.err = d_err;
         P.item_counter = d_ctr;
+        P.work_count = d_wcount;
 
         PL.f64 = f64;
         PL.chunk = 16;
+        PL.pp = 2;
         if (const char *ev = std::getenv("CF_PAIR_CHUNK")) {  // tuning experiments
             const int c = std::atoi(ev);
             if (c == 8 || c == 16 || c == 32)
                 PL.chunk = c;
+        }
+        if (const char *ev = std::getenv("CF_PAIR_PP")) {
+            const int v = std::atoi(ev);
+            if (v == 1 || v == 2)
+                PL.pp = v;
         }
         PL.evals = (c->flags & (CF_FLAG_COUNT_EVALS | CF_FLAG_VERIFY_BAND)) ? 1 : 0;
         PL.verify = (!f64 && (c->flags & CF_FLAG_VERIFY_BAND)) ? 1 : 0;
@@ -757,7 +770,7 @@ int run(Request &q)
         }
         CF_CUDA(cudaEventRecord(g_events.ev[2], st), "cudaEventRecord");
         trace.point("pair kernel");
-        CF_CUDA(cudaMemcpyAsync(ho->hist, d_hist, sizeof(unsigned long long) * (nslots + 5 + nacc),
+        CF_CUDA(cudaMemcpyAsync(ho->hist, d_hist, sizeof(unsigned long long) * (nslots + 6 + nacc),
                                 cudaMemcpyDeviceToHost, st),
                 "D2H results");
     }
@@ -792,7 +805,7 @@ int run(Request &q)
         for (int k = 0; k < nslots; ++k)
             res->npairs[k] = ho->hist[k] * mult;
         if (wacc) {
-            const double *ws = reinterpret_cast<const double *>(ho->hist + nslots + 5);
+            const double *ws = reinterpret_cast<const double *>(ho->hist + nslots + 6);
             const double *rs = ws + nslots;
             for (int k = 0; k < nslots; ++k) {
                 const double wk = ws[k] * (double)mult, rk = rs[k] * (double)mult;
@@ -804,14 +817,16 @@ int run(Request &q)
                 }
             }
         }
-        res->n_cellpairs = ho->diag[0];
+        unsigned wcount = 0;
+        std::memcpy(&wcount, reinterpret_cast<const unsigned *>(ho->hist + nslots + 4) + 2, 4);
+        res->n_cellpairs = wcount;
         res->n_evaluated = ho->diag[1];
         res->n_rechecked = ho->diag[2];
         res->n_band_violations = ho->diag[3];
         for (int t = 0; t < ncat; ++t)
             res->n_kernels += cf::grid_kernels(cats[t]->n) +
                               (c->periodic ? 0 : cf::bbox_kernels(cats[t]->n));
-        res->n_kernels += P.n_items > 0 ? 1 : 0;
+        res->n_kernels += P.n_items > 0 ? 2 : 0;  // work list + pair kernel
     }
     rc = CF_OK;
 cleanup:
@@ -1005,7 +1020,7 @@ int noalloc_xi(int autocorr, const cf_catalog *d1, const cf_catalog *d2, const d
     bump.base = (char *)scratch;
     unsigned long long *bbox_keys = bump.take<unsigned long long>(6);
     unsigned *d_err = bump.take<unsigned>(1);
-    unsigned *d_ctr = bump.take<unsigned>(1);
+    unsigned *d_ctr = bump.take<unsigned>(2);  // [0] item counter, [1] kept column pairs
     unsigned long long *d_hist = bump.take<unsigned long long>(cf::NB_MAX);
     unsigned long long *d_diag = bump.take<unsigned long long>(4);
     float *d_thr = bump.take<float>(2 * (cf::NB_MAX + 1));
@@ -1015,7 +1030,7 @@ int noalloc_xi(int autocorr, const cf_catalog *d1, const cf_catalog *d2, const d
         unsigned long long keys[6];
         unsigned long long hist[cf::NB_MAX];
         unsigned long long diag[4];
-        unsigned err;
+        unsigned err, kept;
     } h;
     if ((e = cudaMemsetAsync(d_err, 0, sizeof(unsigned), st)) != cudaSuccess)
         return cuda_fail(e, "memset");
@@ -1099,10 +1114,13 @@ int noalloc_xi(int autocorr, const cf_catalog *d1, const cf_catalog *d2, const d
     tmp.counts = bump.take<uint32_t>(g.ncells);
     tmp.pad = bump.take<uint32_t>(g.ncols);
     tmp.bsum = bump.take<uint32_t>(g.ncells / 4096 + 2);
+    const int nstencil_max = autocorr ? ((2 * g.reach_x + 1) * (2 * g.reach_y + 1) + 1) / 2
+                                      : (2 * g.reach_x + 1) * (2 * g.reach_y + 1);
+    cf::WorkItem *work = bump.take<cf::WorkItem>((size_t)g.ncols * nstencil_max);
     if (bump.off > NOALLOC_BYTES)
         return fail(CF_EINVAL, "no-alloc entry point: problem does not fit the 32 MiB static scratch");
 
-    if ((e = cudaMemsetAsync(d_ctr, 0, sizeof(unsigned), st)) ||
+    if ((e = cudaMemsetAsync(d_ctr, 0, 2 * sizeof(unsigned), st)) ||
         (e = cudaMemsetAsync(d_hist, 0, sizeof(unsigned long long) * nb, st)) ||
         (e = cudaMemsetAsync(d_diag, 0, sizeof(unsigned long long) * 4, st)))
         return cuda_fail(e, "memset");
@@ -1130,6 +1148,8 @@ int noalloc_xi(int autocorr, const cf_catalog *d1, const cf_catalog *d2, const d
             P.stencil[P.nstencil++] = make_int2(ox, oy);
         }
     P.n_items = g.ncols * P.nstencil;
+    P.work = work;
+    P.work_count = d_ctr + 1;
     P.tile_max = 1024;
     P.flags = c->flags & (CF_FLAG_NO_PRUNE | CF_FLAG_COUNT_EVALS);
     const double M = std::max(g.extent[0], std::max(g.extent[1], g.extent[2]));
@@ -1149,7 +1169,7 @@ int noalloc_xi(int autocorr, const cf_catalog *d1, const cf_catalog *d2, const d
         P.nthr = tb.nthr;
         P.lut_n = tb.lut_n;
         P.lut_shift = tb.shift;
-        P.u0 = tb.u0;
+        P.u0 = tb.u0s;
         if ((e = cudaMemcpyAsync(d_thr, T, sizeof(float) * P.nthr, cudaMemcpyHostToDevice, st)) ||
             (e = cudaMemcpyAsync(d_lut, tab, P.lut_n, cudaMemcpyHostToDevice, st)))
             return cuda_fail(e, "H2D tables");
@@ -1167,12 +1187,14 @@ int noalloc_xi(int autocorr, const cf_catalog *d1, const cf_catalog *d2, const d
     std::memset(&PL, 0, sizeof(PL));
     PL.f64 = f64;
     PL.chunk = 16;
+    PL.pp = 2;
     PL.evals = (P.flags & CF_FLAG_COUNT_EVALS) ? 1 : 0;
     cf::plan_pairs(P, PL);
     if (P.n_items > 0 && (e = cf::launch_pairs(P, PL, sms, st)))
         return cuda_fail(e, "pair kernel launch");
     if ((e = cudaMemcpyAsync(h.hist, d_hist, sizeof(unsigned long long) * nb, cudaMemcpyDeviceToHost, st)) ||
         (e = cudaMemcpyAsync(h.diag, d_diag, sizeof(h.diag), cudaMemcpyDeviceToHost, st)) ||
+        (e = cudaMemcpyAsync(&h.kept, d_ctr + 1, 4, cudaMemcpyDeviceToHost, st)) ||
         (e = cudaMemcpyAsync(&h.err, d_err, 4, cudaMemcpyDeviceToHost, st)) ||
         (e = cudaStreamSynchronize(st)))
         return cuda_fail(e, "result readback");
@@ -1185,12 +1207,12 @@ int noalloc_xi(int autocorr, const cf_catalog *d1, const cf_catalog *d2, const d
     const uint64_t mult = autocorr ? 2u : 1u;
     for (int k = 0; k < nb; ++k)
         res->npairs[k] = h.hist[k] * mult;
-    res->n_cellpairs = h.diag[0];
+    res->n_cellpairs = h.kept;
     res->n_evaluated = h.diag[1];
     res->n_rechecked = h.diag[2];
     for (int t = 0; t < ncat; ++t)
         res->n_kernels += cf::grid_kernels(cats[t]->n) + (c->periodic ? 0 : cf::bbox_kernels(cats[t]->n));
-    res->n_kernels += P.n_items > 0 ? 1 : 0;
+    res->n_kernels += P.n_items > 0 ? 2 : 0;  // work list + pair kernel
     return CF_OK;
 }
 

@@ -28,10 +28,10 @@ enum : unsigned {
 };
 
 // Lookup-table entry (one byte): 0..nbins-1 -> the bin (the cell lies wholly
-// between hi_k and lo_{k+1}); nbins -> surely not counted (dummy row);
-// LUT_FLAG | h -> the cell touches a threshold: the thresholds below index 2h
-// are all below the cell, so counting from 2h settles it (maybe re-check).
-constexpr uint32_t LUT_FLAG = 0x80u;
+// between hi_k and lo_{k+1}); nbins -> surely not counted; nbins + 1 -> the
+// cell touches a threshold or a band (settled by the thresholds, maybe a
+// binary64 re-check).  The float32 DD(r) kernel keeps a histogram row for each
+// of the nbins + 2 values, so an entry is a row index without a clamp.
 
 // Shared layout of the float32 DD(r) kernel (compile-time offsets):
 // [0,128) barrier + work item; LUT; x, y, z tiles of TILE32 + 64 floats each;
@@ -87,6 +87,14 @@ struct Gridded {
     double4_32a *colbox;      // per column (xmin, xmax, ymin, ymax)
 };
 
+// One kept column pair (Sec. 2.2 pruning done), written by the work-list kernel.
+struct __align__(16) WorkItem {
+    int a0, a1, b0, b1;  // point ranges of columns a and b
+    double dzmax;        // z reach of the pair (binary64, already widened)
+    int code;            // bits 0-1: qx + 1, bits 2-3: qy + 1 (periodic image), bit 4: self pair
+    int pad;
+};
+
 // Everything a pair kernel needs (passed by value, lives in the constant bank).
 struct PairParams {
     Gridded A, B;
@@ -95,7 +103,9 @@ struct PairParams {
     int kind;           // 0 = xi, 1 = rp-pi
     int nstencil;
     int2 stencil[MAX_STENCIL];
-    int n_items;
+    int n_items;        // (column, stencil offset) candidates
+    WorkItem *work;     // kept column pairs (work-list kernel output)
+    unsigned *work_count;  // number of kept column pairs
     int tile_max;       // points per staged tile
     uint32_t flags;
     // radii (binary64 decisions on bounding boxes)
@@ -109,7 +119,7 @@ struct PairParams {
     int npibins;        // rp-pi only
     int nthr;           // 2 * nbins + 2 float32 thresholds
     int lut_n, lut_shift; // table entries (last one = out of range), cell width 2^shift
-    uint32_t u0;          // float bit pattern of the table's first cell
+    uint32_t u0;          // (float bit pattern of the table's first cell) >> lut_shift
     float pscale;       // rp-pi: fl32(npibins / pimax), pi edges at integer t = |dz| * pscale
     float pband;        // rp-pi: |t - 1/2 - round(t - 1/2)| > pband means t is near an edge
     int hcopies;        // rp-pi: shared histogram copies per CTA (warp w uses w % hcopies)

@@ -61,6 +61,7 @@ void plan_pairs(PairParams &P, PairLaunch &L)
             L.smem = align_up(P.rows_off + align_up(WARPS * nr * 32, 128) + 2 * WARPS * nr * 32 * 4,
                               128);
         } else {
+            L.hist_words = WARPS * (nb + 2) * 32;  // + a row for flagged table cells
             P.hist_off = XI32_HIST_OFF;
             L.smem = align_up(XI32_HIST_OFF + L.hist_words * 4, 128);
         }
@@ -222,47 +223,38 @@ __device__ void warp_flush(uint32_t *hw, int nb, unsigned long long *ghist, int 
     }
 }
 
-// One work item decoded (identical in every thread of the CTA).
-struct Item {
-    int a0, a1, b0, b1;
-    double Sx, Sy, dzmax;
-    bool self;
-    int kmin, kmax;
-};
-
-// Decode item -> column pair, image, pruning (Sec. 2.2) and z reach.
-// Returns false if the item has no work.
-__device__ __forceinline__ bool decode_item(const PairParams &P, int item, Item &it)
+// Candidate (column a, stencil offset) -> column pair, image, pruning
+// (Sec. 2.2) and z reach, in binary64.  Returns false if the pair has no work.
+__device__ __forceinline__ bool plan_item(const PairParams &P, int item, WorkItem &w)
 {
     const int a = item / P.nstencil, s = item - a * P.nstencil;
     const int2 o = P.stencil[s];
     const int ax = a / P.g.ncy, ay = a - ax * P.g.ncy;
     int bx = ax + o.x, by = ay + o.y;
-    it.Sx = 0.0;
-    it.Sy = 0.0;
+    int qx = 0, qy = 0;
     if (P.g.periodic) {
-        const int qx = floor_div(bx, P.g.ncx), qy = floor_div(by, P.g.ncy);
+        qx = floor_div(bx, P.g.ncx);
+        qy = floor_div(by, P.g.ncy);
         bx -= qx * P.g.ncx;
         by -= qy * P.g.ncy;
-        it.Sx = qx * P.g.box[0];
-        it.Sy = qy * P.g.box[1];
     } else if (bx < 0 || bx >= P.g.ncx || by < 0 || by >= P.g.ncy) {
         return false;
     }
+    const double Sx = qx * P.g.box[0], Sy = qy * P.g.box[1];
     const int b = bx * P.g.ncy + by;
     const long long nz = P.g.nz;
-    it.a0 = (int)P.A.cell_start[a * nz];
-    it.a1 = (int)P.A.cell_start[(a + 1) * nz];
-    it.b0 = (int)P.B.cell_start[b * nz];
-    it.b1 = (int)P.B.cell_start[(b + 1) * nz];
-    if (it.a0 >= it.a1 || it.b0 >= it.b1)
+    w.a0 = (int)P.A.cell_start[a * nz];
+    w.a1 = (int)P.A.cell_start[(a + 1) * nz];
+    w.b0 = (int)P.B.cell_start[b * nz];
+    w.b1 = (int)P.B.cell_start[(b + 1) * nz];
+    if (w.a0 >= w.a1 || w.b0 >= w.b1)
         return false;
     // minimum possible (x, y) separation of the two columns' bounding boxes
     const double4_32a ba = P.A.colbox[a], bb = P.B.colbox[b];
-    const double gx = fmax(0.0, fmax(__dsub_rn(__dadd_rn(bb.x, it.Sx), ba.y),
-                                     __dsub_rn(ba.x, __dadd_rn(bb.y, it.Sx))));
-    const double gy = fmax(0.0, fmax(__dsub_rn(__dadd_rn(bb.z, it.Sy), ba.w),
-                                     __dsub_rn(ba.z, __dadd_rn(bb.w, it.Sy))));
+    const double gx = fmax(0.0, fmax(__dsub_rn(__dadd_rn(bb.x, Sx), ba.y),
+                                     __dsub_rn(ba.x, __dadd_rn(bb.y, Sx))));
+    const double gy = fmax(0.0, fmax(__dsub_rn(__dadd_rn(bb.z, Sy), ba.w),
+                                     __dsub_rn(ba.z, __dadd_rn(bb.w, Sy))));
     const double g2 = __dadd_rn(__dmul_rn(gx, gx), __dmul_rn(gy, gy));
     if (!(P.flags & CF_FLAG_NO_PRUNE) && g2 >= P.prune_r2)
         return false;
@@ -270,11 +262,54 @@ __device__ __forceinline__ bool decode_item(const PairParams &P, int item, Item 
     double dzmax = P.rz;
     if (P.kind == 0)
         dzmax = sqrt(fmax(0.0, __dsub_rn(P.rxy2, __dmul_rn(g2, 1.0 - 1e-12))));
-    it.dzmax = __dmul_rn(dzmax, 1.0 + 1e-9);
-    it.self = P.autocorr && o.x == 0 && o.y == 0;
+    w.dzmax = __dmul_rn(dzmax, 1.0 + 1e-9);
+    const bool self = P.autocorr && o.x == 0 && o.y == 0;
+    w.code = (qx + 1) | ((qy + 1) << 2) | (self ? 16 : 0);
+    w.pad = 0;
+    return true;
+}
+
+// Work-list kernel (a3): one thread per candidate, kept pairs appended to
+// P.work with one warp-aggregated atomic per warp.
+__global__ void __launch_bounds__(256) k_worklist(const __grid_constant__ PairParams P)
+{
+    const int item = blockIdx.x * blockDim.x + threadIdx.x;
+    WorkItem w;
+    const bool keep = item < P.n_items && plan_item(P, item, w);
+    const unsigned m = __ballot_sync(FULL, keep);
+    if (!m)
+        return;
+    const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
+    unsigned base = 0;
+    if (lane == leader)
+        base = atomicAdd(P.work_count, (unsigned)__popc(m));
+    base = __shfl_sync(FULL, base, leader);
+    if (keep)
+        P.work[base + __popc(m & ((1u << lane) - 1u))] = w;
+}
+
+// One kept column pair, as the pair kernels use it (identical in every thread
+// of the CTA: all read the same record).
+struct Item {
+    int a0, a1, b0, b1;
+    double Sx, Sy, dzmax;
+    bool self;
+    int kmin, kmax;
+};
+
+__device__ __forceinline__ void decode_item(const PairParams &P, int item, Item &it)
+{
+    const WorkItem w = P.work[item];
+    it.a0 = w.a0;
+    it.a1 = w.a1;
+    it.b0 = w.b0;
+    it.b1 = w.b1;
+    it.dzmax = w.dzmax;
+    it.Sx = (double)((w.code & 3) - 1) * P.g.box[0];
+    it.Sy = (double)(((w.code >> 2) & 3) - 1) * P.g.box[1];
+    it.self = (w.code & 16) != 0;
     it.kmin = P.g.periodic ? (it.self ? 0 : -1) : 0;
     it.kmax = P.g.periodic ? 1 : 0;
-    return true;
 }
 
 // Stage the float32 x, y, z tiles (three 1-D bulk copies, one mbarrier):
@@ -364,11 +399,36 @@ struct Sweep32 {
     double Sx, Sy, Sz;
 };
 
-__device__ __forceinline__ uint32_t lut_byte(const unsigned char *smem, uint32_t u0, int shift,
+__device__ __forceinline__ uint32_t lut_byte(const unsigned char *smem, uint32_t u0s, int shift,
                                              uint32_t last, float d2)
 {
-    const uint32_t u = __float_as_uint(d2) - u0;  // below-range values wrap to huge
-    return smem[LUT_OFF + min(u >> shift, last)];
+    const uint32_t q = (__float_as_uint(d2) >> shift) - u0s;  // below-range values wrap to huge
+    return smem[LUT_OFF + min(q, last)];
+}
+
+// Number of thresholds T[c] <= d2 (T non-decreasing, d2 not NaN), scanning
+// down from the top: flagged cells are dominated by the largest edges (the
+// pair density grows with the separation), where this ends in a step or two.
+__device__ __forceinline__ int thr_count_top(const float *T, int nthr, float d2)
+{
+    int c = nthr;
+    while (c > 0 && T[c - 1] > d2)
+        --c;
+    return c;
+}
+
+// Number of thresholds T[c] <= d2 (T is non-decreasing; NaN counts none).
+__device__ __forceinline__ int thr_count(const float *T, int nthr, float d2)
+{
+    int lo = 0, hi = nthr;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (T[mid] <= d2)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    return lo;
 }
 
 __device__ __forceinline__ void red_shared1(uint32_t addr)
@@ -376,17 +436,14 @@ __device__ __forceinline__ void red_shared1(uint32_t addr)
     asm volatile("red.shared.add.u32 [%0], 1;" ::"r"(addr));
 }
 
-// Flagged table cell (entry = LUT_FLAG | h): count the thresholds <= d2 from
-// index 2h (all earlier ones lie below the cell); inside a band re-evaluate in
+// Flagged table cell: count the thresholds <= d2; inside a band re-evaluate in
 // binary64.  Adds the pair to its true bin (the main path has already put it in
-// the dummy row).  Returns 1 if re-evaluated.
+// the flagged row, which is never read).  Returns 1 if re-evaluated.
 __device__ __forceinline__ int resolve_pair(const unsigned char *smem, const Sweep32 &S,
-                                            uint32_t hl, uint32_t e, float d2, int i, int jg)
+                                            uint32_t hl, float d2, int i, int jg)
 {
     const float *T = reinterpret_cast<const float *>(smem + THR_OFF);
-    int c = (int)(e & 0x7fu) * 2;
-    while (c < S.nthr && T[c] <= d2)
-        ++c;
+    const int c = thr_count_top(T, S.nthr, d2);
     int row;
     int re = 0;
     if (!(c & 1)) {
@@ -401,85 +458,133 @@ __device__ __forceinline__ int resolve_pair(const unsigned char *smem, const Swe
     return re;
 }
 
-// Sweep one window [jlo, jhi) of the staged tile.  Lane (ii, jj) holds one
-// primary i (broadcast to both halves of packed registers) and evaluates it
-// against two consecutive secondaries j, j+1 (one 8-byte load per axis); a
-// step covers I primaries x 64/I secondaries, an iteration two steps, with one
-// warp-uniform check for flagged table cells.
-template <int I, bool TRI, bool EVALS, bool VERIFY>
+// A flagged pair recorded by sweep32: recompute its float32 d2 from the
+// staged tile (the same IEEE operations as the packed main path), settle it
+// with the thresholds (binary64 inside a band) and add it to its true row.
+__device__ __forceinline__ int resolve_local(const unsigned char *smem, const Sweep32 &S, uint32_t hl,
+                                          float xh, float yh, float zh, int i, int jl)
+{
+    const float *tx = reinterpret_cast<const float *>(smem + TX_OFF);
+    const float dx = __fsub_rn(tx[jl], xh);
+    const float dy = __fsub_rn(tx[jl + TSTRIDE / 4], yh);
+    const float dz = __fsub_rn(tx[jl + TSTRIDE / 2], zh);
+    const float d2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+    return resolve_pair(smem, S, hl, d2, i, S.t0 + jl);
+}
+
+// Sweep one window [jlo, jhi) of the staged tile.  Lane (ii, jj) holds PP
+// primaries (each broadcast to both halves of packed registers) and evaluates
+// them against two consecutive secondaries j, j+1 (one 8-byte load per axis
+// feeds 2 PP pairs); a step covers I PP primaries x 64/I secondaries, an
+// iteration two steps.  Pairs whose table cell is flagged go to the flagged
+// row and set a bit of the lane's mask; once per block of 8 iterations a
+// warp-uniform test settles the recorded pairs (so the loop body has no
+// data-dependent branch).
+template <int I, int PP, bool TRI, bool EVALS, bool VERIFY>
 __device__ __forceinline__ void sweep32(unsigned char *smem, const Sweep32 &S, uint32_t hl, int jlo,
-                                        int jhi, int jj, u64 XH, u64 YH, u64 ZH, int i, bool vi,
-                                        u64 &n_eval, u64 &n_rck, u64 &n_viol)
+                                        int jhi, int jj, const u64 (&XH)[PP], const u64 (&YH)[PP],
+                                        const u64 (&ZH)[PP], const int (&iv)[PP],
+                                        const bool (&vv)[PP], u64 &n_eval, u64 &n_rck, u64 &n_viol)
 {
     const float qnan = __int_as_float(0x7fc00000);
     const int jstart = jlo & ~1;  // 8-byte aligned pairs; extra j's are never counted
     constexpr int JS = 64 / I;  // secondaries per step
     const int nit = (jhi - jstart + 2 * JS - 1) / (2 * JS);
-    const unsigned char *p = smem + TX_OFF + (jstart + 2 * jj) * 4;
-    int jA = jstart + 2 * jj;
-    for (int it = 0; it < nit; ++it, p += 8 * JS, jA += 2 * JS) {
-        const u64 xA = *reinterpret_cast<const u64 *>(p);
-        const u64 yA = *reinterpret_cast<const u64 *>(p + TSTRIDE);
-        const u64 zA = *reinterpret_cast<const u64 *>(p + 2 * TSTRIDE);
-        const u64 xB = *reinterpret_cast<const u64 *>(p + 4 * JS);
-        const u64 yB = *reinterpret_cast<const u64 *>(p + 4 * JS + TSTRIDE);
-        const u64 zB = *reinterpret_cast<const u64 *>(p + 4 * JS + 2 * TSTRIDE);
-        u64 dx = fsub2(xA, XH), dy = fsub2(yA, YH), dz = fsub2(zA, ZH);
-        const u64 dA = ffma2(dz, dz, ffma2(dy, dy, fmul2(dx, dx)));
-        dx = fsub2(xB, XH);
-        dy = fsub2(yB, YH);
-        dz = fsub2(zB, ZH);
-        const u64 dB = ffma2(dz, dz, ffma2(dy, dy, fmul2(dx, dx)));
-        float a0, a1, b0, b1;
-        unpack2(dA, a0, a1);
-        unpack2(dB, b0, b1);
-        const int gA = S.t0 + jA, gB = gA + JS;  // global indices of (a0, b0); a1, b1 are +1
-        bool la0 = true, la1 = true, lb0 = true, lb1 = true;
-        if (TRI) {
-            la0 = gA > i;
-            la1 = gA + 1 > i;
-            lb0 = gB > i;
-            lb1 = gB + 1 > i;
-            a0 = la0 ? a0 : qnan;
-            a1 = la1 ? a1 : qnan;
-            b0 = lb0 ? b0 : qnan;
-            b1 = lb1 ? b1 : qnan;
-        }
-        if (EVALS) {
-            const int jB = jA + JS;
-            n_eval += (u64)((vi && jA >= jlo && jA < jhi && la0) +
-                            (vi && jA + 1 >= jlo && jA + 1 < jhi && la1) +
-                            (vi && jB >= jlo && jB < jhi && lb0) +
-                            (vi && jB + 1 >= jlo && jB + 1 < jhi && lb1));
-        }
-        const uint32_t ea0 = lut_byte(smem, S.u0, S.shift, S.lut_last, a0), ea1 = lut_byte(smem, S.u0, S.shift, S.lut_last, a1);
-        const uint32_t eb0 = lut_byte(smem, S.u0, S.shift, S.lut_last, b0), eb1 = lut_byte(smem, S.u0, S.shift, S.lut_last, b1);
-        const uint32_t nbu = (uint32_t)S.nb;
-        red_shared1(hl + min(ea0, nbu) * 128u);  // flagged entries -> dummy row here
-        red_shared1(hl + min(ea1, nbu) * 128u);
-        red_shared1(hl + min(eb0, nbu) * 128u);
-        red_shared1(hl + min(eb1, nbu) * 128u);
-        if (__any_sync(FULL, (ea0 | ea1 | eb0 | eb1) & LUT_FLAG)) {
-            if (ea0 & LUT_FLAG)
-                n_rck += resolve_pair(smem, S, hl, ea0, a0, i, gA);
-            if (ea1 & LUT_FLAG)
-                n_rck += resolve_pair(smem, S, hl, ea1, a1, i, gA + 1);
-            if (eb0 & LUT_FLAG)
-                n_rck += resolve_pair(smem, S, hl, eb0, b0, i, gB);
-            if (eb1 & LUT_FLAG)
-                n_rck += resolve_pair(smem, S, hl, eb1, b1, i, gB + 1);
-        }
-        if (VERIFY) {
-            const float *T = reinterpret_cast<const float *>(smem + THR_OFF);
-            const double *E2 = reinterpret_cast<const double *>(smem + E2_OFF);
-            // pairs with real points on both sides (sentinels and padding give NaN)
-            const float dv[4] = {a0, a1, b0, b1};
-            const int gv[4] = {gA, gA + 1, gB, gB + 1};
+    const uint32_t nbu = (uint32_t)S.nb;
+    // entries are <= nbu + 1 < 0x80: adding 0x80 - (nbu + 1) to each byte sets its
+    // top bit exactly for the flagged value, without carries between bytes
+    const uint32_t cflag = (0x80u - (nbu + 1u)) * 0x01010101u;
+    for (int b0 = 0; b0 < nit; b0 += 8) {
+        const int jAb = jstart + 2 * jj + b0 * 2 * JS;
+        const unsigned char *pb = smem + TX_OFF + jAb * 4;
+        const int tend = min(8, nit - b0);
+        uint32_t fm[PP];
 #pragma unroll
-            for (int q = 0; q < 4; ++q)
-                if (vi && !isnan(dv[q]))
-                    n_viol += verify_pair(dv[q], T, S.nthr, S.nb, E2, S.pa, S.pb, i, gv[q], S.Sx,
-                                          S.Sy, S.Sz);
+        for (int q = 0; q < PP; ++q)
+            fm[q] = 0u;
+        for (int t = 0; t < tend; ++t) {
+            const unsigned char *p = pb + t * 8 * JS;
+            const int jA = jAb + t * 2 * JS;
+            const u64 xA = *reinterpret_cast<const u64 *>(p);
+            const u64 yA = *reinterpret_cast<const u64 *>(p + TSTRIDE);
+            const u64 zA = *reinterpret_cast<const u64 *>(p + 2 * TSTRIDE);
+            const u64 xB = *reinterpret_cast<const u64 *>(p + 4 * JS);
+            const u64 yB = *reinterpret_cast<const u64 *>(p + 4 * JS + TSTRIDE);
+            const u64 zB = *reinterpret_cast<const u64 *>(p + 4 * JS + 2 * TSTRIDE);
+            float d[PP][4];
+#pragma unroll
+            for (int q = 0; q < PP; ++q) {
+                u64 dx = fsub2(xA, XH[q]), dy = fsub2(yA, YH[q]), dz = fsub2(zA, ZH[q]);
+                const u64 dA = ffma2(dz, dz, ffma2(dy, dy, fmul2(dx, dx)));
+                dx = fsub2(xB, XH[q]);
+                dy = fsub2(yB, YH[q]);
+                dz = fsub2(zB, ZH[q]);
+                const u64 dB = ffma2(dz, dz, ffma2(dy, dy, fmul2(dx, dx)));
+                unpack2(dA, d[q][0], d[q][1]);
+                unpack2(dB, d[q][2], d[q][3]);
+            }
+            const int gA = S.t0 + jA, gB = gA + JS;  // global indices of (a0, b0); a1, b1 are +1
+            const int gv[4] = {gA, gA + 1, gB, gB + 1};
+            if (TRI) {
+#pragma unroll
+                for (int q = 0; q < PP; ++q)
+#pragma unroll
+                    for (int r = 0; r < 4; ++r)
+                        d[q][r] = gv[r] > iv[q] ? d[q][r] : qnan;
+            }
+            if (EVALS) {
+                const int jv[4] = {jA, jA + 1, jA + JS, jA + JS + 1};
+#pragma unroll
+                for (int q = 0; q < PP; ++q)
+#pragma unroll
+                    for (int r = 0; r < 4; ++r)
+                        n_eval += (vv[q] && jv[r] >= jlo && jv[r] < jhi && (!TRI || gv[r] > iv[q]))
+                                      ? 1ull : 0ull;
+            }
+#pragma unroll
+            for (int q = 0; q < PP; ++q) {
+                uint32_t e[4];
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    e[r] = lut_byte(smem, S.u0, S.shift, S.lut_last, d[q][r]);
+                    red_shared1(hl + e[r] * 128u);  // every entry is a row: bin, dummy or flagged
+                }
+                const uint32_t w = e[0] | (e[1] << 8) | (e[2] << 16) | (e[3] << 24);
+                fm[q] |= ((w + cflag) & 0x80808080u) >> (7 - t);  // bit 8 r + t
+            }
+            if (VERIFY) {
+                const float *T = reinterpret_cast<const float *>(smem + THR_OFF);
+                const double *E2 = reinterpret_cast<const double *>(smem + E2_OFF);
+                // pairs with real points on both sides (sentinels and padding give NaN)
+#pragma unroll
+                for (int q = 0; q < PP; ++q)
+#pragma unroll
+                    for (int r = 0; r < 4; ++r)
+                        if (vv[q] && !isnan(d[q][r]))
+                            n_viol += verify_pair(d[q][r], T, S.nthr, S.nb, E2, S.pa, S.pb, iv[q],
+                                                  gv[r], S.Sx, S.Sy, S.Sz);
+            }
+        }
+        uint32_t anyf = 0u;
+#pragma unroll
+        for (int q = 0; q < PP; ++q)
+            anyf |= fm[q];
+        if (__any_sync(FULL, anyf != 0u)) {
+#pragma unroll
+            for (int q = 0; q < PP; ++q) {
+                float xh, yh, zh, tmp;
+                unpack2(XH[q], xh, tmp);
+                unpack2(YH[q], yh, tmp);
+                unpack2(ZH[q], zh, tmp);
+                uint32_t m = fm[q];
+                while (m) {
+                    const int bit = __ffs(m) - 1;
+                    m &= m - 1u;
+                    const int t = bit & 7, r = bit >> 3;
+                    const int jl = jAb + t * 2 * JS + ((r & 2) ? JS : 0) + (r & 1);
+                    n_rck += resolve_local(smem, S, hl, xh, yh, zh, iv[q], jl);
+                }
+            }
         }
     }
 }
@@ -504,11 +609,12 @@ __device__ __forceinline__ int warp_bound_from(Key key, int start, int n, V v, b
     return lo + warp_bound([&](int t) { return key(lo + t); }, hi - lo, v, upper, lane);
 }
 
-template <int I, bool EVALS, bool VERIFY>
+template <int I, int PP, bool EVALS, bool VERIFY>
 __global__ void __launch_bounds__(THREADS, 3) k_xi32(const __grid_constant__ PairParams P)
 {
-    // I primaries per chunk (one per lane ii = lane % I); jj = lane / I picks the
-    // pair of secondaries.
+    // I * PP primaries per chunk (lane ii = lane % I holds primaries ii, ii + I,
+    // ...); jj = lane / I picks the pair of secondaries.
+    constexpr int CH = I * PP;
     extern __shared__ __align__(128) unsigned char smem[];
     const int nb = P.nbins;
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
@@ -525,7 +631,7 @@ __global__ void __launch_bounds__(THREADS, 3) k_xi32(const __grid_constant__ Pai
         thr[q] = P.thr[q];
     for (int q = tid; q <= nb; q += THREADS)
         E2[q] = P.E2[q];
-    for (int q = tid; q < WARPS * (nb + 1) * 32; q += THREADS)
+    for (int q = tid; q < WARPS * (nb + 2) * 32; q += THREADS)
         hist[q] = 0u;
     if (tid == 0) {
         mbar_init(bar, 1);
@@ -533,7 +639,7 @@ __global__ void __launch_bounds__(THREADS, 3) k_xi32(const __grid_constant__ Pai
     }
     __syncthreads();
 
-    uint32_t *hw = hist + warp * (nb + 1) * 32;
+    uint32_t *hw = hist + warp * (nb + 2) * 32;  // rows: bins, not counted, flagged
     const uint32_t hl = smem_u32(hw + lane);  // this lane's histogram column (shared address)
     const int ii = lane % I, jj = lane / I;
     Sweep32 S;
@@ -550,24 +656,22 @@ __global__ void __launch_bounds__(THREADS, 3) k_xi32(const __grid_constant__ Pai
     bool aborted = false;
     const float qnan = __int_as_float(0x7fc00000);
 
+    const int n_work = (int)*P.work_count;
     for (;;) {
         if (tid == 0)
             *s_item = (int)atomicAdd(P.item_counter, 1u);
         __syncthreads();
         const int item = *s_item;
         __syncthreads();
-        if (item >= P.n_items)
+        if (item >= n_work)
             break;
         Item it;
-        if (!decode_item(P, item, it))
-            continue;
-        if (tid == 0)
-            atomicAdd(&P.diag[0], 1ull);
+        decode_item(P, item, it);
         const float dzw = __fadd_ru(__double2float_ru(it.dzmax), P.zslack);
         const float Sxf = __double2float_rn(it.Sx), Syf = __double2float_rn(it.Sy);
         S.Sx = it.Sx;
         S.Sy = it.Sy;
-        const int nchunks = (it.a1 - it.a0 + I - 1) / I;
+        const int nchunks = (it.a1 - it.a0 + CH - 1) / CH;
 
         for (int t0 = it.b0; t0 < it.b1; t0 += TILE32) {
             const int nt = min(TILE32, it.b1 - t0);
@@ -584,20 +688,31 @@ __global__ void __launch_bounds__(THREADS, 3) k_xi32(const __grid_constant__ Pai
             int lo_prev[3] = {0, 0, 0}, hi_prev[3] = {0, 0, 0};
 
             for (int c = warp; c < nchunks; c += WARPS) {
-                const int ib = it.a0 + c * I;
-                const int nvi = min(I, it.a1 - ib);
-                const int i = ib + ii;
-                float xi = qnan, yi = qnan, zi = qnan;
-                if (ii < nvi) {
-                    xi = P.A.xs[i];
-                    yi = P.A.ys[i];
-                    zi = P.A.zs[i];
+                const int ib = it.a0 + c * CH;
+                u64 XH[PP], YH[PP], ZH[PP];
+                int iv[PP];
+                bool vv[PP];
+                float zq[PP];
+                float zmax = qnan;
+#pragma unroll
+                for (int q = 0; q < PP; ++q) {
+                    const int i = ib + q * I + ii;
+                    float xi = qnan, yi = qnan, zi = qnan;
+                    if (i < it.a1) {
+                        xi = P.A.xs[i];
+                        yi = P.A.ys[i];
+                        zi = P.A.zs[i];
+                    }
+                    iv[q] = i;
+                    vv[q] = !isnan(xi);  // chunk tail and column padding are NaN
+                    const float xh = __fsub_rn(xi, Sxf), yh = __fsub_rn(yi, Syf);
+                    XH[q] = pack2(xh, xh);
+                    YH[q] = pack2(yh, yh);
+                    zq[q] = zi;
+                    zmax = (isnan(zmax) || zi > zmax) ? zi : zmax;
                 }
-                const bool vi = !isnan(xi);  // chunk tail and column padding are NaN
-                const float xh = __fsub_rn(xi, Sxf), yh = __fsub_rn(yi, Syf);
-                const u64 XH = pack2(xh, xh), YH = pack2(yh, yh);
-                const float zlo = __shfl_sync(FULL, zi, 0);
-                float zhi = zi;
+                const float zlo = __shfl_sync(FULL, zq[0], 0);
+                float zhi = zmax;
 #pragma unroll
                 for (int o = 1; o < I; o <<= 1) {  // largest real z of the chunk
                     const float t = __shfl_xor_sync(FULL, zhi, o);
@@ -624,16 +739,19 @@ __global__ void __launch_bounds__(THREADS, 3) k_xi32(const __grid_constant__ Pai
                         jlo = max(jlo, ib + 1 - t0);
                     if (jlo >= jhi)
                         continue;
-                    pending += (unsigned)((jhi - jlo) / (64 / I) + 4) * 2u;
-                    const float zh = __fsub_rn(zi, kz);
-                    const u64 ZH = pack2(zh, zh);
+                    pending += (unsigned)((jhi - jlo) / (64 / I) + 4) * 2u * PP;
+#pragma unroll
+                    for (int q = 0; q < PP; ++q) {
+                        const float zh = __fsub_rn(zq[q], kz);
+                        ZH[q] = pack2(zh, zh);
+                    }
                     S.Sz = k == 0 ? 0.0 : (k > 0 ? P.g.box[2] : -P.g.box[2]);
                     if (tri)
-                        sweep32<I, true, EVALS, VERIFY>(smem, S, hl, jlo, jhi, jj, XH, YH, ZH, i, vi,
-                                                     n_eval, n_rck, n_viol);
+                        sweep32<I, PP, true, EVALS, VERIFY>(smem, S, hl, jlo, jhi, jj, XH, YH, ZH, iv,
+                                                         vv, n_eval, n_rck, n_viol);
                     else
-                        sweep32<I, false, EVALS, VERIFY>(smem, S, hl, jlo, jhi, jj, XH, YH, ZH, i,
-                                                      vi, n_eval, n_rck, n_viol);
+                        sweep32<I, PP, false, EVALS, VERIFY>(smem, S, hl, jlo, jhi, jj, XH, YH, ZH,
+                                                          iv, vv, n_eval, n_rck, n_viol);
                 }
                 if (pending > (1u << 30)) {  // keep every per-lane u32 count far from overflow
                     __syncwarp();
@@ -651,7 +769,7 @@ __global__ void __launch_bounds__(THREADS, 3) k_xi32(const __grid_constant__ Pai
         u64 sum = 0;
         for (int w = 0; w < WARPS; ++w)
             for (int l = 0; l < 32; ++l)
-                sum += hist[(w * (nb + 1) + bn) * 32 + l];
+                sum += hist[(w * (nb + 2) + bn) * 32 + l];
         if (sum)
             atomicAdd(&P.hist[bn], sum);
     }
@@ -718,13 +836,10 @@ __device__ __forceinline__ void acc_pair(const AccW &A, uint32_t row, float pw, 
 // Flagged table cell, weighted kernel: as resolve_pair, but the pair's weight
 // and r * weight go with it to its true bin.
 __device__ __forceinline__ int resolve_pair_w(const unsigned char *smem, const Sweep32 &S,
-                                              const AccW &A, uint32_t e, float d2, float pw, int i,
-                                              int jg)
+                                              const AccW &A, float d2, float pw, int i, int jg)
 {
     const float *T = reinterpret_cast<const float *>(smem + THR_OFF);
-    int c = (int)(e & 0x7fu) * 2;
-    while (c < S.nthr && T[c] <= d2)
-        ++c;
+    const int c = thr_count(T, S.nthr, d2);
     int row;
     int re = 0;
     if (!(c & 1)) {
@@ -798,20 +913,20 @@ __device__ __forceinline__ void sweep32w(unsigned char *smem, const Sweep32 &S, 
         const uint32_t ea1 = lut_byte(smem, S.u0, S.shift, S.lut_last, a1);
         const uint32_t eb0 = lut_byte(smem, S.u0, S.shift, S.lut_last, b0);
         const uint32_t eb1 = lut_byte(smem, S.u0, S.shift, S.lut_last, b1);
-        // flagged entries -> dummy row here, settled below
+        // flagged entries -> the not-counted row here, settled below
         acc_pair(A, min(ea0, nbu), pa0, sqrt_approx(a0) * pa0);
         acc_pair(A, min(ea1, nbu), pa1, sqrt_approx(a1) * pa1);
         acc_pair(A, min(eb0, nbu), pb0, sqrt_approx(b0) * pb0);
         acc_pair(A, min(eb1, nbu), pb1, sqrt_approx(b1) * pb1);
-        if (__any_sync(FULL, (ea0 | ea1 | eb0 | eb1) & LUT_FLAG)) {
-            if (ea0 & LUT_FLAG)
-                n_rck += resolve_pair_w(smem, S, A, ea0, a0, pa0, i, gA);
-            if (ea1 & LUT_FLAG)
-                n_rck += resolve_pair_w(smem, S, A, ea1, a1, pa1, i, gA + 1);
-            if (eb0 & LUT_FLAG)
-                n_rck += resolve_pair_w(smem, S, A, eb0, b0, pb0, i, gB);
-            if (eb1 & LUT_FLAG)
-                n_rck += resolve_pair_w(smem, S, A, eb1, b1, pb1, i, gB + 1);
+        if (__any_sync(FULL, max(max(ea0, ea1), max(eb0, eb1)) > nbu)) {
+            if (ea0 > nbu)
+                n_rck += resolve_pair_w(smem, S, A, a0, pa0, i, gA);
+            if (ea1 > nbu)
+                n_rck += resolve_pair_w(smem, S, A, a1, pa1, i, gA + 1);
+            if (eb0 > nbu)
+                n_rck += resolve_pair_w(smem, S, A, b0, pb0, i, gB);
+            if (eb1 > nbu)
+                n_rck += resolve_pair_w(smem, S, A, b1, pb1, i, gB + 1);
         }
     }
 }
@@ -873,19 +988,17 @@ __global__ void __launch_bounds__(THREADS, 2) k_xi32w(const __grid_constant__ Pa
     bool aborted = false;
     const float qnan = __int_as_float(0x7fc00000);
 
+    const int n_work = (int)*P.work_count;
     for (;;) {
         if (tid == 0)
             *s_item = (int)atomicAdd(P.item_counter, 1u);
         __syncthreads();
         const int item = *s_item;
         __syncthreads();
-        if (item >= P.n_items)
+        if (item >= n_work)
             break;
         Item it;
-        if (!decode_item(P, item, it))
-            continue;
-        if (tid == 0)
-            atomicAdd(&P.diag[0], 1ull);
+        decode_item(P, item, it);
         const float dzw = __fadd_ru(__double2float_ru(it.dzmax), P.zslack);
         const float Sxf = __double2float_rn(it.Sx), Syf = __double2float_rn(it.Sy);
         S.Sx = it.Sx;
@@ -1035,19 +1148,17 @@ __global__ void __launch_bounds__(THREADS) k_xi64(const __grid_constant__ PairPa
     bool aborted = false;
     const double qnan = __longlong_as_double(0x7ff8000000000000ll);
 
+    const int n_work = (int)*P.work_count;
     for (;;) {
         if (tid == 0)
             *s_item = (int)atomicAdd(P.item_counter, 1u);
         __syncthreads();
         const int item = *s_item;
         __syncthreads();
-        if (item >= P.n_items)
+        if (item >= n_work)
             break;
         Item it;
-        if (!decode_item(P, item, it))
-            continue;
-        if (tid == 0)
-            atomicAdd(&P.diag[0], 1ull);
+        decode_item(P, item, it);
         const double dzw = __dadd_rn(it.dzmax, 1e-9 * (P.rz + P.g.box[2] + 1.0));
         const int nchunks = (it.a1 - it.a0 + I - 1) / I;
 
@@ -1239,11 +1350,9 @@ __device__ __forceinline__ int resolve_rppi(const unsigned char *smem, const Swe
                                             uint32_t addr_main, int i, int jg, float pw)
 {
     int k, re = 0;
-    if (e & LUT_FLAG) {
+    if (e > (uint32_t)S.nb) {
         const float *T = reinterpret_cast<const float *>(smem + THR_OFF);
-        int c = (int)(e & 0x7fu) * 2;
-        while (c < S.nthr && T[c] <= rp2)
-            ++c;
+        const int c = thr_count(T, S.nthr, rp2);
         if (c & 1) {
             k = recheck_rp64(reinterpret_cast<const double *>(smem + E2_OFF), S.nb, S.pa, S.pb, i,
                              jg, S.Sx, S.Sy);
@@ -1358,23 +1467,25 @@ __device__ __forceinline__ void sweep_rppi32(unsigned char *smem, const SweepRP 
                 unpack2(fmul2(*reinterpret_cast<const u64 *>(pw8 + 4 * JS), WH), wb0, wb1);
             }
             // pairs settled by the float32 path; flagged ones are added when resolved
-            if (!(ea0 & LUT_FLAG) && !pa0 && ea0 < nbu && ma0 < npiu)
+            if (!pa0 && ea0 < nbu && ma0 < npiu)
                 acc_rppi(S, (int)(ea0 * (npiu + 1) + ma0), wa0, a0);
-            if (!(ea1 & LUT_FLAG) && !pa1 && ea1 < nbu && ma1 < npiu)
+            if (!pa1 && ea1 < nbu && ma1 < npiu)
                 acc_rppi(S, (int)(ea1 * (npiu + 1) + ma1), wa1, a1);
-            if (!(eb0 & LUT_FLAG) && !pb0 && eb0 < nbu && mb0 < npiu)
+            if (!pb0 && eb0 < nbu && mb0 < npiu)
                 acc_rppi(S, (int)(eb0 * (npiu + 1) + mb0), wb0, b0);
-            if (!(eb1 & LUT_FLAG) && !pb1 && eb1 < nbu && mb1 < npiu)
+            if (!pb1 && eb1 < nbu && mb1 < npiu)
                 acc_rppi(S, (int)(eb1 * (npiu + 1) + mb1), wb1, b1);
         }
-        if (__any_sync(FULL, ((ea0 | ea1 | eb0 | eb1) & LUT_FLAG) || pa0 || pa1 || pb0 || pb1)) {
-            if ((ea0 & LUT_FLAG) || pa0)
+        const bool ga0 = ea0 > nbu || pa0, ga1 = ea1 > nbu || pa1;
+        const bool gb0 = eb0 > nbu || pb0, gb1 = eb1 > nbu || pb1;
+        if (__any_sync(FULL, ga0 || ga1 || gb0 || gb1)) {
+            if (ga0)
                 n_rck += resolve_rppi<WACC>(smem, S, ea0, a0, ma0, pa0, ha0, i, gA, wa0);
-            if ((ea1 & LUT_FLAG) || pa1)
+            if (ga1)
                 n_rck += resolve_rppi<WACC>(smem, S, ea1, a1, ma1, pa1, ha1, i, gA + 1, wa1);
-            if ((eb0 & LUT_FLAG) || pb0)
+            if (gb0)
                 n_rck += resolve_rppi<WACC>(smem, S, eb0, b0, mb0, pb0, hb0, i, gB, wb0);
-            if ((eb1 & LUT_FLAG) || pb1)
+            if (gb1)
                 n_rck += resolve_rppi<WACC>(smem, S, eb1, b1, mb1, pb1, hb1, i, gB + 1, wb1);
         }
         if (VERIFY) {
@@ -1498,19 +1609,17 @@ __global__ void __launch_bounds__(THREADS, 3) k_rppi32(const __grid_constant__ P
     bool aborted = false;
     const float qnan = __int_as_float(0x7fc00000);
 
+    const int n_work = (int)*P.work_count;
     for (;;) {
         if (tid == 0)
             *s_item = (int)atomicAdd(P.item_counter, 1u);
         __syncthreads();
         const int item = *s_item;
         __syncthreads();
-        if (item >= P.n_items)
+        if (item >= n_work)
             break;
         Item it;
-        if (!decode_item(P, item, it))
-            continue;
-        if (tid == 0)
-            atomicAdd(&P.diag[0], 1ull);
+        decode_item(P, item, it);
         const float dzw = __fadd_ru(__double2float_ru(it.dzmax), P.zslack);
         const float Sxf = __double2float_rn(it.Sx), Syf = __double2float_rn(it.Sy);
         S.Sx = it.Sx;
@@ -1654,19 +1763,17 @@ __global__ void __launch_bounds__(THREADS) k_rppi64(const __grid_constant__ Pair
     bool aborted = false;
     const double qnan = __longlong_as_double(0x7ff8000000000000ll);
 
+    const int n_work = (int)*P.work_count;
     for (;;) {
         if (tid == 0)
             *s_item = (int)atomicAdd(P.item_counter, 1u);
         __syncthreads();
         const int item = *s_item;
         __syncthreads();
-        if (item >= P.n_items)
+        if (item >= n_work)
             break;
         Item it;
-        if (!decode_item(P, item, it))
-            continue;
-        if (tid == 0)
-            atomicAdd(&P.diag[0], 1ull);
+        decode_item(P, item, it);
         const double dzw = __dadd_rn(it.dzmax, 1e-9 * (P.rz + P.g.box[2] + 1.0));
         const int nchunks = (it.a1 - it.a0 + I - 1) / I;
 
@@ -1827,6 +1934,12 @@ cudaError_t launch_persistent(K kern, const PairParams &P, PairLaunch &L, int sm
 
 cudaError_t launch_pairs(const PairParams &P, PairLaunch &L, int sms, cudaStream_t st)
 {
+    if (P.n_items <= 0)
+        return cudaSuccess;
+    k_worklist<<<(P.n_items + 255) / 256, 256, 0, st>>>(P);
+    const cudaError_t e = cudaGetLastError();
+    if (e)
+        return e;
     if (P.kind == 1) {
         if (L.f64) {
             if (P.wacc)
@@ -1865,17 +1978,24 @@ cudaError_t launch_pairs(const PairParams &P, PairLaunch &L, int sms, cudaStream
         return L.evals ? launch_persistent(k_xi32w<16, true>, P, L, sms, st)
                        : launch_persistent(k_xi32w<16, false>, P, L, sms, st);
     if (L.verify)
-        return launch_persistent(k_xi32<8, true, true>, P, L, sms, st);
+        return launch_persistent(k_xi32<8, 1, true, true>, P, L, sms, st);
+    if (L.pp == 2) {
+        if (L.chunk == 8)
+            return L.evals ? launch_persistent(k_xi32<8, 2, true, false>, P, L, sms, st)
+                           : launch_persistent(k_xi32<8, 2, false, false>, P, L, sms, st);
+        return L.evals ? launch_persistent(k_xi32<16, 2, true, false>, P, L, sms, st)
+                       : launch_persistent(k_xi32<16, 2, false, false>, P, L, sms, st);
+    }
     switch (L.chunk) {
     case 16:
-        return L.evals ? launch_persistent(k_xi32<16, true, false>, P, L, sms, st)
-                       : launch_persistent(k_xi32<16, false, false>, P, L, sms, st);
+        return L.evals ? launch_persistent(k_xi32<16, 1, true, false>, P, L, sms, st)
+                       : launch_persistent(k_xi32<16, 1, false, false>, P, L, sms, st);
     case 32:
-        return L.evals ? launch_persistent(k_xi32<32, true, false>, P, L, sms, st)
-                       : launch_persistent(k_xi32<32, false, false>, P, L, sms, st);
+        return L.evals ? launch_persistent(k_xi32<32, 1, true, false>, P, L, sms, st)
+                       : launch_persistent(k_xi32<32, 1, false, false>, P, L, sms, st);
     default:
-        return L.evals ? launch_persistent(k_xi32<8, true, false>, P, L, sms, st)
-                       : launch_persistent(k_xi32<8, false, false>, P, L, sms, st);
+        return L.evals ? launch_persistent(k_xi32<8, 1, true, false>, P, L, sms, st)
+                       : launch_persistent(k_xi32<8, 1, false, false>, P, L, sms, st);
     }
 }
 

@@ -32,7 +32,8 @@ __host__ __device__ inline Smem64 smem64_layout(int tile_max, int nbins, int npi
 
 struct PairLaunch {
     int f64;         // 1: binary64 path
-    int chunk;       // primary points per warp chunk (8, 16 or 32)
+    int chunk;       // primary lanes per warp chunk (8, 16 or 32)
+    int pp;          // primaries per lane (1 or 2; float32 DD(r))
     int evals;       // count evaluations
     int verify;      // verify float32 decisions against binary64
     int blocks;      // persistent CTAs
