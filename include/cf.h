@@ -93,6 +93,15 @@ typedef struct {
                             granularity of the in-column sort.                   */
     uint32_t flags;      /* CF_FLAG_*                                             */
     void *stream;        /* cudaStream_t to run on; NULL = legacy default stream  */
+    int autotune;        /* 1: choose refine (and the float32 DD(r) kernel shape)
+                            by timing candidates once per problem signature and
+                            caching the winner (Sec. 3.1 asks for an automatic
+                            choice of the refinement); fields set explicitly
+                            (refine != {0,0,0}, pair_chunk, pair_pp) are kept.   */
+    int pair_chunk;      /* float32 DD(r) kernel: primary lanes per warp chunk
+                            (8, 16 or 32); 0 = default 16                         */
+    int pair_pp;         /* float32 DD(r) kernel: primaries per lane (1 or 2);
+                            0 = default 2                                         */
 } cf_config;
 
 /* Caller-owned host outputs.  Arrays are NULL when not wanted. */
@@ -108,7 +117,13 @@ typedef struct {
     double kernel_ms;           /* device time of the pair kernel                 */
     double total_ms;            /* device time of the whole call                  */
     uint64_t n_kernels;         /* kernels the call launched (gridding, bounding
-                                   box, pair kernel; copies and memsets excluded) */
+                                   box, work list, pair kernel; copies and memsets
+                                   excluded)                                      */
+    int refine_used[3];         /* refinement the call used                        */
+    int chunk_used, pp_used;    /* float32 DD(r) kernel shape the call used        */
+    int tuned;                  /* 0 no autotuning, 1 this call tuned (timed the
+                                   candidates, then counted with the winner),
+                                   2 the cached choice was used                   */
 } cf_result;
 
 /*
@@ -164,6 +179,26 @@ int cf_countpairs_rp_pi(int autocorr, const cf_catalog *d1, const cf_catalog *d2
 int cf_countpairs_xi_noalloc(int autocorr, const cf_catalog *d1, const cf_catalog *d2,
                              const double *edges, int nedges, const cf_config *cfg,
                              cf_result *res);
+
+/*
+ * Autotuner cache (Sec. 3.1 leaves the refinement to the user and asks for an
+ * automatic choice).  Entries map a problem signature -- kind, mode, dtype,
+ * auto/cross, periodic, weighted, half-octave buckets of N1, N2 and of the
+ * mean neighbour count within Rmax, number of bins -- to the refinement and
+ * kernel shape that timed fastest.  The cache lives in host memory of the
+ * process (shared by all threads); with the environment variable
+ * CF_TUNE_CACHE=<path> it is loaded from that JSON file on first use and
+ * written back after every new entry.
+ *   cf_tune_save/cf_tune_load: write / merge a JSON file ({"version": 1,
+ *     "entries": [{"key", "refine", "chunk", "pp", "ms"}, ...]}).  CF_EINVAL
+ *     for an unreadable or malformed file (the cache is left unchanged).
+ *   cf_tune_clear: drop every entry.   cf_tune_count: number of entries.
+ * None of these touch the GPU.
+ */
+int cf_tune_save(const char *path);
+int cf_tune_load(const char *path);
+int cf_tune_clear(void);
+int cf_tune_count(void);
 
 /* Text of the last non-zero status returned on the calling thread. */
 const char *cf_last_error(void);

@@ -34,7 +34,8 @@ _STATUS = {CF_EINVAL: "CF_EINVAL", CF_ENOMEM: "CF_ENOMEM", CF_ECUDA: "CF_ECUDA",
 
 # Names exported by the library; they must match include/cf.h.
 EXPORTS = ("cf_countpairs_xi", "cf_countpairs_rp_pi", "cf_last_error", "cf_version",
-           "cf_countpairs_xi_noalloc")
+           "cf_countpairs_xi_noalloc", "cf_tune_save", "cf_tune_load", "cf_tune_clear",
+           "cf_tune_count")
 
 
 class cf_catalog(ctypes.Structure):
@@ -46,7 +47,8 @@ class cf_config(ctypes.Structure):
     _fields_ = [("periodic", ctypes.c_int), ("boxsize", ctypes.c_double * 3),
                 ("dtype", ctypes.c_int), ("mode", ctypes.c_int), ("weighted", ctypes.c_int),
                 ("want_ravg", ctypes.c_int), ("refine", ctypes.c_int * 3),
-                ("flags", ctypes.c_uint32), ("stream", ctypes.c_void_p)]
+                ("flags", ctypes.c_uint32), ("stream", ctypes.c_void_p), ("autotune", ctypes.c_int),
+                ("pair_chunk", ctypes.c_int), ("pair_pp", ctypes.c_int)]
 
 
 class cf_result(ctypes.Structure):
@@ -54,7 +56,9 @@ class cf_result(ctypes.Structure):
                 ("ravg", ctypes.POINTER(ctypes.c_double)), ("n_cellpairs", ctypes.c_uint64),
                 ("n_evaluated", ctypes.c_uint64), ("n_rechecked", ctypes.c_uint64),
                 ("n_band_violations", ctypes.c_uint64), ("kernel_ms", ctypes.c_double),
-                ("total_ms", ctypes.c_double), ("n_kernels", ctypes.c_uint64)]
+                ("total_ms", ctypes.c_double), ("n_kernels", ctypes.c_uint64),
+                ("refine_used", ctypes.c_int * 3), ("chunk_used", ctypes.c_int),
+                ("pp_used", ctypes.c_int), ("tuned", ctypes.c_int)]
 
 
 class CfError(RuntimeError):
@@ -109,6 +113,10 @@ class Result:
     kernel_ms: float
     total_ms: float
     n_kernels: int = 0
+    refine_used: tuple = (0, 0, 0)
+    chunk_used: int = 0
+    pp_used: int = 0
+    tuned: int = 0
 
 
 def _is_torch(a) -> bool:
@@ -147,8 +155,13 @@ def _catalog(x, y, z, w, keep):
     return cf_catalog(ax[0], ay[0], az[0], wp, ax[2]), ax[1], ax[3]
 
 
-def _config(dtype, periodic, boxsize, mode, weighted, want_ravg, refine, flags, stream, cuda):
+def _config(dtype, periodic, boxsize, mode, weighted, want_ravg, refine, flags, stream, cuda,
+            tuning=None):
     c = cf_config()
+    tuning = tuning or {}
+    c.autotune = 1 if tuning.get("autotune") else 0
+    c.pair_chunk = int(tuning.get("pair_chunk", 0))
+    c.pair_pp = int(tuning.get("pair_pp", 0))
     c.periodic = 1 if periodic else 0
     b = np.broadcast_to(np.asarray(boxsize if boxsize is not None else 0.0, dtype=np.float64), (3,))
     c.boxsize[:] = [float(v) for v in b]
@@ -166,7 +179,7 @@ def _config(dtype, periodic, boxsize, mode, weighted, want_ravg, refine, flags, 
 
 
 def _run(fn, nslots, autocorr, x, y, z, w, x2, y2, z2, w2, extra, periodic, boxsize, mode,
-         want_ravg, refine, flags, stream):
+         want_ravg, refine, flags, stream, tuning=None):
     L = lib()
     keep = []
     c1, dt, cuda = _catalog(x, y, z, w, keep)
@@ -179,7 +192,8 @@ def _run(fn, nslots, autocorr, x, y, z, w, x2, y2, z2, w2, extra, periodic, boxs
             raise ValueError("both catalogues must share one dtype")
         cuda = cuda or cuda2
     weighted = w is not None
-    cfg = _config(dt, periodic, boxsize, mode, weighted, want_ravg, refine, flags, stream, cuda)
+    cfg = _config(dt, periodic, boxsize, mode, weighted, want_ravg, refine, flags, stream, cuda,
+                  tuning)
     npairs = np.zeros(nslots, dtype=np.uint64)
     wsum = np.zeros(nslots) if weighted else None
     ravg = np.zeros(nslots) if want_ravg else None
@@ -193,12 +207,14 @@ def _run(fn, nslots, autocorr, x, y, z, w, x2, y2, z2, w2, extra, periodic, boxs
         raise CfError(st, L.cf_last_error().decode())
     return Result(npairs, wsum, ravg, int(res.n_cellpairs), int(res.n_evaluated),
                   int(res.n_rechecked), int(res.n_band_violations), float(res.kernel_ms),
-                  float(res.total_ms), int(res.n_kernels))
+                  float(res.total_ms), int(res.n_kernels), tuple(res.refine_used),
+                  int(res.chunk_used), int(res.pp_used), int(res.tuned))
 
 
 def countpairs_xi(x, y, z, edges, *, w=None, x2=None, y2=None, z2=None, w2=None, autocorr=None,
                   periodic=True, boxsize=420.0, mode="fp32_recheck", want_ravg=False,
-                  refine=(0, 0, 0), flags=0, stream=None) -> Result:
+                  refine=(0, 0, 0), flags=0, stream=None, autotune=False, pair_chunk=0,
+                  pair_pp=0) -> Result:
     """DD(r) histogram through ``cf_countpairs_xi`` (see include/cf.h)."""
     edges = np.ascontiguousarray(edges, dtype=np.float64)
     if autocorr is None:
@@ -206,12 +222,14 @@ def countpairs_xi(x, y, z, edges, *, w=None, x2=None, y2=None, z2=None, w2=None,
     fn = lambda L, *a: L.cf_countpairs_xi(*a)  # noqa: E731
     extra = (edges.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), int(edges.size))
     return _run(fn, edges.size - 1, autocorr, x, y, z, w, x2, y2, z2, w2, extra, periodic, boxsize,
-                mode, want_ravg, refine, flags, stream)
+                mode, want_ravg, refine, flags, stream,
+                dict(autotune=autotune, pair_chunk=pair_chunk, pair_pp=pair_pp))
 
 
 def countpairs_rp_pi(x, y, z, rp_edges, pimax, npibins, *, w=None, x2=None, y2=None, z2=None,
                      w2=None, autocorr=None, periodic=True, boxsize=420.0, mode="fp32_recheck",
-                     want_ravg=False, refine=(0, 0, 0), flags=0, stream=None) -> Result:
+                     want_ravg=False, refine=(0, 0, 0), flags=0, stream=None,
+                     autotune=False) -> Result:
     """DD(rp, pi) histogram (rp-major, shape (nrp, npibins)) through ``cf_countpairs_rp_pi``."""
     rp_edges = np.ascontiguousarray(rp_edges, dtype=np.float64)
     if autocorr is None:
@@ -220,7 +238,7 @@ def countpairs_rp_pi(x, y, z, rp_edges, pimax, npibins, *, w=None, x2=None, y2=N
     extra = (rp_edges.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), int(rp_edges.size),
              ctypes.c_double(float(pimax)), int(npibins))
     r = _run(fn, (rp_edges.size - 1) * int(npibins), autocorr, x, y, z, w, x2, y2, z2, w2, extra,
-             periodic, boxsize, mode, want_ravg, refine, flags, stream)
+             periodic, boxsize, mode, want_ravg, refine, flags, stream, dict(autotune=autotune))
     shp = (rp_edges.size - 1, int(npibins))
     r.npairs = r.npairs.reshape(shp)
     if r.wsum is not None:
@@ -232,6 +250,34 @@ def countpairs_rp_pi(x, y, z, rp_edges, pimax, npibins, *, w=None, x2=None, y2=N
 
 def version() -> str:
     return lib().cf_version().decode()
+
+
+def _tune_call(name, *args):
+    L = lib()
+    f = getattr(L, name)
+    f.restype = ctypes.c_int
+    st = f(*args)
+    if st < 0:
+        raise CfError(st, L.cf_last_error().decode())
+    return st
+
+
+def tune_save(path: str) -> None:
+    """Write the autotuner cache to a JSON file (``cf_tune_save``)."""
+    _tune_call("cf_tune_save", os.fsencode(path))
+
+
+def tune_load(path: str) -> None:
+    """Merge a JSON autotuner cache file into the cache (``cf_tune_load``)."""
+    _tune_call("cf_tune_load", os.fsencode(path))
+
+
+def tune_clear() -> None:
+    _tune_call("cf_tune_clear")
+
+
+def tune_count() -> int:
+    return _tune_call("cf_tune_count")
 
 
 def countpairs_xi_noalloc(x, y, z, edges, *, x2=None, y2=None, z2=None, autocorr=None,

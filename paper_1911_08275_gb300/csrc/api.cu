@@ -10,6 +10,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -393,6 +394,10 @@ int validate(const Request &q)
     for (int a = 0; a < 3; ++a)
         if (c->refine[a] < 0 || c->refine[a] > 16)
             return fail(CF_EINVAL, "refine factors must be in [0, 16]");
+    if (c->pair_chunk != 0 && c->pair_chunk != 8 && c->pair_chunk != 16 && c->pair_chunk != 32)
+        return fail(CF_EINVAL, "pair_chunk must be 0, 8, 16 or 32");
+    if (c->pair_pp < 0 || c->pair_pp > 2)
+        return fail(CF_EINVAL, "pair_pp must be 0, 1 or 2");
     return CF_OK;
 }
 
@@ -408,20 +413,31 @@ void finish_geom(cf::Geom &g)
     }
 }
 
+// The refinement a call uses: {0,0,0} -> the paper's default (2, 2, 1);
+// x, y clamped to [1, MAX_REACH], z to >= 1.
+void resolve_refine(const cf_config *c, int r[3])
+{
+    r[0] = c->refine[0];
+    r[1] = c->refine[1];
+    r[2] = c->refine[2];
+    if (r[0] == 0 && r[1] == 0 && r[2] == 0) {
+        r[0] = 2;
+        r[1] = 2;
+        r[2] = 1;
+    }
+    r[0] = std::max(1, std::min(r[0], cf::MAX_REACH));
+    r[1] = std::max(1, std::min(r[1], cf::MAX_REACH));
+    r[2] = std::max(1, r[2]);
+}
+
 // Grid geometry: columns of side >= Rxy / refine in x, y; z-cells for the sort.
 int plan_geom(const Request &q, const double lo[3], const double hi[3], long long ntot, cf::Geom &g)
 {
     const cf_config *c = q.cfg;
     const double R = q.edges.back();
-    int rx = c->refine[0], ry = c->refine[1], rz = c->refine[2];
-    if (rx == 0 && ry == 0 && rz == 0) {
-        rx = 2;
-        ry = 2;
-        rz = 1;
-    }
-    rx = std::max(1, std::min(rx, cf::MAX_REACH));
-    ry = std::max(1, std::min(ry, cf::MAX_REACH));
-    rz = std::max(1, rz);
+    int rr[3];
+    resolve_refine(c, rr);
+    const int rx = rr[0], ry = rr[1], rz = rr[2];
     std::memset(&g, 0, sizeof(g));
     g.periodic = c->periodic ? 1 : 0;
     for (int a = 0; a < 3; ++a) {
@@ -497,6 +513,10 @@ int run(Request &q)
     res->n_cellpairs = res->n_evaluated = res->n_rechecked = res->n_band_violations = 0;
     res->kernel_ms = res->total_ms = 0.0;
     res->n_kernels = 0;
+    resolve_refine(c, res->refine_used);
+    res->chunk_used = c->pair_chunk ? c->pair_chunk : 16;
+    res->pp_used = c->pair_pp ? c->pair_pp : 2;
+    res->tuned = 0;
 
     int dev = 0, sms = 0;
     void *ws = nullptr, *ws2 = nullptr;
@@ -744,18 +764,8 @@ int run(Request &q)
         P.work_count = d_wcount;
 
         PL.f64 = f64;
-        PL.chunk = 16;
-        PL.pp = 2;
-        if (const char *ev = std::getenv("CF_PAIR_CHUNK")) {  // tuning experiments
-            const int c = std::atoi(ev);
-            if (c == 8 || c == 16 || c == 32)
-                PL.chunk = c;
-        }
-        if (const char *ev = std::getenv("CF_PAIR_PP")) {
-            const int v = std::atoi(ev);
-            if (v == 1 || v == 2)
-                PL.pp = v;
-        }
+        PL.chunk = c->pair_chunk ? c->pair_chunk : 16;
+        PL.pp = c->pair_pp ? c->pair_pp : 2;
         PL.evals = (c->flags & (CF_FLAG_COUNT_EVALS | CF_FLAG_VERIFY_BAND)) ? 1 : 0;
         PL.verify = (!f64 && (c->flags & CF_FLAG_VERIFY_BAND)) ? 1 : 0;
         cf::plan_pairs(P, PL);
@@ -843,6 +853,263 @@ cleanup:
     return rc;
 }
 
+
+// ---------------------------------------------------------------- autotuner
+// Sec. 3.1 sweeps the refinement by hand and asks for an automatic choice: the
+// tuner times a few candidates once per problem signature (the counts do not
+// depend on the choice) and caches the fastest.
+struct TuneChoice {
+    int refine[3];
+    int chunk, pp;
+    double ms;
+};
+
+struct TuneCache {
+    std::mutex mu;
+    std::map<std::string, TuneChoice> m;
+    bool env_loaded = false;
+};
+TuneCache g_tune;
+
+int bucket(double v) { return (int)std::lround(2.0 * std::log2(std::max(v, 1e-3))); }
+
+// Problem signature (half-octave buckets of the sizes and of the mean number of
+// neighbours within reach).  vol: box volume (periodic) or bounding-box volume.
+std::string tune_key(const Request &q, double vol)
+{
+    const cf_config *c = q.cfg;
+    const double R = q.edges.back();
+    const double n1 = (double)q.d1->n, n2 = (double)(q.autocorr ? q.d1->n : q.d2->n);
+    const double reach = q.kind == 0 ? 4.0 / 3.0 * M_PI * R * R * R : M_PI * R * R * 2.0 * q.pimax;
+    const double nbr = n2 * reach / std::max(vol, 1e-300);
+    char buf[160];
+    std::snprintf(buf, sizeof(buf), "k%d m%d d%d a%d p%d w%d n%d n%d r%d b%d", q.kind, (int)c->mode,
+                  (int)c->dtype, q.autocorr, c->periodic ? 1 : 0,
+                  (c->weighted || c->want_ravg) ? 1 : 0, bucket(n1), bucket(n2), bucket(nbr),
+                  (int)(q.edges.size() - 1) * (q.kind == 1 ? q.npibins : 1));
+    return buf;
+}
+
+int tune_save_locked(const char *path)
+{
+    FILE *f = std::fopen(path, "w");
+    if (!f)
+        return fail(CF_EINVAL, std::string("cannot write tuning cache ") + path);
+    std::fprintf(f, "{\"version\": 1, \"entries\": [");
+    bool first = true;
+    for (const auto &kv : g_tune.m) {
+        const TuneChoice &t = kv.second;
+        std::fprintf(f, "%s\n {\"key\": \"%s\", \"refine\": [%d, %d, %d], \"chunk\": %d, \"pp\": %d, "
+                        "\"ms\": %.6g}",
+                     first ? "" : ",", kv.first.c_str(), t.refine[0], t.refine[1], t.refine[2],
+                     t.chunk, t.pp, t.ms);
+        first = false;
+    }
+    std::fprintf(f, "\n]}\n");
+    return std::fclose(f) == 0 ? CF_OK : fail(CF_EINVAL, "error writing tuning cache");
+}
+
+// Parses the format tune_save_locked writes; all or nothing.
+int tune_load_locked(const char *path)
+{
+    FILE *f = std::fopen(path, "r");
+    if (!f)
+        return fail(CF_EINVAL, std::string("cannot read tuning cache ") + path);
+    std::string txt;
+    char buf[4096];
+    size_t got;
+    while ((got = std::fread(buf, 1, sizeof(buf), f)) > 0)
+        txt.append(buf, got);
+    std::fclose(f);
+    if (txt.find("\"version\": 1") == std::string::npos)
+        return fail(CF_EINVAL, "tuning cache: missing version 1");
+    std::map<std::string, TuneChoice> add;
+    size_t pos = 0;
+    while ((pos = txt.find("{\"key\": \"", pos)) != std::string::npos) {
+        pos += 9;
+        const size_t end = txt.find('"', pos);
+        if (end == std::string::npos)
+            return fail(CF_EINVAL, "tuning cache: unterminated key");
+        const std::string key = txt.substr(pos, end - pos);
+        TuneChoice t;
+        if (std::sscanf(txt.c_str() + end, "\", \"refine\": [%d, %d, %d], \"chunk\": %d, \"pp\": %d, "
+                                           "\"ms\": %lf}",
+                        &t.refine[0], &t.refine[1], &t.refine[2], &t.chunk, &t.pp, &t.ms) != 6)
+            return fail(CF_EINVAL, "tuning cache: malformed entry for key " + key);
+        if (t.refine[0] < 1 || t.refine[0] > cf::MAX_REACH || t.refine[1] < 1 ||
+            t.refine[1] > cf::MAX_REACH || t.refine[2] < 1 || t.refine[2] > 16 ||
+            (t.chunk != 8 && t.chunk != 16 && t.chunk != 32) || (t.pp != 1 && t.pp != 2))
+            return fail(CF_EINVAL, "tuning cache: out-of-range values for key " + key);
+        add[key] = t;
+        pos = end;
+    }
+    for (const auto &kv : add)
+        g_tune.m[kv.first] = kv.second;
+    return CF_OK;
+}
+
+void tune_env_load_locked()
+{
+    if (g_tune.env_loaded)
+        return;
+    g_tune.env_loaded = true;
+    if (const char *p = std::getenv("CF_TUNE_CACHE")) {
+        if (FILE *f = std::fopen(p, "r")) {
+            std::fclose(f);
+            const std::string keep = g_err;
+            tune_load_locked(p);  // a bad file leaves the cache empty; tuning refills it
+            g_err = keep;
+        }
+    }
+}
+
+// Volume the signature uses: the periodic box, or the bounding box of the
+// inputs (one small device pass).
+int tune_volume(const Request &q, double &vol)
+{
+    const cf_config *c = q.cfg;
+    if (c->periodic) {
+        vol = c->boxsize[0] * c->boxsize[1] * c->boxsize[2];
+        return CF_OK;
+    }
+    const cudaStream_t st = (cudaStream_t)c->stream;
+    const cf_catalog *cats[2] = {q.d1, q.autocorr ? q.d1 : q.d2};
+    const int ncat = q.autocorr ? 1 : 2;
+    int dev = 0, sms = 0;
+    cudaError_t e;
+    if ((e = cudaGetDevice(&dev)) || (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)))
+        return cuda_fail(e, "device query");
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int t = 0; t < ncat; ++t) {
+        const long long n = cats[t]->n;
+        if (n <= 0)
+            continue;
+        const void *xyz[3] = {cats[t]->x, cats[t]->y, cats[t]->z};
+        if (!is_device_ptr(cats[t]->x)) {  // host inputs: scan them on the host
+            for (int a = 0; a < 3; ++a)
+                for (long long i = 0; i < n; ++i) {
+                    const double v = c->dtype == CF_FLOAT32 ? (double)((const float *)xyz[a])[i]
+                                                            : ((const double *)xyz[a])[i];
+                    lo[a] = std::min(lo[a], v);
+                    hi[a] = std::max(hi[a], v);
+                }
+            continue;
+        }
+        void *tmp = nullptr;
+        if ((e = cudaMallocAsync(&tmp, 7 * 8, st)))
+            return cuda_fail(e, "cudaMallocAsync (tuner bbox)");
+        unsigned long long *keys = (unsigned long long *)tmp;
+        unsigned *err = (unsigned *)(keys + 6);
+        unsigned long long init[7] = {~0ull, ~0ull, ~0ull, 0ull, 0ull, 0ull, 0ull}, out[7];
+        e = cudaMemcpyAsync(keys, init, sizeof(init), cudaMemcpyHostToDevice, st);
+        if (!e)
+            e = cf::launch_bbox(c->dtype, xyz[0], xyz[1], xyz[2], n, keys, sms, err, st);
+        if (!e)
+            e = cudaMemcpyAsync(out, keys, sizeof(out), cudaMemcpyDeviceToHost, st);
+        if (!e)
+            e = cudaStreamSynchronize(st);
+        cudaFreeAsync(tmp, st);
+        if (e)
+            return cuda_fail(e, "tuner bbox");
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = std::min(lo[a], cf::decode_dkey(out[a]));
+            hi[a] = std::max(hi[a], cf::decode_dkey(out[3 + a]));
+        }
+    }
+    vol = 1.0;
+    for (int a = 0; a < 3; ++a)
+        vol *= std::isfinite(hi[a] - lo[a]) ? std::max(hi[a] - lo[a], q.edges.back()) : 1.0;
+    return CF_OK;
+}
+
+int run_tuned(Request &q)
+{
+    const cf_config *c0 = q.cfg;
+    if (!c0 || !c0->autotune)
+        return run(q);
+    int rc = validate(q);
+    if (rc)
+        return rc;
+    double vol = 1.0;
+    if ((rc = tune_volume(q, vol)))
+        return rc;
+    const std::string key = tune_key(q, vol);
+    const bool fixed_refine = c0->refine[0] || c0->refine[1] || c0->refine[2];
+    const bool shape = q.kind == 0 && c0->mode == CF_MODE_FP32_RECHECK && !c0->weighted &&
+                       !c0->want_ravg && !c0->pair_chunk && !c0->pair_pp;
+    TuneChoice best;
+    bool have = false;
+    {
+        std::lock_guard<std::mutex> lock(g_tune.mu);
+        tune_env_load_locked();
+        auto it = g_tune.m.find(key);
+        if (it != g_tune.m.end()) {
+            best = it->second;
+            have = true;
+        }
+    }
+    cf_config cfg = *c0;
+    cfg.autotune = 0;
+    Request r = q;
+    r.cfg = &cfg;
+    auto apply = [&](const TuneChoice &t) {
+        if (!fixed_refine)
+            for (int a = 0; a < 3; ++a)
+                cfg.refine[a] = t.refine[a];
+        if (shape) {
+            cfg.pair_chunk = t.chunk;
+            cfg.pair_pp = t.pp;
+        }
+    };
+    if (!have) {
+        std::vector<TuneChoice> cand;
+        const int refs[3] = {1, 2, 3};
+        for (int k = 0; k < (fixed_refine ? 1 : 3); ++k)
+            cand.push_back(TuneChoice{{refs[k], refs[k], 1}, 16, 2, 0.0});
+        auto time_one = [&](TuneChoice &t, int reps) -> int {
+            apply(t);
+            t.ms = INFINITY;
+            for (int k = 0; k < reps; ++k) {
+                const int e = run(r);
+                if (e)
+                    return e;
+                t.ms = std::min(t.ms, q.res->total_ms);
+            }
+            return CF_OK;
+        };
+        // stage 1: refinement (the first candidate once more, to absorb one-time costs)
+        for (size_t k = 0; k < cand.size(); ++k)
+            if ((rc = time_one(cand[k], k == 0 ? 2 : 1)))
+                return rc;
+        best = *std::min_element(cand.begin(), cand.end(),
+                                 [](const TuneChoice &a, const TuneChoice &b) { return a.ms < b.ms; });
+        // stage 2: kernel shape at that refinement
+        if (shape) {
+            const int shapes[3][2] = {{8, 2}, {16, 1}, {32, 1}};
+            for (const auto &sh : shapes) {
+                TuneChoice t = best;
+                t.chunk = sh[0];
+                t.pp = sh[1];
+                if ((rc = time_one(t, 1)))
+                    return rc;
+                if (t.ms < best.ms)
+                    best = t;
+            }
+        }
+        std::lock_guard<std::mutex> lock(g_tune.mu);
+        g_tune.m[key] = best;
+        if (const char *p = std::getenv("CF_TUNE_CACHE")) {
+            const std::string keep = g_err;
+            tune_save_locked(p);
+            g_err = keep;
+        }
+    }
+    apply(best);
+    rc = run(r);
+    if (rc == CF_OK)
+        q.res->tuned = have ? 2 : 1;
+    return rc;
+}
 }  // namespace
 
 extern "C" {
@@ -862,7 +1129,7 @@ int cf_countpairs_xi(int autocorr, const cf_catalog *d1, const cf_catalog *d2, c
     q.npibins = 0;
     q.cfg = cfg;
     q.res = res;
-    return run(q);
+    return run_tuned(q);
 }
 
 int cf_countpairs_rp_pi(int autocorr, const cf_catalog *d1, const cf_catalog *d2,
@@ -881,7 +1148,36 @@ int cf_countpairs_rp_pi(int autocorr, const cf_catalog *d1, const cf_catalog *d2
     q.npibins = npibins;
     q.cfg = cfg;
     q.res = res;
-    return run(q);
+    return run_tuned(q);
+}
+
+int cf_tune_save(const char *path)
+{
+    if (!path)
+        return fail(CF_EINVAL, "path is NULL");
+    std::lock_guard<std::mutex> lock(g_tune.mu);
+    return tune_save_locked(path);
+}
+
+int cf_tune_load(const char *path)
+{
+    if (!path)
+        return fail(CF_EINVAL, "path is NULL");
+    std::lock_guard<std::mutex> lock(g_tune.mu);
+    return tune_load_locked(path);
+}
+
+int cf_tune_clear(void)
+{
+    std::lock_guard<std::mutex> lock(g_tune.mu);
+    g_tune.m.clear();
+    return CF_OK;
+}
+
+int cf_tune_count(void)
+{
+    std::lock_guard<std::mutex> lock(g_tune.mu);
+    return (int)g_tune.m.size();
 }
 
 const char *cf_last_error(void) { return g_err.c_str(); }
@@ -996,6 +1292,10 @@ int noalloc_xi(int autocorr, const cf_catalog *d1, const cf_catalog *d2, const d
     res->n_cellpairs = res->n_evaluated = res->n_rechecked = res->n_band_violations = 0;
     res->kernel_ms = res->total_ms = 0.0;
     res->n_kernels = 0;
+    resolve_refine(c, res->refine_used);
+    res->chunk_used = 16;
+    res->pp_used = 2;
+    res->tuned = 0;
 
     int dev = 0, sms = 0, rc = CF_OK;
     cudaError_t e;
