@@ -297,6 +297,13 @@ struct Item {
     int kmin, kmax;
 };
 
+// Per-CTA state a pair path carries from one work item to the next.
+struct PathState {
+    u64 n_eval, n_rck, n_viol;  // diagnostics (evaluations, re-checks, band violations)
+    unsigned pending;           // pairs added to the shared u32 counts since the last flush
+    unsigned phase;             // parity of the tile mbarrier
+};
+
 __device__ __forceinline__ void decode_item(const PairParams &P, int item, Item &it)
 {
     const WorkItem w = P.work[item];
@@ -610,63 +617,58 @@ __device__ __forceinline__ int warp_bound_from(Key key, int start, int n, V v, b
 }
 
 template <int I, int PP, bool EVALS, bool VERIFY>
-__global__ void __launch_bounds__(THREADS, 3) k_xi32(const __grid_constant__ PairParams P)
-{
-    // I * PP primaries per chunk (lane ii = lane % I holds primaries ii, ii + I,
-    // ...); jj = lane / I picks the pair of secondaries.
-    constexpr int CH = I * PP;
-    extern __shared__ __align__(128) unsigned char smem[];
-    const int nb = P.nbins;
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
-    volatile int *s_item = reinterpret_cast<volatile int *>(smem + 8);
-    const float *tz = reinterpret_cast<const float *>(smem + TX_OFF + 2 * TSTRIDE);
-    float *thr = reinterpret_cast<float *>(smem + THR_OFF);
-    double *E2 = reinterpret_cast<double *>(smem + E2_OFF);
-    uint32_t *hist = reinterpret_cast<uint32_t *>(smem + HIST_OFF);
+struct Xi32Path {
+    static __device__ __forceinline__ void init(const PairParams &P, unsigned char *smem)
+    {
+        // I * PP primaries per chunk (lane ii = lane % I holds primaries ii, ii + I,
+        // ...); jj = lane / I picks the pair of secondaries.
+        const int nb = P.nbins;
+        float *thr = reinterpret_cast<float *>(smem + THR_OFF);
+        double *E2 = reinterpret_cast<double *>(smem + E2_OFF);
+        uint32_t *hist = reinterpret_cast<uint32_t *>(smem + HIST_OFF);
 
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    for (int q = tid; q < P.lut_n; q += THREADS)
-        smem[LUT_OFF + q] = P.lut[q];
-    for (int q = tid; q < P.nthr; q += THREADS)
-        thr[q] = P.thr[q];
-    for (int q = tid; q <= nb; q += THREADS)
-        E2[q] = P.E2[q];
-    for (int q = tid; q < WARPS * (nb + 2) * 32; q += THREADS)
-        hist[q] = 0u;
-    if (tid == 0) {
-        mbar_init(bar, 1);
-        fence_mbar_init();
+        const int tid = threadIdx.x;
+        for (int q = tid; q < P.lut_n; q += THREADS)
+            smem[LUT_OFF + q] = P.lut[q];
+        for (int q = tid; q < P.nthr; q += THREADS)
+            thr[q] = P.thr[q];
+        for (int q = tid; q <= nb; q += THREADS)
+            E2[q] = P.E2[q];
+        for (int q = tid; q < WARPS * (nb + 2) * 32; q += THREADS)
+            hist[q] = 0u;
     }
-    __syncthreads();
 
-    uint32_t *hw = hist + warp * (nb + 2) * 32;  // rows: bins, not counted, flagged
-    const uint32_t hl = smem_u32(hw + lane);  // this lane's histogram column (shared address)
-    const int ii = lane % I, jj = lane / I;
-    Sweep32 S;
-    S.nb = nb;
-    S.u0 = P.u0;
-    S.lut_last = (uint32_t)(P.lut_n - 1);
-    S.shift = P.lut_shift;
-    S.nthr = P.nthr;
-    S.pa = P.A.pos64;
-    S.pb = P.B.pos64;
-    unsigned phase = 0;
-    u64 n_eval = 0, n_rck = 0, n_viol = 0;
-    unsigned pending = 0;
-    bool aborted = false;
-    const float qnan = __int_as_float(0x7fc00000);
+    static __device__ __forceinline__ bool item(const PairParams &P, const Item &it,
+                                                unsigned char *smem, PathState &st)
+    {
+        // I * PP primaries per chunk (lane ii = lane % I holds primaries ii, ii + I,
+        // ...); jj = lane / I picks the pair of secondaries.
+        constexpr int CH = I * PP;
+        const int nb = P.nbins;
+        uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
+        const float *tz = reinterpret_cast<const float *>(smem + TX_OFF + 2 * TSTRIDE);
+        uint32_t *hist = reinterpret_cast<uint32_t *>(smem + HIST_OFF);
 
-    const int n_work = (int)*P.work_count;
-    for (;;) {
-        if (tid == 0)
-            *s_item = (int)atomicAdd(P.item_counter, 1u);
-        __syncthreads();
-        const int item = *s_item;
-        __syncthreads();
-        if (item >= n_work)
-            break;
-        Item it;
-        decode_item(P, item, it);
+        const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+        unsigned &phase = st.phase;
+        u64 &n_eval = st.n_eval;
+        u64 &n_rck = st.n_rck;
+        u64 &n_viol = st.n_viol;
+        unsigned &pending = st.pending;
+
+        uint32_t *hw = hist + warp * (nb + 2) * 32;  // rows: bins, not counted, flagged
+        const uint32_t hl = smem_u32(hw + lane);  // this lane's histogram column (shared address)
+        const int ii = lane % I, jj = lane / I;
+        Sweep32 S;
+        S.nb = nb;
+        S.u0 = P.u0;
+        S.lut_last = (uint32_t)(P.lut_n - 1);
+        S.shift = P.lut_shift;
+        S.nthr = P.nthr;
+        S.pa = P.A.pos64;
+        S.pb = P.B.pos64;
+        const float qnan = __int_as_float(0x7fc00000);
+
         const float dzw = __fadd_ru(__double2float_ru(it.dzmax), P.zslack);
         const float Sxf = __double2float_rn(it.Sx), Syf = __double2float_rn(it.Sy);
         S.Sx = it.Sx;
@@ -676,8 +678,7 @@ __global__ void __launch_bounds__(THREADS, 3) k_xi32(const __grid_constant__ Pai
         for (int t0 = it.b0; t0 < it.b1; t0 += TILE32) {
             const int nt = min(TILE32, it.b1 - t0);
             if (!stage_tiles32(smem, P.B, t0, nt, bar, phase, P.err)) {
-                aborted = true;
-                break;
+                return false;
             }
             S.t0 = t0;
             const float zt_lo = tz[0];
@@ -694,7 +695,7 @@ __global__ void __launch_bounds__(THREADS, 3) k_xi32(const __grid_constant__ Pai
                 bool vv[PP];
                 float zq[PP];
                 float zmax = qnan;
-#pragma unroll
+    #pragma unroll
                 for (int q = 0; q < PP; ++q) {
                     const int i = ib + q * I + ii;
                     float xi = qnan, yi = qnan, zi = qnan;
@@ -713,7 +714,7 @@ __global__ void __launch_bounds__(THREADS, 3) k_xi32(const __grid_constant__ Pai
                 }
                 const float zlo = __shfl_sync(FULL, zq[0], 0);
                 float zhi = zmax;
-#pragma unroll
+    #pragma unroll
                 for (int o = 1; o < I; o <<= 1) {  // largest real z of the chunk
                     const float t = __shfl_xor_sync(FULL, zhi, o);
                     zhi = (isnan(zhi) || t > zhi) ? t : zhi;
@@ -721,7 +722,7 @@ __global__ void __launch_bounds__(THREADS, 3) k_xi32(const __grid_constant__ Pai
                 if (isnan(zlo))
                     continue;
 
-#pragma unroll
+    #pragma unroll
                 for (int kk = 0; kk < 3; ++kk) {
                     const int k = kk - 1;
                     if (k < it.kmin || k > it.kmax)
@@ -740,7 +741,7 @@ __global__ void __launch_bounds__(THREADS, 3) k_xi32(const __grid_constant__ Pai
                     if (jlo >= jhi)
                         continue;
                     pending += (unsigned)((jhi - jlo) / (64 / I) + 4) * 2u * PP;
-#pragma unroll
+    #pragma unroll
                     for (int q = 0; q < PP; ++q) {
                         const float zh = __fsub_rn(zq[q], kz);
                         ZH[q] = pack2(zh, zh);
@@ -760,31 +761,43 @@ __global__ void __launch_bounds__(THREADS, 3) k_xi32(const __grid_constant__ Pai
                 }
             }
         }
-        if (aborted)
-            break;
+        return true;
     }
 
-    __syncthreads();
-    for (int bn = tid; bn < nb; bn += THREADS) {
-        u64 sum = 0;
-        for (int w = 0; w < WARPS; ++w)
-            for (int l = 0; l < 32; ++l)
-                sum += hist[(w * (nb + 2) + bn) * 32 + l];
-        if (sum)
-            atomicAdd(&P.hist[bn], sum);
+    static __device__ __forceinline__ void fini(const PairParams &P, unsigned char *smem, PathState &st)
+    {
+        // I * PP primaries per chunk (lane ii = lane % I holds primaries ii, ii + I,
+        // ...); jj = lane / I picks the pair of secondaries.
+        const int nb = P.nbins;
+        uint32_t *hist = reinterpret_cast<uint32_t *>(smem + HIST_OFF);
+
+        const int tid = threadIdx.x, lane = tid & 31;
+        u64 &n_eval = st.n_eval;
+        u64 &n_rck = st.n_rck;
+        u64 &n_viol = st.n_viol;
+
+        __syncthreads();
+        for (int bn = tid; bn < nb; bn += THREADS) {
+            u64 sum = 0;
+            for (int w = 0; w < WARPS; ++w)
+                for (int l = 0; l < 32; ++l)
+                    sum += hist[(w * (nb + 2) + bn) * 32 + l];
+            if (sum)
+                atomicAdd(&P.hist[bn], sum);
+        }
+        n_eval = warp_sum_u64(n_eval);
+        n_rck = warp_sum_u64(n_rck);
+        n_viol = warp_sum_u64(n_viol);
+        if (lane == 0) {
+            if (n_eval)
+                atomicAdd(&P.diag[1], n_eval);
+            if (n_rck)
+                atomicAdd(&P.diag[2], n_rck);
+            if (n_viol)
+                atomicAdd(&P.diag[3], n_viol);
+        }
     }
-    n_eval = warp_sum_u64(n_eval);
-    n_rck = warp_sum_u64(n_rck);
-    n_viol = warp_sum_u64(n_viol);
-    if (lane == 0) {
-        if (n_eval)
-            atomicAdd(&P.diag[1], n_eval);
-        if (n_rck)
-            atomicAdd(&P.diag[2], n_rck);
-        if (n_viol)
-            atomicAdd(&P.diag[3], n_viol);
-    }
-}
+};
 
 // ============================================ float32 DD(r) with weights / ravg
 // Code 1 adds a weight per counted pair; here the pair weight is w_i * w_j
@@ -1112,61 +1125,54 @@ __global__ void __launch_bounds__(THREADS, 2) k_xi32w(const __grid_constant__ Pa
 
 // ============================================================ binary64 kernel
 template <int I, bool EVALS, bool WACC>
-__global__ void __launch_bounds__(THREADS) k_xi64(const __grid_constant__ PairParams P)
-{
-    constexpr int J = 32 / I;
-    extern __shared__ __align__(128) unsigned char smem[];
-    const int nb = P.nbins;
-    const Smem64 L = smem64_layout(P.tile_max, nb, 0, WARPS * (nb + 1) * 32);
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
-    volatile int *s_item = reinterpret_cast<volatile int *>(smem + 8);
-    double4_32a *tile = reinterpret_cast<double4_32a *>(smem + L.tile);
-    double *E2 = reinterpret_cast<double *>(smem + L.e2);
-    uint32_t *hist = reinterpret_cast<uint32_t *>(smem + L.hist);
-    double *acc = WACC ? reinterpret_cast<double *>(smem + P.acc_off) : nullptr;  // [warp][bin][2]
+struct Xi64Path {
+    static __device__ __forceinline__ void init(const PairParams &P, unsigned char *smem)
+    {
+        const int nb = P.nbins;
+        const Smem64 L = smem64_layout(P.tile_max, nb, 0, WARPS * (nb + 1) * 32);
+        double *E2 = reinterpret_cast<double *>(smem + L.e2);
+        uint32_t *hist = reinterpret_cast<uint32_t *>(smem + L.hist);
+        double *acc = WACC ? reinterpret_cast<double *>(smem + P.acc_off) : nullptr;  // [warp][bin][2]
 
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    for (int q = tid; q <= nb; q += THREADS)
-        E2[q] = P.E2[q];
-    for (int q = tid; q < WARPS * (nb + 1) * 32; q += THREADS)
-        hist[q] = 0u;
-    if (WACC)
-        for (int q = tid; q < WARPS * nb * 2; q += THREADS)
-            acc[q] = 0.0;
-    if (tid == 0) {
-        mbar_init(bar, 1);
-        fence_mbar_init();
+        const int tid = threadIdx.x;
+        for (int q = tid; q <= nb; q += THREADS)
+            E2[q] = P.E2[q];
+        for (int q = tid; q < WARPS * (nb + 1) * 32; q += THREADS)
+            hist[q] = 0u;
+        if (WACC)
+            for (int q = tid; q < WARPS * nb * 2; q += THREADS)
+                acc[q] = 0.0;
     }
-    __syncthreads();
 
-    uint32_t *hw = hist + warp * (nb + 1) * 32;
-    uint32_t *hl = hw + lane;
-    const int ii = lane % I, jj = lane / I;
-    unsigned phase = 0;
-    u64 n_eval = 0;
-    unsigned pending = 0;
-    bool aborted = false;
-    const double qnan = __longlong_as_double(0x7ff8000000000000ll);
+    static __device__ __forceinline__ bool item(const PairParams &P, const Item &it,
+                                                unsigned char *smem, PathState &st)
+    {
+        constexpr int J = 32 / I;
+        const int nb = P.nbins;
+        const Smem64 L = smem64_layout(P.tile_max, nb, 0, WARPS * (nb + 1) * 32);
+        uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
+        double4_32a *tile = reinterpret_cast<double4_32a *>(smem + L.tile);
+        double *E2 = reinterpret_cast<double *>(smem + L.e2);
+        uint32_t *hist = reinterpret_cast<uint32_t *>(smem + L.hist);
+        double *acc = WACC ? reinterpret_cast<double *>(smem + P.acc_off) : nullptr;  // [warp][bin][2]
 
-    const int n_work = (int)*P.work_count;
-    for (;;) {
-        if (tid == 0)
-            *s_item = (int)atomicAdd(P.item_counter, 1u);
-        __syncthreads();
-        const int item = *s_item;
-        __syncthreads();
-        if (item >= n_work)
-            break;
-        Item it;
-        decode_item(P, item, it);
+        const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+        unsigned &phase = st.phase;
+        u64 &n_eval = st.n_eval;
+        unsigned &pending = st.pending;
+
+        uint32_t *hw = hist + warp * (nb + 1) * 32;
+        uint32_t *hl = hw + lane;
+        const int ii = lane % I, jj = lane / I;
+        const double qnan = __longlong_as_double(0x7ff8000000000000ll);
+
         const double dzw = __dadd_rn(it.dzmax, 1e-9 * (P.rz + P.g.box[2] + 1.0));
         const int nchunks = (it.a1 - it.a0 + I - 1) / I;
 
         for (int t0 = it.b0; t0 < it.b1; t0 += P.tile_max) {
             const int nt = min(P.tile_max, it.b1 - t0);
             if (!stage_tile(tile, P.B.pos64 + t0, nt, 32, bar, phase, P.err)) {
-                aborted = true;
-                break;
+                return false;
             }
             const double zt_lo = tile[0].z, zt_hi = tile[nt - 1].z;
             auto zkey = [&](int p) { return tile[p].z; };
@@ -1180,7 +1186,7 @@ __global__ void __launch_bounds__(THREADS) k_xi64(const __grid_constant__ PairPa
                     pi = P.A.pos64[i];  // column padding entries are NaN
                 const double zlo = __shfl_sync(FULL, pi.z, 0);
                 double zhi = pi.z;
-#pragma unroll
+    #pragma unroll
                 for (int o = 1; o < I; o <<= 1) {  // largest real z of the chunk
                     const double t = __shfl_xor_sync(FULL, zhi, o);
                     zhi = (isnan(zhi) || t > zhi) ? t : zhi;
@@ -1228,35 +1234,45 @@ __global__ void __launch_bounds__(THREADS) k_xi64(const __grid_constant__ PairPa
                 }
             }
         }
-        if (aborted)
-            break;
+        return true;
     }
 
-    __syncthreads();
-    for (int bn = tid; bn < nb; bn += THREADS) {
-        u64 sum = 0;
-        double ws = 0.0, rs = 0.0;
-        for (int w = 0; w < WARPS; ++w) {
-            for (int l = 0; l < 32; ++l)
-                sum += hist[(w * (nb + 1) + bn) * 32 + l];
-            if (WACC) {
-                ws += acc[(w * nb + bn) * 2];
-                rs += acc[(w * nb + bn) * 2 + 1];
+    static __device__ __forceinline__ void fini(const PairParams &P, unsigned char *smem, PathState &st)
+    {
+        const int nb = P.nbins;
+        const Smem64 L = smem64_layout(P.tile_max, nb, 0, WARPS * (nb + 1) * 32);
+        uint32_t *hist = reinterpret_cast<uint32_t *>(smem + L.hist);
+        double *acc = WACC ? reinterpret_cast<double *>(smem + P.acc_off) : nullptr;  // [warp][bin][2]
+
+        const int tid = threadIdx.x, lane = tid & 31;
+        u64 &n_eval = st.n_eval;
+
+        __syncthreads();
+        for (int bn = tid; bn < nb; bn += THREADS) {
+            u64 sum = 0;
+            double ws = 0.0, rs = 0.0;
+            for (int w = 0; w < WARPS; ++w) {
+                for (int l = 0; l < 32; ++l)
+                    sum += hist[(w * (nb + 1) + bn) * 32 + l];
+                if (WACC) {
+                    ws += acc[(w * nb + bn) * 2];
+                    rs += acc[(w * nb + bn) * 2 + 1];
+                }
+            }
+            if (sum) {
+                atomicAdd(&P.hist[bn], sum);
+                if (WACC) {
+                    atomicAdd(&P.wsum[bn], ws);
+                    if (P.want_r)
+                        atomicAdd(&P.rsum[bn], rs);
+                }
             }
         }
-        if (sum) {
-            atomicAdd(&P.hist[bn], sum);
-            if (WACC) {
-                atomicAdd(&P.wsum[bn], ws);
-                if (P.want_r)
-                    atomicAdd(&P.rsum[bn], rs);
-            }
-        }
+        n_eval = warp_sum_u64(n_eval);
+        if (lane == 0 && n_eval)
+            atomicAdd(&P.diag[1], n_eval);
     }
-    n_eval = warp_sum_u64(n_eval);
-    if (lane == 0 && n_eval)
-        atomicAdd(&P.diag[1], n_eval);
-}
+};
 
 // ============================================================ DD(rp, pi) kernels
 // rp^2 = dx^2 + dy^2 is binned like r^2 (bits-indexed table of float32
@@ -1550,76 +1566,71 @@ __device__ void merge_rppi(const PairParams &P, const uint32_t *hist, const doub
 }
 
 template <int I, bool EVALS, bool VERIFY, bool WACC>
-__global__ void __launch_bounds__(THREADS, 3) k_rppi32(const __grid_constant__ PairParams P)
-{
-    extern __shared__ __align__(128) unsigned char smem[];
-    const int nb = P.nbins, npi = P.npibins;
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
-    volatile int *s_item = reinterpret_cast<volatile int *>(smem + 8);
-    const float *tz = reinterpret_cast<const float *>(smem + TX_OFF + 2 * TSTRIDE);
-    float *thr = reinterpret_cast<float *>(smem + THR_OFF);
-    double *E2 = reinterpret_cast<double *>(smem + E2_OFF);
-    double *Pe = reinterpret_cast<double *>(smem + RPPI_P_OFF);
-    uint32_t *hist = reinterpret_cast<uint32_t *>(smem + P.hist_off);
-    double *acc = WACC ? reinterpret_cast<double *>(smem + P.acc_off) : nullptr;
-    const int copy = (nb + 1) * (npi + 1);
+struct Rppi32Path {
+    static __device__ __forceinline__ void init(const PairParams &P, unsigned char *smem)
+    {
+        const int nb = P.nbins, npi = P.npibins;
+        float *thr = reinterpret_cast<float *>(smem + THR_OFF);
+        double *E2 = reinterpret_cast<double *>(smem + E2_OFF);
+        double *Pe = reinterpret_cast<double *>(smem + RPPI_P_OFF);
+        uint32_t *hist = reinterpret_cast<uint32_t *>(smem + P.hist_off);
+        double *acc = WACC ? reinterpret_cast<double *>(smem + P.acc_off) : nullptr;
+        const int copy = (nb + 1) * (npi + 1);
 
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    for (int q = tid; q < P.lut_n; q += THREADS)
-        smem[LUT_OFF + q] = P.lut[q];
-    for (int q = tid; q < P.nthr; q += THREADS)
-        thr[q] = P.thr[q];
-    for (int q = tid; q <= nb; q += THREADS)
-        E2[q] = P.E2[q];
-    for (int q = tid; q <= npi; q += THREADS)
-        Pe[q] = P.P[q];
-    for (int q = tid; q < P.hcopies * copy; q += THREADS)
-        hist[q] = 0u;
-    if (WACC)
-        for (int q = tid; q < 2 * P.hcopies * copy; q += THREADS)
-            acc[q] = 0.0;
-    if (tid == 0) {
-        mbar_init(bar, 1);
-        fence_mbar_init();
+        const int tid = threadIdx.x;
+        for (int q = tid; q < P.lut_n; q += THREADS)
+            smem[LUT_OFF + q] = P.lut[q];
+        for (int q = tid; q < P.nthr; q += THREADS)
+            thr[q] = P.thr[q];
+        for (int q = tid; q <= nb; q += THREADS)
+            E2[q] = P.E2[q];
+        for (int q = tid; q <= npi; q += THREADS)
+            Pe[q] = P.P[q];
+        for (int q = tid; q < P.hcopies * copy; q += THREADS)
+            hist[q] = 0u;
+        if (WACC)
+            for (int q = tid; q < 2 * P.hcopies * copy; q += THREADS)
+                acc[q] = 0.0;
     }
-    __syncthreads();
 
-    uint32_t *hc = hist + (warp % P.hcopies) * copy;
-    const int ii = lane % I, jj = lane / I;
-    SweepRP S;
-    S.nb = nb;
-    S.npi = npi;
-    S.u0 = P.u0;
-    S.lut_last = (uint32_t)(P.lut_n - 1);
-    S.shift = P.lut_shift;
-    S.nthr = P.nthr;
-    S.hbase = smem_u32(hc);
-    S.rowb = (uint32_t)(npi + 1) * 4u;
-    S.pband = P.pband;
-    S.pa = P.A.pos64;
-    S.pb = P.B.pos64;
-    S.acc = WACC ? acc + 2 * (warp % P.hcopies) * copy : nullptr;
-    S.weighted = WACC && P.weighted;
-    S.want_r = WACC && P.want_r;
-    const u64 SC = pack2(P.pscale, P.pscale);
-    const unsigned flush_at = (1u << 30) / (unsigned)(WARPS / P.hcopies);
-    unsigned phase = 0;
-    u64 n_eval = 0, n_rck = 0, n_viol = 0;
-    unsigned pending = 0;
-    bool aborted = false;
-    const float qnan = __int_as_float(0x7fc00000);
+    static __device__ __forceinline__ bool item(const PairParams &P, const Item &it,
+                                                unsigned char *smem, PathState &st)
+    {
+        const int nb = P.nbins, npi = P.npibins;
+        uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
+        const float *tz = reinterpret_cast<const float *>(smem + TX_OFF + 2 * TSTRIDE);
+        uint32_t *hist = reinterpret_cast<uint32_t *>(smem + P.hist_off);
+        double *acc = WACC ? reinterpret_cast<double *>(smem + P.acc_off) : nullptr;
+        const int copy = (nb + 1) * (npi + 1);
 
-    const int n_work = (int)*P.work_count;
-    for (;;) {
-        if (tid == 0)
-            *s_item = (int)atomicAdd(P.item_counter, 1u);
-        __syncthreads();
-        const int item = *s_item;
-        __syncthreads();
-        if (item >= n_work)
-            break;
-        Item it;
-        decode_item(P, item, it);
+        const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+        unsigned &phase = st.phase;
+        u64 &n_eval = st.n_eval;
+        u64 &n_rck = st.n_rck;
+        u64 &n_viol = st.n_viol;
+        unsigned &pending = st.pending;
+
+        uint32_t *hc = hist + (warp % P.hcopies) * copy;
+        const int ii = lane % I, jj = lane / I;
+        SweepRP S;
+        S.nb = nb;
+        S.npi = npi;
+        S.u0 = P.u0;
+        S.lut_last = (uint32_t)(P.lut_n - 1);
+        S.shift = P.lut_shift;
+        S.nthr = P.nthr;
+        S.hbase = smem_u32(hc);
+        S.rowb = (uint32_t)(npi + 1) * 4u;
+        S.pband = P.pband;
+        S.pa = P.A.pos64;
+        S.pb = P.B.pos64;
+        S.acc = WACC ? acc + 2 * (warp % P.hcopies) * copy : nullptr;
+        S.weighted = WACC && P.weighted;
+        S.want_r = WACC && P.want_r;
+        const u64 SC = pack2(P.pscale, P.pscale);
+        const unsigned flush_at = (1u << 30) / (unsigned)(WARPS / P.hcopies);
+        const float qnan = __int_as_float(0x7fc00000);
+
         const float dzw = __fadd_ru(__double2float_ru(it.dzmax), P.zslack);
         const float Sxf = __double2float_rn(it.Sx), Syf = __double2float_rn(it.Sy);
         S.Sx = it.Sx;
@@ -1629,8 +1640,7 @@ __global__ void __launch_bounds__(THREADS, 3) k_rppi32(const __grid_constant__ P
         for (int t0 = it.b0; t0 < it.b1; t0 += TILE32) {
             const int nt = min(TILE32, it.b1 - t0);
             if (!stage_tiles32(smem, P.B, t0, nt, bar, phase, P.err, S.weighted)) {
-                aborted = true;
-                break;
+                return false;
             }
             S.t0 = t0;
             const float zt_lo = tz[0];
@@ -1657,7 +1667,7 @@ __global__ void __launch_bounds__(THREADS, 3) k_rppi32(const __grid_constant__ P
                 const u64 XH = pack2(xh, xh), YH = pack2(yh, yh), WH = pack2(wi, wi);
                 const float zlo = __shfl_sync(FULL, zi, 0);
                 float zhi = zi;
-#pragma unroll
+    #pragma unroll
                 for (int o = 1; o < I; o <<= 1) {
                     const float t = __shfl_xor_sync(FULL, zhi, o);
                     zhi = (isnan(zhi) || t > zhi) ? t : zhi;
@@ -1665,7 +1675,7 @@ __global__ void __launch_bounds__(THREADS, 3) k_rppi32(const __grid_constant__ P
                 if (isnan(zlo))
                     continue;
 
-#pragma unroll
+    #pragma unroll
                 for (int kk = 0; kk < 3; ++kk) {
                     const int k = kk - 1;
                     if (k < it.kmin || k > it.kmax)
@@ -1702,86 +1712,91 @@ __global__ void __launch_bounds__(THREADS, 3) k_rppi32(const __grid_constant__ P
                 }
             }
         }
-        if (aborted)
-            break;
+        return true;
     }
 
-    __syncthreads();
-    merge_rppi(P, hist, acc);
-    n_eval = warp_sum_u64(n_eval);
-    n_rck = warp_sum_u64(n_rck);
-    n_viol = warp_sum_u64(n_viol);
-    if (lane == 0) {
-        if (n_eval)
-            atomicAdd(&P.diag[1], n_eval);
-        if (n_rck)
-            atomicAdd(&P.diag[2], n_rck);
-        if (n_viol)
-            atomicAdd(&P.diag[3], n_viol);
+    static __device__ __forceinline__ void fini(const PairParams &P, unsigned char *smem, PathState &st)
+    {
+
+        uint32_t *hist = reinterpret_cast<uint32_t *>(smem + P.hist_off);
+        double *acc = WACC ? reinterpret_cast<double *>(smem + P.acc_off) : nullptr;
+
+        const int tid = threadIdx.x, lane = tid & 31;
+        u64 &n_eval = st.n_eval;
+        u64 &n_rck = st.n_rck;
+        u64 &n_viol = st.n_viol;
+
+        __syncthreads();
+        merge_rppi(P, hist, acc);
+        n_eval = warp_sum_u64(n_eval);
+        n_rck = warp_sum_u64(n_rck);
+        n_viol = warp_sum_u64(n_viol);
+        if (lane == 0) {
+            if (n_eval)
+                atomicAdd(&P.diag[1], n_eval);
+            if (n_rck)
+                atomicAdd(&P.diag[2], n_rck);
+            if (n_viol)
+                atomicAdd(&P.diag[3], n_viol);
+        }
     }
-}
+};
 
 // Binary64 DD(rp, pi): canonical rp^2 and |dz|, exact edge compares.
 template <int I, bool EVALS, bool WACC>
-__global__ void __launch_bounds__(THREADS) k_rppi64(const __grid_constant__ PairParams P)
-{
-    constexpr int J = 32 / I;
-    extern __shared__ __align__(128) unsigned char smem[];
-    const int nb = P.nbins, npi = P.npibins, row = npi + 1, copy = (nb + 1) * row;
-    const Smem64 L = smem64_layout(P.tile_max, nb, npi, 0);
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
-    volatile int *s_item = reinterpret_cast<volatile int *>(smem + 8);
-    double4_32a *tile = reinterpret_cast<double4_32a *>(smem + L.tile);
-    double *E2 = reinterpret_cast<double *>(smem + L.e2);
-    double *Pe = reinterpret_cast<double *>(smem + L.p);
-    uint32_t *hist = reinterpret_cast<uint32_t *>(smem + P.hist_off);
-    double *acc = WACC ? reinterpret_cast<double *>(smem + P.acc_off) : nullptr;
+struct Rppi64Path {
+    static __device__ __forceinline__ void init(const PairParams &P, unsigned char *smem)
+    {
+        const int nb = P.nbins, npi = P.npibins, row = npi + 1, copy = (nb + 1) * row;
+        const Smem64 L = smem64_layout(P.tile_max, nb, npi, 0);
+        double *E2 = reinterpret_cast<double *>(smem + L.e2);
+        double *Pe = reinterpret_cast<double *>(smem + L.p);
+        uint32_t *hist = reinterpret_cast<uint32_t *>(smem + P.hist_off);
+        double *acc = WACC ? reinterpret_cast<double *>(smem + P.acc_off) : nullptr;
 
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    for (int q = tid; q <= nb; q += THREADS)
-        E2[q] = P.E2[q];
-    for (int q = tid; q <= npi; q += THREADS)
-        Pe[q] = P.P[q];
-    for (int q = tid; q < P.hcopies * copy; q += THREADS)
-        hist[q] = 0u;
-    if (WACC)
-        for (int q = tid; q < 2 * P.hcopies * copy; q += THREADS)
-            acc[q] = 0.0;
-    if (tid == 0) {
-        mbar_init(bar, 1);
-        fence_mbar_init();
+        const int tid = threadIdx.x;
+        for (int q = tid; q <= nb; q += THREADS)
+            E2[q] = P.E2[q];
+        for (int q = tid; q <= npi; q += THREADS)
+            Pe[q] = P.P[q];
+        for (int q = tid; q < P.hcopies * copy; q += THREADS)
+            hist[q] = 0u;
+        if (WACC)
+            for (int q = tid; q < 2 * P.hcopies * copy; q += THREADS)
+                acc[q] = 0.0;
     }
-    __syncthreads();
 
-    uint32_t *hc = hist + (warp % P.hcopies) * copy;
-    double *ac = WACC ? acc + 2 * (warp % P.hcopies) * copy : nullptr;
-    const unsigned flush_at = (1u << 30) / (unsigned)(WARPS / P.hcopies);
-    const int ii = lane % I, jj = lane / I;
-    unsigned phase = 0;
-    u64 n_eval = 0;
-    unsigned pending = 0;
-    bool aborted = false;
-    const double qnan = __longlong_as_double(0x7ff8000000000000ll);
+    static __device__ __forceinline__ bool item(const PairParams &P, const Item &it,
+                                                unsigned char *smem, PathState &st)
+    {
+        constexpr int J = 32 / I;
+        const int nb = P.nbins, npi = P.npibins, row = npi + 1, copy = (nb + 1) * row;
+        const Smem64 L = smem64_layout(P.tile_max, nb, npi, 0);
+        uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
+        double4_32a *tile = reinterpret_cast<double4_32a *>(smem + L.tile);
+        double *E2 = reinterpret_cast<double *>(smem + L.e2);
+        double *Pe = reinterpret_cast<double *>(smem + L.p);
+        uint32_t *hist = reinterpret_cast<uint32_t *>(smem + P.hist_off);
+        double *acc = WACC ? reinterpret_cast<double *>(smem + P.acc_off) : nullptr;
 
-    const int n_work = (int)*P.work_count;
-    for (;;) {
-        if (tid == 0)
-            *s_item = (int)atomicAdd(P.item_counter, 1u);
-        __syncthreads();
-        const int item = *s_item;
-        __syncthreads();
-        if (item >= n_work)
-            break;
-        Item it;
-        decode_item(P, item, it);
+        const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+        unsigned &phase = st.phase;
+        u64 &n_eval = st.n_eval;
+        unsigned &pending = st.pending;
+
+        uint32_t *hc = hist + (warp % P.hcopies) * copy;
+        double *ac = WACC ? acc + 2 * (warp % P.hcopies) * copy : nullptr;
+        const unsigned flush_at = (1u << 30) / (unsigned)(WARPS / P.hcopies);
+        const int ii = lane % I, jj = lane / I;
+        const double qnan = __longlong_as_double(0x7ff8000000000000ll);
+
         const double dzw = __dadd_rn(it.dzmax, 1e-9 * (P.rz + P.g.box[2] + 1.0));
         const int nchunks = (it.a1 - it.a0 + I - 1) / I;
 
         for (int t0 = it.b0; t0 < it.b1; t0 += P.tile_max) {
             const int nt = min(P.tile_max, it.b1 - t0);
             if (!stage_tile(tile, P.B.pos64 + t0, nt, 32, bar, phase, P.err)) {
-                aborted = true;
-                break;
+                return false;
             }
             double zt_hi = tile[nt - 1].z;
             if (isnan(zt_hi))
@@ -1798,7 +1813,7 @@ __global__ void __launch_bounds__(THREADS) k_rppi64(const __grid_constant__ Pair
                     pi = P.A.pos64[i];
                 const double zlo = __shfl_sync(FULL, pi.z, 0);
                 double zhi = pi.z;
-#pragma unroll
+    #pragma unroll
                 for (int o = 1; o < I; o <<= 1) {
                     const double t = __shfl_xor_sync(FULL, zhi, o);
                     zhi = (isnan(zhi) || t > zhi) ? t : zhi;
@@ -1853,15 +1868,58 @@ __global__ void __launch_bounds__(THREADS) k_rppi64(const __grid_constant__ Pair
                 }
             }
         }
-        if (aborted)
-            break;
+        return true;
     }
 
+    static __device__ __forceinline__ void fini(const PairParams &P, unsigned char *smem, PathState &st)
+    {
+        const int nb = P.nbins, npi = P.npibins, row = npi + 1;
+        const Smem64 L = smem64_layout(P.tile_max, nb, npi, 0);
+        uint32_t *hist = reinterpret_cast<uint32_t *>(smem + P.hist_off);
+        double *acc = WACC ? reinterpret_cast<double *>(smem + P.acc_off) : nullptr;
+
+        const int tid = threadIdx.x, lane = tid & 31;
+        u64 &n_eval = st.n_eval;
+
+        __syncthreads();
+        merge_rppi(P, hist, acc);
+        n_eval = warp_sum_u64(n_eval);
+        if (lane == 0 && n_eval)
+            atomicAdd(&P.diag[1], n_eval);
+    }
+};
+
+// One persistent kernel per path: init the CTA's tables and histograms, pull
+// kept column pairs from the global counter, merge at the end.
+template <class Path, int MINB>
+__global__ void __launch_bounds__(THREADS, MINB) k_path(const __grid_constant__ PairParams P)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
+    volatile int *s_item = reinterpret_cast<volatile int *>(smem + 8);
+    Path::init(P, smem);
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        fence_mbar_init();
+    }
     __syncthreads();
-    merge_rppi(P, hist, acc);
-    n_eval = warp_sum_u64(n_eval);
-    if (lane == 0 && n_eval)
-        atomicAdd(&P.diag[1], n_eval);
+    PathState st = {0ull, 0ull, 0ull, 0u, 0u};
+    const int n_work = (int)*P.work_count;
+    for (;;) {
+        if (threadIdx.x == 0)
+            *s_item = (int)atomicAdd(P.item_counter, 1u);
+        __syncthreads();
+        const int item = *s_item;
+        __syncthreads();
+        if (item >= n_work)
+            break;
+        Item it;
+        decode_item(P, item, it);
+        if (!Path::item(P, it, smem, st))
+            break;
+    }
+    __syncthreads();
+    Path::fini(P, smem, st);
 }
 
 // Per (kernel, device): the dynamic shared-memory limit set so far (only ever
@@ -1943,59 +2001,59 @@ cudaError_t launch_pairs(const PairParams &P, PairLaunch &L, int sms, cudaStream
     if (P.kind == 1) {
         if (L.f64) {
             if (P.wacc)
-                return L.evals ? launch_persistent(k_rppi64<8, true, true>, P, L, sms, st)
-                               : launch_persistent(k_rppi64<8, false, true>, P, L, sms, st);
-            return L.evals ? launch_persistent(k_rppi64<8, true, false>, P, L, sms, st)
-                           : launch_persistent(k_rppi64<8, false, false>, P, L, sms, st);
+                return L.evals ? launch_persistent(k_path<Rppi64Path<8, true, true>, 1>, P, L, sms, st)
+                               : launch_persistent(k_path<Rppi64Path<8, false, true>, 1>, P, L, sms, st);
+            return L.evals ? launch_persistent(k_path<Rppi64Path<8, true, false>, 1>, P, L, sms, st)
+                           : launch_persistent(k_path<Rppi64Path<8, false, false>, 1>, P, L, sms, st);
         }
         if (P.wacc)
-            return L.evals ? launch_persistent(k_rppi32<16, true, false, true>, P, L, sms, st)
-                           : launch_persistent(k_rppi32<16, false, false, true>, P, L, sms, st);
+            return L.evals ? launch_persistent(k_path<Rppi32Path<16, true, false, true>, 3>, P, L, sms, st)
+                           : launch_persistent(k_path<Rppi32Path<16, false, false, true>, 3>, P, L, sms, st);
         if (L.verify)
-            return launch_persistent(k_rppi32<8, true, true, false>, P, L, sms, st);
+            return launch_persistent(k_path<Rppi32Path<8, true, true, false>, 3>, P, L, sms, st);
         switch (L.chunk) {
         case 16:
-            return L.evals ? launch_persistent(k_rppi32<16, true, false, false>, P, L, sms, st)
-                           : launch_persistent(k_rppi32<16, false, false, false>, P, L, sms, st);
+            return L.evals ? launch_persistent(k_path<Rppi32Path<16, true, false, false>, 3>, P, L, sms, st)
+                           : launch_persistent(k_path<Rppi32Path<16, false, false, false>, 3>, P, L, sms, st);
         case 32:
-            return L.evals ? launch_persistent(k_rppi32<32, true, false, false>, P, L, sms, st)
-                           : launch_persistent(k_rppi32<32, false, false, false>, P, L, sms, st);
+            return L.evals ? launch_persistent(k_path<Rppi32Path<32, true, false, false>, 3>, P, L, sms, st)
+                           : launch_persistent(k_path<Rppi32Path<32, false, false, false>, 3>, P, L, sms, st);
         default:
-            return L.evals ? launch_persistent(k_rppi32<8, true, false, false>, P, L, sms, st)
-                           : launch_persistent(k_rppi32<8, false, false, false>, P, L, sms, st);
+            return L.evals ? launch_persistent(k_path<Rppi32Path<8, true, false, false>, 3>, P, L, sms, st)
+                           : launch_persistent(k_path<Rppi32Path<8, false, false, false>, 3>, P, L, sms, st);
         }
     }
     if (P.kind != 0)
         return cudaErrorNotSupported;
     if (L.f64) {
         if (P.wacc)
-            return L.evals ? launch_persistent(k_xi64<8, true, true>, P, L, sms, st)
-                           : launch_persistent(k_xi64<8, false, true>, P, L, sms, st);
-        return L.evals ? launch_persistent(k_xi64<8, true, false>, P, L, sms, st)
-                       : launch_persistent(k_xi64<8, false, false>, P, L, sms, st);
+            return L.evals ? launch_persistent(k_path<Xi64Path<8, true, true>, 1>, P, L, sms, st)
+                           : launch_persistent(k_path<Xi64Path<8, false, true>, 1>, P, L, sms, st);
+        return L.evals ? launch_persistent(k_path<Xi64Path<8, true, false>, 1>, P, L, sms, st)
+                       : launch_persistent(k_path<Xi64Path<8, false, false>, 1>, P, L, sms, st);
     }
     if (P.wacc)
         return L.evals ? launch_persistent(k_xi32w<16, true>, P, L, sms, st)
                        : launch_persistent(k_xi32w<16, false>, P, L, sms, st);
     if (L.verify)
-        return launch_persistent(k_xi32<8, 1, true, true>, P, L, sms, st);
+        return launch_persistent(k_path<Xi32Path<8, 1, true, true>, 3>, P, L, sms, st);
     if (L.pp == 2) {
         if (L.chunk == 8)
-            return L.evals ? launch_persistent(k_xi32<8, 2, true, false>, P, L, sms, st)
-                           : launch_persistent(k_xi32<8, 2, false, false>, P, L, sms, st);
-        return L.evals ? launch_persistent(k_xi32<16, 2, true, false>, P, L, sms, st)
-                       : launch_persistent(k_xi32<16, 2, false, false>, P, L, sms, st);
+            return L.evals ? launch_persistent(k_path<Xi32Path<8, 2, true, false>, 3>, P, L, sms, st)
+                           : launch_persistent(k_path<Xi32Path<8, 2, false, false>, 3>, P, L, sms, st);
+        return L.evals ? launch_persistent(k_path<Xi32Path<16, 2, true, false>, 3>, P, L, sms, st)
+                       : launch_persistent(k_path<Xi32Path<16, 2, false, false>, 3>, P, L, sms, st);
     }
     switch (L.chunk) {
     case 16:
-        return L.evals ? launch_persistent(k_xi32<16, 1, true, false>, P, L, sms, st)
-                       : launch_persistent(k_xi32<16, 1, false, false>, P, L, sms, st);
+        return L.evals ? launch_persistent(k_path<Xi32Path<16, 1, true, false>, 3>, P, L, sms, st)
+                       : launch_persistent(k_path<Xi32Path<16, 1, false, false>, 3>, P, L, sms, st);
     case 32:
-        return L.evals ? launch_persistent(k_xi32<32, 1, true, false>, P, L, sms, st)
-                       : launch_persistent(k_xi32<32, 1, false, false>, P, L, sms, st);
+        return L.evals ? launch_persistent(k_path<Xi32Path<32, 1, true, false>, 3>, P, L, sms, st)
+                       : launch_persistent(k_path<Xi32Path<32, 1, false, false>, 3>, P, L, sms, st);
     default:
-        return L.evals ? launch_persistent(k_xi32<8, 1, true, false>, P, L, sms, st)
-                       : launch_persistent(k_xi32<8, 1, false, false>, P, L, sms, st);
+        return L.evals ? launch_persistent(k_path<Xi32Path<8, 1, true, false>, 3>, P, L, sms, st)
+                       : launch_persistent(k_path<Xi32Path<8, 1, false, false>, 3>, P, L, sms, st);
     }
 }
 
