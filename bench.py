@@ -18,7 +18,8 @@ ordered pairs the histogram holds (P_cnt) per second.
          against SMs x 128 lanes x max SM clock; traffic = DRAM bytes per launch
          from the committed ncu summary while the kernel sources are unchanged.
   other_workloads  a few calls each of DD(r) at Rmax 10 and 50, DD(rp, pi)
-         14 x 40, and the weighted DR count with ravg (1.2M x 12M, open box).
+         14 x 40, the weighted DR count with ravg (1.2M x 12M, open box), and the
+         48-job batched launch (graph replay vs 48 single calls).
 
 --impl reference times the CPU oracle (brute force, canonical binary64) on a
 bounded sample of the same workload: each step counts the pairs of a slice of
@@ -228,6 +229,55 @@ def other_workloads(cf, synth, torch, cat, xyz, dev, stream, flush):
         "fp32_recheck": {"ms": ms, "kernel_ms": kms,
                          "Gpairs_s": float(r.npairs.sum()) / (ms * 1e-3) / 1e9}}
     del b, a_w
+    out["batch_48_jobs"] = batch_workload(cf, synth, torch, dev, flush)
+    return out
+
+
+def batch_workload(cf, synth, torch, dev, flush):
+    """48 independent DD(r) / DD(rp, pi) jobs (synth.batch_job) in one batched
+    persistent launch replayed from a CUDA graph, against the same jobs as 48
+    single calls; per-job counts must be identical."""
+    jobs = [synth.batch_job(j) for j in range(48)]
+    xyz = [[torch.from_numpy(v).to(dev) for v in (jb["cat"].x, jb["cat"].y, jb["cat"].z)]
+           for jb in jobs]
+    b = cf.Batch()
+    res = []
+    for jb, x in zip(jobs, xyz):
+        if jb["kind"] == "xi":
+            res.append(b.add_xi(*x, jb["edges"], boxsize=jb["box"], mode=jb["mode"]))
+        else:
+            res.append(b.add_rp_pi(*x, jb["edges"], jb["pimax"], jb["npibins"], boxsize=jb["box"],
+                                   mode=jb["mode"]))
+    first = b.run(use_graph=True)  # plan + capture
+    runs = []
+    for _ in range(3):
+        flush.zero_()
+        runs.append(b.run(use_graph=True))
+    direct = []
+    for _ in range(2):
+        flush.zero_()
+        direct.append(b.run(use_graph=False))
+    ms = statistics.median(r["total_ms"] for r in runs)
+    single_ms, exact = 0.0, 0
+    for jb, x, r in zip(jobs, xyz, res):
+        flush.zero_()
+        if jb["kind"] == "xi":
+            s = cf.countpairs_xi(*x, jb["edges"], boxsize=jb["box"], mode=jb["mode"])
+        else:
+            s = cf.countpairs_rp_pi(*x, jb["edges"], jb["pimax"], jb["npibins"], boxsize=jb["box"],
+                                    mode=jb["mode"])
+        single_ms += s.total_ms
+        exact += int(np.array_equal(s.npairs, r.npairs))
+    pairs = runs[-1]["pairs"]
+    out = {"jobs": 48, "points": int(sum(jb["cat"].n for jb in jobs)), "pairs": int(pairs),
+           "ms": ms, "kernel_ms": statistics.median(r["kernel_ms"] for r in direct),
+           "ms_without_graph": statistics.median(r["total_ms"] for r in direct),
+           "Gpairs_s": pairs / (ms * 1e-3) / 1e9, "graph": True,
+           "kernels_per_run": int(runs[-1]["n_kernels"]), "blocks": int(runs[-1]["blocks"]),
+           "first_run_ms_plan_and_capture": first["total_ms"],
+           "single_calls_ms": single_ms, "single_calls_Gpairs_s": pairs / (single_ms * 1e-3) / 1e9,
+           "jobs_exact_vs_single_calls": exact}
+    b.close()
     return out
 
 

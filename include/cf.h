@@ -181,6 +181,56 @@ int cf_countpairs_xi_noalloc(int autocorr, const cf_catalog *d1, const cf_catalo
                              cf_result *res);
 
 /*
+ * Batched counting (a persistent launch over many jobs).  Jobs -- catalogues
+ * of uneven sizes, DD(r) or DD(rp, pi), float32+re-check or binary64, auto or
+ * cross, periodic or open -- are added to a batch and then run together: their
+ * gridding and work lists run on a few side streams, and one persistent kernel
+ * pulls column pairs from a single queue over all jobs' work lists (the GPU
+ * analogue of the paper's OpenMP loop over cell pairs, Sec. 2.1).  With
+ * use_graph the whole sequence is captured once into a CUDA graph and replayed
+ * by later runs.
+ *   cf_batch_add_xi / cf_batch_add_rp_pi: arguments as cf_countpairs_xi /
+ *     cf_countpairs_rp_pi, validated at once.  Batched jobs count unweighted
+ *     pairs (cfg->weighted and cfg->want_ravg must be 0), take coordinates in
+ *     DEVICE memory, and use the float32 kernel shape 16 x 2; flags other than
+ *     CF_FLAG_NO_PRUNE are ignored; with cfg->autotune a cached refinement is
+ *     used when the tuning cache has one (a batch never times candidates).
+ *     The catalogues and res stay borrowed until cf_batch_destroy; their
+ *     contents may change between runs.
+ *   cf_batch_run: plans the jobs on the first run (open boxes: one bounding-box
+ *     pass with a host synchronisation), counts every job and writes each
+ *     job's res before returning (one synchronisation of the stream).  Later
+ *     runs reuse the plan, and with use_graph replay the captured graph; an
+ *     open-box job whose bounding box changed makes the run plan and capture
+ *     again.  stream NULL runs on a stream owned by the batch.  stats may be
+ *     NULL.  Errors name the job index in cf_last_error(); a failed job leaves
+ *     every res of that run undefined.
+ *   cf_batch_destroy: frees the batch's device memory, streams and graph.
+ */
+typedef struct cf_batch cf_batch;
+
+typedef struct {
+    uint64_t n_jobs;
+    uint64_t n_kernels;   /* kernels of one run (gridding, work lists, offsets, batched kernel) */
+    uint64_t pairs;       /* sum over jobs of the counted pairs                   */
+    int used_graph;       /* 1 if the run launched the captured graph             */
+    int planned;          /* 1 if the run (re)planned the jobs                    */
+    int blocks;           /* CTAs of the batched kernel                           */
+    double kernel_ms;     /* device time of the batched pair kernel (-1 when the
+                             run replayed a graph: only the whole run is timed)  */
+    double total_ms;      /* device time of the run (memsets to the final copy)   */
+} cf_batch_stats;
+
+int cf_batch_create(cf_batch **out);
+int cf_batch_add_xi(cf_batch *b, int autocorr, const cf_catalog *d1, const cf_catalog *d2,
+                    const double *edges, int nedges, const cf_config *cfg, cf_result *res);
+int cf_batch_add_rp_pi(cf_batch *b, int autocorr, const cf_catalog *d1, const cf_catalog *d2,
+                       const double *rp_edges, int n_rp_edges, double pimax, int npibins,
+                       const cf_config *cfg, cf_result *res);
+int cf_batch_run(cf_batch *b, void *stream, int use_graph, cf_batch_stats *stats);
+int cf_batch_destroy(cf_batch *b);
+
+/*
  * Autotuner cache (Sec. 3.1 leaves the refinement to the user and asks for an
  * automatic choice).  Entries map a problem signature -- kind, mode, dtype,
  * auto/cross, periodic, weighted, half-octave buckets of N1, N2 and of the

@@ -35,7 +35,8 @@ _STATUS = {CF_EINVAL: "CF_EINVAL", CF_ENOMEM: "CF_ENOMEM", CF_ECUDA: "CF_ECUDA",
 # Names exported by the library; they must match include/cf.h.
 EXPORTS = ("cf_countpairs_xi", "cf_countpairs_rp_pi", "cf_last_error", "cf_version",
            "cf_countpairs_xi_noalloc", "cf_tune_save", "cf_tune_load", "cf_tune_clear",
-           "cf_tune_count")
+           "cf_tune_count", "cf_batch_create", "cf_batch_add_xi", "cf_batch_add_rp_pi",
+           "cf_batch_run", "cf_batch_destroy")
 
 
 class cf_catalog(ctypes.Structure):
@@ -300,3 +301,122 @@ def countpairs_xi_noalloc(x, y, z, edges, *, x2=None, y2=None, z2=None, autocorr
     extra = (edges.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), int(edges.size))
     return _run(fn, edges.size - 1, autocorr, x, y, z, None, x2, y2, z2, None, extra, periodic,
                 boxsize, mode, False, refine, flags, stream)
+
+
+class cf_batch_stats(ctypes.Structure):
+    _fields_ = [("n_jobs", ctypes.c_uint64), ("n_kernels", ctypes.c_uint64),
+                ("pairs", ctypes.c_uint64), ("used_graph", ctypes.c_int), ("planned", ctypes.c_int),
+                ("blocks", ctypes.c_int), ("kernel_ms", ctypes.c_double),
+                ("total_ms", ctypes.c_double)]
+
+
+class Batch:
+    """Many DD(r) / DD(rp, pi) jobs in one persistent launch (``cf_batch_*``).
+
+    ``add_xi`` / ``add_rp_pi`` take the arguments of ``countpairs_xi`` /
+    ``countpairs_rp_pi`` (CUDA tensors, unweighted) and return a ``Result``
+    that ``run`` fills.  ``run(use_graph=True)`` captures the launch sequence
+    into a CUDA graph on its first call and replays it afterwards.
+    """
+
+    def __init__(self):
+        L = lib()
+        self._L = L
+        self._ptr = ctypes.c_void_p()
+        L.cf_batch_create.argtypes = [ctypes.POINTER(ctypes.c_void_p)]
+        L.cf_batch_create.restype = ctypes.c_int
+        P = ctypes.POINTER
+        L.cf_batch_add_xi.argtypes = [ctypes.c_void_p, ctypes.c_int, P(cf_catalog), P(cf_catalog),
+                                      P(ctypes.c_double), ctypes.c_int, P(cf_config), P(cf_result)]
+        L.cf_batch_add_xi.restype = ctypes.c_int
+        L.cf_batch_add_rp_pi.argtypes = [ctypes.c_void_p, ctypes.c_int, P(cf_catalog),
+                                         P(cf_catalog), P(ctypes.c_double), ctypes.c_int,
+                                         ctypes.c_double, ctypes.c_int, P(cf_config), P(cf_result)]
+        L.cf_batch_add_rp_pi.restype = ctypes.c_int
+        L.cf_batch_run.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                   P(cf_batch_stats)]
+        L.cf_batch_run.restype = ctypes.c_int
+        L.cf_batch_destroy.argtypes = [ctypes.c_void_p]
+        L.cf_batch_destroy.restype = ctypes.c_int
+        st = L.cf_batch_create(ctypes.byref(self._ptr))
+        if st != CF_OK:
+            raise CfError(st, L.cf_last_error().decode())
+        self._jobs = []  # (Result, cf_result, shape, keepalive)
+
+    def _add(self, kind, x, y, z, edges, x2, y2, z2, autocorr, periodic, boxsize, mode, refine,
+             flags, autotune, pimax=0.0, npibins=0):
+        keep = []
+        c1, dt, cuda = _catalog(x, y, z, None, keep)
+        if autocorr is None:
+            autocorr = x2 is None
+        c2 = None
+        if not autocorr:
+            c2, dt2, _ = _catalog(x2, y2, z2, None, keep)
+            if dt2 != dt:
+                raise ValueError("both catalogues must share one dtype")
+        cfg = _config(dt, periodic, boxsize, mode, False, False, refine, flags, None, False,
+                      dict(autotune=autotune))
+        edges = np.ascontiguousarray(edges, dtype=np.float64)
+        nslots = (edges.size - 1) * (int(npibins) if kind == 1 else 1)
+        npairs = np.zeros(nslots, dtype=np.uint64)
+        res = cf_result()
+        res.npairs = npairs.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))
+        eptr = edges.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        c2p = ctypes.byref(c2) if c2 is not None else None
+        if kind == 0:
+            st = self._L.cf_batch_add_xi(self._ptr, int(bool(autocorr)), ctypes.byref(c1), c2p,
+                                         eptr, int(edges.size), ctypes.byref(cfg),
+                                         ctypes.byref(res))
+        else:
+            st = self._L.cf_batch_add_rp_pi(self._ptr, int(bool(autocorr)), ctypes.byref(c1), c2p,
+                                            eptr, int(edges.size), ctypes.c_double(float(pimax)),
+                                            int(npibins), ctypes.byref(cfg), ctypes.byref(res))
+        if st != CF_OK:
+            raise CfError(st, self._L.cf_last_error().decode())
+        r = Result(npairs if kind == 0 else npairs.reshape(edges.size - 1, int(npibins)), None,
+                   None, 0, 0, 0, 0, 0.0, 0.0)
+        self._jobs.append((r, res, (c1, c2, cfg, edges, npairs, keep)))
+        return r
+
+    def add_xi(self, x, y, z, edges, *, x2=None, y2=None, z2=None, autocorr=None, periodic=True,
+               boxsize=420.0, mode="fp32_recheck", refine=(0, 0, 0), flags=0,
+               autotune=False) -> Result:
+        return self._add(0, x, y, z, edges, x2, y2, z2, autocorr, periodic, boxsize, mode, refine,
+                         flags, autotune)
+
+    def add_rp_pi(self, x, y, z, rp_edges, pimax, npibins, *, x2=None, y2=None, z2=None,
+                  autocorr=None, periodic=True, boxsize=420.0, mode="fp32_recheck",
+                  refine=(0, 0, 0), flags=0, autotune=False) -> Result:
+        return self._add(1, x, y, z, rp_edges, x2, y2, z2, autocorr, periodic, boxsize, mode,
+                         refine, flags, autotune, pimax, npibins)
+
+    def run(self, use_graph: bool = True, stream=None) -> dict:
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream().cuda_stream
+        stats = cf_batch_stats()
+        st = self._L.cf_batch_run(self._ptr, ctypes.c_void_p(int(stream) if stream else None),
+                                  int(bool(use_graph)), ctypes.byref(stats))
+        if st != CF_OK:
+            raise CfError(st, self._L.cf_last_error().decode())
+        for r, res, _ in self._jobs:
+            r.n_cellpairs = int(res.n_cellpairs)
+            r.n_rechecked = int(res.n_rechecked)
+            r.kernel_ms = float(res.kernel_ms)
+            r.total_ms = float(res.total_ms)
+            r.n_kernels = int(res.n_kernels)
+            r.refine_used = tuple(res.refine_used)
+            r.chunk_used = int(res.chunk_used)
+            r.pp_used = int(res.pp_used)
+        return {f: getattr(stats, f) for f, _ in cf_batch_stats._fields_}
+
+    def close(self) -> None:
+        if self._ptr:
+            self._L.cf_batch_destroy(self._ptr)
+            self._ptr = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -12,6 +13,7 @@
 #include <cstring>
 #include <map>
 #include <mutex>
+#include <new>
 #include <string>
 #include <vector>
 
@@ -486,6 +488,67 @@ int plan_geom(const Request &q, const double lo[3], const double hi[3], long lon
     return CF_OK;
 }
 
+// Pair-kernel parameters that depend only on the request and the geometry:
+// stencil (Sec. 2.1: half stencil for auto), pruning radius and z reach
+// (Sec. 2.2), float32 slacks, bins and the pi-bin error band.  M and Ls return
+// the coordinate extent and the periodic shift bound of the error model.
+void base_params(const Request &q, const cf::Geom &g, const cf::Gridded &A, const cf::Gridded &B,
+                 cf::PairParams &P, double &M, double &Ls)
+{
+    const cf_config *c = q.cfg;
+    const double R = q.edges.back();
+    std::memset(&P, 0, sizeof(P));
+    P.A = A;
+    P.B = B;
+    P.g = g;
+    P.autocorr = q.autocorr;
+    P.kind = q.kind;
+    P.nstencil = 0;
+    for (int ox = -g.reach_x; ox <= g.reach_x; ++ox)
+        for (int oy = -g.reach_y; oy <= g.reach_y; ++oy) {
+            if (q.autocorr && !(ox > 0 || (ox == 0 && oy >= 0)))
+                continue;  // Sec. 2.1: each unordered column pair once
+            P.stencil[P.nstencil++] = make_int2(ox, oy);
+        }
+    P.n_items = g.ncols * P.nstencil;
+    P.tile_max = 1024;
+    P.flags = c->flags;
+    M = std::max(g.extent[0], std::max(g.extent[1], g.extent[2]));
+    Ls = g.periodic ? std::max(g.box[0], std::max(g.box[1], g.box[2])) : 0.0;
+    const double Rp = R * (1.0 + 1e-9) + 8.0 * U64 * (M + Ls);
+    P.prune_r2 = Rp * Rp;
+    P.rxy2 = Rp * Rp;
+    P.rz = q.kind == 0 ? R : q.pimax;
+    const double Rz = std::max(R, P.rz);
+    P.zslack = (float)(8.0 * U32 * (M + Ls + Rz) + 1e-6 * Rz);
+    for (int a = 0; a < 3; ++a)
+        P.boxf[a] = (float)g.box[a];
+    P.nbins = (int)q.edges.size() - 1;
+    if (q.kind == 1) {
+        P.npibins = q.npibins;
+        const double s = (double)q.npibins / q.pimax;
+        P.pscale = (float)s;
+        // t = |dz| * s: float32 error in t (dz error, the scale's and the fma's
+        // roundings, the binary64 edges' own rounding), doubled for safety.
+        const double tmax = q.npibins + 1.0;
+        const double eps_z = eps_axis(q.pimax * (1.0 + 1e-6), M, Ls) + 2.0 * U64 * (M + Ls + 2.0 * q.pimax);
+        const double beta = 2.0 * (eps_z * s * (1.0 + 1e-6) + (2.0 * tmax + 2.0) * U32 +
+                                   4.0 * tmax * U64) + 1e-30;
+        P.pband = 0.5 - beta > 0.0 ? f32_down(0.5 - beta) : -1.0f;  // -1: every pair re-checked
+    }
+}
+
+// pi edges P_m = (pimax * m) / npibins, P_npibins = pimax (rp-pi only).
+void pi_edges(const Request &q, std::vector<double> &Pe)
+{
+    Pe.assign(q.kind == 1 ? q.npibins + 1 : 0, 0.0);
+    if (q.kind != 1)
+        return;
+    for (int m = 0; m < q.npibins; ++m)
+        Pe[m] = (q.pimax * (double)m) / (double)q.npibins;
+    Pe[q.npibins] = q.pimax;
+}
+
 int run(Request &q)
 {
     int rc = validate(q);
@@ -568,11 +631,7 @@ int run(Request &q)
     }
     for (int k = 0; k <= nb; ++k)
         E2[k] = q.edges[k] * q.edges[k];
-    if (q.kind == 1) {  // pi edges P_m = (pimax * m) / npibins, P_npibins = pimax
-        for (int m = 0; m < q.npibins; ++m)
-            Pe[m] = (q.pimax * (double)m) / (double)q.npibins;
-        Pe[q.npibins] = q.pimax;
-    }
+    pi_edges(q, Pe);
 
     // Pass 1: sizes of everything except the grid (known only after the bbox).
     for (int pass = 0; pass < 2; ++pass) {
@@ -693,45 +752,10 @@ int run(Request &q)
         trace.point("gridding");
 
         // ---- pair kernel parameters
-        std::memset(&P, 0, sizeof(P));
-        P.A = G[0];
-        P.B = G[1];
-        P.g = g;
-        P.autocorr = q.autocorr;
-        P.kind = q.kind;
-        P.nstencil = 0;
-        for (int ox = -g.reach_x; ox <= g.reach_x; ++ox)
-            for (int oy = -g.reach_y; oy <= g.reach_y; ++oy) {
-                if (q.autocorr && !(ox > 0 || (ox == 0 && oy >= 0)))
-                    continue;  // Sec. 2.1: each unordered column pair once
-                P.stencil[P.nstencil++] = make_int2(ox, oy);
-            }
-        P.n_items = g.ncols * P.nstencil;
+        double M = 0.0, Ls = 0.0;
+        base_params(q, g, G[0], G[1], P, M, Ls);
         P.work = work;
-        P.tile_max = 1024;
-        P.flags = c->flags;
-        const double M = std::max(g.extent[0], std::max(g.extent[1], g.extent[2]));
-        const double Ls = g.periodic ? std::max(g.box[0], std::max(g.box[1], g.box[2])) : 0.0;
-        const double Rp = R * (1.0 + 1e-9) + 8.0 * U64 * (M + Ls);
-        P.prune_r2 = Rp * Rp;
-        P.rxy2 = Rp * Rp;
-        P.rz = q.kind == 0 ? R : q.pimax;
-        const double Rz = std::max(R, P.rz);
-        P.zslack = (float)(8.0 * U32 * (M + Ls + Rz) + 1e-6 * Rz);
-        for (int a = 0; a < 3; ++a)
-            P.boxf[a] = (float)g.box[a];
-        P.nbins = nb;
         if (q.kind == 1) {
-            P.npibins = q.npibins;
-            const double s = (double)q.npibins / q.pimax;
-            P.pscale = (float)s;
-            // t = |dz| * s: float32 error in t (dz error, the scale's and the fma's
-            // roundings, the binary64 edges' own rounding), doubled for safety.
-            const double tmax = q.npibins + 1.0;
-            const double eps_z = eps_axis(q.pimax * (1.0 + 1e-6), M, Ls) + 2.0 * U64 * (M + Ls + 2.0 * q.pimax);
-            const double beta = 2.0 * (eps_z * s * (1.0 + 1e-6) + (2.0 * tmax + 2.0) * U32 +
-                                       4.0 * tmax * U64) + 1e-30;
-            P.pband = 0.5 - beta > 0.0 ? f32_down(0.5 - beta) : -1.0f;  // -1: every pair re-checked
             std::memcpy(ho->pe, Pe.data(), 8 * Pe.size());
             CF_CUDA(cudaMemcpyAsync(d_P, ho->pe, 8 * Pe.size(), cudaMemcpyHostToDevice, st), "H2D pi edges");
         }
@@ -1524,3 +1548,591 @@ extern "C" int cf_countpairs_xi_noalloc(int autocorr, const cf_catalog *d1, cons
 {
     return noalloc_xi(autocorr ? 1 : 0, d1, d2, edges, nedges, cfg, res);
 }
+
+// ============================================================================
+// Batched counting: cf_batch_*.
+// ============================================================================
+namespace {
+
+constexpr int BATCH_STREAMS = 4;  // side streams for the jobs' gridding and work lists
+
+struct BatchJob {
+    Request q;
+    cf_catalog cat[2];
+    cf_config cfg;
+    std::vector<double> edges;
+    int ncat = 1;
+    // plan
+    double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+    cf::Geom g;
+    cf::Gridded G[2] = {};
+    cf::PairParams P;
+    int path = 0, nslots = 0, smem = 0;
+    size_t out_off = 0;  // u64 words into the output block: [hist | diag(4) | err, - | kept, -]
+    uint64_t n_kernels = 0;
+};
+
+}  // namespace
+
+struct cf_batch {
+    std::vector<BatchJob> jobs;
+    bool planned = false;
+    int dev = -1, sms = 0, smem_max = 0, blocks = 0;
+    void *ws = nullptr;                  // one device workspace for every job
+    unsigned long long *d_out = nullptr; // output block (all jobs)
+    size_t out_words = 0;
+    unsigned long long *h_out = nullptr; // page-locked copy of the output block
+    cf::PairParams *d_jobs = nullptr;
+    int *d_path = nullptr;
+    unsigned *d_offsets = nullptr, *d_counter = nullptr;
+    unsigned long long *d_bbox = nullptr;
+    cf::GridTemps tmp[BATCH_STREAMS] = {};
+    cudaStream_t side[BATCH_STREAMS] = {};
+    cudaStream_t own = nullptr;
+    cudaEvent_t fork = nullptr, join[BATCH_STREAMS] = {}, ev[4] = {};
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    uint64_t n_kernels = 0;
+};
+
+namespace {
+
+void batch_free_plan(cf_batch *b)
+{
+    if (b->gexec)
+        cudaGraphExecDestroy(b->gexec);
+    if (b->graph)
+        cudaGraphDestroy(b->graph);
+    b->gexec = nullptr;
+    b->graph = nullptr;
+    if (b->ws)
+        cudaFree(b->ws);
+    if (b->h_out)
+        cudaFreeHost(b->h_out);
+    b->ws = nullptr;
+    b->h_out = nullptr;
+    b->planned = false;
+    cudaGetLastError();
+}
+
+int batch_add(cf_batch *b, Request &q)
+{
+    if (!b)
+        return fail(CF_EINVAL, "batch is NULL");
+    if ((int)b->jobs.size() >= cf::BATCH_MAX)
+        return fail(CF_EINVAL, "a batch holds at most 1024 jobs");
+    int rc = validate(q);
+    if (rc)
+        return rc;
+    if (q.cfg->weighted || q.cfg->want_ravg)
+        return fail(CF_EINVAL, "batched jobs count unweighted pairs (no weights, no ravg)");
+    const cf_catalog *cats[2] = {q.d1, q.autocorr ? q.d1 : q.d2};
+    for (int t = 0; t < (q.autocorr ? 1 : 2); ++t)
+        if (cats[t]->n > 0 && (!is_device_ptr(cats[t]->x) || !is_device_ptr(cats[t]->y) ||
+                               !is_device_ptr(cats[t]->z)))
+            return fail(CF_EINVAL, "batched jobs take coordinates in device memory");
+    BatchJob j;
+    j.cat[0] = *q.d1;
+    if (!q.autocorr)
+        j.cat[1] = *q.d2;
+    j.cfg = *q.cfg;
+    j.edges = q.edges;
+    j.ncat = q.autocorr ? 1 : 2;
+    j.q = q;
+    b->jobs.push_back(j);
+    b->planned = false;  // a new job invalidates the plan and the graph
+    return CF_OK;
+}
+
+// Request of job k with its pointers into the job's own copies.
+void batch_bind(BatchJob &j)
+{
+    j.q.d1 = &j.cat[0];
+    j.q.d2 = j.q.autocorr ? nullptr : &j.cat[1];
+    j.q.cfg = &j.cfg;
+    j.q.edges = j.edges;
+}
+
+// Bounding boxes of every open-box job (one pass, one synchronisation).
+int batch_bboxes(cf_batch *b, cudaStream_t st, std::vector<std::array<double, 6>> &box)
+{
+    const int nj = (int)b->jobs.size();
+    box.assign(nj, {0, 0, 0, 0, 0, 0});
+    int nopen = 0;
+    for (auto &j : b->jobs)
+        nopen += j.cfg.periodic ? 0 : 1;
+    if (!nopen)
+        return CF_OK;
+    unsigned long long *keys = nullptr;
+    const size_t words = (size_t)nj * 2 * 7;
+    cudaError_t e = cudaMallocAsync(&keys, words * 8, st);
+    if (e)
+        return cuda_fail(e, "cudaMallocAsync (batch bbox)");
+    std::vector<unsigned long long> h(words, 0ull);
+    for (int k = 0; k < nj * 2; ++k)
+        for (int a = 0; a < 3; ++a)
+            h[k * 7 + a] = ~0ull;
+    e = cudaMemcpyAsync(keys, h.data(), words * 8, cudaMemcpyHostToDevice, st);
+    for (int k = 0; k < nj && !e; ++k) {
+        BatchJob &j = b->jobs[k];
+        if (j.cfg.periodic)
+            continue;
+        for (int t = 0; t < j.ncat && !e; ++t)
+            e = cf::launch_bbox(j.cfg.dtype, j.cat[t].x, j.cat[t].y, j.cat[t].z, j.cat[t].n,
+                                keys + (k * 2 + t) * 7, b->sms,
+                                reinterpret_cast<unsigned *>(keys + (k * 2 + t) * 7 + 6), st);
+    }
+    if (!e)
+        e = cudaMemcpyAsync(h.data(), keys, words * 8, cudaMemcpyDeviceToHost, st);
+    if (!e)
+        e = cudaStreamSynchronize(st);
+    cudaFreeAsync(keys, st);
+    if (e)
+        return cuda_fail(e, "batch bounding boxes");
+    for (int k = 0; k < nj; ++k) {
+        BatchJob &j = b->jobs[k];
+        if (j.cfg.periodic)
+            continue;
+        double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+        bool any = false;
+        for (int t = 0; t < j.ncat; ++t) {
+            const unsigned long long *kk = h.data() + (k * 2 + t) * 7;
+            if (reinterpret_cast<const unsigned *>(kk + 6)[0] & cf::ERR_COORD)
+                return fail(CF_EINVAL, "batch job " + std::to_string(k) + ": non-finite coordinate");
+            if (j.cat[t].n <= 0)
+                continue;
+            for (int a = 0; a < 3; ++a) {
+                const double l = cf::decode_dkey(kk[a]), u = cf::decode_dkey(kk[3 + a]);
+                lo[a] = any ? std::min(lo[a], l) : l;
+                hi[a] = any ? std::max(hi[a], u) : u;
+            }
+            any = true;
+        }
+        box[k] = {lo[0], lo[1], lo[2], hi[0], hi[1], hi[2]};
+    }
+    return CF_OK;
+}
+
+int batch_plan(cf_batch *b, cudaStream_t st, const std::vector<std::array<double, 6>> &box)
+{
+    batch_free_plan(b);
+    const int nj = (int)b->jobs.size();
+    // refinement: a cached autotuner choice, else the job's own
+    for (int k = 0; k < nj; ++k) {
+        BatchJob &j = b->jobs[k];
+        batch_bind(j);
+        for (int a = 0; a < 3; ++a) {
+            j.lo[a] = box[k][a];
+            j.hi[a] = box[k][3 + a];
+        }
+        if (j.cfg.autotune && !(j.cfg.refine[0] || j.cfg.refine[1] || j.cfg.refine[2])) {
+            double vol = 1.0;
+            for (int a = 0; a < 3; ++a)
+                vol *= j.cfg.periodic ? j.cfg.boxsize[a] : std::max(j.hi[a] - j.lo[a], j.edges.back());
+            std::lock_guard<std::mutex> lock(g_tune.mu);
+            tune_env_load_locked();
+            auto it = g_tune.m.find(tune_key(j.q, vol));
+            if (it != g_tune.m.end())
+                for (int a = 0; a < 3; ++a)
+                    j.cfg.refine[a] = it->second.refine[a];
+        }
+        long long ntot = 0;
+        for (int t = 0; t < j.ncat; ++t)
+            ntot += j.cat[t].n;
+        plan_geom(j.q, j.lo, j.hi, ntot, j.g);
+        j.nslots = j.q.kind == 0 ? (int)j.edges.size() - 1 : ((int)j.edges.size() - 1) * j.q.npibins;
+    }
+    // sizes, then the workspace, then pointers (two passes of the same carving)
+    std::vector<std::vector<float>> T(nj);
+    std::vector<std::vector<uint8_t>> tab(nj);
+    std::vector<Tables> tb(nj);
+    std::vector<std::vector<double>> E2(nj), Pe(nj);
+    size_t out_words = 0;
+    for (int k = 0; k < nj; ++k) {
+        b->jobs[k].out_off = out_words;
+        out_words += (size_t)b->jobs[k].nslots + 8;
+    }
+    long long tmax_n[BATCH_STREAMS] = {0}, tmax_cells[BATCH_STREAMS] = {0}, tmax_cols[BATCH_STREAMS] = {0};
+    for (int k = 0; k < nj; ++k) {
+        const BatchJob &j = b->jobs[k];
+        const int s = k % BATCH_STREAMS;
+        for (int t = 0; t < j.ncat; ++t)
+            tmax_n[s] = std::max<long long>(tmax_n[s], j.cat[t].n);
+        tmax_cells[s] = std::max<long long>(tmax_cells[s], j.g.ncells);
+        tmax_cols[s] = std::max<long long>(tmax_cols[s], j.g.ncols);
+    }
+    Bump bump;
+    cudaError_t e;
+    for (int pass = 0; pass < 2; ++pass) {
+        bump.base = pass ? (char *)b->ws : nullptr;
+        bump.off = 0;
+        b->d_out = bump.take<unsigned long long>(out_words);
+        b->d_jobs = bump.take<cf::PairParams>(nj);
+        b->d_path = bump.take<int>(nj);
+        b->d_offsets = bump.take<unsigned>(nj + 1);
+        b->d_counter = bump.take<unsigned>(1);
+        for (int s = 0; s < BATCH_STREAMS; ++s) {
+            cf::GridTemps &tp = b->tmp[s];
+            const long long nm = tmax_n[s], nc = tmax_cells[s], ncol = tmax_cols[s];
+            tp.cell_of = bump.take<uint32_t>(nm);
+            tp.slot = bump.take<uint32_t>(nm);
+            tp.tmp_idx = bump.take<int>(nm + 3 * ncol);
+            tp.tmp_key = bump.take<unsigned long long>(nm + 3 * ncol);
+            tp.counts = bump.take<uint32_t>(nc);
+            tp.pad = bump.take<uint32_t>(ncol);
+            tp.bsum = bump.take<uint32_t>(nc / 4096 + 2);
+        }
+        for (int k = 0; k < nj; ++k) {
+            BatchJob &j = b->jobs[k];
+            for (int t = 0; t < j.ncat; ++t) {
+                const long long n = j.cat[t].n + 3ll * j.g.ncols;
+                cf::Gridded &G = j.G[t];
+                G.xs = bump.take<float>(n);
+                G.ys = bump.take<float>(n);
+                G.zs = bump.take<float>(n);
+                G.ws = nullptr;
+                G.pos64 = bump.take<double4_32a>(n);
+                G.perm = bump.take<int>(n);
+                G.cell_start = bump.take<uint32_t>(j.g.ncells + 1);
+                G.colbox = bump.take<double4_32a>(j.g.ncols);
+            }
+            if (j.ncat == 1)
+                j.G[1] = j.G[0];
+            const int nb = (int)j.edges.size() - 1;
+            j.P.work = bump.take<cf::WorkItem>((size_t)j.g.ncols * cf::MAX_STENCIL);
+            j.P.thr = bump.take<float>(2 * (nb + 1));
+            j.P.lut = bump.take<uint8_t>(cf::LUT_MAX);
+            j.P.E2 = bump.take<double>(nb + 1);
+            j.P.P = bump.take<double>(j.q.kind == 1 ? j.q.npibins + 1 : 1);
+        }
+        if (pass == 0) {
+            if ((e = cudaMalloc(&b->ws, bump.off)))
+                return cuda_fail(e, "cudaMalloc (batch workspace)");
+        }
+    }
+    if ((e = cudaHostAlloc((void **)&b->h_out, out_words * 8, cudaHostAllocDefault)))
+        return cuda_fail(e, "cudaHostAlloc (batch results)");
+    b->out_words = out_words;
+    // parameters and tables of every job
+    std::vector<cf::PairParams> hp(nj);
+    std::vector<int> hpath(nj);
+    b->smem_max = 0;
+    for (int k = 0; k < nj; ++k) {
+        BatchJob &j = b->jobs[k];
+        const int nb = (int)j.edges.size() - 1;
+        const bool f64 = j.cfg.mode == CF_MODE_FP64;
+        cf::WorkItem *work = j.P.work;
+        const float *dthr = j.P.thr;
+        const uint8_t *dlut = j.P.lut;
+        const double *dE2 = j.P.E2, *dP = j.P.P;
+        double M = 0.0, Ls = 0.0;
+        base_params(j.q, j.g, j.G[0], j.G[1], j.P, M, Ls);
+        j.P.flags = j.cfg.flags & CF_FLAG_NO_PRUNE;
+        j.P.work = work;
+        j.P.thr = dthr;
+        j.P.lut = dlut;
+        j.P.E2 = dE2;
+        j.P.P = dP;
+        E2[k].resize(nb + 1);
+        for (int q = 0; q <= nb; ++q)
+            E2[k][q] = j.edges[q] * j.edges[q];
+        pi_edges(j.q, Pe[k]);
+        if (!f64) {
+            T[k].resize(2 * (nb + 1));
+            tab[k].resize(cf::LUT_MAX);
+            tb[k] = build_tables(E2[k].data(), nb + 1, j.q.kind == 0 ? 3 : 2, M, Ls, j.edges.back(),
+                                 T[k].data(), tab[k].data());
+            j.P.nthr = tb[k].nthr;
+            j.P.lut_n = tb[k].lut_n;
+            j.P.lut_shift = tb[k].shift;
+            j.P.u0 = tb[k].u0s;
+            if ((e = cudaMemcpy((void *)dthr, T[k].data(), 4 * j.P.nthr, cudaMemcpyHostToDevice)) ||
+                (e = cudaMemcpy((void *)dlut, tab[k].data(), j.P.lut_n, cudaMemcpyHostToDevice)))
+                return cuda_fail(e, "H2D batch tables");
+        }
+        if ((e = cudaMemcpy((void *)dE2, E2[k].data(), 8 * (nb + 1), cudaMemcpyHostToDevice)))
+            return cuda_fail(e, "H2D batch edges");
+        if (j.q.kind == 1 &&
+            (e = cudaMemcpy((void *)dP, Pe[k].data(), 8 * Pe[k].size(), cudaMemcpyHostToDevice)))
+            return cuda_fail(e, "H2D batch pi edges");
+        unsigned long long *o = b->d_out + j.out_off;
+        j.P.hist = o;
+        j.P.diag = o + j.nslots;
+        j.P.err = reinterpret_cast<unsigned *>(o + j.nslots + 4);
+        j.P.item_counter = j.P.err + 1;
+        j.P.work_count = j.P.err + 2;
+        cf::PairLaunch PL;
+        std::memset(&PL, 0, sizeof(PL));
+        PL.f64 = f64;
+        PL.chunk = 16;
+        PL.pp = 2;
+        cf::plan_pairs(j.P, PL);
+        j.smem = PL.smem;
+        j.path = cf::batch_path(j.P, f64);
+        b->smem_max = std::max(b->smem_max, PL.smem);
+        hp[k] = j.P;
+        hpath[k] = j.path;
+        j.n_kernels = 0;
+        for (int t = 0; t < j.ncat; ++t)
+            j.n_kernels += cf::grid_kernels(j.cat[t].n);
+        j.n_kernels += j.P.n_items > 0 ? 1 : 0;
+    }
+    if ((e = cudaMemcpy(b->d_jobs, hp.data(), sizeof(cf::PairParams) * nj, cudaMemcpyHostToDevice)) ||
+        (e = cudaMemcpy(b->d_path, hpath.data(), sizeof(int) * nj, cudaMemcpyHostToDevice)))
+        return cuda_fail(e, "H2D batch jobs");
+    b->n_kernels = 2;  // offsets + batched kernel
+    for (auto &j : b->jobs)
+        b->n_kernels += j.n_kernels;
+    b->planned = true;
+    (void)st;
+    return CF_OK;
+}
+
+// The whole device sequence of one run, on stream st (captured or direct;
+// timing events are recorded only when not capturing).
+int batch_issue(cf_batch *b, cudaStream_t st, bool capturing)
+{
+    cudaError_t e;
+    const int nj = (int)b->jobs.size();
+    if ((!capturing && (e = cudaEventRecord(b->ev[0], st))) ||
+        (e = cudaMemsetAsync(b->d_out, 0, b->out_words * 8, st)) ||
+        (e = cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned), st)) ||
+        (e = cudaEventRecord(b->fork, st)))
+        return cuda_fail(e, "batch start");
+    for (int s = 0; s < BATCH_STREAMS; ++s)
+        if ((e = cudaStreamWaitEvent(b->side[s], b->fork, 0)))
+            return cuda_fail(e, "batch fork");
+    for (int k = 0; k < nj; ++k) {
+        BatchJob &j = b->jobs[k];
+        const int s = k % BATCH_STREAMS;
+        for (int t = 0; t < j.ncat; ++t)
+            if ((e = cf::build_grid(j.cfg.dtype, j.cat[t].x, j.cat[t].y, j.cat[t].z, nullptr,
+                                    j.cat[t].n, j.g, b->tmp[s], j.G[t], b->sms, j.P.err, b->side[s])))
+                return cuda_fail(e, ("batch job " + std::to_string(k) + " gridding").c_str());
+        if ((e = cf::launch_worklist(j.P, b->side[s])))
+            return cuda_fail(e, ("batch job " + std::to_string(k) + " work list").c_str());
+    }
+    for (int s = 0; s < BATCH_STREAMS; ++s)
+        if ((e = cudaEventRecord(b->join[s], b->side[s])) || (e = cudaStreamWaitEvent(st, b->join[s], 0)))
+            return cuda_fail(e, "batch join");
+    cf::BatchParams B;
+    B.jobs = b->d_jobs;
+    B.path = b->d_path;
+    B.njobs = nj;
+    B.offsets = b->d_offsets;
+    B.item_counter = b->d_counter;
+    if ((!capturing && (e = cudaEventRecord(b->ev[1], st))) ||
+        (e = cf::launch_batch(B, b->smem_max, b->sms, b->blocks, st)) ||
+        (!capturing && (e = cudaEventRecord(b->ev[2], st))) ||
+        (e = cudaMemcpyAsync(b->h_out, b->d_out, b->out_words * 8, cudaMemcpyDeviceToHost, st)) ||
+        (!capturing && (e = cudaEventRecord(b->ev[3], st))))
+        return cuda_fail(e, "batched kernel");
+    return CF_OK;
+}
+
+int batch_run(cf_batch *b, cudaStream_t user, int use_graph, cf_batch_stats *stats)
+{
+    if (!b)
+        return fail(CF_EINVAL, "batch is NULL");
+    if (b->jobs.empty())
+        return fail(CF_EINVAL, "the batch has no jobs");
+    cudaError_t e;
+    int dev = 0;
+    if ((e = cudaGetDevice(&dev)))
+        return cuda_fail(e, "cudaGetDevice");
+    if (b->dev >= 0 && b->dev != dev)
+        return fail(CF_EINVAL, "a batch runs on the device that was current at its first run");
+    if (b->dev < 0) {
+        b->dev = dev;
+        if ((e = cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev)))
+            return cuda_fail(e, "device attribute");
+        for (int s = 0; s < BATCH_STREAMS; ++s)
+            if ((e = cudaStreamCreateWithFlags(&b->side[s], cudaStreamNonBlocking)) ||
+                (e = cudaEventCreateWithFlags(&b->join[s], cudaEventDisableTiming)))
+                return cuda_fail(e, "batch streams");
+        if ((e = cudaStreamCreateWithFlags(&b->own, cudaStreamNonBlocking)) ||
+            (e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming)))
+            return cuda_fail(e, "batch streams");
+        for (auto &ev : b->ev)
+            if ((e = cudaEventCreate(&ev)))
+                return cuda_fail(e, "batch events");
+    }
+    const cudaStream_t st = user ? user : b->own;
+    int planned = 0, rc;
+    std::vector<std::array<double, 6>> box;
+    if ((rc = batch_bboxes(b, st, box)))
+        return rc;
+    bool same = b->planned;
+    for (size_t k = 0; same && k < b->jobs.size(); ++k)
+        for (int a = 0; a < 3 && same; ++a)
+            same = b->jobs[k].cfg.periodic ||
+                   (b->jobs[k].lo[a] == box[k][a] && b->jobs[k].hi[a] == box[k][3 + a]);
+    if (!same) {
+        if ((rc = batch_plan(b, st, box)))
+            return rc;
+        planned = 1;
+    }
+    if (use_graph) {
+        if (!b->gexec) {
+            // capture on the batch's own stream (the legacy stream cannot capture)
+            if ((e = cudaStreamBeginCapture(b->own, cudaStreamCaptureModeThreadLocal)))
+                return cuda_fail(e, "cudaStreamBeginCapture");
+            rc = batch_issue(b, b->own, true);
+            cudaGraph_t g = nullptr;
+            e = cudaStreamEndCapture(b->own, &g);
+            if (rc) {
+                if (g)
+                    cudaGraphDestroy(g);
+                return rc;
+            }
+            if (e)
+                return cuda_fail(e, "cudaStreamEndCapture");
+            b->graph = g;
+            if ((e = cudaGraphInstantiate(&b->gexec, g, 0)))
+                return cuda_fail(e, "cudaGraphInstantiate");
+        }
+        // the graph run is timed from outside the graph
+        if ((e = cudaEventRecord(b->ev[0], st)) || (e = cudaGraphLaunch(b->gexec, st)) ||
+            (e = cudaEventRecord(b->ev[3], st)))
+            return cuda_fail(e, "cudaGraphLaunch");
+    } else if ((rc = batch_issue(b, st, false))) {
+        return rc;
+    }
+    if ((e = cudaStreamSynchronize(st)))
+        return cuda_fail(e, "batch synchronize");
+    float kms = -1.f, tms = 0.f;
+    if (!use_graph && cudaEventElapsedTime(&kms, b->ev[1], b->ev[2]) != cudaSuccess)
+        kms = -1.f;  // the batched kernel alone is timed only outside a graph
+    cudaEventElapsedTime(&tms, b->ev[0], b->ev[3]);
+    cudaGetLastError();
+    uint64_t pairs = 0;
+    for (size_t k = 0; k < b->jobs.size(); ++k) {
+        BatchJob &j = b->jobs[k];
+        const unsigned long long *o = b->h_out + j.out_off;
+        unsigned err = 0, kept = 0;
+        std::memcpy(&err, o + j.nslots + 4, 4);
+        std::memcpy(&kept, reinterpret_cast<const unsigned *>(o + j.nslots + 4) + 2, 4);
+        if (err & cf::ERR_COORD)
+            return fail(CF_EINVAL, "batch job " + std::to_string(k) +
+                                       ": coordinate outside [0, boxsize) or non-finite");
+        if (err & cf::ERR_TIMEOUT)
+            return fail(CF_ETIMEOUT, "batch job " + std::to_string(k) + ": a bounded device wait gave up");
+        if (err)
+            return fail(CF_EDEVICE, "batch job " + std::to_string(k) + ": internal inconsistency");
+        cf_result *res = j.q.res;
+        const uint64_t mult = j.q.autocorr ? 2u : 1u;
+        for (int s = 0; s < j.nslots; ++s) {
+            res->npairs[s] = o[s] * mult;
+            pairs += res->npairs[s];
+        }
+        if (res->wsum)
+            std::memset(res->wsum, 0, sizeof(double) * j.nslots);
+        if (res->ravg)
+            std::memset(res->ravg, 0, sizeof(double) * j.nslots);
+        res->n_cellpairs = kept;
+        res->n_evaluated = 0;
+        res->n_rechecked = o[j.nslots + 2];
+        res->n_band_violations = 0;
+        res->kernel_ms = kms;
+        res->total_ms = tms;
+        res->n_kernels = j.n_kernels;
+        res->refine_used[0] = j.g.reach_x;
+        res->refine_used[1] = j.g.reach_y;
+        int rr[3];
+        resolve_refine(&j.cfg, rr);
+        res->refine_used[2] = rr[2];
+        res->chunk_used = 16;
+        res->pp_used = 2;
+        res->tuned = 0;
+    }
+    if (stats) {
+        stats->n_jobs = b->jobs.size();
+        stats->n_kernels = b->n_kernels;
+        stats->pairs = pairs;
+        stats->used_graph = use_graph ? 1 : 0;
+        stats->planned = planned;
+        stats->blocks = b->blocks;
+        stats->kernel_ms = kms;
+        stats->total_ms = tms;
+    }
+    return CF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int cf_batch_create(cf_batch **out)
+{
+    if (!out)
+        return fail(CF_EINVAL, "out is NULL");
+    *out = new (std::nothrow) cf_batch();
+    return *out ? CF_OK : fail(CF_ENOMEM, "out of host memory");
+}
+
+int cf_batch_add_xi(cf_batch *b, int autocorr, const cf_catalog *d1, const cf_catalog *d2,
+                    const double *edges, int nedges, const cf_config *cfg, cf_result *res)
+{
+    if (!edges || nedges < 2)
+        return fail(CF_EINVAL, "need at least 2 bin edges");
+    Request q;
+    q.kind = 0;
+    q.autocorr = autocorr ? 1 : 0;
+    q.d1 = d1;
+    q.d2 = d2;
+    q.edges.assign(edges, edges + nedges);
+    q.pimax = 0.0;
+    q.npibins = 0;
+    q.cfg = cfg;
+    q.res = res;
+    return batch_add(b, q);
+}
+
+int cf_batch_add_rp_pi(cf_batch *b, int autocorr, const cf_catalog *d1, const cf_catalog *d2,
+                       const double *rp_edges, int n_rp_edges, double pimax, int npibins,
+                       const cf_config *cfg, cf_result *res)
+{
+    if (!rp_edges || n_rp_edges < 2)
+        return fail(CF_EINVAL, "need at least 2 rp bin edges");
+    Request q;
+    q.kind = 1;
+    q.autocorr = autocorr ? 1 : 0;
+    q.d1 = d1;
+    q.d2 = d2;
+    q.edges.assign(rp_edges, rp_edges + n_rp_edges);
+    q.pimax = pimax;
+    q.npibins = npibins;
+    q.cfg = cfg;
+    q.res = res;
+    return batch_add(b, q);
+}
+
+int cf_batch_run(cf_batch *b, void *stream, int use_graph, cf_batch_stats *stats)
+{
+    return batch_run(b, (cudaStream_t)stream, use_graph, stats);
+}
+
+int cf_batch_destroy(cf_batch *b)
+{
+    if (!b)
+        return CF_OK;
+    batch_free_plan(b);
+    for (int s = 0; s < BATCH_STREAMS; ++s) {
+        if (b->side[s])
+            cudaStreamDestroy(b->side[s]);
+        if (b->join[s])
+            cudaEventDestroy(b->join[s]);
+    }
+    if (b->own)
+        cudaStreamDestroy(b->own);
+    if (b->fork)
+        cudaEventDestroy(b->fork);
+    for (auto &ev : b->ev)
+        if (ev)
+            cudaEventDestroy(ev);
+    cudaGetLastError();
+    delete b;
+    return CF_OK;
+}
+
+}  // extern "C"

@@ -1873,8 +1873,6 @@ struct Rppi64Path {
 
     static __device__ __forceinline__ void fini(const PairParams &P, unsigned char *smem, PathState &st)
     {
-        const int nb = P.nbins, npi = P.npibins, row = npi + 1;
-        const Smem64 L = smem64_layout(P.tile_max, nb, npi, 0);
         uint32_t *hist = reinterpret_cast<uint32_t *>(smem + P.hist_off);
         double *acc = WACC ? reinterpret_cast<double *>(smem + P.acc_off) : nullptr;
 
@@ -1920,6 +1918,114 @@ __global__ void __launch_bounds__(THREADS, MINB) k_path(const __grid_constant__ 
     }
     __syncthreads();
     Path::fini(P, smem, st);
+}
+
+// ============================================================ batched kernel
+// Many independent jobs (catalogues, bins, modes) in one persistent launch: the
+// CTAs pull items from one global counter over the concatenation of the jobs'
+// kept column pairs; a CTA that moves on to another job merges its histograms
+// into the previous job's output and loads the next job's tables.
+using XiF32 = Xi32Path<16, 2, false, false>;
+using XiF64 = Xi64Path<8, false, false>;
+using RpF32 = Rppi32Path<16, false, false, false>;
+using RpF64 = Rppi64Path<8, false, false>;
+
+__device__ __forceinline__ void batch_init(int path, const PairParams &P, unsigned char *smem)
+{
+    switch (path) {
+    case BATCH_XI32: XiF32::init(P, smem); break;
+    case BATCH_XI64: XiF64::init(P, smem); break;
+    case BATCH_RPPI32: RpF32::init(P, smem); break;
+    default: RpF64::init(P, smem); break;
+    }
+}
+
+__device__ __forceinline__ bool batch_item(int path, const PairParams &P, const Item &it,
+                                           unsigned char *smem, PathState &st)
+{
+    switch (path) {
+    case BATCH_XI32: return XiF32::item(P, it, smem, st);
+    case BATCH_XI64: return XiF64::item(P, it, smem, st);
+    case BATCH_RPPI32: return RpF32::item(P, it, smem, st);
+    default: return RpF64::item(P, it, smem, st);
+    }
+}
+
+__device__ __forceinline__ void batch_fini(int path, const PairParams &P, unsigned char *smem,
+                                           PathState &st)
+{
+    switch (path) {
+    case BATCH_XI32: XiF32::fini(P, smem, st); break;
+    case BATCH_XI64: XiF64::fini(P, smem, st); break;
+    case BATCH_RPPI32: RpF32::fini(P, smem, st); break;
+    default: RpF64::fini(P, smem, st); break;
+    }
+}
+
+// offsets[j] = kept column pairs of jobs 0..j-1 (one thread; a few thousand jobs at most).
+__global__ void k_batch_offsets(const __grid_constant__ BatchParams B)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0)
+        return;
+    unsigned acc = 0;
+    for (int j = 0; j < B.njobs; ++j) {
+        B.offsets[j] = acc;
+        acc += *B.jobs[j].work_count;
+    }
+    B.offsets[B.njobs] = acc;
+}
+
+__global__ void __launch_bounds__(THREADS, 2) k_batch(const __grid_constant__ BatchParams B)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ unsigned s_off[BATCH_MAX + 1];
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
+    volatile int *s_item = reinterpret_cast<volatile int *>(smem + 8);
+    for (int j = threadIdx.x; j <= B.njobs; j += THREADS)
+        s_off[j] = B.offsets[j];
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    const unsigned total = s_off[B.njobs];
+    PathState st = {0ull, 0ull, 0ull, 0u, 0u};
+    int cur = -1;
+    for (;;) {
+        if (threadIdx.x == 0)
+            *s_item = (int)atomicAdd(B.item_counter, 1u);
+        __syncthreads();
+        const unsigned item = (unsigned)*s_item;
+        __syncthreads();
+        if (item >= total)
+            break;
+        int lo = 0, hi = B.njobs;  // largest job with s_off[job] <= item
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (s_off[mid] <= item)
+                lo = mid;
+            else
+                hi = mid;
+        }
+        const int job = lo;
+        if (job != cur) {  // CTA-uniform: every thread holds the same item
+            if (cur >= 0)
+                batch_fini(B.path[cur], B.jobs[cur], smem, st);
+            __syncthreads();
+            batch_init(B.path[job], B.jobs[job], smem);
+            st.n_eval = st.n_rck = st.n_viol = 0ull;
+            st.pending = 0u;
+            __syncthreads();
+            cur = job;
+        }
+        const PairParams &P = B.jobs[job];
+        Item it;
+        decode_item(P, (int)(item - s_off[job]), it);
+        if (!batch_item(B.path[job], P, it, smem, st))
+            break;
+    }
+    if (cur >= 0)
+        batch_fini(B.path[cur], B.jobs[cur], smem, st);
 }
 
 // Per (kernel, device): the dynamic shared-memory limit set so far (only ever
@@ -1989,6 +2095,39 @@ cudaError_t launch_persistent(K kern, const PairParams &P, PairLaunch &L, int sm
 }
 
 }  // namespace
+
+int batch_path(const PairParams &P, int f64)
+{
+    if (P.kind == 0)
+        return f64 ? BATCH_XI64 : BATCH_XI32;
+    return f64 ? BATCH_RPPI64 : BATCH_RPPI32;
+}
+
+cudaError_t launch_worklist(const PairParams &P, cudaStream_t st)
+{
+    if (P.n_items <= 0)
+        return cudaSuccess;
+    k_worklist<<<(P.n_items + 255) / 256, 256, 0, st>>>(P);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch(const BatchParams &B, int smem, int sms, int &blocks, cudaStream_t st)
+{
+    if (B.njobs < 1 || B.njobs > BATCH_MAX)
+        return cudaErrorInvalidValue;
+    k_batch_offsets<<<1, 32, 0, st>>>(B);
+    cudaError_t e = cudaGetLastError();
+    if (e)
+        return e;
+    int occ = 0;
+    if ((e = occupancy(k_batch, smem, occ)))
+        return e;
+    if (occ < 1)
+        return cudaErrorInvalidConfiguration;
+    blocks = sms * occ;
+    k_batch<<<blocks, THREADS, smem, st>>>(B);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_pairs(const PairParams &P, PairLaunch &L, int sms, cudaStream_t st)
 {

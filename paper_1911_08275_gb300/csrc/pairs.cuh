@@ -46,7 +46,33 @@ struct PairLaunch {
 // P.tile_max and L.f64.
 void plan_pairs(PairParams &P, PairLaunch &L);
 
-// Configure (max dynamic smem), pick the occupancy-based grid and launch.
+// Configure (max dynamic smem), pick the occupancy-based grid and launch
+// (the work-list kernel, then the pair kernel).
 cudaError_t launch_pairs(const PairParams &P, PairLaunch &L, int sms, cudaStream_t st);
+
+// ---- batched launch: jobs of these paths share one persistent kernel
+enum : int { BATCH_XI32 = 0, BATCH_XI64 = 1, BATCH_RPPI32 = 2, BATCH_RPPI64 = 3 };
+constexpr int BATCH_MAX = 1024;  // jobs per batched launch
+
+struct BatchParams {
+    const PairParams *jobs;  // device array, one per job (work lists already built)
+    const int *path;         // device array: BATCH_* per job
+    int njobs;
+    unsigned *offsets;       // device, njobs + 1 (written by the launch)
+    unsigned *item_counter;  // device, zeroed before the launch
+};
+
+// Path of a job: float32 (kernel shape 16 x 2) or binary64, DD(r) or DD(rp, pi);
+// unweighted only.
+int batch_path(const PairParams &P, int f64);
+
+// The work-list kernel of one job (kept column pairs into P.work, count into
+// *P.work_count, which must be zero).
+cudaError_t launch_worklist(const PairParams &P, cudaStream_t st);
+
+// Offsets over the jobs' kept pairs, then the batched persistent kernel with
+// smem bytes of dynamic shared memory (the largest job's plan); blocks returns
+// the grid size.
+cudaError_t launch_batch(const BatchParams &B, int smem, int sms, int &blocks, cudaStream_t st);
 
 }  // namespace cf

@@ -245,3 +245,36 @@ def c2_clustered() -> Catalog:
 def c4_randoms(n: int = 12_000_000) -> Catalog:
     """12M uniform randoms in the box 420, seed 3."""
     return uniform_box(n, BOX, seed=3)
+
+
+def batch_job(j: int, scale: float = 1.0) -> dict:
+    """Job j of the 48-job batched workload (seed 1000 + j).
+
+    N log-uniform in [5e4, 2e6] (times ``scale``); even j Neyman-Scott with
+    N/20 parents (Poisson(20) children, sigma 2), odd j uniform; box side L
+    log-uniform in [100, 1000]; Rmax = round(log-uniform [5, 40]) < L/2.
+    Kind alternates in pairs of jobs: DD(r) with 20 log bins 0.1 -> Rmax, then
+    DD(rp, pi) with 14 log rp bins 0.1 -> Rmax and pimax = Rmax in unit pi
+    bins.  Mode alternates in blocks of four: float32 + re-check, then binary64.
+    """
+    seed = 1000 + j
+    u = uniform01(seed, 20, 3)
+    lg = lambda lo, hi, t: float(_exp(np.array([_ln(np.array([lo]))[0] + t * (  # noqa: E731
+        _ln(np.array([hi]))[0] - _ln(np.array([lo]))[0])]))[0])
+    n = max(2, int(round(lg(5e4, 2e6, u[0]) * scale)))
+    box = lg(100.0, 1000.0, u[1])
+    rmax = float(min(round(lg(5.0, 40.0, u[2])), int(box / 2.0) - 1))
+    if j % 2 == 0:
+        cat = neyman_scott(max(1, int(round(n / 20.0))), 20.0, 2.0, box, seed=seed)
+    else:
+        cat = uniform_box(n, box, seed=seed)
+    kind = "xi" if (j // 2) % 2 == 0 else "rppi"
+    mode = "fp32_recheck" if (j // 4) % 2 == 0 else "fp64"
+    job = dict(j=j, kind=kind, mode=mode, cat=cat, box=box, rmax=rmax)
+    if kind == "xi":
+        job["edges"] = log_edges(0.1, rmax, 20)
+    else:
+        job["edges"] = log_edges(0.1, rmax, 14)
+        job["pimax"] = rmax
+        job["npibins"] = int(rmax)
+    return job

@@ -1,0 +1,124 @@
+"""Batched persistent launch (cf_batch_*): every job's counts equal the
+single-call path (itself parity-tested against the oracle), with and without
+the captured CUDA graph, across job switches, in-place input updates and
+re-planning of open boxes."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1911_08275_gb300 as cf
+from paper_1911_08275_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def dev(cat):
+    import torch
+    return [torch.from_numpy(np.ascontiguousarray(v)).cuda() for v in (cat.x, cat.y, cat.z)]
+
+
+def single(job, xyz, xyz2=None):
+    kw = dict(boxsize=job["box"], mode=job["mode"], periodic=job.get("periodic", True))
+    if xyz2 is not None:
+        kw.update(x2=xyz2[0], y2=xyz2[1], z2=xyz2[2])
+    if job["kind"] == "xi":
+        return cf.countpairs_xi(*xyz, job["edges"], **kw).npairs
+    return cf.countpairs_rp_pi(*xyz, job["edges"], job["pimax"], job["npibins"], **kw).npairs
+
+
+def add(b, job, xyz, xyz2=None):
+    kw = dict(boxsize=job["box"], mode=job["mode"], periodic=job.get("periodic", True))
+    if xyz2 is not None:
+        kw.update(x2=xyz2[0], y2=xyz2[1], z2=xyz2[2])
+    if job["kind"] == "xi":
+        return b.add_xi(*xyz, job["edges"], **kw)
+    return b.add_rp_pi(*xyz, job["edges"], job["pimax"], job["npibins"], **kw)
+
+
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_batch_equals_single_calls(cuda_device, use_graph):
+    jobs = [synth.batch_job(j, scale=0.01) for j in range(16)]
+    b = cf.Batch()
+    xyz = [dev(jb["cat"]) for jb in jobs]
+    res = [add(b, jb, x) for jb, x in zip(jobs, xyz)]
+    stats = b.run(use_graph=use_graph)
+    assert stats["n_jobs"] == 16 and stats["planned"] == 1
+    for jb, x, r in zip(jobs, xyz, res):
+        assert np.array_equal(r.npairs, single(jb, x)), jb["j"]
+    assert stats["pairs"] == sum(int(r.npairs.sum()) for r in res)
+    # second run: replay (or re-issue) on the same plan
+    stats2 = b.run(use_graph=use_graph)
+    assert stats2["planned"] == 0
+    for jb, x, r in zip(jobs, xyz, res):
+        assert np.array_equal(r.npairs, single(jb, x)), jb["j"]
+    b.close()
+
+
+def test_batch_small_jobs_against_oracle(cuda_device):
+    jobs = [synth.batch_job(j, scale=0.002) for j in range(8)]
+    b = cf.Batch()
+    res = [add(b, jb, dev(jb["cat"])) for jb in jobs]
+    b.run()
+    for jb, r in zip(jobs, res):
+        c = jb["cat"]
+        if jb["kind"] == "xi":
+            ref = oracle.xi(c.x, c.y, c.z, edges=jb["edges"], periodic=True, box=jb["box"])[0]
+        else:
+            ref = oracle.rppi(c.x, c.y, c.z, rp_edges=jb["edges"], pimax=jb["pimax"],
+                              npibins=jb["npibins"], periodic=True, box=jb["box"])[0]
+        assert np.array_equal(r.npairs, ref), jb["j"]
+    b.close()
+
+
+def test_batch_cross_open_and_many_job_switches(cuda_device):
+    b = cf.Batch()
+    cases = []
+    for k in range(40):  # many tiny jobs: every CTA switches job many times
+        a = synth.neyman_scott(30 + k, 10.0, 2.0, 120.0, seed=200 + k)
+        u = synth.uniform_box(800 + 10 * k, 120.0, seed=300 + k)
+        job = dict(kind="xi" if k % 2 == 0 else "rppi", mode="fp64" if k % 3 == 0 else "fp32_recheck",
+                   box=120.0, periodic=(k % 4 != 1), edges=synth.log_edges(0.2, 15.0, 10),
+                   pimax=12.0, npibins=12)
+        xa, xu = dev(a), dev(u)
+        cases.append((job, xa, xu, add(b, job, xa, xu)))
+    b.run(use_graph=True)
+    for job, xa, xu, r in cases:
+        assert np.array_equal(r.npairs, single(job, xa, xu))
+    b.close()
+
+
+def test_graph_replay_sees_in_place_updates_and_open_box_replans(cuda_device):
+    import torch
+    p = synth.neyman_scott(400, 20.0, 2.0, 150.0, seed=401)
+    o = synth.uniform_box(20000, 150.0, seed=402)
+    e = synth.log_edges(0.1, 20.0, 12)
+    xp, xo = dev(p), dev(o)
+    b = cf.Batch()
+    rp = b.add_xi(*xp, e, boxsize=150.0)
+    ro = b.add_rp_pi(*xo, e, 15.0, 15, periodic=False)
+    b.run(use_graph=True)
+    # periodic job: new positions of the same size, replay without re-planning
+    q = synth.neyman_scott(400, 20.0, 2.0, 150.0, seed=403)
+    n = min(p.n, q.n)
+    for t, v in zip(xp, (q.x, q.y, q.z)):
+        t[:n] = torch.from_numpy(v[:n]).cuda()
+    s = b.run(use_graph=True)
+    assert s["planned"] == 0
+    assert np.array_equal(rp.npairs, cf.countpairs_xi(*xp, e, boxsize=150.0).npairs)
+    # open job: points moved outside the planned bounding box -> re-plan and recapture
+    xo[0].mul_(1.5)
+    s = b.run(use_graph=True)
+    assert s["planned"] == 1
+    assert np.array_equal(ro.npairs, cf.countpairs_rp_pi(*xo, e, 15.0, 15, periodic=False).npairs)
+    b.close()
+
+
+def test_batch_rejects_host_inputs_and_empty_runs(cuda_device):
+    c = synth.uniform_box(100, 10.0, seed=404)
+    b = cf.Batch()
+    with pytest.raises(cf.CfError) as ei:
+        b.add_xi(c.x, c.y, c.z, [0.1, 1.0], boxsize=10.0)
+    assert ei.value.status == cf.CF_EINVAL
+    with pytest.raises(cf.CfError):
+        b.run()
+    b.close()
