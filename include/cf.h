@@ -102,6 +102,11 @@ typedef struct {
                             (8, 16 or 32); 0 = default 16                         */
     int pair_pp;         /* float32 DD(r) kernel: primaries per lane (1 or 2);
                             0 = default 2                                         */
+    int shard_index;     /* with shard_count > 1: count only the column pairs
+                            whose primary column starts in slice shard_index of
+                            shard_count equal slices of the gridded d1 points;  */
+    int shard_count;     /* the shards' histograms sum to the full one (one shard
+                            per process / GPU).  0 or 1 = no sharding.            */
 } cf_config;
 
 /* Caller-owned host outputs.  Arrays are NULL when not wanted. */

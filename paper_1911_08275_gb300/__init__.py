@@ -49,7 +49,8 @@ class cf_config(ctypes.Structure):
                 ("dtype", ctypes.c_int), ("mode", ctypes.c_int), ("weighted", ctypes.c_int),
                 ("want_ravg", ctypes.c_int), ("refine", ctypes.c_int * 3),
                 ("flags", ctypes.c_uint32), ("stream", ctypes.c_void_p), ("autotune", ctypes.c_int),
-                ("pair_chunk", ctypes.c_int), ("pair_pp", ctypes.c_int)]
+                ("pair_chunk", ctypes.c_int), ("pair_pp", ctypes.c_int),
+                ("shard_index", ctypes.c_int), ("shard_count", ctypes.c_int)]
 
 
 class cf_result(ctypes.Structure):
@@ -163,6 +164,8 @@ def _config(dtype, periodic, boxsize, mode, weighted, want_ravg, refine, flags, 
     c.autotune = 1 if tuning.get("autotune") else 0
     c.pair_chunk = int(tuning.get("pair_chunk", 0))
     c.pair_pp = int(tuning.get("pair_pp", 0))
+    shard = tuning.get("shard") or (0, 0)
+    c.shard_index, c.shard_count = int(shard[0]), int(shard[1])
     c.periodic = 1 if periodic else 0
     b = np.broadcast_to(np.asarray(boxsize if boxsize is not None else 0.0, dtype=np.float64), (3,))
     c.boxsize[:] = [float(v) for v in b]
@@ -215,8 +218,11 @@ def _run(fn, nslots, autocorr, x, y, z, w, x2, y2, z2, w2, extra, periodic, boxs
 def countpairs_xi(x, y, z, edges, *, w=None, x2=None, y2=None, z2=None, w2=None, autocorr=None,
                   periodic=True, boxsize=420.0, mode="fp32_recheck", want_ravg=False,
                   refine=(0, 0, 0), flags=0, stream=None, autotune=False, pair_chunk=0,
-                  pair_pp=0) -> Result:
-    """DD(r) histogram through ``cf_countpairs_xi`` (see include/cf.h)."""
+                  pair_pp=0, shard=None) -> Result:
+    """DD(r) histogram through ``cf_countpairs_xi`` (see include/cf.h).
+
+    shard=(k, n) counts only shard k of n (see cf_config.shard_index); the n
+    shards' histograms sum to the full result."""
     edges = np.ascontiguousarray(edges, dtype=np.float64)
     if autocorr is None:
         autocorr = x2 is None
@@ -224,13 +230,13 @@ def countpairs_xi(x, y, z, edges, *, w=None, x2=None, y2=None, z2=None, w2=None,
     extra = (edges.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), int(edges.size))
     return _run(fn, edges.size - 1, autocorr, x, y, z, w, x2, y2, z2, w2, extra, periodic, boxsize,
                 mode, want_ravg, refine, flags, stream,
-                dict(autotune=autotune, pair_chunk=pair_chunk, pair_pp=pair_pp))
+                dict(autotune=autotune, pair_chunk=pair_chunk, pair_pp=pair_pp, shard=shard))
 
 
 def countpairs_rp_pi(x, y, z, rp_edges, pimax, npibins, *, w=None, x2=None, y2=None, z2=None,
                      w2=None, autocorr=None, periodic=True, boxsize=420.0, mode="fp32_recheck",
                      want_ravg=False, refine=(0, 0, 0), flags=0, stream=None,
-                     autotune=False) -> Result:
+                     autotune=False, shard=None) -> Result:
     """DD(rp, pi) histogram (rp-major, shape (nrp, npibins)) through ``cf_countpairs_rp_pi``."""
     rp_edges = np.ascontiguousarray(rp_edges, dtype=np.float64)
     if autocorr is None:
@@ -239,7 +245,8 @@ def countpairs_rp_pi(x, y, z, rp_edges, pimax, npibins, *, w=None, x2=None, y2=N
     extra = (rp_edges.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), int(rp_edges.size),
              ctypes.c_double(float(pimax)), int(npibins))
     r = _run(fn, (rp_edges.size - 1) * int(npibins), autocorr, x, y, z, w, x2, y2, z2, w2, extra,
-             periodic, boxsize, mode, want_ravg, refine, flags, stream, dict(autotune=autotune))
+             periodic, boxsize, mode, want_ravg, refine, flags, stream,
+             dict(autotune=autotune, shard=shard))
     shp = (rp_edges.size - 1, int(npibins))
     r.npairs = r.npairs.reshape(shp)
     if r.wsum is not None:

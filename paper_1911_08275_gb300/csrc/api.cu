@@ -400,6 +400,9 @@ int validate(const Request &q)
         return fail(CF_EINVAL, "pair_chunk must be 0, 8, 16 or 32");
     if (c->pair_pp < 0 || c->pair_pp > 2)
         return fail(CF_EINVAL, "pair_pp must be 0, 1 or 2");
+    if (c->shard_count < 0 || (c->shard_count > 1 &&
+                               (c->shard_index < 0 || c->shard_index >= c->shard_count)))
+        return fail(CF_EINVAL, "shard_index must be in [0, shard_count)");
     return CF_OK;
 }
 
@@ -511,6 +514,8 @@ void base_params(const Request &q, const cf::Geom &g, const cf::Gridded &A, cons
             P.stencil[P.nstencil++] = make_int2(ox, oy);
         }
     P.n_items = g.ncols * P.nstencil;
+    P.shard_n = c->shard_count > 1 ? c->shard_count : 1;
+    P.shard_k = c->shard_count > 1 ? c->shard_index : 0;
     P.tile_max = 1024;
     P.flags = c->flags;
     M = std::max(g.extent[0], std::max(g.extent[1], g.extent[2]));

@@ -104,6 +104,7 @@ struct PairParams {
     int nstencil;
     int2 stencil[MAX_STENCIL];
     int n_items;        // (column, stencil offset) candidates
+    int shard_k, shard_n;  // keep columns whose first point lies in slice k of n (n > 1)
     WorkItem *work;     // kept column pairs (work-list kernel output)
     unsigned *work_count;  // number of kept column pairs
     int tile_max;       // points per staged tile

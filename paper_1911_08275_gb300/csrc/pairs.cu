@@ -243,6 +243,14 @@ __device__ __forceinline__ bool plan_item(const PairParams &P, int item, WorkIte
     const double Sx = qx * P.g.box[0], Sy = qy * P.g.box[1];
     const int b = bx * P.g.ncy + by;
     const long long nz = P.g.nz;
+    if (P.shard_n > 1) {  // deterministic split of the primary columns over shards
+        const unsigned long long total = P.A.cell_start[(long long)P.g.ncols * nz];
+        const unsigned long long first = P.A.cell_start[a * nz];
+        const unsigned long long lo = total * (unsigned long long)P.shard_k / P.shard_n;
+        const unsigned long long hi = total * (unsigned long long)(P.shard_k + 1) / P.shard_n;
+        if (first < lo || first >= hi)
+            return false;
+    }
     w.a0 = (int)P.A.cell_start[a * nz];
     w.a1 = (int)P.A.cell_start[(a + 1) * nz];
     w.b0 = (int)P.B.cell_start[b * nz];
