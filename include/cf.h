@@ -129,6 +129,8 @@ typedef struct {
     int tuned;                  /* 0 no autotuning, 1 this call tuned (timed the
                                    candidates, then counted with the winner),
                                    2 the cached choice was used                   */
+    int table_linear;           /* float32 paths: 1 if the bin table's cells are
+                                   linear in d2, 0 if logarithmic                 */
 } cf_result;
 
 /*

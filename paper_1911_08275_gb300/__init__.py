@@ -60,7 +60,8 @@ class cf_result(ctypes.Structure):
                 ("n_band_violations", ctypes.c_uint64), ("kernel_ms", ctypes.c_double),
                 ("total_ms", ctypes.c_double), ("n_kernels", ctypes.c_uint64),
                 ("refine_used", ctypes.c_int * 3), ("chunk_used", ctypes.c_int),
-                ("pp_used", ctypes.c_int), ("tuned", ctypes.c_int)]
+                ("pp_used", ctypes.c_int), ("tuned", ctypes.c_int),
+                ("table_linear", ctypes.c_int)]
 
 
 class CfError(RuntimeError):
@@ -119,6 +120,7 @@ class Result:
     chunk_used: int = 0
     pp_used: int = 0
     tuned: int = 0
+    table_linear: int = 0
 
 
 def _is_torch(a) -> bool:
@@ -212,7 +214,7 @@ def _run(fn, nslots, autocorr, x, y, z, w, x2, y2, z2, w2, extra, periodic, boxs
     return Result(npairs, wsum, ravg, int(res.n_cellpairs), int(res.n_evaluated),
                   int(res.n_rechecked), int(res.n_band_violations), float(res.kernel_ms),
                   float(res.total_ms), int(res.n_kernels), tuple(res.refine_used),
-                  int(res.chunk_used), int(res.pp_used), int(res.tuned))
+                  int(res.chunk_used), int(res.pp_used), int(res.tuned), int(res.table_linear))
 
 
 def countpairs_xi(x, y, z, edges, *, w=None, x2=None, y2=None, z2=None, w2=None, autocorr=None,

@@ -134,14 +134,15 @@ double band_sq(double S, int ncomp, double M, double Ls, double R)
 //     cell contains a threshold or lies inside a band).
 struct Tables {
     int nthr, lut_n, shift;
-    uint32_t u0s;  // first cell's bit pattern >> shift
+    uint32_t u0s;  // first cell's bit pattern >> shift (logarithmic cells)
+    int lin;       // 1: cells linear in d2, cell = round(d2 * lscale)
+    float lscale;
 };
 
-Tables build_tables(const double *E2, int ne, int ncomp, double M, double Ls, double R, float *T,
-                    uint8_t *tab)
+// Thresholds T[0..2 ne) (see above).
+void build_thresholds(const double *E2, int ne, int ncomp, double M, double Ls, double R, float *T)
 {
-    Tables t;
-    const int nthr = 2 * ne, nbins = ne - 1;
+    const int nthr = 2 * ne;
     for (int k = 0; k < ne; ++k) {
         if (E2[k] == 0.0) {  // every d2 >= 0 is surely >= 0
             T[2 * k] = 0.0f;
@@ -156,39 +157,107 @@ Tables build_tables(const double *E2, int ne, int ncomp, double M, double Ls, do
     }
     for (int q = 1; q < nthr; ++q)  // raising a threshold only widens the re-check set
         T[q] = std::max(T[q], T[q - 1]);
+}
+
+// Classify cells [vlo[q], vhi[q]] (increasing, closed) against the thresholds;
+// returns the pair mass of the flagged cells under the density w(v) = v^(1/2)
+// (separations in 3-D) or 1 (rp^2 in 2-D), up to a constant.
+template <class Bounds>
+double classify_cells(const float *T, int nthr, int nbins, int n, int ncomp, Bounds bounds,
+                      uint8_t *tab)
+{
+    const uint8_t dummy = (uint8_t)nbins, flagged = (uint8_t)(nbins + 1);
+    auto mass = [&](double a, double b) {
+        a = std::max(a, 0.0);
+        b = std::max(b, a);
+        return ncomp == 3 ? (std::pow(b, 1.5) - std::pow(a, 1.5)) : (b - a);
+    };
+    double fm = 0.0;
+    // Cells are visited in increasing value, so the threshold counts at the cell
+    // ends only move forward: one sweep over cells and thresholds.
+    int clo = 0, chi = 0;
+    for (int q = 0; q < n; ++q) {
+        double vlo, vhi;
+        bounds(q, vlo, vhi);
+        while (clo < nthr && (double)T[clo] <= vlo)
+            ++clo;
+        chi = std::max(chi, clo);
+        while (chi < nthr && (double)T[chi] <= vhi)
+            ++chi;
+        if (clo == chi && !(clo & 1)) {
+            tab[q] = (clo >= 2 && clo <= 2 * nbins) ? (uint8_t)((clo - 2) / 2) : dummy;
+        } else {
+            tab[q] = flagged;
+            fm += mass(vlo, vhi);
+        }
+    }
+    tab[n] = dummy;
+    return fm;
+}
+
+// Logarithmic cells: cells aligned to multiples of 2^s in the float bit
+// pattern, so a kernel finds a value's cell as (bits >> s) - u0s; the last
+// cell holds T[nthr - 1].
+double log_table(const float *T, int nthr, int nbins, int ncomp, uint8_t *tab, Tables &t)
+{
     const uint32_t u0 = T[0] > 0.0f ? fbits(T[0]) : 0u;
     const uint32_t uhi = fbits(T[nthr - 1]);
-    // cells are aligned to multiples of 2^s, so a kernel finds a value's cell as
-    // (bits >> s) - u0s; the last cell holds T[nthr - 1]
     int s = 0;
     while (((uhi >> s) - (u0 >> s)) + 1 > (uint32_t)(cf::LUT_MAX - 1))
         ++s;
     const uint32_t u0s = u0 >> s;
     const int n = (int)((uhi >> s) - u0s) + 1;
-    const uint8_t dummy = (uint8_t)nbins, flagged = (uint8_t)(nbins + 1);
-    // Cells are visited in increasing value, so the threshold counts at the cell
-    // ends only move forward: one sweep over cells and thresholds.
-    int clo = 0, chi = 0;
-    for (int q = 0; q < n; ++q) {
+    const double fm = classify_cells(T, nthr, nbins, n, ncomp, [&](int q, double &lo, double &hi) {
         const uint32_t blo = (u0s + (uint32_t)q) << s;
-        const uint32_t bhi = blo + (uint32_t)((1ull << s) - 1);
-        const float vlo = bitsf(blo), vhi = bitsf(bhi);
-        while (clo < nthr && T[clo] <= vlo)
-            ++clo;
-        chi = std::max(chi, clo);
-        while (chi < nthr && T[chi] <= vhi)
-            ++chi;
-        if (clo == chi && !(clo & 1))
-            tab[q] = (clo >= 2 && clo <= 2 * nbins) ? (uint8_t)((clo - 2) / 2) : dummy;
-        else
-            tab[q] = flagged;
-    }
-    tab[n] = dummy;
-    t.nthr = nthr;
+        lo = bitsf(blo);
+        hi = bitsf(blo + (uint32_t)((1ull << s) - 1));
+    }, tab);
     t.lut_n = n + 1;
     t.shift = s;
     t.u0s = u0s;
-    return t;
+    t.lin = 0;
+    t.lscale = 0.0f;
+    return fm;
+}
+
+// Linear cells: cell q holds the floats v with round(v * lscale) == q (the
+// kernel computes it exactly with one fma against 2^23), lscale chosen so that
+// the last threshold falls in the last cell; every value above maps past it.
+double lin_table(const float *T, int nthr, int nbins, int ncomp, uint8_t *tab, Tables &t)
+{
+    const int n = cf::LUT_MAX - 1;
+    const double top = std::max((double)T[nthr - 1], 1e-30);
+    const float ls = f32_down((n - 1.5) / top);
+    const double lsd = ls;
+    const double out = 1.0 - 1e-12, up = 1.0 + 1e-12;  // closed, slightly widened cell bounds
+    const double fm = classify_cells(T, nthr, nbins, n, ncomp, [&](int q, double &lo, double &hi) {
+        lo = q == 0 ? 0.0 : (q - 0.5) / lsd * out;
+        hi = (q + 0.5) / lsd * up;
+    }, tab);
+    t.lut_n = n + 1;
+    t.shift = 0;
+    t.u0s = 0;
+    t.lin = 1;
+    t.lscale = ls;
+    return fm;
+}
+
+// Both cell shapes, keeping the one whose flagged cells hold less pair mass.
+Tables build_tables(const double *E2, int ne, int ncomp, double M, double Ls, double R, float *T,
+                    uint8_t *tab)
+{
+    Tables tl, tg;
+    const int nthr = 2 * ne, nbins = ne - 1;
+    build_thresholds(E2, ne, ncomp, M, Ls, R, T);
+    tl.nthr = tg.nthr = nthr;
+    static thread_local std::vector<uint8_t> other;
+    other.resize(cf::LUT_MAX);
+    const double fl = lin_table(T, nthr, nbins, ncomp, tab, tl);
+    const double fg = log_table(T, nthr, nbins, ncomp, other.data(), tg);
+    if (fl <= fg)
+        return tl;
+    std::memcpy(tab, other.data(), tg.lut_n);
+    return tg;
 }
 
 // The last tables built on this thread, reused when the inputs repeat (a
@@ -398,8 +467,8 @@ int validate(const Request &q)
             return fail(CF_EINVAL, "refine factors must be in [0, 16]");
     if (c->pair_chunk != 0 && c->pair_chunk != 8 && c->pair_chunk != 16 && c->pair_chunk != 32)
         return fail(CF_EINVAL, "pair_chunk must be 0, 8, 16 or 32");
-    if (c->pair_pp < 0 || c->pair_pp > 2)
-        return fail(CF_EINVAL, "pair_pp must be 0, 1 or 2");
+    if (c->pair_pp < 0 || c->pair_pp > 4 || c->pair_pp == 3)
+        return fail(CF_EINVAL, "pair_pp must be 0, 1, 2 or 4");
     if (c->shard_count < 0 || (c->shard_count > 1 &&
                                (c->shard_index < 0 || c->shard_index >= c->shard_count)))
         return fail(CF_EINVAL, "shard_index must be in [0, shard_count)");
@@ -585,6 +654,7 @@ int run(Request &q)
     res->chunk_used = c->pair_chunk ? c->pair_chunk : 16;
     res->pp_used = c->pair_pp ? c->pair_pp : 2;
     res->tuned = 0;
+    res->table_linear = 0;
 
     int dev = 0, sms = 0;
     void *ws = nullptr, *ws2 = nullptr;
@@ -770,6 +840,9 @@ int run(Request &q)
             P.lut_n = tb.lut_n;
             P.lut_shift = tb.shift;
             P.u0 = tb.u0s;
+            P.lut_lin = tb.lin;
+            P.lut_scale = tb.lscale;
+            res->table_linear = tb.lin;
             std::memcpy(ho->thr, T, 4 * P.nthr);
             std::memcpy(ho->lut, tab, P.lut_n);
             CF_CUDA(cudaMemcpyAsync(d_thr, ho->thr, 4 * P.nthr, cudaMemcpyHostToDevice, st), "H2D thresholds");
@@ -1325,6 +1398,7 @@ int noalloc_xi(int autocorr, const cf_catalog *d1, const cf_catalog *d2, const d
     res->chunk_used = 16;
     res->pp_used = 2;
     res->tuned = 0;
+    res->table_linear = 0;
 
     int dev = 0, sms = 0, rc = CF_OK;
     cudaError_t e;
@@ -1499,6 +1573,9 @@ int noalloc_xi(int autocorr, const cf_catalog *d1, const cf_catalog *d2, const d
         P.lut_n = tb.lut_n;
         P.lut_shift = tb.shift;
         P.u0 = tb.u0s;
+        P.lut_lin = tb.lin;
+        P.lut_scale = tb.lscale;
+        res->table_linear = tb.lin;
         if ((e = cudaMemcpyAsync(d_thr, T, sizeof(float) * P.nthr, cudaMemcpyHostToDevice, st)) ||
             (e = cudaMemcpyAsync(d_lut, tab, P.lut_n, cudaMemcpyHostToDevice, st)))
             return cuda_fail(e, "H2D tables");
@@ -1851,6 +1928,8 @@ int batch_plan(cf_batch *b, cudaStream_t st, const std::vector<std::array<double
             j.P.lut_n = tb[k].lut_n;
             j.P.lut_shift = tb[k].shift;
             j.P.u0 = tb[k].u0s;
+            j.P.lut_lin = tb[k].lin;
+            j.P.lut_scale = tb[k].lscale;
             if ((e = cudaMemcpy((void *)dthr, T[k].data(), 4 * j.P.nthr, cudaMemcpyHostToDevice)) ||
                 (e = cudaMemcpy((void *)dlut, tab[k].data(), j.P.lut_n, cudaMemcpyHostToDevice)))
                 return cuda_fail(e, "H2D batch tables");
@@ -2049,6 +2128,7 @@ int batch_run(cf_batch *b, cudaStream_t user, int use_graph, cf_batch_stats *sta
         res->chunk_used = 16;
         res->pp_used = 2;
         res->tuned = 0;
+        res->table_linear = j.P.lut_lin;
     }
     if (stats) {
         stats->n_jobs = b->jobs.size();

@@ -121,6 +121,8 @@ struct PairParams {
     int nthr;           // 2 * nbins + 2 float32 thresholds
     int lut_n, lut_shift; // table entries (last one = out of range), cell width 2^shift
     uint32_t u0;          // (float bit pattern of the table's first cell) >> lut_shift
+    int lut_lin;          // 1: cells linear in d2 (cell = round(d2 * lut_scale)), else logarithmic
+    float lut_scale;
     float pscale;       // rp-pi: fl32(npibins / pimax), pi edges at integer t = |dz| * pscale
     float pband;        // rp-pi: |t - 1/2 - round(t - 1/2)| > pband means t is near an edge
     int hcopies;        // rp-pi: shared histogram copies per CTA (warp w uses w % hcopies)

@@ -410,6 +410,8 @@ struct Sweep32 {
     uint32_t u0, lut_last;
     int shift;
     int nthr;
+    int lin;                  // table cells linear in d2 (scale lscale) or logarithmic
+    float lscale;
     const double4_32a *pa, *pb;
     double Sx, Sy, Sz;
 };
@@ -419,6 +421,26 @@ __device__ __forceinline__ uint32_t lut_byte(const unsigned char *smem, uint32_t
 {
     const uint32_t q = (__float_as_uint(d2) >> shift) - u0s;  // below-range values wrap to huge
     return smem[LUT_OFF + min(q, last)];
+}
+
+// Cells linear in d2: adding 2^23 in the fma rounds d2 * scale to an integer q
+// held in the sum's low bits (exact below 2^22; larger values, and NaN, give
+// larger bit patterns and clamp to the out-of-range entry).
+constexpr float LIN_MAGIC = 8388608.0f;  // 2^23: spacing 1 in [2^23, 2^24)
+constexpr uint32_t LIN_MAGIC_BITS = 0x4b000000u;
+
+__device__ __forceinline__ uint32_t lut_byte_lin(const unsigned char *smem, float scale,
+                                                 uint32_t last, float d2)
+{
+    const uint32_t q = __float_as_uint(__fmaf_rn(d2, scale, LIN_MAGIC)) - LIN_MAGIC_BITS;
+    return smem[LUT_OFF + min(q, last)];
+}
+
+template <bool LIN>
+__device__ __forceinline__ uint32_t lut_entry(const unsigned char *smem, uint32_t u0s, int shift,
+                                              uint32_t last, float scale, float d2)
+{
+    return LIN ? lut_byte_lin(smem, scale, last, d2) : lut_byte(smem, u0s, shift, last, d2);
 }
 
 // Number of thresholds T[c] <= d2 (T non-decreasing, d2 not NaN), scanning
@@ -495,7 +517,7 @@ __device__ __forceinline__ int resolve_local(const unsigned char *smem, const Sw
 // row and set a bit of the lane's mask; once per block of 8 iterations a
 // warp-uniform test settles the recorded pairs (so the loop body has no
 // data-dependent branch).
-template <int I, int PP, bool TRI, bool EVALS, bool VERIFY>
+template <int I, int PP, bool TRI, bool EVALS, bool VERIFY, bool LIN>
 __device__ __forceinline__ void sweep32(unsigned char *smem, const Sweep32 &S, uint32_t hl, int jlo,
                                         int jhi, int jj, const u64 (&XH)[PP], const u64 (&YH)[PP],
                                         const u64 (&ZH)[PP], const int (&iv)[PP],
@@ -509,6 +531,7 @@ __device__ __forceinline__ void sweep32(unsigned char *smem, const Sweep32 &S, u
     // entries are <= nbu + 1 < 0x80: adding 0x80 - (nbu + 1) to each byte sets its
     // top bit exactly for the flagged value, without carries between bytes
     const uint32_t cflag = (0x80u - (nbu + 1u)) * 0x01010101u;
+    const u64 LS = pack2(S.lscale, S.lscale), LM = pack2(LIN_MAGIC, LIN_MAGIC);
     for (int b0 = 0; b0 < nit; b0 += 8) {
         const int jAb = jstart + 2 * jj + b0 * 2 * JS;
         const unsigned char *pb = smem + TX_OFF + jAb * 4;
@@ -527,6 +550,7 @@ __device__ __forceinline__ void sweep32(unsigned char *smem, const Sweep32 &S, u
             const u64 yB = *reinterpret_cast<const u64 *>(p + 4 * JS + TSTRIDE);
             const u64 zB = *reinterpret_cast<const u64 *>(p + 4 * JS + 2 * TSTRIDE);
             float d[PP][4];
+            uint32_t cq[PP][4];  // table cell of each pair
 #pragma unroll
             for (int q = 0; q < PP; ++q) {
                 u64 dx = fsub2(xA, XH[q]), dy = fsub2(yA, YH[q]), dz = fsub2(zA, ZH[q]);
@@ -537,15 +561,29 @@ __device__ __forceinline__ void sweep32(unsigned char *smem, const Sweep32 &S, u
                 const u64 dB = ffma2(dz, dz, ffma2(dy, dy, fmul2(dx, dx)));
                 unpack2(dA, d[q][0], d[q][1]);
                 unpack2(dB, d[q][2], d[q][3]);
+                if (LIN) {  // one packed fma gives two cells
+                    float t[4];
+                    unpack2(ffma2(dA, LS, LM), t[0], t[1]);
+                    unpack2(ffma2(dB, LS, LM), t[2], t[3]);
+#pragma unroll
+                    for (int r = 0; r < 4; ++r)
+                        cq[q][r] = __float_as_uint(t[r]) - LIN_MAGIC_BITS;
+                } else {
+#pragma unroll
+                    for (int r = 0; r < 4; ++r)
+                        cq[q][r] = (__float_as_uint(d[q][r]) >> S.shift) - S.u0;
+                }
             }
             const int gA = S.t0 + jA, gB = gA + JS;  // global indices of (a0, b0); a1, b1 are +1
             const int gv[4] = {gA, gA + 1, gB, gB + 1};
-            if (TRI) {
+            if (TRI) {  // pairs with j <= i: the out-of-range entry (and NaN for the checks)
 #pragma unroll
                 for (int q = 0; q < PP; ++q)
 #pragma unroll
-                    for (int r = 0; r < 4; ++r)
+                    for (int r = 0; r < 4; ++r) {
+                        cq[q][r] = gv[r] > iv[q] ? cq[q][r] : S.lut_last;
                         d[q][r] = gv[r] > iv[q] ? d[q][r] : qnan;
+                    }
             }
             if (EVALS) {
                 const int jv[4] = {jA, jA + 1, jA + JS, jA + JS + 1};
@@ -561,10 +599,11 @@ __device__ __forceinline__ void sweep32(unsigned char *smem, const Sweep32 &S, u
                 uint32_t e[4];
 #pragma unroll
                 for (int r = 0; r < 4; ++r) {
-                    e[r] = lut_byte(smem, S.u0, S.shift, S.lut_last, d[q][r]);
+                    e[r] = smem[LUT_OFF + min(cq[q][r], S.lut_last)];
                     red_shared1(hl + e[r] * 128u);  // every entry is a row: bin, dummy or flagged
                 }
-                const uint32_t w = e[0] | (e[1] << 8) | (e[2] << 16) | (e[3] << 24);
+                const uint32_t w = __byte_perm(__byte_perm(e[0], e[1], 0x0040),
+                                               __byte_perm(e[2], e[3], 0x0040), 0x5410);
                 fm[q] |= ((w + cflag) & 0x80808080u) >> (7 - t);  // bit 8 r + t
             }
             if (VERIFY) {
@@ -673,6 +712,8 @@ struct Xi32Path {
         S.lut_last = (uint32_t)(P.lut_n - 1);
         S.shift = P.lut_shift;
         S.nthr = P.nthr;
+        S.lin = P.lut_lin;
+        S.lscale = P.lut_scale;
         S.pa = P.A.pos64;
         S.pb = P.B.pos64;
         const float qnan = __int_as_float(0x7fc00000);
@@ -755,12 +796,21 @@ struct Xi32Path {
                         ZH[q] = pack2(zh, zh);
                     }
                     S.Sz = k == 0 ? 0.0 : (k > 0 ? P.g.box[2] : -P.g.box[2]);
-                    if (tri)
-                        sweep32<I, PP, true, EVALS, VERIFY>(smem, S, hl, jlo, jhi, jj, XH, YH, ZH, iv,
-                                                         vv, n_eval, n_rck, n_viol);
-                    else
-                        sweep32<I, PP, false, EVALS, VERIFY>(smem, S, hl, jlo, jhi, jj, XH, YH, ZH,
-                                                          iv, vv, n_eval, n_rck, n_viol);
+                    if (tri) {
+                        if (S.lin)
+                            sweep32<I, PP, true, EVALS, VERIFY, true>(smem, S, hl, jlo, jhi, jj, XH, YH,
+                                                                   ZH, iv, vv, n_eval, n_rck, n_viol);
+                        else
+                            sweep32<I, PP, true, EVALS, VERIFY, false>(smem, S, hl, jlo, jhi, jj, XH, YH,
+                                                                    ZH, iv, vv, n_eval, n_rck, n_viol);
+                    } else {
+                        if (S.lin)
+                            sweep32<I, PP, false, EVALS, VERIFY, true>(smem, S, hl, jlo, jhi, jj, XH, YH,
+                                                                    ZH, iv, vv, n_eval, n_rck, n_viol);
+                        else
+                            sweep32<I, PP, false, EVALS, VERIFY, false>(smem, S, hl, jlo, jhi, jj, XH, YH,
+                                                                     ZH, iv, vv, n_eval, n_rck, n_viol);
+                    }
                 }
                 if (pending > (1u << 30)) {  // keep every per-lane u32 count far from overflow
                     __syncwarp();
@@ -875,7 +925,7 @@ __device__ __forceinline__ int resolve_pair_w(const unsigned char *smem, const S
     return re;
 }
 
-template <int I, bool TRI, bool EVALS>
+template <int I, bool TRI, bool EVALS, bool LIN>
 __device__ __forceinline__ void sweep32w(unsigned char *smem, const Sweep32 &S, const AccW &A,
                                          bool weighted, int jlo, int jhi, int jj, u64 XH, u64 YH,
                                          u64 ZH, u64 WH, int i, bool vi, u64 &n_eval, u64 &n_rck)
@@ -930,10 +980,10 @@ __device__ __forceinline__ void sweep32w(unsigned char *smem, const Sweep32 &S, 
                             (vi && jB >= jlo && jB < jhi && lb0) +
                             (vi && jB + 1 >= jlo && jB + 1 < jhi && lb1));
         }
-        const uint32_t ea0 = lut_byte(smem, S.u0, S.shift, S.lut_last, a0);
-        const uint32_t ea1 = lut_byte(smem, S.u0, S.shift, S.lut_last, a1);
-        const uint32_t eb0 = lut_byte(smem, S.u0, S.shift, S.lut_last, b0);
-        const uint32_t eb1 = lut_byte(smem, S.u0, S.shift, S.lut_last, b1);
+        const uint32_t ea0 = lut_entry<LIN>(smem, S.u0, S.shift, S.lut_last, S.lscale, a0);
+        const uint32_t ea1 = lut_entry<LIN>(smem, S.u0, S.shift, S.lut_last, S.lscale, a1);
+        const uint32_t eb0 = lut_entry<LIN>(smem, S.u0, S.shift, S.lut_last, S.lscale, b0);
+        const uint32_t eb1 = lut_entry<LIN>(smem, S.u0, S.shift, S.lut_last, S.lscale, b1);
         // flagged entries -> the not-counted row here, settled below
         acc_pair(A, min(ea0, nbu), pa0, sqrt_approx(a0) * pa0);
         acc_pair(A, min(ea1, nbu), pa1, sqrt_approx(a1) * pa1);
@@ -1002,6 +1052,8 @@ __global__ void __launch_bounds__(THREADS, 2) k_xi32w(const __grid_constant__ Pa
     S.lut_last = (uint32_t)(P.lut_n - 1);
     S.shift = P.lut_shift;
     S.nthr = P.nthr;
+    S.lin = P.lut_lin;
+    S.lscale = P.lut_scale;
     S.pa = P.A.pos64;
     S.pb = P.B.pos64;
     unsigned phase = 0;
@@ -1085,12 +1137,21 @@ __global__ void __launch_bounds__(THREADS, 2) k_xi32w(const __grid_constant__ Pa
                     const float zh = __fsub_rn(zi, kz);
                     const u64 ZH = pack2(zh, zh);
                     S.Sz = k == 0 ? 0.0 : (k > 0 ? P.g.box[2] : -P.g.box[2]);
-                    if (tri)
-                        sweep32w<I, true, EVALS>(smem, S, A, weighted, jlo, jhi, jj, XH, YH, ZH, WH,
-                                                 i, vi, n_eval, n_rck);
-                    else
-                        sweep32w<I, false, EVALS>(smem, S, A, weighted, jlo, jhi, jj, XH, YH, ZH,
-                                                  WH, i, vi, n_eval, n_rck);
+                    if (tri) {
+                        if (S.lin)
+                            sweep32w<I, true, EVALS, true>(smem, S, A, weighted, jlo, jhi, jj, XH, YH,
+                                                           ZH, WH, i, vi, n_eval, n_rck);
+                        else
+                            sweep32w<I, true, EVALS, false>(smem, S, A, weighted, jlo, jhi, jj, XH, YH,
+                                                            ZH, WH, i, vi, n_eval, n_rck);
+                    } else {
+                        if (S.lin)
+                            sweep32w<I, false, EVALS, true>(smem, S, A, weighted, jlo, jhi, jj, XH, YH,
+                                                            ZH, WH, i, vi, n_eval, n_rck);
+                        else
+                            sweep32w<I, false, EVALS, false>(smem, S, A, weighted, jlo, jhi, jj, XH,
+                                                             YH, ZH, WH, i, vi, n_eval, n_rck);
+                    }
                 }
             }
         }
@@ -1349,6 +1410,8 @@ struct SweepRP {
     int t0, nb, npi;
     uint32_t u0, lut_last;
     int shift, nthr;
+    int lin;       // rp^2 table cells linear (scale lscale) or logarithmic
+    float lscale;
     uint32_t hbase, rowb;  // shared address of this warp's histogram copy; bytes per rp row
     float pband;
     double *acc;           // weighted sums: this copy's binary64 [slot][w, r w] (or NULL)
@@ -1410,7 +1473,7 @@ __device__ __forceinline__ int resolve_rppi(const unsigned char *smem, const Swe
 // rp^2 and t' = |dz| * s - 1/2 in packed float32, the rp table byte, the pi
 // index from the rounding, one shared atomic into the warp's 2-D histogram
 // copy; one warp-uniform check for flagged pairs per iteration.
-template <int I, bool TRI, bool EVALS, bool VERIFY, bool WACC>
+template <int I, bool TRI, bool EVALS, bool VERIFY, bool WACC, bool LIN>
 __device__ __forceinline__ void sweep_rppi32(unsigned char *smem, const SweepRP &S, int jlo, int jhi,
                                              int jj, u64 XH, u64 YH, u64 ZH, u64 SC, u64 WH, int i,
                                              bool vi, u64 &n_eval, u64 &n_rck, u64 &n_viol)
@@ -1465,10 +1528,10 @@ __device__ __forceinline__ void sweep_rppi32(unsigned char *smem, const SweepRP 
                             (vi && jB >= jlo && jB < jhi && lb0) +
                             (vi && jB + 1 >= jlo && jB + 1 < jhi && lb1));
         }
-        const uint32_t ea0 = lut_byte(smem, S.u0, S.shift, S.lut_last, a0);
-        const uint32_t ea1 = lut_byte(smem, S.u0, S.shift, S.lut_last, a1);
-        const uint32_t eb0 = lut_byte(smem, S.u0, S.shift, S.lut_last, b0);
-        const uint32_t eb1 = lut_byte(smem, S.u0, S.shift, S.lut_last, b1);
+        const uint32_t ea0 = lut_entry<LIN>(smem, S.u0, S.shift, S.lut_last, S.lscale, a0);
+        const uint32_t ea1 = lut_entry<LIN>(smem, S.u0, S.shift, S.lut_last, S.lscale, a1);
+        const uint32_t eb0 = lut_entry<LIN>(smem, S.u0, S.shift, S.lut_last, S.lscale, b0);
+        const uint32_t eb1 = lut_entry<LIN>(smem, S.u0, S.shift, S.lut_last, S.lscale, b1);
         const uint32_t ma0 = min(__float_as_uint(qa0) - PI_MAGIC_BITS, npiu);
         const uint32_t ma1 = min(__float_as_uint(qa1) - PI_MAGIC_BITS, npiu);
         const uint32_t mb0 = min(__float_as_uint(qb0) - PI_MAGIC_BITS, npiu);
@@ -1627,6 +1690,8 @@ struct Rppi32Path {
         S.lut_last = (uint32_t)(P.lut_n - 1);
         S.shift = P.lut_shift;
         S.nthr = P.nthr;
+        S.lin = P.lut_lin;
+        S.lscale = P.lut_scale;
         S.hbase = smem_u32(hc);
         S.rowb = (uint32_t)(npi + 1) * 4u;
         S.pband = P.pband;
@@ -1705,13 +1770,21 @@ struct Rppi32Path {
                     const float zh = __fsub_rn(zi, kz);
                     const u64 ZH = pack2(zh, zh);
                     S.Sz = k == 0 ? 0.0 : (k > 0 ? P.g.box[2] : -P.g.box[2]);
-                    if (tri)
-                        sweep_rppi32<I, true, EVALS, VERIFY, WACC>(smem, S, jlo, jhi, jj, XH, YH, ZH,
-                                                                SC, WH, i, vi, n_eval, n_rck, n_viol);
-                    else
-                        sweep_rppi32<I, false, EVALS, VERIFY, WACC>(smem, S, jlo, jhi, jj, XH, YH, ZH,
-                                                                 SC, WH, i, vi, n_eval, n_rck,
-                                                                 n_viol);
+                    if (tri) {
+                        if (S.lin)
+                            sweep_rppi32<I, true, EVALS, VERIFY, WACC, true>(
+                                smem, S, jlo, jhi, jj, XH, YH, ZH, SC, WH, i, vi, n_eval, n_rck, n_viol);
+                        else
+                            sweep_rppi32<I, true, EVALS, VERIFY, WACC, false>(
+                                smem, S, jlo, jhi, jj, XH, YH, ZH, SC, WH, i, vi, n_eval, n_rck, n_viol);
+                    } else {
+                        if (S.lin)
+                            sweep_rppi32<I, false, EVALS, VERIFY, WACC, true>(
+                                smem, S, jlo, jhi, jj, XH, YH, ZH, SC, WH, i, vi, n_eval, n_rck, n_viol);
+                        else
+                            sweep_rppi32<I, false, EVALS, VERIFY, WACC, false>(
+                                smem, S, jlo, jhi, jj, XH, YH, ZH, SC, WH, i, vi, n_eval, n_rck, n_viol);
+                    }
                 }
                 if (pending > flush_at) {  // keep every shared u32 count far from overflow
                     __syncwarp();
@@ -2184,6 +2257,9 @@ cudaError_t launch_pairs(const PairParams &P, PairLaunch &L, int sms, cudaStream
                        : launch_persistent(k_xi32w<16, false>, P, L, sms, st);
     if (L.verify)
         return launch_persistent(k_path<Xi32Path<8, 1, true, true>, 3>, P, L, sms, st);
+    if (L.pp == 4)
+        return L.evals ? launch_persistent(k_path<Xi32Path<8, 4, true, false>, 2>, P, L, sms, st)
+                       : launch_persistent(k_path<Xi32Path<8, 4, false, false>, 2>, P, L, sms, st);
     if (L.pp == 2) {
         if (L.chunk == 8)
             return L.evals ? launch_persistent(k_path<Xi32Path<8, 2, true, false>, 3>, P, L, sms, st)

@@ -211,3 +211,16 @@ def test_invalid_inputs_rejected(cuda_device, bad):
     r = cf.countpairs_xi(*[torch.from_numpy(v).cuda() for v in (cat.x, cat.y, cat.z)], [0.1, 1.0],
                          boxsize=10.0)
     assert r.npairs.shape == (1,)
+
+
+@pytest.mark.parametrize("edges", [synth.log_edges(1e-3, 30.0, 40),  # wide: logarithmic cells
+                                   synth.linear_edges(0.0, 25.0, 25),  # from 0: linear cells
+                                   synth.log_edges(0.1, 25.0, 20)])
+def test_table_shapes_verify_band(cuda_device, edges):
+    cat = synth.neyman_scott(1500, 20.0, 2.0, 200.0, seed=44)
+    for dtype in (np.float64, np.float32):
+        r, c = gpu_xi(cat, edges, dtype, boxsize=200.0, flags=cf.CF_FLAG_VERIFY_BAND)
+        assert r.n_band_violations == 0
+        assert np.array_equal(r.npairs, oracle_xi(c, edges, periodic=True, box=200.0))
+        r2, _ = gpu_xi(cat, edges, dtype, boxsize=200.0, pair_chunk=16, pair_pp=2)
+        assert np.array_equal(r2.npairs, r.npairs)
