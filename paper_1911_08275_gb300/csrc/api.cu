@@ -660,7 +660,7 @@ int run(Request &q)
     void *ws = nullptr, *ws2 = nullptr;
     cf::Geom g;
     cf::PairParams P;
-    cf::PairLaunch PL;
+    cf::PairLaunch PL = {};
     std::vector<double> E2(nb + 1);
     std::vector<double> Pe(q.kind == 1 ? q.npibins + 1 : 0);
     float T[2 * (cf::NB_MAX + 1)];
@@ -676,13 +676,14 @@ int run(Request &q)
     unsigned long long *bbox_keys = nullptr;
     unsigned *d_err = nullptr, *d_ctr = nullptr, *d_wcount = nullptr;
     cf::WorkItem *work = nullptr;
+    long long *wscratch = nullptr;
     unsigned long long *d_hist = nullptr, *d_diag = nullptr;
     float *d_thr = nullptr;
     uint8_t *d_lut = nullptr;
     double *d_E2 = nullptr, *d_P = nullptr;
     size_t total = 0;
     struct HostOut {
-        unsigned long long hist[3 * cf::NBINS2D_MAX + 6];  // hist | diag(4) | err, counter | kept | wsum | rsum
+        unsigned long long hist[3 * cf::NBINS2D_MAX + 7];  // hist | diag(4) | err, counter | kept | max |w| (2) | wsum | rsum
         unsigned long long *diag;
         unsigned err;
         float thr[2 * (cf::NB_MAX + 1)];  // page-locked staging of the tables
@@ -727,7 +728,7 @@ int run(Request &q)
         }
         bbox_keys = bump.take<unsigned long long>(6);
         // one block, one memset, one copy back: [hist | diag(4) | err, counter | wsum | rsum]
-        d_hist = bump.take<unsigned long long>(nslots + 6 + nacc);
+        d_hist = bump.take<unsigned long long>(nslots + 7 + nacc);
         d_diag = d_hist + nslots;
         d_err = reinterpret_cast<unsigned *>(d_hist + nslots + 4);
         d_ctr = d_err + 1;
@@ -751,7 +752,7 @@ int run(Request &q)
         if (dw[t])
             CF_CUDA(cudaMemcpyAsync((void *)dw[t], cats[t]->w, n * 8, cudaMemcpyHostToDevice, st), "H2D w");
     }
-    CF_CUDA(cudaMemsetAsync(d_hist, 0, sizeof(unsigned long long) * (nslots + 6 + nacc), st), "memset");
+    CF_CUDA(cudaMemsetAsync(d_hist, 0, sizeof(unsigned long long) * (nslots + 7 + nacc), st), "memset");
 
     ho = (HostOut *)g_pinned.get(sizeof(HostOut));
     if (!ho) {
@@ -792,7 +793,8 @@ int run(Request &q)
                 G[t].xs = bump.take<float>(n);
                 G[t].ys = bump.take<float>(n);
                 G[t].zs = bump.take<float>(n);
-                G[t].ws = c->weighted ? bump.take<float>(n) : nullptr;
+                G[t].ws = c->weighted ? bump.take<float>(n + 64) : nullptr;  // + slack for tile reads
+                G[t].wmax = c->weighted ? reinterpret_cast<unsigned *>(d_hist + nslots + 6) + t : nullptr;
                 G[t].pos64 = bump.take<double4_32a>(n);
                 G[t].perm = bump.take<int>(n);
                 G[t].cell_start = bump.take<uint32_t>(g.ncells + 1);
@@ -806,6 +808,9 @@ int run(Request &q)
             tmp.pad = bump.take<uint32_t>(g.ncols);
             tmp.bsum = bump.take<uint32_t>(g.ncells / 4096 + 2);
             work = bump.take<cf::WorkItem>((size_t)g.ncols * cf::MAX_STENCIL);
+            // float32 weighted DD(r): 64-bit sums per thread of at most 2 CTAs per SM
+            wscratch = (wacc && !f64 && q.kind == 0) ? bump.take<long long>((size_t)sms * 2 * cf::THREADS * 3 * nb)
+                                                     : nullptr;
             if (pass == 0) {
                 const cudaError_t e = cudaMallocAsync(&ws2, bump.off, st);
                 if (e) {
@@ -830,6 +835,7 @@ int run(Request &q)
         double M = 0.0, Ls = 0.0;
         base_params(q, g, G[0], G[1], P, M, Ls);
         P.work = work;
+        P.wscratch = wscratch;
         if (q.kind == 1) {
             std::memcpy(ho->pe, Pe.data(), 8 * Pe.size());
             CF_CUDA(cudaMemcpyAsync(d_P, ho->pe, 8 * Pe.size(), cudaMemcpyHostToDevice, st), "H2D pi edges");
@@ -858,7 +864,7 @@ int run(Request &q)
         P.weighted = c->weighted ? 1 : 0;
         P.want_r = c->want_ravg ? 1 : 0;
         P.wacc = wacc ? 1 : 0;
-        P.wsum = wacc ? reinterpret_cast<double *>(d_hist + nslots + 6) : nullptr;
+        P.wsum = wacc ? reinterpret_cast<double *>(d_hist + nslots + 7) : nullptr;
         P.rsum = wacc ? P.wsum + nslots : nullptr;
         P.diag = d_diag;
         P.err = d_err;
@@ -870,7 +876,14 @@ int run(Request &q)
         PL.pp = c->pair_pp ? c->pair_pp : 2;
         PL.evals = (c->flags & (CF_FLAG_COUNT_EVALS | CF_FLAG_VERIFY_BAND)) ? 1 : 0;
         PL.verify = (!f64 && (c->flags & CF_FLAG_VERIFY_BAND)) ? 1 : 0;
+        PL.max_blocks = wscratch ? sms * 2 : 0;
         cf::plan_pairs(P, PL);
+        if (!f64 && PL.smem > cf::SMEM_MAX) {
+            // float32 weighted rows for this many bins exceed shared memory: count
+            // with the binary64 kernel instead (same results, exact per-pair terms)
+            PL.f64 = 1;
+            cf::plan_pairs(P, PL);
+        }
         trace.point("tables");
         CF_CUDA(cudaEventRecord(g_events.ev[1], st), "cudaEventRecord");
         if (P.n_items > 0) {
@@ -882,7 +895,7 @@ int run(Request &q)
         }
         CF_CUDA(cudaEventRecord(g_events.ev[2], st), "cudaEventRecord");
         trace.point("pair kernel");
-        CF_CUDA(cudaMemcpyAsync(ho->hist, d_hist, sizeof(unsigned long long) * (nslots + 6 + nacc),
+        CF_CUDA(cudaMemcpyAsync(ho->hist, d_hist, sizeof(unsigned long long) * (nslots + 7 + nacc),
                                 cudaMemcpyDeviceToHost, st),
                 "D2H results");
     }
@@ -917,7 +930,7 @@ int run(Request &q)
         for (int k = 0; k < nslots; ++k)
             res->npairs[k] = ho->hist[k] * mult;
         if (wacc) {
-            const double *ws = reinterpret_cast<const double *>(ho->hist + nslots + 6);
+            const double *ws = reinterpret_cast<const double *>(ho->hist + nslots + 7);
             const double *rs = ws + nslots;
             for (int k = 0; k < nslots; ++k) {
                 const double wk = ws[k] * (double)mult, rk = rs[k] * (double)mult;

@@ -43,14 +43,10 @@ constexpr int XI32_THR_OFF = XI32_TX_OFF + 3 * XI32_TSTRIDE;
 constexpr int XI32_E2_OFF = XI32_THR_OFF + 2 * (NB_MAX + 1) * 4;
 constexpr int XI32_HIST_OFF = XI32_E2_OFF + (NB_MAX + 1) * 8;
 
-// The weighted / mean-separation float32 DD(r) kernel adds, after the DD(r)
-// layout's squared edges: a weight tile; per warp and bin the binary64
-// accumulators {count (u64), sum w, sum r w}; per warp, bin and lane a byte
-// count and two float32 partial sums that hold at most 63 terms each.
+// The weighted float32 DD(rp, pi) kernel stages a weight tile after the squared
+// edges.
 constexpr int XIW_W_OFF = XI32_HIST_OFF;
-constexpr int XIW_ACC_OFF = XIW_W_OFF + XI32_TSTRIDE;
-constexpr unsigned XIW_FLUSH = 64;  // terms per float32 partial before it moves to binary64
-static_assert(XIW_W_OFF % 16 == 0 && XIW_ACC_OFF % 16 == 0, "bulk-copy destinations need 16 B");
+static_assert(XIW_W_OFF % 16 == 0, "bulk-copy destinations need 16 B");
 
 // The float32 DD(rp, pi) kernel uses the DD(r) layout up to the thresholds and
 // squared rp edges, then a weight tile (as above), the pi edges (binary64) and,
@@ -80,7 +76,8 @@ struct Geom {
 struct Gridded {
     long long n;
     float *xs, *ys, *zs;  // float32 coordinates in the grid frame (padded columns)
-    float *ws;            // float32 weights (padded columns; NULL without weights)
+    float *ws;            // float32 weights (padded columns, 64 floats of slack; NULL without weights)
+    unsigned *wmax;       // bit pattern of max |w| as float (written by gridding; NULL without weights)
     double4_32a *pos64;       // (x, y, z, w) binary64, exact inputs
     int *perm;            // original index of each sorted point
     uint32_t *cell_start; // ncells + 1
@@ -132,7 +129,7 @@ struct PairParams {
     int want_r;         // accumulate r (xi) or rp (rp-pi) times the pair weight
     int wacc;           // weighted || want_r
     int acc_off;        // byte offset of the binary64 accumulators in shared memory
-    int rows_off;       // float32 DD(r) kernel: byte offset of the per-lane partial rows
+    long long *wscratch;  // float32 weighted DD(r): per-thread [bin][count, w, r w] int64 sums
     const float *thr;        // nthr
     const uint8_t *lut;      // lut_n
     const double *E2;        // nbins + 1

@@ -260,9 +260,11 @@ __global__ void k_sort_cells(const T *__restrict__ x, const T *__restrict__ y,
                              const unsigned long long *__restrict__ tmp_key,
                              float *__restrict__ xs, float *__restrict__ ys,
                              float *__restrict__ zs, float *__restrict__ ws,
-                             double4_32a *__restrict__ pos64, int *__restrict__ perm)
+                             unsigned *__restrict__ wmax, double4_32a *__restrict__ pos64,
+                             int *__restrict__ perm)
 {
     const int lane = threadIdx.x & 31;
+    unsigned wm = 0;  // bit pattern of the largest |w| (float) this thread stored
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
     for (long long c = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < ncells;
          c += nwarps) {
@@ -301,10 +303,25 @@ __global__ void k_sort_cells(const T *__restrict__ x, const T *__restrict__ y,
                 xs[d] = fx;
                 ys[d] = fy;
                 zs[d] = fz;
-                if (ws)
+                if (ws) {
                     ws[d] = (float)W;
+                    wm = max(wm, __float_as_uint(fabsf((float)W)));
+                }
                 perm[d] = iq;
             }
+        }
+    }
+    if (wmax) {  // one atomic per block
+        __shared__ unsigned red[8];
+        wm = __reduce_max_sync(FULL, wm);
+        if (lane == 0)
+            red[threadIdx.x >> 5] = wm;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned m = 0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
+                m = max(m, red[w]);
+            atomicMax(wmax, m);
         }
     }
 }
@@ -464,7 +481,7 @@ cudaError_t build_grid_t(const void *x, const void *y, const void *z, const doub
         const long long cwarps = std::min<long long>(nc, (long long)sms * 64);
         k_sort_cells<T><<<(int)((cwarps * 32 + 255) / 256), 256, 0, st>>>(
             (const T *)x, (const T *)y, w, nc, g, t.counts, out.cell_start, t.tmp_idx, t.tmp_key,
-            out.xs, out.ys, out.zs, out.ws, out.pos64, out.perm);
+            out.xs, out.ys, out.zs, out.ws, out.ws ? out.wmax : nullptr, out.pos64, out.perm);
     }
     k_padfill<<<(g.ncols + 255) / 256, 256, 0, st>>>(out.cell_start, t.pad, g.ncols, g.nz, out.xs,
                                                       out.ys, out.zs, out.ws, out.pos64, out.perm);

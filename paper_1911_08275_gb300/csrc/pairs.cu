@@ -43,7 +43,7 @@ namespace cf {
 void plan_pairs(PairParams &P, PairLaunch &L)
 {
     const int nb = P.nbins, nr = nb + 1;
-    P.acc_off = P.rows_off = 0;
+    P.acc_off = 0;
     if (P.kind == 0) {
         L.hist_words = WARPS * nr * 32;  // per-lane rows + one dummy row per warp
         P.hcopies = WARPS;
@@ -53,13 +53,12 @@ void plan_pairs(PairParams &P, PairLaunch &L)
             P.acc_off = S.total;  // [warp][bin][w, r w] binary64 when weighted
             L.smem = P.wacc ? align_up(S.total + WARPS * nb * 16, 128) : S.total;
         } else if (P.wacc) {
-            // [warp][bin] {u64, f64, f64}; byte-count plane; two float32 planes
-            P.hist_off = XIW_ACC_OFF;
-            P.acc_off = XIW_ACC_OFF;
-            P.rows_off = align_up(XIW_ACC_OFF + WARPS * nr * 24, 128);
-            L.hist_words = 0;
-            L.smem = align_up(P.rows_off + align_up(WARPS * nr * 32, 128) + 2 * WARPS * nr * 32 * 4,
-                              128);
+            // count rows, then w and / or r w rows ([warp][row][lane] u32), then the
+            // per-row scales of r w
+            const int planes = 1 + (P.weighted ? 1 : 0) + (P.want_r ? 1 : 0);
+            P.hist_off = XI32_HIST_OFF;
+            L.hist_words = planes * WARPS * (nb + 2) * 32;
+            L.smem = align_up(XI32_HIST_OFF + L.hist_words * 4 + (nb + 2) * 4, 128);
         } else {
             L.hist_words = WARPS * (nb + 2) * 32;  // + a row for flagged table cells
             P.hist_off = XI32_HIST_OFF;
@@ -310,6 +309,7 @@ struct PathState {
     u64 n_eval, n_rck, n_viol;  // diagnostics (evaluations, re-checks, band violations)
     unsigned pending;           // pairs added to the shared u32 counts since the last flush
     unsigned phase;             // parity of the tile mbarrier
+    unsigned wpend;             // weighted sums: pair slots per lane since the last row flush
 };
 
 __device__ __forceinline__ void decode_item(const PairParams &P, int item, Item &it)
@@ -495,18 +495,98 @@ __device__ __forceinline__ int resolve_pair(const unsigned char *smem, const Swe
     return re;
 }
 
+// ---- weighted sums in the float32 DD(r) sweep (Code 1's weight per pair)
+// A pair adds round(v * scale) for its weight v = w_i w_j (scale sw) and for
+// r * v (a scale per bin) to 32-bit per-lane rows, as the low mantissa bits of
+// fma(v, scale, 1.5 * 2^23): the row then holds count * bits(1.5 * 2^23) plus
+// the exact integer sum, which the lane recovers with its own count.  Scales
+// are powers of two with every term below 2^21 in size, so 512 terms cannot
+// overflow; rows move to per-thread 64-bit sums every 64 iterations.  The
+// rounding error of one term is at most half a unit: relative to the term
+// 2^-22 max|w_i w_j| / |w_i w_j| (times Rmax / e_k for r w).
+constexpr float QMAGIC = 12582912.0f;      // 1.5 * 2^23
+constexpr uint32_t QMAGIC_BITS = 0x4b400000u;
+constexpr unsigned WFLUSH_PAIRS = 448;     // flush before any row holds more terms
+
+struct WAcc {
+    uint32_t hlw, hlr;     // shared addresses of this lane's w and r w rows (row stride 128 B)
+    const float *sr;       // per-row scale of r w (shared; 0 for the two dummy rows)
+    float sw;              // scale of w
+    const float *wsj;      // secondary weights of the staged tile (global, from tile element 0)
+    uint32_t *cnt, *wq, *rq;  // this lane's rows (generic pointers, stride 32 words)
+    long long *g;          // this thread's [bin][count, w, r w] 64-bit sums (global)
+    int nb;
+};
+
+__device__ __forceinline__ void red_shared_u32(uint32_t addr, uint32_t v)
+{
+    asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(addr), "r"(v));
+}
+
+template <bool W, bool RV>
+__device__ __forceinline__ void wacc_add(const WAcc &A, uint32_t e, float pw, float d2)
+{
+    if (W)
+        red_shared_u32(A.hlw + e * 128u, __float_as_uint(__fmaf_rn(pw, A.sw, QMAGIC)));
+    if (RV) {
+        float r;
+        asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(d2));
+        const float rw = W ? r * pw : r;
+        red_shared_u32(A.hlr + e * 128u, __float_as_uint(__fmaf_rn(rw, A.sr[e], QMAGIC)));
+    }
+}
+
+// Move this lane's rows of the counted bins to its 64-bit sums (lane-private).
+template <bool W, bool RV>
+__device__ __noinline__ void wacc_flush(const WAcc &A)
+{
+    for (int k = 0; k < A.nb; ++k) {
+        const uint32_t c = A.cnt[k * 32];
+        if (!c)
+            continue;
+        A.cnt[k * 32] = 0u;
+        A.g[3 * k] += (long long)c;
+        if (W) {
+            A.g[3 * k + 1] += (long long)(int)(A.wq[k * 32] - c * QMAGIC_BITS);
+            A.wq[k * 32] = 0u;
+        }
+        if (RV) {
+            A.g[3 * k + 2] += (long long)(int)(A.rq[k * 32] - c * QMAGIC_BITS);
+            A.rq[k * 32] = 0u;
+        }
+    }
+}
+
 // A flagged pair recorded by sweep32: recompute its float32 d2 from the
 // staged tile (the same IEEE operations as the packed main path), settle it
 // with the thresholds (binary64 inside a band) and add it to its true row.
+template <bool W, bool RV>
 __device__ __forceinline__ int resolve_local(const unsigned char *smem, const Sweep32 &S, uint32_t hl,
-                                          float xh, float yh, float zh, int i, int jl)
+                                          float xh, float yh, float zh, int i, int jl,
+                                          const WAcc &A, float wi)
 {
     const float *tx = reinterpret_cast<const float *>(smem + TX_OFF);
     const float dx = __fsub_rn(tx[jl], xh);
     const float dy = __fsub_rn(tx[jl + TSTRIDE / 4], yh);
     const float dz = __fsub_rn(tx[jl + TSTRIDE / 2], zh);
     const float d2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
-    return resolve_pair(smem, S, hl, d2, i, S.t0 + jl);
+    if (!W && !RV)
+        return resolve_pair(smem, S, hl, d2, i, S.t0 + jl);
+    const float *T = reinterpret_cast<const float *>(smem + THR_OFF);
+    const int c = thr_count_top(T, S.nthr, d2);
+    int row, re = 0;
+    if (!(c & 1)) {
+        row = (c >= 2 && c <= 2 * S.nb) ? (c - 2) >> 1 : -1;
+    } else {
+        row = recheck64(reinterpret_cast<const double *>(smem + E2_OFF), S.nb, S.pa, S.pb, i,
+                        S.t0 + jl, S.Sx, S.Sy, S.Sz);
+        re = 1;
+    }
+    if (row >= 0) {
+        red_shared1(hl + (uint32_t)row * 128u);
+        wacc_add<W, RV>(A, (uint32_t)row, W ? __fmul_rn(A.wsj[jl], wi) : 1.0f, d2);
+    }
+    return re;
 }
 
 // Sweep one window [jlo, jhi) of the staged tile.  Lane (ii, jj) holds PP
@@ -517,11 +597,12 @@ __device__ __forceinline__ int resolve_local(const unsigned char *smem, const Sw
 // row and set a bit of the lane's mask; once per block of 8 iterations a
 // warp-uniform test settles the recorded pairs (so the loop body has no
 // data-dependent branch).
-template <int I, int PP, bool TRI, bool EVALS, bool VERIFY, bool LIN>
+template <int I, int PP, bool TRI, bool EVALS, bool VERIFY, bool LIN, bool W, bool RV>
 __device__ __forceinline__ void sweep32(unsigned char *smem, const Sweep32 &S, uint32_t hl, int jlo,
                                         int jhi, int jj, const u64 (&XH)[PP], const u64 (&YH)[PP],
                                         const u64 (&ZH)[PP], const int (&iv)[PP],
-                                        const bool (&vv)[PP], u64 &n_eval, u64 &n_rck, u64 &n_viol)
+                                        const bool (&vv)[PP], u64 &n_eval, u64 &n_rck, u64 &n_viol,
+                                        const WAcc &A, const float (&wi)[PP], unsigned &wpend)
 {
     const float qnan = __int_as_float(0x7fc00000);
     const int jstart = jlo & ~1;  // 8-byte aligned pairs; extra j's are never counted
@@ -550,7 +631,18 @@ __device__ __forceinline__ void sweep32(unsigned char *smem, const Sweep32 &S, u
             const u64 yB = *reinterpret_cast<const u64 *>(p + 4 * JS + TSTRIDE);
             const u64 zB = *reinterpret_cast<const u64 *>(p + 4 * JS + 2 * TSTRIDE);
             float d[PP][4];
+            float pw[PP][4];     // pair weights (weighted sums only)
             uint32_t cq[PP][4];  // table cell of each pair
+            if (W) {  // w_j of the two secondary pairs (global, 8-byte aligned)
+                const u64 wA = *reinterpret_cast<const u64 *>(A.wsj + jA);
+                const u64 wB = *reinterpret_cast<const u64 *>(A.wsj + jA + JS);
+#pragma unroll
+                for (int q = 0; q < PP; ++q) {
+                    const u64 WI = pack2(wi[q], wi[q]);
+                    unpack2(fmul2(wA, WI), pw[q][0], pw[q][1]);
+                    unpack2(fmul2(wB, WI), pw[q][2], pw[q][3]);
+                }
+            }
 #pragma unroll
             for (int q = 0; q < PP; ++q) {
                 u64 dx = fsub2(xA, XH[q]), dy = fsub2(yA, YH[q]), dz = fsub2(zA, ZH[q]);
@@ -601,6 +693,8 @@ __device__ __forceinline__ void sweep32(unsigned char *smem, const Sweep32 &S, u
                 for (int r = 0; r < 4; ++r) {
                     e[r] = smem[LUT_OFF + min(cq[q][r], S.lut_last)];
                     red_shared1(hl + e[r] * 128u);  // every entry is a row: bin, dummy or flagged
+                    if (W || RV)
+                        wacc_add<W, RV>(A, e[r], W ? pw[q][r] : 1.0f, d[q][r]);
                 }
                 const uint32_t w = __byte_perm(__byte_perm(e[0], e[1], 0x0040),
                                                __byte_perm(e[2], e[3], 0x0040), 0x5410);
@@ -636,8 +730,15 @@ __device__ __forceinline__ void sweep32(unsigned char *smem, const Sweep32 &S, u
                     m &= m - 1u;
                     const int t = bit & 7, r = bit >> 3;
                     const int jl = jAb + t * 2 * JS + ((r & 2) ? JS : 0) + (r & 1);
-                    n_rck += resolve_local(smem, S, hl, xh, yh, zh, iv[q], jl);
+                    n_rck += resolve_local<W, RV>(smem, S, hl, xh, yh, zh, iv[q], jl, A, wi[q]);
                 }
+            }
+        }
+        if (W || RV) {  // warp-uniform: every lane ran the same iterations
+            wpend += (unsigned)tend * 4u * PP;
+            if (wpend > WFLUSH_PAIRS - 64u * PP) {
+                wacc_flush<W, RV>(A);
+                wpend = 0;
             }
         }
     }
@@ -663,7 +764,20 @@ __device__ __forceinline__ int warp_bound_from(Key key, int start, int n, V v, b
     return lo + warp_bound([&](int t) { return key(lo + t); }, hi - lo, v, upper, lane);
 }
 
-template <int I, int PP, bool EVALS, bool VERIFY>
+// Weighted float32 DD(r): shared rows after the count rows, [warp][row][lane]
+// for w, then for r w, then the per-row scale of r w; power-of-two scales from
+// the largest weights (gridding wrote their bit patterns).
+__device__ __forceinline__ float pow2_floor(float x)
+{
+    return (x > 0.0f && x < INFINITY) ? __uint_as_float(__float_as_uint(x) & 0x7f800000u) : 1.0f;
+}
+
+__device__ __forceinline__ float wmax_pair(const PairParams &P)
+{
+    return __uint_as_float(*P.A.wmax) * __uint_as_float(*P.B.wmax);
+}
+
+template <int I, int PP, bool EVALS, bool VERIFY, bool W = false, bool RV = false>
 struct Xi32Path {
     static __device__ __forceinline__ void init(const PairParams &P, unsigned char *smem)
     {
@@ -681,8 +795,18 @@ struct Xi32Path {
             thr[q] = P.thr[q];
         for (int q = tid; q <= nb; q += THREADS)
             E2[q] = P.E2[q];
-        for (int q = tid; q < WARPS * (nb + 2) * 32; q += THREADS)
+        constexpr int planes = 1 + (W ? 1 : 0) + (RV ? 1 : 0);
+        for (int q = tid; q < planes * WARPS * (nb + 2) * 32; q += THREADS)
             hist[q] = 0u;
+        if (W || RV) {
+            float *sr = reinterpret_cast<float *>(hist + planes * WARPS * (nb + 2) * 32);
+            const float mw = W ? wmax_pair(P) : 1.0f;
+            for (int k = tid; k < nb + 2; k += THREADS)  // r w < 2^20 scale in bin k (headroom 2)
+                sr[k] = k < nb ? pow2_floor(1048576.0f / (sqrtf((float)E2[k + 1]) * mw)) : 0.0f;
+            long long *g = P.wscratch + ((long long)blockIdx.x * THREADS + tid) * 3 * nb;
+            for (int k = 0; k < 3 * nb; ++k)
+                g[k] = 0;
+        }
     }
 
     static __device__ __forceinline__ bool item(const PairParams &P, const Item &it,
@@ -706,6 +830,20 @@ struct Xi32Path {
         uint32_t *hw = hist + warp * (nb + 2) * 32;  // rows: bins, not counted, flagged
         const uint32_t hl = smem_u32(hw + lane);  // this lane's histogram column (shared address)
         const int ii = lane % I, jj = lane / I;
+        WAcc A;
+        if (W || RV) {
+            const int plane = WARPS * (nb + 2) * 32;
+            A.cnt = hw + lane;
+            A.wq = A.cnt + plane;
+            A.rq = A.cnt + (W ? 2 : 1) * plane;
+            A.hlw = smem_u32(A.wq);
+            A.hlr = smem_u32(A.rq);
+            A.sr = reinterpret_cast<const float *>(hist + (1 + (W ? 1 : 0) + (RV ? 1 : 0)) * plane);
+            A.sw = W ? pow2_floor(2097152.0f / wmax_pair(P)) : 1.0f;
+            A.wsj = P.B.ws;
+            A.g = P.wscratch + ((long long)blockIdx.x * THREADS + tid) * 3 * nb;
+            A.nb = nb;
+        }
         Sweep32 S;
         S.nb = nb;
         S.u0 = P.u0;
@@ -742,16 +880,19 @@ struct Xi32Path {
                 u64 XH[PP], YH[PP], ZH[PP];
                 int iv[PP];
                 bool vv[PP];
-                float zq[PP];
+                float zq[PP], wi[PP];
                 float zmax = qnan;
     #pragma unroll
                 for (int q = 0; q < PP; ++q) {
                     const int i = ib + q * I + ii;
                     float xi = qnan, yi = qnan, zi = qnan;
+                    wi[q] = 1.0f;
                     if (i < it.a1) {
                         xi = P.A.xs[i];
                         yi = P.A.ys[i];
                         zi = P.A.zs[i];
+                        if (W)
+                            wi[q] = P.A.ws[i];
                     }
                     iv[q] = i;
                     vv[q] = !isnan(xi);  // chunk tail and column padding are NaN
@@ -796,23 +937,29 @@ struct Xi32Path {
                         ZH[q] = pack2(zh, zh);
                     }
                     S.Sz = k == 0 ? 0.0 : (k > 0 ? P.g.box[2] : -P.g.box[2]);
+                    if (W)
+                        A.wsj = P.B.ws + t0;
                     if (tri) {
                         if (S.lin)
-                            sweep32<I, PP, true, EVALS, VERIFY, true>(smem, S, hl, jlo, jhi, jj, XH, YH,
-                                                                   ZH, iv, vv, n_eval, n_rck, n_viol);
+                            sweep32<I, PP, true, EVALS, VERIFY, true, W, RV>(
+                                smem, S, hl, jlo, jhi, jj, XH, YH, ZH, iv, vv, n_eval, n_rck, n_viol,
+                                A, wi, st.wpend);
                         else
-                            sweep32<I, PP, true, EVALS, VERIFY, false>(smem, S, hl, jlo, jhi, jj, XH, YH,
-                                                                    ZH, iv, vv, n_eval, n_rck, n_viol);
+                            sweep32<I, PP, true, EVALS, VERIFY, false, W, RV>(
+                                smem, S, hl, jlo, jhi, jj, XH, YH, ZH, iv, vv, n_eval, n_rck, n_viol,
+                                A, wi, st.wpend);
                     } else {
                         if (S.lin)
-                            sweep32<I, PP, false, EVALS, VERIFY, true>(smem, S, hl, jlo, jhi, jj, XH, YH,
-                                                                    ZH, iv, vv, n_eval, n_rck, n_viol);
+                            sweep32<I, PP, false, EVALS, VERIFY, true, W, RV>(
+                                smem, S, hl, jlo, jhi, jj, XH, YH, ZH, iv, vv, n_eval, n_rck, n_viol,
+                                A, wi, st.wpend);
                         else
-                            sweep32<I, PP, false, EVALS, VERIFY, false>(smem, S, hl, jlo, jhi, jj, XH, YH,
-                                                                     ZH, iv, vv, n_eval, n_rck, n_viol);
+                            sweep32<I, PP, false, EVALS, VERIFY, false, W, RV>(
+                                smem, S, hl, jlo, jhi, jj, XH, YH, ZH, iv, vv, n_eval, n_rck, n_viol,
+                                A, wi, st.wpend);
                     }
                 }
-                if (pending > (1u << 30)) {  // keep every per-lane u32 count far from overflow
+                if (!(W || RV) && pending > (1u << 30)) {  // keep per-lane u32 counts far from overflow
                     __syncwarp();
                     warp_flush(hw, nb, P.hist, lane);
                     pending = 0;
@@ -834,14 +981,46 @@ struct Xi32Path {
         u64 &n_rck = st.n_rck;
         u64 &n_viol = st.n_viol;
 
-        __syncthreads();
-        for (int bn = tid; bn < nb; bn += THREADS) {
-            u64 sum = 0;
-            for (int w = 0; w < WARPS; ++w)
-                for (int l = 0; l < 32; ++l)
-                    sum += hist[(w * (nb + 2) + bn) * 32 + l];
-            if (sum)
-                atomicAdd(&P.hist[bn], sum);
+        if (W || RV) {
+            // the lane's last rows, then the CTA's 64-bit sums -> global
+            const int plane = WARPS * (nb + 2) * 32, warp = tid >> 5;
+            WAcc A;
+            A.cnt = hist + warp * (nb + 2) * 32 + lane;
+            A.wq = A.cnt + plane;
+            A.rq = A.cnt + (W ? 2 : 1) * plane;
+            A.g = P.wscratch + ((long long)blockIdx.x * THREADS + tid) * 3 * nb;
+            A.nb = nb;
+            wacc_flush<W, RV>(A);
+            __threadfence_block();
+            __syncthreads();
+            const float *sr = reinterpret_cast<const float *>(hist + (1 + (W ? 1 : 0) + (RV ? 1 : 0)) * plane);
+            const float sw = W ? pow2_floor(2097152.0f / wmax_pair(P)) : 1.0f;
+            const long long *gb = P.wscratch + (long long)blockIdx.x * THREADS * 3 * nb;
+            for (int bn = tid; bn < nb; bn += THREADS) {
+                long long c = 0, wsum = 0, rsum = 0;
+                for (int t = 0; t < THREADS; ++t) {
+                    c += gb[((long long)t * nb + bn) * 3];
+                    wsum += gb[((long long)t * nb + bn) * 3 + 1];
+                    rsum += gb[((long long)t * nb + bn) * 3 + 2];
+                }
+                if (c) {
+                    atomicAdd(&P.hist[bn], (u64)c);
+                    if (W)
+                        atomicAdd(&P.wsum[bn], (double)wsum / (double)sw);
+                    if (RV)
+                        atomicAdd(&P.rsum[bn], (double)rsum / (double)sr[bn]);
+                }
+            }
+        } else {
+            __syncthreads();
+            for (int bn = tid; bn < nb; bn += THREADS) {
+                u64 sum = 0;
+                for (int w = 0; w < WARPS; ++w)
+                    for (int l = 0; l < 32; ++l)
+                        sum += hist[(w * (nb + 2) + bn) * 32 + l];
+                if (sum)
+                    atomicAdd(&P.hist[bn], sum);
+            }
         }
         n_eval = warp_sum_u64(n_eval);
         n_rck = warp_sum_u64(n_rck);
@@ -857,339 +1036,11 @@ struct Xi32Path {
     }
 };
 
-// ============================================ float32 DD(r) with weights / ravg
-// Code 1 adds a weight per counted pair; here the pair weight is w_i * w_j
-// (float32 product of the float32 weights, or 1) and the mean separation sums
-// r * weight with r = sqrt(d2) in float32.  Sums are binary64: each lane keeps,
-// per bin, a byte count and float32 partial sums of at most 63 terms (so each
-// partial's relative rounding error stays below 63 u32 for same-sign terms);
-// the 64th term moves the partials to the warp's binary64 accumulators.
-struct AccW {
-    unsigned char *cnt;  // this warp's byte-count plane + lane (stride 32 per bin)
-    float *wp, *rp;      // float32 partial planes + lane (stride 32 per bin)
-    double *acc;         // this warp's binary64 accumulators: [bin][count(u64), w, r w]
-    bool want_r;
-};
-
 __device__ __forceinline__ float sqrt_approx(float v)
 {
     float r;
     asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
     return r;
-}
-
-__device__ __forceinline__ void acc_pair(const AccW &A, uint32_t row, float pw, float rw)
-{
-    unsigned char *cp = A.cnt + row * 32u;
-    float *wp = A.wp + row * 32u;
-    const unsigned c = (unsigned)*cp + 1u;
-    const float ws = *wp + pw;
-    if (c == XIW_FLUSH) {
-        atomicAdd(reinterpret_cast<unsigned long long *>(A.acc + row * 3u), (u64)XIW_FLUSH);
-        atomicAdd(A.acc + row * 3u + 1u, (double)ws);
-        if (A.want_r) {
-            float *rp = A.rp + row * 32u;
-            atomicAdd(A.acc + row * 3u + 2u, (double)(*rp + rw));
-            *rp = 0.0f;
-        }
-        *cp = 0;
-        *wp = 0.0f;
-    } else {
-        *cp = (unsigned char)c;
-        *wp = ws;
-        if (A.want_r) {
-            float *rp = A.rp + row * 32u;
-            *rp += rw;
-        }
-    }
-}
-
-// Flagged table cell, weighted kernel: as resolve_pair, but the pair's weight
-// and r * weight go with it to its true bin.
-__device__ __forceinline__ int resolve_pair_w(const unsigned char *smem, const Sweep32 &S,
-                                              const AccW &A, float d2, float pw, int i, int jg)
-{
-    const float *T = reinterpret_cast<const float *>(smem + THR_OFF);
-    const int c = thr_count(T, S.nthr, d2);
-    int row;
-    int re = 0;
-    if (!(c & 1)) {
-        row = (c >= 2 && c <= 2 * S.nb) ? (c - 2) >> 1 : -1;
-    } else {
-        row = recheck64(reinterpret_cast<const double *>(smem + E2_OFF), S.nb, S.pa, S.pb, i, jg,
-                        S.Sx, S.Sy, S.Sz);
-        re = 1;
-    }
-    if (row >= 0)
-        acc_pair(A, (uint32_t)row, pw, sqrt_approx(d2) * pw);
-    return re;
-}
-
-template <int I, bool TRI, bool EVALS, bool LIN>
-__device__ __forceinline__ void sweep32w(unsigned char *smem, const Sweep32 &S, const AccW &A,
-                                         bool weighted, int jlo, int jhi, int jj, u64 XH, u64 YH,
-                                         u64 ZH, u64 WH, int i, bool vi, u64 &n_eval, u64 &n_rck)
-{
-    const float qnan = __int_as_float(0x7fc00000);
-    const int jstart = jlo & ~1;
-    constexpr int JS = 64 / I;
-    const int nit = (jhi - jstart + 2 * JS - 1) / (2 * JS);
-    const unsigned char *p = smem + TX_OFF + (jstart + 2 * jj) * 4;
-    const unsigned char *pw8 = smem + XIW_W_OFF + (jstart + 2 * jj) * 4;
-    const uint32_t nbu = (uint32_t)S.nb;
-    int jA = jstart + 2 * jj;
-    for (int it = 0; it < nit; ++it, p += 8 * JS, pw8 += 8 * JS, jA += 2 * JS) {
-        const u64 xA = *reinterpret_cast<const u64 *>(p);
-        const u64 yA = *reinterpret_cast<const u64 *>(p + TSTRIDE);
-        const u64 zA = *reinterpret_cast<const u64 *>(p + 2 * TSTRIDE);
-        const u64 xB = *reinterpret_cast<const u64 *>(p + 4 * JS);
-        const u64 yB = *reinterpret_cast<const u64 *>(p + 4 * JS + TSTRIDE);
-        const u64 zB = *reinterpret_cast<const u64 *>(p + 4 * JS + 2 * TSTRIDE);
-        u64 dx = fsub2(xA, XH), dy = fsub2(yA, YH), dz = fsub2(zA, ZH);
-        const u64 dA = ffma2(dz, dz, ffma2(dy, dy, fmul2(dx, dx)));
-        dx = fsub2(xB, XH);
-        dy = fsub2(yB, YH);
-        dz = fsub2(zB, ZH);
-        const u64 dB = ffma2(dz, dz, ffma2(dy, dy, fmul2(dx, dx)));
-        float pa0 = 1.0f, pa1 = 1.0f, pb0 = 1.0f, pb1 = 1.0f;
-        if (weighted) {
-            const u64 wA = fmul2(*reinterpret_cast<const u64 *>(pw8), WH);
-            const u64 wB = fmul2(*reinterpret_cast<const u64 *>(pw8 + 4 * JS), WH);
-            unpack2(wA, pa0, pa1);
-            unpack2(wB, pb0, pb1);
-        }
-        float a0, a1, b0, b1;
-        unpack2(dA, a0, a1);
-        unpack2(dB, b0, b1);
-        const int gA = S.t0 + jA, gB = gA + JS;
-        bool la0 = true, la1 = true, lb0 = true, lb1 = true;
-        if (TRI) {
-            la0 = gA > i;
-            la1 = gA + 1 > i;
-            lb0 = gB > i;
-            lb1 = gB + 1 > i;
-            a0 = la0 ? a0 : qnan;
-            a1 = la1 ? a1 : qnan;
-            b0 = lb0 ? b0 : qnan;
-            b1 = lb1 ? b1 : qnan;
-        }
-        if (EVALS) {
-            const int jB = jA + JS;
-            n_eval += (u64)((vi && jA >= jlo && jA < jhi && la0) +
-                            (vi && jA + 1 >= jlo && jA + 1 < jhi && la1) +
-                            (vi && jB >= jlo && jB < jhi && lb0) +
-                            (vi && jB + 1 >= jlo && jB + 1 < jhi && lb1));
-        }
-        const uint32_t ea0 = lut_entry<LIN>(smem, S.u0, S.shift, S.lut_last, S.lscale, a0);
-        const uint32_t ea1 = lut_entry<LIN>(smem, S.u0, S.shift, S.lut_last, S.lscale, a1);
-        const uint32_t eb0 = lut_entry<LIN>(smem, S.u0, S.shift, S.lut_last, S.lscale, b0);
-        const uint32_t eb1 = lut_entry<LIN>(smem, S.u0, S.shift, S.lut_last, S.lscale, b1);
-        // flagged entries -> the not-counted row here, settled below
-        acc_pair(A, min(ea0, nbu), pa0, sqrt_approx(a0) * pa0);
-        acc_pair(A, min(ea1, nbu), pa1, sqrt_approx(a1) * pa1);
-        acc_pair(A, min(eb0, nbu), pb0, sqrt_approx(b0) * pb0);
-        acc_pair(A, min(eb1, nbu), pb1, sqrt_approx(b1) * pb1);
-        if (__any_sync(FULL, max(max(ea0, ea1), max(eb0, eb1)) > nbu)) {
-            if (ea0 > nbu)
-                n_rck += resolve_pair_w(smem, S, A, a0, pa0, i, gA);
-            if (ea1 > nbu)
-                n_rck += resolve_pair_w(smem, S, A, a1, pa1, i, gA + 1);
-            if (eb0 > nbu)
-                n_rck += resolve_pair_w(smem, S, A, b0, pb0, i, gB);
-            if (eb1 > nbu)
-                n_rck += resolve_pair_w(smem, S, A, b1, pb1, i, gB + 1);
-        }
-    }
-}
-
-template <int I, bool EVALS>
-__global__ void __launch_bounds__(THREADS, 2) k_xi32w(const __grid_constant__ PairParams P)
-{
-    extern __shared__ __align__(128) unsigned char smem[];
-    const int nb = P.nbins, nr = nb + 1;
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
-    volatile int *s_item = reinterpret_cast<volatile int *>(smem + 8);
-    const float *tz = reinterpret_cast<const float *>(smem + TX_OFF + 2 * TSTRIDE);
-    float *thr = reinterpret_cast<float *>(smem + THR_OFF);
-    double *E2 = reinterpret_cast<double *>(smem + E2_OFF);
-    double *acc = reinterpret_cast<double *>(smem + XIW_ACC_OFF);  // [warp][bin][3]
-    unsigned char *cplane = smem + P.rows_off;                      // [warp][bin][lane] bytes
-    const int cbytes = align_up(WARPS * nr * 32, 128);
-    float *wplane = reinterpret_cast<float *>(smem + P.rows_off + cbytes);  // [warp][bin][lane]
-    float *rplane = wplane + WARPS * nr * 32;
-
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    for (int q = tid; q < P.lut_n; q += THREADS)
-        smem[LUT_OFF + q] = P.lut[q];
-    for (int q = tid; q < P.nthr; q += THREADS)
-        thr[q] = P.thr[q];
-    for (int q = tid; q <= nb; q += THREADS)
-        E2[q] = P.E2[q];
-    for (int q = tid; q < WARPS * nr * 3; q += THREADS)
-        acc[q] = 0.0;  // the count words' bit pattern 0 is also the u64 zero
-    for (int q = tid; q < WARPS * nr * 32; q += THREADS) {
-        cplane[q] = 0;
-        wplane[q] = 0.0f;
-        rplane[q] = 0.0f;
-    }
-    if (tid == 0) {
-        mbar_init(bar, 1);
-        fence_mbar_init();
-    }
-    __syncthreads();
-
-    AccW A;
-    A.cnt = cplane + warp * nr * 32 + lane;
-    A.wp = wplane + warp * nr * 32 + lane;
-    A.rp = rplane + warp * nr * 32 + lane;
-    A.acc = acc + warp * nr * 3;
-    A.want_r = P.want_r != 0;
-    const bool weighted = P.weighted != 0;
-    const int ii = lane % I, jj = lane / I;
-    Sweep32 S;
-    S.nb = nb;
-    S.u0 = P.u0;
-    S.lut_last = (uint32_t)(P.lut_n - 1);
-    S.shift = P.lut_shift;
-    S.nthr = P.nthr;
-    S.lin = P.lut_lin;
-    S.lscale = P.lut_scale;
-    S.pa = P.A.pos64;
-    S.pb = P.B.pos64;
-    unsigned phase = 0;
-    u64 n_eval = 0, n_rck = 0;
-    bool aborted = false;
-    const float qnan = __int_as_float(0x7fc00000);
-
-    const int n_work = (int)*P.work_count;
-    for (;;) {
-        if (tid == 0)
-            *s_item = (int)atomicAdd(P.item_counter, 1u);
-        __syncthreads();
-        const int item = *s_item;
-        __syncthreads();
-        if (item >= n_work)
-            break;
-        Item it;
-        decode_item(P, item, it);
-        const float dzw = __fadd_ru(__double2float_ru(it.dzmax), P.zslack);
-        const float Sxf = __double2float_rn(it.Sx), Syf = __double2float_rn(it.Sy);
-        S.Sx = it.Sx;
-        S.Sy = it.Sy;
-        const int nchunks = (it.a1 - it.a0 + I - 1) / I;
-
-        for (int t0 = it.b0; t0 < it.b1; t0 += TILE32) {
-            const int nt = min(TILE32, it.b1 - t0);
-            if (!stage_tiles32(smem, P.B, t0, nt, bar, phase, P.err, weighted)) {
-                aborted = true;
-                break;
-            }
-            S.t0 = t0;
-            const float zt_lo = tz[0];
-            float zt_hi = tz[nt - 1];
-            if (isnan(zt_hi))
-                zt_hi = INFINITY;
-            auto zkey = [&](int q) { return tz[q]; };
-            int lo_prev[3] = {0, 0, 0}, hi_prev[3] = {0, 0, 0};
-
-            for (int c = warp; c < nchunks; c += WARPS) {
-                const int ib = it.a0 + c * I;
-                const int nvi = min(I, it.a1 - ib);
-                const int i = ib + ii;
-                float xi = qnan, yi = qnan, zi = qnan, wi = 1.0f;
-                if (ii < nvi) {
-                    xi = P.A.xs[i];
-                    yi = P.A.ys[i];
-                    zi = P.A.zs[i];
-                    if (weighted)
-                        wi = P.A.ws[i];
-                }
-                const bool vi = !isnan(xi);
-                const float xh = __fsub_rn(xi, Sxf), yh = __fsub_rn(yi, Syf);
-                const u64 XH = pack2(xh, xh), YH = pack2(yh, yh), WH = pack2(wi, wi);
-                const float zlo = __shfl_sync(FULL, zi, 0);
-                float zhi = zi;
-#pragma unroll
-                for (int o = 1; o < I; o <<= 1) {
-                    const float t = __shfl_xor_sync(FULL, zhi, o);
-                    zhi = (isnan(zhi) || t > zhi) ? t : zhi;
-                }
-                if (isnan(zlo))
-                    continue;
-#pragma unroll
-                for (int kk = 0; kk < 3; ++kk) {
-                    const int k = kk - 1;
-                    if (k < it.kmin || k > it.kmax)
-                        continue;
-                    const float kz = (float)k * P.boxf[2];
-                    const float wlo = zlo - kz - dzw, whi = zhi - kz + dzw;
-                    if (whi < zt_lo || wlo > zt_hi)
-                        continue;
-                    int jlo = warp_bound_from(zkey, lo_prev[kk], nt, wlo, false, lane);
-                    const int jhi = warp_bound_from(zkey, max(hi_prev[kk], jlo), nt, whi, true, lane);
-                    lo_prev[kk] = jlo;
-                    hi_prev[kk] = jhi;
-                    const bool tri = it.self && k == 0;
-                    if (tri)
-                        jlo = max(jlo, ib + 1 - t0);
-                    if (jlo >= jhi)
-                        continue;
-                    const float zh = __fsub_rn(zi, kz);
-                    const u64 ZH = pack2(zh, zh);
-                    S.Sz = k == 0 ? 0.0 : (k > 0 ? P.g.box[2] : -P.g.box[2]);
-                    if (tri) {
-                        if (S.lin)
-                            sweep32w<I, true, EVALS, true>(smem, S, A, weighted, jlo, jhi, jj, XH, YH,
-                                                           ZH, WH, i, vi, n_eval, n_rck);
-                        else
-                            sweep32w<I, true, EVALS, false>(smem, S, A, weighted, jlo, jhi, jj, XH, YH,
-                                                            ZH, WH, i, vi, n_eval, n_rck);
-                    } else {
-                        if (S.lin)
-                            sweep32w<I, false, EVALS, true>(smem, S, A, weighted, jlo, jhi, jj, XH, YH,
-                                                            ZH, WH, i, vi, n_eval, n_rck);
-                        else
-                            sweep32w<I, false, EVALS, false>(smem, S, A, weighted, jlo, jhi, jj, XH,
-                                                             YH, ZH, WH, i, vi, n_eval, n_rck);
-                    }
-                }
-            }
-        }
-        if (aborted)
-            break;
-    }
-
-    __syncthreads();
-    for (int bn = tid; bn < nb; bn += THREADS) {
-        u64 cnt = 0;
-        double ws = 0.0, rs = 0.0;
-        for (int w = 0; w < WARPS; ++w) {
-            const double *aw = acc + (w * nr + bn) * 3;
-            cnt += *reinterpret_cast<const u64 *>(aw);
-            ws += aw[1];
-            rs += aw[2];
-            const int base = (w * nr + bn) * 32;
-            for (int l = 0; l < 32; ++l) {
-                cnt += cplane[base + l];
-                ws += (double)wplane[base + l];
-                rs += (double)rplane[base + l];
-            }
-        }
-        if (cnt) {
-            atomicAdd(&P.hist[bn], cnt);
-            atomicAdd(&P.wsum[bn], ws);
-            if (P.want_r)
-                atomicAdd(&P.rsum[bn], rs);
-        }
-    }
-    n_eval = warp_sum_u64(n_eval);
-    n_rck = warp_sum_u64(n_rck);
-    if (lane == 0) {
-        if (n_eval)
-            atomicAdd(&P.diag[1], n_eval);
-        if (n_rck)
-            atomicAdd(&P.diag[2], n_rck);
-    }
 }
 
 // ============================================================ binary64 kernel
@@ -1982,7 +1833,7 @@ __global__ void __launch_bounds__(THREADS, MINB) k_path(const __grid_constant__ 
         fence_mbar_init();
     }
     __syncthreads();
-    PathState st = {0ull, 0ull, 0ull, 0u, 0u};
+    PathState st = {0ull, 0ull, 0ull, 0u, 0u, 0u};
     const int n_work = (int)*P.work_count;
     for (;;) {
         if (threadIdx.x == 0)
@@ -2070,7 +1921,7 @@ __global__ void __launch_bounds__(THREADS, 2) k_batch(const __grid_constant__ Ba
     }
     __syncthreads();
     const unsigned total = s_off[B.njobs];
-    PathState st = {0ull, 0ull, 0ull, 0u, 0u};
+    PathState st = {0ull, 0ull, 0ull, 0u, 0u, 0u};
     int cur = -1;
     for (;;) {
         if (threadIdx.x == 0)
@@ -2168,6 +2019,8 @@ cudaError_t launch_persistent(K kern, const PairParams &P, PairLaunch &L, int sm
     if (occ < 1)
         return cudaErrorInvalidConfiguration;
     long long blocks = (long long)sms * occ;
+    if (L.max_blocks > 0 && blocks > L.max_blocks)
+        blocks = L.max_blocks;  // per-CTA scratch was sized for this many
     if (blocks > P.n_items)
         blocks = P.n_items > 0 ? P.n_items : 1;
     L.blocks = (int)blocks;
@@ -2252,9 +2105,16 @@ cudaError_t launch_pairs(const PairParams &P, PairLaunch &L, int sms, cudaStream
         return L.evals ? launch_persistent(k_path<Xi64Path<8, true, false>, 1>, P, L, sms, st)
                        : launch_persistent(k_path<Xi64Path<8, false, false>, 1>, P, L, sms, st);
     }
-    if (P.wacc)
-        return L.evals ? launch_persistent(k_xi32w<16, true>, P, L, sms, st)
-                       : launch_persistent(k_xi32w<16, false>, P, L, sms, st);
+    if (P.wacc) {  // pair weights and / or mean separation: integer sums in the same sweep
+        if (P.weighted && P.want_r)
+            return L.evals ? launch_persistent(k_path<Xi32Path<16, 1, true, false, true, true>, 2>, P, L, sms, st)
+                           : launch_persistent(k_path<Xi32Path<16, 1, false, false, true, true>, 2>, P, L, sms, st);
+        if (P.weighted)
+            return L.evals ? launch_persistent(k_path<Xi32Path<16, 1, true, false, true, false>, 2>, P, L, sms, st)
+                           : launch_persistent(k_path<Xi32Path<16, 1, false, false, true, false>, 2>, P, L, sms, st);
+        return L.evals ? launch_persistent(k_path<Xi32Path<16, 1, true, false, false, true>, 2>, P, L, sms, st)
+                       : launch_persistent(k_path<Xi32Path<16, 1, false, false, false, true>, 2>, P, L, sms, st);
+    }
     if (L.verify)
         return launch_persistent(k_path<Xi32Path<8, 1, true, true>, 3>, P, L, sms, st);
     if (L.pp == 4)

@@ -30,6 +30,8 @@ __host__ __device__ inline Smem64 smem64_layout(int tile_max, int nbins, int npi
     return L;
 }
 
+constexpr int SMEM_MAX = 232448;  // dynamic shared memory a CTA may opt in to (227 KB)
+
 struct PairLaunch {
     int f64;         // 1: binary64 path
     int chunk;       // primary lanes per warp chunk (8, 16 or 32)
@@ -39,6 +41,7 @@ struct PairLaunch {
     int blocks;      // persistent CTAs
     int smem;        // dynamic shared memory bytes
     int hist_words;  // shared histogram words
+    int max_blocks;  // upper bound on the persistent grid (0 = none)
 };
 
 // Fill the shared-memory plan of a launch: L.smem, L.hist_words and, for

@@ -5,7 +5,8 @@ order and, in float32 mode, by float32 arithmetic:
   - binary64 mode: per-pair terms are the oracle's exact binary64 products and
     square roots, so sums agree to 1e-12 relative;
   - float32 mode: weights are rounded to float32 (product error <= 3 u32) and
-    partial sums hold at most 63 terms (error <= 63 u32), so wsum agrees to
+    each term to a power-of-two fixed-point grid, then summed exactly in
+    integers (error <= 2^-22 max|w w| / |w w| per term), so wsum agrees to
     1e-5 relative; r comes from float32 coordinates, so ravg agrees to 1e-5
     relative when those coordinates are the caller's float32 inputs (periodic
     box) and otherwise within 1e-5 plus the coordinate-rounding bound
