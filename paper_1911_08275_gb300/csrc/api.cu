@@ -877,6 +877,7 @@ int run(Request &q)
         PL.evals = (c->flags & (CF_FLAG_COUNT_EVALS | CF_FLAG_VERIFY_BAND)) ? 1 : 0;
         PL.verify = (!f64 && (c->flags & CF_FLAG_VERIFY_BAND)) ? 1 : 0;
         PL.max_blocks = wscratch ? sms * 2 : 0;
+        PL.pipe = 1;
         cf::plan_pairs(P, PL);
         if (!f64 && PL.smem > cf::SMEM_MAX) {
             // float32 weighted rows for this many bins exceed shared memory: count
@@ -1608,6 +1609,7 @@ int noalloc_xi(int autocorr, const cf_catalog *d1, const cf_catalog *d2, const d
     PL.chunk = 16;
     PL.pp = 2;
     PL.evals = (P.flags & CF_FLAG_COUNT_EVALS) ? 1 : 0;
+    PL.pipe = 1;
     cf::plan_pairs(P, PL);
     if (P.n_items > 0 && (e = cf::launch_pairs(P, PL, sms, st)))
         return cuda_fail(e, "pair kernel launch");

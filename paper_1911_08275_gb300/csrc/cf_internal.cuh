@@ -43,6 +43,13 @@ constexpr int XI32_THR_OFF = XI32_TX_OFF + 3 * XI32_TSTRIDE;
 constexpr int XI32_E2_OFF = XI32_THR_OFF + 2 * (NB_MAX + 1) * 4;
 constexpr int XI32_HIST_OFF = XI32_E2_OFF + (NB_MAX + 1) * 8;
 
+// The pipelined float32 DD(r) kernel keeps one histogram copy shared by all
+// warps and places its second tile buffer after it.
+__host__ __device__ constexpr int pipe_slot1_off(int nbins)
+{
+    return (XI32_HIST_OFF + (nbins + 2) * 128 + 127) & ~127;
+}
+
 // The weighted float32 DD(rp, pi) kernel stages a weight tile after the squared
 // edges.
 constexpr int XIW_W_OFF = XI32_HIST_OFF;
@@ -159,6 +166,12 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, unsigned by
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
                  "r"(bytes)
                  : "memory");
+}
+
+// Plain arrive (no transaction bytes): completes a phase that carries no copy.
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
 // One bounded wait on phase `parity`; returns false if the limit was reached.

@@ -59,6 +59,11 @@ void plan_pairs(PairParams &P, PairLaunch &L)
             P.hist_off = XI32_HIST_OFF;
             L.hist_words = planes * WARPS * (nb + 2) * 32;
             L.smem = align_up(XI32_HIST_OFF + L.hist_words * 4 + (nb + 2) * 4, 128);
+        } else if (L.pipe) {
+            // one histogram copy shared by all warps, then the second tile buffer
+            L.hist_words = (nb + 2) * 32;
+            P.hist_off = XI32_HIST_OFF;
+            L.smem = pipe_slot1_off(nb) + 3 * XI32_TSTRIDE;
         } else {
             L.hist_words = WARPS * (nb + 2) * 32;  // + a row for flagged table cells
             P.hist_off = XI32_HIST_OFF;
@@ -222,6 +227,17 @@ __device__ void warp_flush(uint32_t *hw, int nb, unsigned long long *ghist, int 
     }
 }
 
+// The same for a copy that other warps add to concurrently: each count is read
+// and cleared in one atomic exchange, so no concurrent increment is lost.
+__device__ void warp_flush_shared(uint32_t *hw, int nb, unsigned long long *ghist, int lane)
+{
+    for (int b = 0; b < nb; ++b) {
+        const u64 v = warp_sum_u64(atomicExch(&hw[b * 32 + lane], 0u));
+        if (lane == 0 && v)
+            atomicAdd(&ghist[b], v);
+    }
+}
+
 // Candidate (column a, stencil offset) -> column pair, image, pruning
 // (Sec. 2.2) and z reach, in binary64.  Returns false if the pair has no work.
 __device__ __forceinline__ bool plan_item(const PairParams &P, int item, WorkItem &w)
@@ -312,9 +328,8 @@ struct PathState {
     unsigned wpend;             // weighted sums: pair slots per lane since the last row flush
 };
 
-__device__ __forceinline__ void decode_item(const PairParams &P, int item, Item &it)
+__device__ __forceinline__ void decode_record(const PairParams &P, const WorkItem &w, Item &it)
 {
-    const WorkItem w = P.work[item];
     it.a0 = w.a0;
     it.a1 = w.a1;
     it.b0 = w.b0;
@@ -326,6 +341,16 @@ __device__ __forceinline__ void decode_item(const PairParams &P, int item, Item 
     it.kmin = P.g.periodic ? (it.self ? 0 : -1) : 0;
     it.kmax = P.g.periodic ? 1 : 0;
 }
+
+__device__ __forceinline__ void decode_item(const PairParams &P, int item, Item &it)
+{
+    const WorkItem w = P.work[item];
+    decode_record(P, w, it);
+}
+
+// Byte offset in the shared block of the chunk counter that the warps of a CTA
+// claim chunks of the staged tile from ([0, 128) holds the barrier, the item).
+constexpr int CLAIM_OFF = 16;
 
 // Stage the float32 x, y, z tiles (three 1-D bulk copies, one mbarrier):
 // thread 0 issues the copies, every thread pads and waits (bounded).  The
@@ -339,6 +364,7 @@ __device__ __forceinline__ bool stage_tiles32(unsigned char *smem, const Gridded
     __syncthreads();  // previous tile fully consumed
     const unsigned bytes = (unsigned)count * 4u;
     if (threadIdx.x == 0) {
+        *reinterpret_cast<volatile int *>(smem + CLAIM_OFF) = 0;  // chunk counter of the new tile
         fence_proxy_async_smem();
         mbar_arrive_expect_tx(bar, (with_w ? 4u : 3u) * bytes);
         bulk_g2s(smem + XI32_TX_OFF, B.xs + t0, bytes, bar);
@@ -405,6 +431,7 @@ constexpr int HIST_OFF = XI32_HIST_OFF;
 
 // Per-window constants of the sweep.
 struct Sweep32 {
+    const unsigned char *tb;  // staged tile: x, y, z arrays TSTRIDE bytes apart
     int t0;                   // global index of tile element 0
     int nb;                   // bins; row nb is the dummy row
     uint32_t u0, lut_last;
@@ -565,7 +592,7 @@ __device__ __forceinline__ int resolve_local(const unsigned char *smem, const Sw
                                           float xh, float yh, float zh, int i, int jl,
                                           const WAcc &A, float wi)
 {
-    const float *tx = reinterpret_cast<const float *>(smem + TX_OFF);
+    const float *tx = reinterpret_cast<const float *>(S.tb);
     const float dx = __fsub_rn(tx[jl], xh);
     const float dy = __fsub_rn(tx[jl + TSTRIDE / 4], yh);
     const float dz = __fsub_rn(tx[jl + TSTRIDE / 2], zh);
@@ -615,7 +642,7 @@ __device__ __forceinline__ void sweep32(unsigned char *smem, const Sweep32 &S, u
     const u64 LS = pack2(S.lscale, S.lscale), LM = pack2(LIN_MAGIC, LIN_MAGIC);
     for (int b0 = 0; b0 < nit; b0 += 8) {
         const int jAb = jstart + 2 * jj + b0 * 2 * JS;
-        const unsigned char *pb = smem + TX_OFF + jAb * 4;
+        const unsigned char *pb = S.tb + jAb * 4;
         const int tend = min(8, nit - b0);
         uint32_t fm[PP];
 #pragma unroll
@@ -777,8 +804,13 @@ __device__ __forceinline__ float wmax_pair(const PairParams &P)
     return __uint_as_float(*P.A.wmax) * __uint_as_float(*P.B.wmax);
 }
 
-template <int I, int PP, bool EVALS, bool VERIFY, bool W = false, bool RV = false>
+// HC histogram copies, each shared by WARPS / HC warps (red.shared is atomic);
+// the weighted rows are per warp.
+template <int I, int PP, bool EVALS, bool VERIFY, bool W = false, bool RV = false, int HC = WARPS>
 struct Xi32Path {
+    static_assert(HC == WARPS || !(W || RV), "weighted rows are per warp");
+    static_assert(WARPS % HC == 0, "warps share copies evenly");
+
     static __device__ __forceinline__ void init(const PairParams &P, unsigned char *smem)
     {
         // I * PP primaries per chunk (lane ii = lane % I holds primaries ii, ii + I,
@@ -796,7 +828,7 @@ struct Xi32Path {
         for (int q = tid; q <= nb; q += THREADS)
             E2[q] = P.E2[q];
         constexpr int planes = 1 + (W ? 1 : 0) + (RV ? 1 : 0);
-        for (int q = tid; q < planes * WARPS * (nb + 2) * 32; q += THREADS)
+        for (int q = tid; q < planes * HC * (nb + 2) * 32; q += THREADS)
             hist[q] = 0u;
         if (W || RV) {
             float *sr = reinterpret_cast<float *>(hist + planes * WARPS * (nb + 2) * 32);
@@ -809,25 +841,41 @@ struct Xi32Path {
         }
     }
 
+    // One work item through the CTA's single tile buffer: stage each tile of
+    // column b, then sweep it.
     static __device__ __forceinline__ bool item(const PairParams &P, const Item &it,
+                                                unsigned char *smem, PathState &st)
+    {
+        uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
+        for (int t0 = it.b0; t0 < it.b1; t0 += TILE32) {
+            const int nt = min(TILE32, it.b1 - t0);
+            if (!stage_tiles32(smem, P.B, t0, nt, bar, st.phase, P.err))
+                return false;
+            tile(P, it, t0, nt, smem + TX_OFF, reinterpret_cast<int *>(smem + CLAIM_OFF), smem, st);
+        }
+        return true;
+    }
+
+    // Sweep the staged tile [t0, t0 + nt) of column b (at tb) against every
+    // chunk of column a; the warps claim chunks from *claim in increasing order.
+    static __device__ __forceinline__ void tile(const PairParams &P, const Item &it, int t0, int nt,
+                                                const unsigned char *tb, int *claim,
                                                 unsigned char *smem, PathState &st)
     {
         // I * PP primaries per chunk (lane ii = lane % I holds primaries ii, ii + I,
         // ...); jj = lane / I picks the pair of secondaries.
         constexpr int CH = I * PP;
         const int nb = P.nbins;
-        uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
-        const float *tz = reinterpret_cast<const float *>(smem + TX_OFF + 2 * TSTRIDE);
+        const float *tz = reinterpret_cast<const float *>(tb + 2 * TSTRIDE);
         uint32_t *hist = reinterpret_cast<uint32_t *>(smem + HIST_OFF);
 
         const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-        unsigned &phase = st.phase;
         u64 &n_eval = st.n_eval;
         u64 &n_rck = st.n_rck;
         u64 &n_viol = st.n_viol;
         unsigned &pending = st.pending;
 
-        uint32_t *hw = hist + warp * (nb + 2) * 32;  // rows: bins, not counted, flagged
+        uint32_t *hw = hist + (warp % HC) * (nb + 2) * 32;  // rows: bins, not counted, flagged
         const uint32_t hl = smem_u32(hw + lane);  // this lane's histogram column (shared address)
         const int ii = lane % I, jj = lane / I;
         WAcc A;
@@ -861,12 +909,8 @@ struct Xi32Path {
         S.Sx = it.Sx;
         S.Sy = it.Sy;
         const int nchunks = (it.a1 - it.a0 + CH - 1) / CH;
-
-        for (int t0 = it.b0; t0 < it.b1; t0 += TILE32) {
-            const int nt = min(TILE32, it.b1 - t0);
-            if (!stage_tiles32(smem, P.B, t0, nt, bar, phase, P.err)) {
-                return false;
-            }
+        S.tb = tb;
+        {
             S.t0 = t0;
             const float zt_lo = tz[0];
             float zt_hi = tz[nt - 1];
@@ -875,7 +919,13 @@ struct Xi32Path {
             auto zkey = [&](int q) { return tz[q]; };
             int lo_prev[3] = {0, 0, 0}, hi_prev[3] = {0, 0, 0};
 
-            for (int c = warp; c < nchunks; c += WARPS) {
+            auto next_chunk = [&]() {
+                int v = 0;
+                if (lane == 0)
+                    v = atomicAdd(claim, 1);
+                return __shfl_sync(FULL, v, 0);
+            };
+            for (int c = next_chunk(); c < nchunks; c = next_chunk()) {
                 const int ib = it.a0 + c * CH;
                 u64 XH[PP], YH[PP], ZH[PP];
                 int iv[PP];
@@ -959,14 +1009,17 @@ struct Xi32Path {
                                 A, wi, st.wpend);
                     }
                 }
-                if (!(W || RV) && pending > (1u << 30)) {  // keep per-lane u32 counts far from overflow
+                // keep every shared u32 count far from overflow (WARPS / HC warps add to a copy)
+                if (!(W || RV) && pending > (1u << 30) / (WARPS / HC)) {
                     __syncwarp();
-                    warp_flush(hw, nb, P.hist, lane);
+                    if (HC == WARPS)
+                        warp_flush(hw, nb, P.hist, lane);
+                    else
+                        warp_flush_shared(hw, nb, P.hist, lane);
                     pending = 0;
                 }
             }
         }
-        return true;
     }
 
     static __device__ __forceinline__ void fini(const PairParams &P, unsigned char *smem, PathState &st)
@@ -1015,7 +1068,7 @@ struct Xi32Path {
             __syncthreads();
             for (int bn = tid; bn < nb; bn += THREADS) {
                 u64 sum = 0;
-                for (int w = 0; w < WARPS; ++w)
+                for (int w = 0; w < HC; ++w)
                     for (int l = 0; l < 32; ++l)
                         sum += hist[(w * (nb + 2) + bn) * 32 + l];
                 if (sum)
@@ -1852,6 +1905,144 @@ __global__ void __launch_bounds__(THREADS, MINB) k_path(const __grid_constant__ 
     Path::fini(P, smem, st);
 }
 
+// ============================================ pipelined float32 DD(r) kernel
+// Two tile buffers: while the warps sweep the tile in one, the next tile is
+// already staged in the other, so no CTA-wide barrier separates work items.
+// A unit is one tile of one work item.  The warp that finishes a unit last
+// (counted in done[s]) refills its buffer with the unit after next: it claims
+// the next item when the cursor's item has no tile left, pads, and issues the
+// bulk copies; the other warps move straight on to the other buffer.  Within
+// a unit the warps claim chunks from claim[s].  Every wait is bounded.
+struct PipeHdr {
+    uint64_t full[2];    // tile-ready barrier of each buffer
+    WorkItem w[2];       // work item of each buffer's unit
+    int item[2];         // its index (-1: no more work)
+    int t0[2], nt[2];    // its tile of column b
+    int claim[2];        // next chunk of the unit
+    int done[2];         // warps finished with the unit
+    int cur, next_t0;    // cursor: item of the last issued unit, start of its next tile
+};
+static_assert(sizeof(PipeHdr) <= XI32_LUT_OFF, "pipeline header fits before the table");
+
+// Fill buffer s with the next unit (called by one whole warp; lane 0 claims,
+// every lane pads, lane 0 issues the copies and arrives on the barrier).
+__device__ __forceinline__ void pipe_issue(const PairParams &P, PipeHdr *H, int s, int n_work,
+                                           unsigned char *buf, int lane)
+{
+    int item = -1, t0 = 0, nt = 0;
+    if (lane == 0) {
+        const int cur = H->cur;
+        if (cur >= 0 && H->next_t0 < H->w[s ^ 1].b1 && H->item[s ^ 1] == cur) {
+            item = cur;  // the cursor's item has tiles left (its record is in the other buffer)
+            t0 = H->next_t0;
+            H->w[s] = H->w[s ^ 1];
+        } else {
+            for (;;) {  // next item with points on both sides (bounded by the work count)
+                const int c = (int)atomicAdd(P.item_counter, 1u);
+                if (c >= n_work)
+                    break;
+                const WorkItem w = P.work[c];
+                if (w.a1 > w.a0 && w.b1 > w.b0) {
+                    item = c;
+                    t0 = w.b0;
+                    H->w[s] = w;
+                    break;
+                }
+            }
+            H->cur = item;
+        }
+        if (item >= 0) {
+            nt = min(TILE32, H->w[s].b1 - t0);
+            H->next_t0 = t0 + nt;
+        }
+    }
+    item = __shfl_sync(FULL, item, 0);
+    nt = __shfl_sync(FULL, nt, 0);
+    t0 = __shfl_sync(FULL, t0, 0);
+    if (item >= 0) {
+        float *t = reinterpret_cast<float *>(buf);
+        for (int q = lane; q < 3 * 64; q += 32)  // sentinels after the copied range: never counted
+            t[(q >> 6) * (XI32_TSTRIDE / 4) + nt + (q & 63)] = __int_as_float(0x7fc00000);
+    }
+    __syncwarp();
+    if (lane == 0) {
+        H->item[s] = item;
+        H->t0[s] = t0;
+        H->nt[s] = nt;
+        if (item >= 0) {
+            const unsigned bytes = (unsigned)nt * 4u;
+            fence_proxy_async_smem();
+            mbar_arrive_expect_tx(&H->full[s], 3u * bytes);
+            bulk_g2s(buf, P.B.xs + t0, bytes, &H->full[s]);
+            bulk_g2s(buf + XI32_TSTRIDE, P.B.ys + t0, bytes, &H->full[s]);
+            bulk_g2s(buf + 2 * XI32_TSTRIDE, P.B.zs + t0, bytes, &H->full[s]);
+        } else {
+            mbar_arrive(&H->full[s]);
+        }
+    }
+}
+
+template <class Path, int MINB>
+__global__ void __launch_bounds__(THREADS, MINB) k_pipe(const __grid_constant__ PairParams P)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    PipeHdr *H = reinterpret_cast<PipeHdr *>(smem);
+    unsigned char *buf0 = smem + XI32_TX_OFF, *buf1 = smem + pipe_slot1_off(P.nbins);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    Path::init(P, smem);
+    if (threadIdx.x == 0) {
+        mbar_init(&H->full[0], 1);
+        mbar_init(&H->full[1], 1);
+        fence_mbar_init();
+        H->item[0] = H->item[1] = -1;
+        H->claim[0] = H->claim[1] = 0;
+        H->done[0] = H->done[1] = 0;
+        H->cur = -1;
+        H->next_t0 = 0;
+    }
+    __syncthreads();
+    const int n_work = (int)*P.work_count;
+    if (warp == 0) {
+        pipe_issue(P, H, 0, n_work, buf0, lane);
+        pipe_issue(P, H, 1, n_work, buf1, lane);
+    }
+    PathState st = {0ull, 0ull, 0ull, 0u, 0u, 0u};
+    unsigned par = 0u;  // bit s: parity of buffer s's next phase
+    for (int u = 0;; ++u) {
+        const int s = u & 1;
+        unsigned char *buf = s ? buf1 : buf0;
+        if (!mbar_wait(&H->full[s], (par >> s) & 1u, WAIT_LIMIT)) {
+            if (lane == 0)
+                atomicOr(P.err, ERR_TIMEOUT);
+            break;
+        }
+        par ^= 1u << s;
+        const int item = reinterpret_cast<volatile int *>(H->item)[s];
+        if (item < 0)
+            break;
+        Item it;
+        decode_record(P, H->w[s], it);
+        Path::tile(P, it, H->t0[s], H->nt[s], buf, &H->claim[s], smem, st);
+        __syncwarp();
+        int last = 0;
+        if (lane == 0) {
+            __threadfence_block();  // this warp's reads of the buffer come first
+            last = atomicAdd(&H->done[s], 1) == WARPS - 1;
+        }
+        if (__shfl_sync(FULL, last, 0)) {
+            if (lane == 0) {
+                __threadfence_block();
+                H->done[s] = 0;
+                H->claim[s] = 0;
+            }
+            __syncwarp();
+            pipe_issue(P, H, s, n_work, buf, lane);
+        }
+    }
+    __syncthreads();
+    Path::fini(P, smem, st);
+}
+
 // ============================================================ batched kernel
 // Many independent jobs (catalogues, bins, modes) in one persistent launch: the
 // CTAs pull items from one global counter over the concatenation of the jobs'
@@ -2115,28 +2306,36 @@ cudaError_t launch_pairs(const PairParams &P, PairLaunch &L, int sms, cudaStream
         return L.evals ? launch_persistent(k_path<Xi32Path<16, 1, true, false, false, true>, 2>, P, L, sms, st)
                        : launch_persistent(k_path<Xi32Path<16, 1, false, false, false, true>, 2>, P, L, sms, st);
     }
-    if (L.verify)
-        return launch_persistent(k_path<Xi32Path<8, 1, true, true>, 3>, P, L, sms, st);
-    if (L.pp == 4)
-        return L.evals ? launch_persistent(k_path<Xi32Path<8, 4, true, false>, 2>, P, L, sms, st)
-                       : launch_persistent(k_path<Xi32Path<8, 4, false, false>, 2>, P, L, sms, st);
-    if (L.pp == 2) {
-        if (L.chunk == 8)
-            return L.evals ? launch_persistent(k_path<Xi32Path<8, 2, true, false>, 3>, P, L, sms, st)
-                           : launch_persistent(k_path<Xi32Path<8, 2, false, false>, 3>, P, L, sms, st);
+    if (!L.pipe) {  // single tile buffer, one histogram copy per warp
+        if (L.verify)
+            return launch_persistent(k_path<Xi32Path<8, 1, true, true>, 3>, P, L, sms, st);
         return L.evals ? launch_persistent(k_path<Xi32Path<16, 2, true, false>, 3>, P, L, sms, st)
                        : launch_persistent(k_path<Xi32Path<16, 2, false, false>, 3>, P, L, sms, st);
     }
+    // two tile buffers, one shared histogram copy
+    constexpr int H1 = 1;
+    if (L.verify)
+        return launch_persistent(k_pipe<Xi32Path<8, 1, true, true, false, false, H1>, 3>, P, L, sms, st);
+    if (L.pp == 4)
+        return L.evals ? launch_persistent(k_pipe<Xi32Path<8, 4, true, false, false, false, H1>, 2>, P, L, sms, st)
+                       : launch_persistent(k_pipe<Xi32Path<8, 4, false, false, false, false, H1>, 2>, P, L, sms, st);
+    if (L.pp == 2) {
+        if (L.chunk == 8)
+            return L.evals ? launch_persistent(k_pipe<Xi32Path<8, 2, true, false, false, false, H1>, 3>, P, L, sms, st)
+                           : launch_persistent(k_pipe<Xi32Path<8, 2, false, false, false, false, H1>, 3>, P, L, sms, st);
+        return L.evals ? launch_persistent(k_pipe<Xi32Path<16, 2, true, false, false, false, H1>, 3>, P, L, sms, st)
+                       : launch_persistent(k_pipe<Xi32Path<16, 2, false, false, false, false, H1>, 3>, P, L, sms, st);
+    }
     switch (L.chunk) {
     case 16:
-        return L.evals ? launch_persistent(k_path<Xi32Path<16, 1, true, false>, 3>, P, L, sms, st)
-                       : launch_persistent(k_path<Xi32Path<16, 1, false, false>, 3>, P, L, sms, st);
+        return L.evals ? launch_persistent(k_pipe<Xi32Path<16, 1, true, false, false, false, H1>, 3>, P, L, sms, st)
+                       : launch_persistent(k_pipe<Xi32Path<16, 1, false, false, false, false, H1>, 3>, P, L, sms, st);
     case 32:
-        return L.evals ? launch_persistent(k_path<Xi32Path<32, 1, true, false>, 3>, P, L, sms, st)
-                       : launch_persistent(k_path<Xi32Path<32, 1, false, false>, 3>, P, L, sms, st);
+        return L.evals ? launch_persistent(k_pipe<Xi32Path<32, 1, true, false, false, false, H1>, 3>, P, L, sms, st)
+                       : launch_persistent(k_pipe<Xi32Path<32, 1, false, false, false, false, H1>, 3>, P, L, sms, st);
     default:
-        return L.evals ? launch_persistent(k_path<Xi32Path<8, 1, true, false>, 3>, P, L, sms, st)
-                       : launch_persistent(k_path<Xi32Path<8, 1, false, false>, 3>, P, L, sms, st);
+        return L.evals ? launch_persistent(k_pipe<Xi32Path<8, 1, true, false, false, false, H1>, 3>, P, L, sms, st)
+                       : launch_persistent(k_pipe<Xi32Path<8, 1, false, false, false, false, H1>, 3>, P, L, sms, st);
     }
 }
 

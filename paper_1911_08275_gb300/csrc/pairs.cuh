@@ -42,6 +42,7 @@ struct PairLaunch {
     int smem;        // dynamic shared memory bytes
     int hist_words;  // shared histogram words
     int max_blocks;  // upper bound on the persistent grid (0 = none)
+    int pipe;        // float32 DD(r) without sums: two tile buffers (no CTA barrier per item)
 };
 
 // Fill the shared-memory plan of a launch: L.smem, L.hist_words and, for
