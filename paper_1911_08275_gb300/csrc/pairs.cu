@@ -725,7 +725,9 @@ __device__ __forceinline__ void sweep32(unsigned char *smem, const Sweep32 &S, u
                 }
                 const uint32_t w = __byte_perm(__byte_perm(e[0], e[1], 0x0040),
                                                __byte_perm(e[2], e[3], 0x0040), 0x5410);
-                fm[q] |= ((w + cflag) & 0x80808080u) >> (7 - t);  // bit 8 r + t
+                // shift the mask one step down and add this step's bits at 8 r + 7: after
+                // tend steps, step t sits at bit 8 r + 8 - tend + t
+                fm[q] = (fm[q] >> 1) | ((w + cflag) & 0x80808080u);
             }
             if (VERIFY) {
                 const float *T = reinterpret_cast<const float *>(smem + THR_OFF);
@@ -755,7 +757,7 @@ __device__ __forceinline__ void sweep32(unsigned char *smem, const Sweep32 &S, u
                 while (m) {
                     const int bit = __ffs(m) - 1;
                     m &= m - 1u;
-                    const int t = bit & 7, r = bit >> 3;
+                    const int t = (bit & 7) - (8 - tend), r = bit >> 3;
                     const int jl = jAb + t * 2 * JS + ((r & 2) ? JS : 0) + (r & 1);
                     n_rck += resolve_local<W, RV>(smem, S, hl, xh, yh, zh, iv[q], jl, A, wi[q]);
                 }
