@@ -397,6 +397,7 @@ __device__ __forceinline__ bool stage_tile(T *tile, const T *src, int count, int
 {
     __syncthreads();  // previous tile fully consumed
     if (threadIdx.x == 0) {
+        *reinterpret_cast<volatile int *>(reinterpret_cast<unsigned char *>(bar) + CLAIM_OFF) = 0;
         fence_proxy_async_smem();
         mbar_arrive_expect_tx(bar, (unsigned)(count * sizeof(T)));
         bulk_g2s(tile, src, (unsigned)(count * sizeof(T)), bar);
@@ -1151,7 +1152,13 @@ struct Xi64Path {
             }
             const double zt_lo = tile[0].z, zt_hi = tile[nt - 1].z;
             auto zkey = [&](int p) { return tile[p].z; };
-            for (int c = warp; c < nchunks; c += WARPS) {
+            auto next_chunk = [&]() {  // chunks in increasing order, claimed by the warps
+                int v = 0;
+                if (lane == 0)
+                    v = atomicAdd(reinterpret_cast<int *>(smem + CLAIM_OFF), 1);
+                return __shfl_sync(FULL, v, 0);
+            };
+            for (int c = next_chunk(); c < nchunks; c = next_chunk()) {
                 const int ib = it.a0 + c * I;
                 const int nvi = min(I, it.a1 - ib);
                 const int i = ib + ii;
@@ -1629,7 +1636,13 @@ struct Rppi32Path {
             auto zkey = [&](int q) { return tz[q]; };
             int lo_prev[3] = {0, 0, 0}, hi_prev[3] = {0, 0, 0};
 
-            for (int c = warp; c < nchunks; c += WARPS) {
+            auto next_chunk = [&]() {  // chunks in increasing order, claimed by the warps
+                int v = 0;
+                if (lane == 0)
+                    v = atomicAdd(reinterpret_cast<int *>(smem + CLAIM_OFF), 1);
+                return __shfl_sync(FULL, v, 0);
+            };
+            for (int c = next_chunk(); c < nchunks; c = next_chunk()) {
                 const int ib = it.a0 + c * I;
                 const int nvi = min(I, it.a1 - ib);
                 const int i = ib + ii;
@@ -1790,7 +1803,13 @@ struct Rppi64Path {
                 zt_hi = INFINITY;
             const double zt_lo = tile[0].z;
             auto zkey = [&](int p) { return tile[p].z; };
-            for (int c = warp; c < nchunks; c += WARPS) {
+            auto next_chunk = [&]() {  // chunks in increasing order, claimed by the warps
+                int v = 0;
+                if (lane == 0)
+                    v = atomicAdd(reinterpret_cast<int *>(smem + CLAIM_OFF), 1);
+                return __shfl_sync(FULL, v, 0);
+            };
+            for (int c = next_chunk(); c < nchunks; c = next_chunk()) {
                 const int ib = it.a0 + c * I;
                 const int nvi = min(I, it.a1 - ib);
                 const int i = ib + ii;
