@@ -247,80 +247,142 @@ __global__ void k_scatter(const T *__restrict__ z, long long n, const uint32_t *
     }
 }
 
-// One warp per cell: rank the cell's real entries by (z, original index) and
-// write the sorted float32 / binary64 copies.  Cells of up to 32 entries are
-// ranked in registers with shuffles; larger cells compare against all of the
-// cell's entries in L1-resident global memory (quadratic in the occupancy;
-// z-cells are sized for ~16 points on average).
+// Write one ranked entry: binary64 copy, float32 frame coordinates, weight,
+// original index.
 template <class T>
-__global__ void k_sort_cells(const T *__restrict__ x, const T *__restrict__ y,
-                             const double *__restrict__ w, long long ncells, Geom g,
-                             const uint32_t *__restrict__ count, const uint32_t *__restrict__ start,
-                             const int *__restrict__ tmp_idx,
-                             const unsigned long long *__restrict__ tmp_key,
-                             float *__restrict__ xs, float *__restrict__ ys,
-                             float *__restrict__ zs, float *__restrict__ ws,
-                             unsigned *__restrict__ wmax, double4_32a *__restrict__ pos64,
-                             int *__restrict__ perm)
+__device__ __forceinline__ void put_entry(const T *__restrict__ x, const T *__restrict__ y,
+                                          const double *__restrict__ w, const Geom &g, uint32_t d,
+                                          int iq, unsigned long long kq, float *__restrict__ xs,
+                                          float *__restrict__ ys, float *__restrict__ zs,
+                                          float *__restrict__ ws, double4_32a *__restrict__ pos64,
+                                          int *__restrict__ perm, unsigned &wm)
 {
-    const int lane = threadIdx.x & 31;
+    const double X = (double)x[iq], Y = (double)y[iq], Z = key_value(kq);
+    const double W = w ? w[iq] : 0.0;
+    pos64[d] = make_double4_32a(X, Y, Z, W);
+    float fx, fy, fz;
+    coord(X, 0, g, fx);
+    coord(Y, 1, g, fy);
+    coord(Z, 2, g, fz);
+    xs[d] = fx;
+    ys[d] = fy;
+    zs[d] = fz;
+    if (ws) {
+        ws[d] = (float)W;
+        wm = max(wm, __float_as_uint(fabsf((float)W)));
+    }
+    perm[d] = iq;
+}
+
+constexpr int SORT_THREADS = 256;
+constexpr int SORT_BUF = 256;  // entries of a cell ranked from shared memory
+
+// Rank the cells' real entries by (z, original index) and write the sorted
+// float32 / binary64 copies.  Each warp takes two cells at a time: cells of up
+// to 16 entries are ranked by a half warp each with shuffles; otherwise the
+// whole warp ranks the two cells one after the other: up to 32 entries in
+// registers, up to SORT_BUF from a copy in shared memory (every lane reads the
+// same entry: a broadcast), beyond that against the cell in global memory.
+template <class T>
+__global__ void __launch_bounds__(SORT_THREADS)
+    k_sort_cells(const T *__restrict__ x, const T *__restrict__ y, const double *__restrict__ w,
+                 long long ncells, Geom g, const uint32_t *__restrict__ count,
+                 const uint32_t *__restrict__ start, const int *__restrict__ tmp_idx,
+                 const unsigned long long *__restrict__ tmp_key, float *__restrict__ xs,
+                 float *__restrict__ ys, float *__restrict__ zs, float *__restrict__ ws,
+                 unsigned *__restrict__ wmax, double4_32a *__restrict__ pos64,
+                 int *__restrict__ perm)
+{
+    __shared__ unsigned long long s_key[SORT_THREADS / 32][SORT_BUF];
+    __shared__ int s_idx[SORT_THREADS / 32][SORT_BUF];
+    const int lane = threadIdx.x & 31, half = lane >> 4, hl = lane & 15, wid = threadIdx.x >> 5;
+    unsigned long long *bk = s_key[wid];
+    int *bi = s_idx[wid];
     unsigned wm = 0;  // bit pattern of the largest |w| (float) this thread stored
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-    for (long long c = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; c < ncells;
-         c += nwarps) {
-        const uint32_t cnt = count[c];
-        if (cnt == 0)
-            continue;
-        const uint32_t s = start[c];
-        for (uint32_t e0 = 0; e0 < cnt; e0 += 32) {
-            const uint32_t e = e0 + lane;
-            const bool mine = e < cnt;
-            const unsigned long long kq = mine ? tmp_key[s + e] : ~0ull;
-            const int iq = mine ? tmp_idx[s + e] : 0x7fffffff;
+    for (long long c0 = (((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 2; c0 < ncells;
+         c0 += 2 * nwarps) {
+        const long long cm = c0 + half;  // this half warp's cell
+        const uint32_t cnt = cm < ncells ? count[cm] : 0u;
+        const uint32_t s = cm < ncells ? start[cm] : 0u;
+        const uint32_t cnt0 = __shfl_sync(FULL, cnt, 0), cnt1 = __shfl_sync(FULL, cnt, 16);
+        if (max(cnt0, cnt1) <= 16u) {
+            const bool mine = (uint32_t)hl < cnt;
+            const unsigned long long kq = mine ? tmp_key[s + hl] : ~0ull;
+            const int iq = mine ? tmp_idx[s + hl] : 0x7fffffff;
             uint32_t rank = 0;
-            if (cnt <= 32) {
-                for (uint32_t m = 0; m < cnt; ++m) {
+            const uint32_t cmax = max(cnt0, cnt1);
+            for (uint32_t m = 0; m < cmax; ++m) {
+                const unsigned long long km = __shfl_sync(FULL, kq, (int)m, 16);
+                const int im = __shfl_sync(FULL, iq, (int)m, 16);
+                rank += (km < kq) || (km == kq && im < iq);  // absent entries rank last
+            }
+            if (mine)
+                put_entry(x, y, w, g, s + rank, iq, kq, xs, ys, zs, ws, pos64, perm, wm);
+            continue;
+        }
+        for (int h = 0; h < 2; ++h) {  // whole warp, one cell after the other
+            const uint32_t cn = h ? cnt1 : cnt0;
+            const uint32_t sc = __shfl_sync(FULL, s, h * 16);
+            if (cn == 0)
+                continue;
+            if (cn <= 32) {
+                const bool mine = (uint32_t)lane < cn;
+                const unsigned long long kq = mine ? tmp_key[sc + lane] : ~0ull;
+                const int iq = mine ? tmp_idx[sc + lane] : 0x7fffffff;
+                uint32_t rank = 0;
+                for (uint32_t m = 0; m < cn; ++m) {
                     const unsigned long long km = __shfl_sync(FULL, kq, (int)m);
                     const int im = __shfl_sync(FULL, iq, (int)m);
                     rank += (km < kq) || (km == kq && im < iq);
                 }
-            } else {
-                for (uint32_t m = 0; m < cnt; ++m) {
-                    const unsigned long long km = tmp_key[s + m];
-                    const int im = tmp_idx[s + m];
-                    rank += (km < kq) || (km == kq && im < iq);
-                }
+                if (mine)
+                    put_entry(x, y, w, g, sc + rank, iq, kq, xs, ys, zs, ws, pos64, perm, wm);
+                continue;
             }
-            if (mine) {
-                const uint32_t d = s + rank;
-                const double X = (double)x[iq], Y = (double)y[iq], Z = key_value(kq);
-                const double W = w ? w[iq] : 0.0;
-                pos64[d] = make_double4_32a(X, Y, Z, W);
-                float fx, fy, fz;
-                coord(X, 0, g, fx);
-                coord(Y, 1, g, fy);
-                coord(Z, 2, g, fz);
-                xs[d] = fx;
-                ys[d] = fy;
-                zs[d] = fz;
-                if (ws) {
-                    ws[d] = (float)W;
-                    wm = max(wm, __float_as_uint(fabsf((float)W)));
+            const bool buffered = cn <= (uint32_t)SORT_BUF;
+            if (buffered) {
+                __syncwarp();
+                for (uint32_t e = lane; e < cn; e += 32) {
+                    bk[e] = tmp_key[sc + e];
+                    bi[e] = tmp_idx[sc + e];
                 }
-                perm[d] = iq;
+                __syncwarp();
+            }
+            for (uint32_t e0 = 0; e0 < cn; e0 += 32) {
+                const uint32_t e = e0 + lane;
+                const bool mine = e < cn;
+                const unsigned long long kq = mine ? (buffered ? bk[e] : tmp_key[sc + e]) : ~0ull;
+                const int iq = mine ? (buffered ? bi[e] : tmp_idx[sc + e]) : 0x7fffffff;
+                uint32_t rank = 0;
+                if (buffered) {
+                    for (uint32_t m = 0; m < cn; ++m) {
+                        const unsigned long long km = bk[m];
+                        const int im = bi[m];
+                        rank += (km < kq) || (km == kq && im < iq);
+                    }
+                } else {
+                    for (uint32_t m = 0; m < cn; ++m) {
+                        const unsigned long long km = tmp_key[sc + m];
+                        const int im = tmp_idx[sc + m];
+                        rank += (km < kq) || (km == kq && im < iq);
+                    }
+                }
+                if (mine)
+                    put_entry(x, y, w, g, sc + rank, iq, kq, xs, ys, zs, ws, pos64, perm, wm);
             }
         }
     }
     if (wmax) {  // one atomic per block
-        __shared__ unsigned red[8];
+        __shared__ unsigned red[SORT_THREADS / 32];
         wm = __reduce_max_sync(FULL, wm);
         if (lane == 0)
-            red[threadIdx.x >> 5] = wm;
+            red[wid] = wm;
         __syncthreads();
         if (threadIdx.x == 0) {
             unsigned m = 0;
-            for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
-                m = max(m, red[w]);
+            for (int q = 0; q < SORT_THREADS / 32; ++q)
+                m = max(m, red[q]);
             atomicMax(wmax, m);
         }
     }
@@ -478,8 +540,8 @@ cudaError_t build_grid_t(const void *x, const void *y, const void *z, const doub
     if (n > 0) {
         k_scatter<T><<<grid_blocks(n, TB, sms), TB, 0, st>>>((const T *)z, n, t.cell_of, t.slot,
                                                              out.cell_start, t.tmp_idx, t.tmp_key);
-        const long long cwarps = std::min<long long>(nc, (long long)sms * 64);
-        k_sort_cells<T><<<(int)((cwarps * 32 + 255) / 256), 256, 0, st>>>(
+        const long long cwarps = std::min<long long>((nc + 1) / 2, (long long)sms * 64);
+        k_sort_cells<T><<<(int)((cwarps * 32 + SORT_THREADS - 1) / SORT_THREADS), SORT_THREADS, 0, st>>>(
             (const T *)x, (const T *)y, w, nc, g, t.counts, out.cell_start, t.tmp_idx, t.tmp_key,
             out.xs, out.ys, out.zs, out.ws, out.ws ? out.wmax : nullptr, out.pos64, out.perm);
     }
