@@ -1742,6 +1742,318 @@ struct Rppi32Path {
     }
 };
 
+// A pair recorded by sweep_rppi32_pp: recompute rp^2 and t' from the staged
+// tile with the same IEEE operations as the packed main path, then settle it
+// as resolve_rppi does (the main path added it at addr_main).
+template <bool LIN>
+__device__ __forceinline__ int resolve_local_rppi(const unsigned char *smem, const SweepRP &S,
+                                                  float xh, float yh, float zh, float s,
+                                                  int i, int jl)
+{
+    const float *tx = reinterpret_cast<const float *>(smem + TX_OFF);
+    const float dx = __fsub_rn(tx[jl], xh);
+    const float dy = __fsub_rn(tx[jl + TSTRIDE / 4], yh);
+    const float dz = __fsub_rn(tx[jl + TSTRIDE / 2], zh);
+    const float rp2 = __fmaf_rn(dy, dy, __fmul_rn(dx, dx));
+    const float t = __fmaf_rn(fabsf(dz), s, -0.5f);
+    const float q = __fadd_rn(t, PI_MAGIC);
+    const float f = __fsub_rn(t, __fsub_rn(q, PI_MAGIC));
+    const uint32_t e = lut_entry<LIN>(smem, S.u0, S.shift, S.lut_last, S.lscale, rp2);
+    const uint32_t m = min(__float_as_uint(q) - PI_MAGIC_BITS, (uint32_t)S.npi);
+    const uint32_t addr = S.hbase + min(e, (uint32_t)S.nb) * S.rowb + m * 4u;
+    return resolve_rppi<false>(smem, S, e, rp2, m, fabsf(f) > S.pband, addr, i, S.t0 + jl, 1.0f);
+}
+
+// Sweep one window with PP primaries per lane (lane layout as in sweep32): per
+// pair rp^2 and t' = |dz| s - 1/2 in packed float32, the rp table byte, the pi
+// index from the rounding, one shared atomic into the warp's 2-D histogram copy.
+// A pair whose rp cell is flagged, or whose t' lies within the error bound of
+// a pi edge (|t' - round(t')| >= pband), sets a bit of the lane's mask; once
+// per block of 8 steps a warp-uniform test settles the recorded pairs.
+template <int I, int PP, bool TRI, bool EVALS, bool LIN>
+__device__ __forceinline__ void sweep_rppi32_pp(unsigned char *smem, const SweepRP &S, int jlo,
+                                                int jhi, int jj, const u64 *XH, const u64 *YH,
+                                                const u64 *ZH, u64 SC, float sc, const int *iv,
+                                                const bool *vv, u64 &n_eval, u64 &n_rck)
+{
+    const float qnan = __int_as_float(0x7fc00000);
+    const u64 MH = pack2(-0.5f, -0.5f), MG = pack2(PI_MAGIC, PI_MAGIC);
+    const u64 PB = pack2(S.pband, S.pband);
+    const u64 LS = pack2(S.lscale, S.lscale), LM = pack2(LIN_MAGIC, LIN_MAGIC);
+    const uint32_t npiu = (uint32_t)S.npi, nbu = (uint32_t)S.nb;
+    // entries are <= nbu + 1 < 0x80: adding 0x80 - (nbu + 1) to each byte sets its
+    // top bit exactly for the flagged value, without carries between bytes
+    const uint32_t cflag = (0x80u - (nbu + 1u)) * 0x01010101u;
+    const int jstart = jlo & ~1;
+    constexpr int JS = 64 / I;
+    const int nit = (jhi - jstart + 2 * JS - 1) / (2 * JS);
+    for (int b0 = 0; b0 < nit; b0 += 8) {
+        const int jAb = jstart + 2 * jj + b0 * 2 * JS;
+        const unsigned char *pb = smem + TX_OFF + jAb * 4;
+        const int tend = min(8, nit - b0);
+        uint32_t fm[PP];
+#pragma unroll
+        for (int q = 0; q < PP; ++q)
+            fm[q] = 0u;
+        for (int t = 0; t < tend; ++t) {
+            const unsigned char *p = pb + t * 8 * JS;
+            const u64 xA = *reinterpret_cast<const u64 *>(p);
+            const u64 yA = *reinterpret_cast<const u64 *>(p + TSTRIDE);
+            const u64 zA = *reinterpret_cast<const u64 *>(p + 2 * TSTRIDE);
+            const u64 xB = *reinterpret_cast<const u64 *>(p + 4 * JS);
+            const u64 yB = *reinterpret_cast<const u64 *>(p + 4 * JS + TSTRIDE);
+            const u64 zB = *reinterpret_cast<const u64 *>(p + 4 * JS + 2 * TSTRIDE);
+            const int jA = jAb + t * 2 * JS;
+            const int gA = S.t0 + jA, gB = gA + JS;  // global indices of (a0, b0); a1, b1 are +1
+            const int gv[4] = {gA, gA + 1, gB, gB + 1};
+#pragma unroll
+            for (int q = 0; q < PP; ++q) {
+                u64 dx = fsub2(xA, XH[q]), dy = fsub2(yA, YH[q]);
+                const u64 rA = ffma2(dy, dy, fmul2(dx, dx));
+                const u64 tA = ffma2(fabs2(fsub2(zA, ZH[q])), SC, MH);
+                dx = fsub2(xB, XH[q]);
+                dy = fsub2(yB, YH[q]);
+                const u64 rB = ffma2(dy, dy, fmul2(dx, dx));
+                const u64 tB = ffma2(fabs2(fsub2(zB, ZH[q])), SC, MH);
+                const u64 qA = fadd2(tA, MG), qB = fadd2(tB, MG);
+                // pband - |t' - round(t')|: sign bit set = near a pi edge (a NaN
+                // sentinel gives a positive NaN: never flagged)
+                const u64 gA2 = fsub2(PB, fabs2(fsub2(tA, fsub2(qA, MG))));
+                const u64 gB2 = fsub2(PB, fabs2(fsub2(tB, fsub2(qB, MG))));
+                float r[4], qv[4], g[4];
+                unpack2(rA, r[0], r[1]);
+                unpack2(rB, r[2], r[3]);
+                unpack2(qA, qv[0], qv[1]);
+                unpack2(qB, qv[2], qv[3]);
+                unpack2(gA2, g[0], g[1]);
+                unpack2(gB2, g[2], g[3]);
+                uint32_t cq[4];
+                if (LIN) {
+                    float c[4];
+                    unpack2(ffma2(rA, LS, LM), c[0], c[1]);
+                    unpack2(ffma2(rB, LS, LM), c[2], c[3]);
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
+                        cq[k] = __float_as_uint(c[k]) - LIN_MAGIC_BITS;
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
+                        cq[k] = (__float_as_uint(r[k]) >> S.shift) - S.u0;
+                }
+                if (TRI) {  // pairs with j <= i: the out-of-range entry, never flagged
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        cq[k] = gv[k] > iv[q] ? cq[k] : S.lut_last;
+                        g[k] = gv[k] > iv[q] ? g[k] : 1.0f;
+                    }
+                }
+                if (EVALS) {
+                    const int jv[4] = {jA, jA + 1, jA + JS, jA + JS + 1};
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
+                        n_eval += (vv[q] && jv[k] >= jlo && jv[k] < jhi && (!TRI || gv[k] > iv[q]))
+                                      ? 1ull : 0ull;
+                }
+                uint32_t e[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    e[k] = smem[LUT_OFF + min(cq[k], S.lut_last)];
+                    const uint32_t m = min(__float_as_uint(qv[k]) - PI_MAGIC_BITS, npiu);
+                    red_shared(S.hbase + min(e[k], nbu) * S.rowb + m * 4u, 1u);
+                }
+                const uint32_t w = __byte_perm(__byte_perm(e[0], e[1], 0x0040),
+                                               __byte_perm(e[2], e[3], 0x0040), 0x5410);
+                // top bytes of g: bit 7 of byte k is the sign of g[k]
+                const uint32_t sg = __byte_perm(__byte_perm(__float_as_uint(g[0]), __float_as_uint(g[1]), 0x0073),
+                                                __byte_perm(__float_as_uint(g[2]), __float_as_uint(g[3]), 0x0073),
+                                                0x5410);
+                // shift the mask one step down, add this step's bits at 8 k + 7
+                fm[q] = (fm[q] >> 1) | (((w + cflag) | sg) & 0x80808080u);
+            }
+        }
+        uint32_t anyf = 0u;
+#pragma unroll
+        for (int q = 0; q < PP; ++q)
+            anyf |= fm[q];
+        if (__any_sync(FULL, anyf != 0u)) {
+#pragma unroll
+            for (int q = 0; q < PP; ++q) {
+                float xh, yh, zh, tmp;
+                unpack2(XH[q], xh, tmp);
+                unpack2(YH[q], yh, tmp);
+                unpack2(ZH[q], zh, tmp);
+                uint32_t m = fm[q];
+                while (m) {
+                    const int bit = __ffs(m) - 1;
+                    m &= m - 1u;
+                    const int t = (bit & 7) - (8 - tend), k = bit >> 3;
+                    const int jl = jAb + t * 2 * JS + ((k & 2) ? JS : 0) + (k & 1);
+                    n_rck += resolve_local_rppi<LIN>(smem, S, xh, yh, zh, sc, iv[q], jl);
+                }
+            }
+        }
+    }
+}
+
+// Float32 DD(rp, pi) without sums: I x PP primaries per chunk (lane ii holds
+// primaries ii, ii + I, ...), deferred flag resolution.  Tables, histograms and
+// the merge are those of Rppi32Path.
+template <int I, int PP, bool EVALS>
+struct Rppi32PathPP {
+    using Base = Rppi32Path<I, EVALS, false, false>;
+    static __device__ __forceinline__ void init(const PairParams &P, unsigned char *smem)
+    {
+        Base::init(P, smem);
+    }
+    static __device__ __forceinline__ void fini(const PairParams &P, unsigned char *smem, PathState &st)
+    {
+        Base::fini(P, smem, st);
+    }
+
+    static __device__ __forceinline__ bool item(const PairParams &P, const Item &it,
+                                                unsigned char *smem, PathState &st)
+    {
+        constexpr int CH = I * PP;
+        const int nb = P.nbins, npi = P.npibins;
+        uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
+        const float *tz = reinterpret_cast<const float *>(smem + TX_OFF + 2 * TSTRIDE);
+        uint32_t *hist = reinterpret_cast<uint32_t *>(smem + P.hist_off);
+        const int copy = (nb + 1) * (npi + 1);
+
+        const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+        unsigned &pending = st.pending;
+
+        uint32_t *hc = hist + (warp % P.hcopies) * copy;
+        const int ii = lane % I, jj = lane / I;
+        SweepRP S;
+        S.nb = nb;
+        S.npi = npi;
+        S.u0 = P.u0;
+        S.lut_last = (uint32_t)(P.lut_n - 1);
+        S.shift = P.lut_shift;
+        S.nthr = P.nthr;
+        S.lin = P.lut_lin;
+        S.lscale = P.lut_scale;
+        S.hbase = smem_u32(hc);
+        S.rowb = (uint32_t)(npi + 1) * 4u;
+        S.pband = P.pband;
+        S.pa = P.A.pos64;
+        S.pb = P.B.pos64;
+        S.acc = nullptr;
+        S.weighted = false;
+        S.want_r = false;
+        const u64 SC = pack2(P.pscale, P.pscale);
+        const unsigned flush_at = (1u << 30) / (unsigned)(WARPS / P.hcopies);
+        const float qnan = __int_as_float(0x7fc00000);
+
+        const float dzw = __fadd_ru(__double2float_ru(it.dzmax), P.zslack);
+        const float Sxf = __double2float_rn(it.Sx), Syf = __double2float_rn(it.Sy);
+        S.Sx = it.Sx;
+        S.Sy = it.Sy;
+        const int nchunks = (it.a1 - it.a0 + CH - 1) / CH;
+
+        for (int t0 = it.b0; t0 < it.b1; t0 += TILE32) {
+            const int nt = min(TILE32, it.b1 - t0);
+            if (!stage_tiles32(smem, P.B, t0, nt, bar, st.phase, P.err))
+                return false;
+            S.t0 = t0;
+            const float zt_lo = tz[0];
+            float zt_hi = tz[nt - 1];
+            if (isnan(zt_hi))
+                zt_hi = INFINITY;
+            auto zkey = [&](int q) { return tz[q]; };
+            int lo_prev[3] = {0, 0, 0}, hi_prev[3] = {0, 0, 0};
+            auto next_chunk = [&]() {  // chunks in increasing order, claimed by the warps
+                int v = 0;
+                if (lane == 0)
+                    v = atomicAdd(reinterpret_cast<int *>(smem + CLAIM_OFF), 1);
+                return __shfl_sync(FULL, v, 0);
+            };
+            for (int c = next_chunk(); c < nchunks; c = next_chunk()) {
+                const int ib = it.a0 + c * CH;
+                u64 XH[PP], YH[PP], ZH[PP];
+                int iv[PP];
+                bool vv[PP];
+                float zq[PP];
+                float zmax = qnan;
+#pragma unroll
+                for (int q = 0; q < PP; ++q) {
+                    const int i = ib + q * I + ii;
+                    float xi = qnan, yi = qnan, zi = qnan;
+                    if (i < it.a1) {
+                        xi = P.A.xs[i];
+                        yi = P.A.ys[i];
+                        zi = P.A.zs[i];
+                    }
+                    iv[q] = i;
+                    vv[q] = !isnan(xi);  // chunk tail and column padding are NaN
+                    const float xh = __fsub_rn(xi, Sxf), yh = __fsub_rn(yi, Syf);
+                    XH[q] = pack2(xh, xh);
+                    YH[q] = pack2(yh, yh);
+                    zq[q] = zi;
+                    zmax = (isnan(zmax) || zi > zmax) ? zi : zmax;
+                }
+                const float zlo = __shfl_sync(FULL, zq[0], 0);
+                float zhi = zmax;
+#pragma unroll
+                for (int o = 1; o < I; o <<= 1) {  // largest real z of the chunk
+                    const float t = __shfl_xor_sync(FULL, zhi, o);
+                    zhi = (isnan(zhi) || t > zhi) ? t : zhi;
+                }
+                if (isnan(zlo))
+                    continue;
+#pragma unroll
+                for (int kk = 0; kk < 3; ++kk) {
+                    const int k = kk - 1;
+                    if (k < it.kmin || k > it.kmax)
+                        continue;
+                    const float kz = (float)k * P.boxf[2];
+                    const float wlo = zlo - kz - dzw, whi = zhi - kz + dzw;
+                    if (whi < zt_lo || wlo > zt_hi)
+                        continue;
+                    int jlo = warp_bound_from(zkey, lo_prev[kk], nt, wlo, false, lane);
+                    const int jhi = warp_bound_from(zkey, max(hi_prev[kk], jlo), nt, whi, true, lane);
+                    lo_prev[kk] = jlo;
+                    hi_prev[kk] = jhi;
+                    const bool tri = it.self && k == 0;
+                    if (tri)
+                        jlo = max(jlo, ib + 1 - t0);
+                    if (jlo >= jhi)
+                        continue;
+                    pending += (unsigned)((jhi - jlo) / (64 / I) + 4) * 2u * PP;
+#pragma unroll
+                    for (int q = 0; q < PP; ++q) {
+                        const float zh = __fsub_rn(zq[q], kz);
+                        ZH[q] = pack2(zh, zh);
+                    }
+                    S.Sz = k == 0 ? 0.0 : (k > 0 ? P.g.box[2] : -P.g.box[2]);
+                    if (tri) {
+                        if (S.lin)
+                            sweep_rppi32_pp<I, PP, true, EVALS, true>(smem, S, jlo, jhi, jj, XH, YH, ZH, SC,
+                                                                      P.pscale, iv, vv, st.n_eval, st.n_rck);
+                        else
+                            sweep_rppi32_pp<I, PP, true, EVALS, false>(smem, S, jlo, jhi, jj, XH, YH, ZH, SC,
+                                                                       P.pscale, iv, vv, st.n_eval, st.n_rck);
+                    } else {
+                        if (S.lin)
+                            sweep_rppi32_pp<I, PP, false, EVALS, true>(smem, S, jlo, jhi, jj, XH, YH, ZH, SC,
+                                                                       P.pscale, iv, vv, st.n_eval, st.n_rck);
+                        else
+                            sweep_rppi32_pp<I, PP, false, EVALS, false>(smem, S, jlo, jhi, jj, XH, YH, ZH, SC,
+                                                                        P.pscale, iv, vv, st.n_eval, st.n_rck);
+                    }
+                }
+                if (pending > flush_at) {  // keep every shared u32 count far from overflow
+                    __syncwarp();
+                    flush_rppi(hc, nb, npi, P.hist, lane);
+                    pending = 0;
+                }
+            }
+        }
+        return true;
+    }
+};
+
 // Binary64 DD(rp, pi): canonical rp^2 and |dz|, exact edge compares.
 template <int I, bool EVALS, bool WACC>
 struct Rppi64Path {
@@ -2296,6 +2608,9 @@ cudaError_t launch_pairs(const PairParams &P, PairLaunch &L, int sms, cudaStream
                            : launch_persistent(k_path<Rppi32Path<16, false, false, true>, 3>, P, L, sms, st);
         if (L.verify)
             return launch_persistent(k_path<Rppi32Path<8, true, true, false>, 3>, P, L, sms, st);
+        if (L.pp == 2)  // two primaries per lane, deferred flags
+            return L.evals ? launch_persistent(k_path<Rppi32PathPP<16, 2, true>, 3>, P, L, sms, st)
+                           : launch_persistent(k_path<Rppi32PathPP<16, 2, false>, 3>, P, L, sms, st);
         switch (L.chunk) {
         case 16:
             return L.evals ? launch_persistent(k_path<Rppi32Path<16, true, false, false>, 3>, P, L, sms, st)
