@@ -2383,7 +2383,7 @@ __global__ void __launch_bounds__(THREADS, MINB) k_pipe(const __grid_constant__ 
 // into the previous job's output and loads the next job's tables.
 using XiF32 = Xi32Path<16, 2, false, false>;
 using XiF64 = Xi64Path<8, false, false>;
-using RpF32 = Rppi32Path<16, false, false, false>;
+using RpF32 = Rppi32PathPP<16, 2, false>;
 using RpF64 = Rppi64Path<8, false, false>;
 
 __device__ __forceinline__ void batch_init(int path, const PairParams &P, unsigned char *smem)
