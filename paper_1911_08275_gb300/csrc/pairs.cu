@@ -686,12 +686,12 @@ __device__ __forceinline__ void sweep32(unsigned char *smem, const Sweep32 &S, u
                     unpack2(ffma2(dA, LS, LM), t[0], t[1]);
                     unpack2(ffma2(dB, LS, LM), t[2], t[3]);
 #pragma unroll
-                    for (int r = 0; r < 4; ++r)
-                        cq[q][r] = __float_as_uint(t[r]) - LIN_MAGIC_BITS;
+                    for (int r = 0; r < 4; ++r)  // below-range values wrap to huge: clamped
+                        cq[q][r] = min(__float_as_uint(t[r]) - LIN_MAGIC_BITS, S.lut_last);
                 } else {
 #pragma unroll
                     for (int r = 0; r < 4; ++r)
-                        cq[q][r] = (__float_as_uint(d[q][r]) >> S.shift) - S.u0;
+                        cq[q][r] = min((__float_as_uint(d[q][r]) >> S.shift) - S.u0, S.lut_last);
                 }
             }
             const int gA = S.t0 + jA, gB = gA + JS;  // global indices of (a0, b0); a1, b1 are +1
@@ -719,7 +719,7 @@ __device__ __forceinline__ void sweep32(unsigned char *smem, const Sweep32 &S, u
                 uint32_t e[4];
 #pragma unroll
                 for (int r = 0; r < 4; ++r) {
-                    e[r] = smem[LUT_OFF + min(cq[q][r], S.lut_last)];
+                    e[r] = smem[LUT_OFF + cq[q][r]];
                     red_shared1(hl + e[r] * 128u);  // every entry is a row: bin, dummy or flagged
                     if (W || RV)
                         wacc_add<W, RV>(A, e[r], W ? pw[q][r] : 1.0f, d[q][r]);
@@ -1833,12 +1833,12 @@ __device__ __forceinline__ void sweep_rppi32_pp(unsigned char *smem, const Sweep
                     unpack2(ffma2(rA, LS, LM), c[0], c[1]);
                     unpack2(ffma2(rB, LS, LM), c[2], c[3]);
 #pragma unroll
-                    for (int k = 0; k < 4; ++k)
-                        cq[k] = __float_as_uint(c[k]) - LIN_MAGIC_BITS;
+                    for (int k = 0; k < 4; ++k)  // below-range values wrap to huge: clamped
+                        cq[k] = min(__float_as_uint(c[k]) - LIN_MAGIC_BITS, S.lut_last);
                 } else {
 #pragma unroll
                     for (int k = 0; k < 4; ++k)
-                        cq[k] = (__float_as_uint(r[k]) >> S.shift) - S.u0;
+                        cq[k] = min((__float_as_uint(r[k]) >> S.shift) - S.u0, S.lut_last);
                 }
                 if (TRI) {  // pairs with j <= i: the out-of-range entry, never flagged
 #pragma unroll
@@ -1857,7 +1857,7 @@ __device__ __forceinline__ void sweep_rppi32_pp(unsigned char *smem, const Sweep
                 uint32_t e[4];
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
-                    e[k] = smem[LUT_OFF + min(cq[k], S.lut_last)];
+                    e[k] = smem[LUT_OFF + cq[k]];
                     const uint32_t m = min(__float_as_uint(qv[k]) - PI_MAGIC_BITS, npiu);
                     red_shared(S.hbase + min(e[k], nbu) * S.rowb + m * 4u, 1u);
                 }
