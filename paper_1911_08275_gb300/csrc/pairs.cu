@@ -617,6 +617,15 @@ __device__ __forceinline__ int resolve_local(const unsigned char *smem, const Sw
     return re;
 }
 
+// 8-byte shared load at a 32-bit shared address plus a constant offset.
+template <int OFF>
+__device__ __forceinline__ u64 lds64(uint32_t a)
+{
+    u64 v;
+    asm volatile("ld.shared.b64 %0, [%1+%2];" : "=l"(v) : "r"(a), "n"(OFF));
+    return v;
+}
+
 // Sweep one window [jlo, jhi) of the staged tile.  Lane (ii, jj) holds PP
 // primaries (each broadcast to both halves of packed registers) and evaluates
 // them against two consecutive secondaries j, j+1 (one 8-byte load per axis
@@ -643,21 +652,21 @@ __device__ __forceinline__ void sweep32(unsigned char *smem, const Sweep32 &S, u
     const u64 LS = pack2(S.lscale, S.lscale), LM = pack2(LIN_MAGIC, LIN_MAGIC);
     for (int b0 = 0; b0 < nit; b0 += 8) {
         const int jAb = jstart + 2 * jj + b0 * 2 * JS;
-        const unsigned char *pb = S.tb + jAb * 4;
+        const uint32_t pb = smem_u32(S.tb) + jAb * 4;
         const int tend = min(8, nit - b0);
         uint32_t fm[PP];
 #pragma unroll
         for (int q = 0; q < PP; ++q)
             fm[q] = 0u;
         for (int t = 0; t < tend; ++t) {
-            const unsigned char *p = pb + t * 8 * JS;
+            const uint32_t p = pb + t * 8 * JS;
             const int jA = jAb + t * 2 * JS;
-            const u64 xA = *reinterpret_cast<const u64 *>(p);
-            const u64 yA = *reinterpret_cast<const u64 *>(p + TSTRIDE);
-            const u64 zA = *reinterpret_cast<const u64 *>(p + 2 * TSTRIDE);
-            const u64 xB = *reinterpret_cast<const u64 *>(p + 4 * JS);
-            const u64 yB = *reinterpret_cast<const u64 *>(p + 4 * JS + TSTRIDE);
-            const u64 zB = *reinterpret_cast<const u64 *>(p + 4 * JS + 2 * TSTRIDE);
+            const u64 xA = lds64<0>(p);
+            const u64 yA = lds64<TSTRIDE>(p);
+            const u64 zA = lds64<2 * TSTRIDE>(p);
+            const u64 xB = lds64<4 * JS>(p);
+            const u64 yB = lds64<4 * JS + TSTRIDE>(p);
+            const u64 zB = lds64<4 * JS + 2 * TSTRIDE>(p);
             float d[PP][4];
             float pw[PP][4];     // pair weights (weighted sums only)
             uint32_t cq[PP][4];  // table cell of each pair
@@ -1789,20 +1798,20 @@ __device__ __forceinline__ void sweep_rppi32_pp(unsigned char *smem, const Sweep
     const int nit = (jhi - jstart + 2 * JS - 1) / (2 * JS);
     for (int b0 = 0; b0 < nit; b0 += 8) {
         const int jAb = jstart + 2 * jj + b0 * 2 * JS;
-        const unsigned char *pb = smem + TX_OFF + jAb * 4;
+        const uint32_t pb = smem_u32(smem + TX_OFF) + jAb * 4;
         const int tend = min(8, nit - b0);
         uint32_t fm[PP];
 #pragma unroll
         for (int q = 0; q < PP; ++q)
             fm[q] = 0u;
         for (int t = 0; t < tend; ++t) {
-            const unsigned char *p = pb + t * 8 * JS;
-            const u64 xA = *reinterpret_cast<const u64 *>(p);
-            const u64 yA = *reinterpret_cast<const u64 *>(p + TSTRIDE);
-            const u64 zA = *reinterpret_cast<const u64 *>(p + 2 * TSTRIDE);
-            const u64 xB = *reinterpret_cast<const u64 *>(p + 4 * JS);
-            const u64 yB = *reinterpret_cast<const u64 *>(p + 4 * JS + TSTRIDE);
-            const u64 zB = *reinterpret_cast<const u64 *>(p + 4 * JS + 2 * TSTRIDE);
+            const uint32_t p = pb + t * 8 * JS;
+            const u64 xA = lds64<0>(p);
+            const u64 yA = lds64<TSTRIDE>(p);
+            const u64 zA = lds64<2 * TSTRIDE>(p);
+            const u64 xB = lds64<4 * JS>(p);
+            const u64 yB = lds64<4 * JS + TSTRIDE>(p);
+            const u64 zB = lds64<4 * JS + 2 * TSTRIDE>(p);
             const int jA = jAb + t * 2 * JS;
             const int gA = S.t0 + jA, gB = gA + JS;  // global indices of (a0, b0); a1, b1 are +1
             const int gv[4] = {gA, gA + 1, gB, gB + 1};
