@@ -277,12 +277,25 @@ __device__ __forceinline__ void put_entry(const T *__restrict__ x, const T *__re
 constexpr int SORT_THREADS = 256;
 constexpr int SORT_BUF = 256;  // entries of a cell ranked from shared memory
 
+// Rank of entry (kq, iq) among the n entries of e[] by (key, original index).
+__device__ __forceinline__ uint32_t rank_in(const ulonglong2 *e, uint32_t n, unsigned long long kq,
+                                            int iq)
+{
+    uint32_t rank = 0;
+    for (uint32_t m = 0; m < n; ++m) {
+        const ulonglong2 em = e[m];  // every lane of the group reads the same entry
+        rank += (em.x < kq) || (em.x == kq && (int)em.y < iq);
+    }
+    return rank;
+}
+
 // Rank the cells' real entries by (z, original index) and write the sorted
 // float32 / binary64 copies.  Each warp takes two cells at a time: cells of up
-// to 16 entries are ranked by a half warp each with shuffles; otherwise the
-// whole warp ranks the two cells one after the other: up to 32 entries in
-// registers, up to SORT_BUF from a copy in shared memory (every lane reads the
-// same entry: a broadcast), beyond that against the cell in global memory.
+// to 16 entries are ranked by a half warp each; otherwise the whole warp ranks
+// the two cells one after the other, up to SORT_BUF entries, beyond that
+// against the cell in global memory.  The entries being ranked are copied to a
+// per-warp shared buffer as 16-byte (key, index) records: one broadcast load
+// per comparison.
 template <class T>
 __global__ void __launch_bounds__(SORT_THREADS)
     k_sort_cells(const T *__restrict__ x, const T *__restrict__ y, const double *__restrict__ w,
@@ -293,11 +306,9 @@ __global__ void __launch_bounds__(SORT_THREADS)
                  unsigned *__restrict__ wmax, double4_32a *__restrict__ pos64,
                  int *__restrict__ perm)
 {
-    __shared__ unsigned long long s_key[SORT_THREADS / 32][SORT_BUF];
-    __shared__ int s_idx[SORT_THREADS / 32][SORT_BUF];
+    __shared__ ulonglong2 s_ent[SORT_THREADS / 32][SORT_BUF];
     const int lane = threadIdx.x & 31, half = lane >> 4, hl = lane & 15, wid = threadIdx.x >> 5;
-    unsigned long long *bk = s_key[wid];
-    int *bi = s_idx[wid];
+    ulonglong2 *be = s_ent[wid];
     unsigned wm = 0;  // bit pattern of the largest |w| (float) this thread stored
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
     for (long long c0 = (((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 2; c0 < ncells;
@@ -308,15 +319,12 @@ __global__ void __launch_bounds__(SORT_THREADS)
         const uint32_t cnt0 = __shfl_sync(FULL, cnt, 0), cnt1 = __shfl_sync(FULL, cnt, 16);
         if (max(cnt0, cnt1) <= 16u) {
             const bool mine = (uint32_t)hl < cnt;
-            const unsigned long long kq = mine ? tmp_key[s + hl] : ~0ull;
+            const unsigned long long kq = mine ? tmp_key[s + hl] : ~0ull;  // absent: ranks last
             const int iq = mine ? tmp_idx[s + hl] : 0x7fffffff;
-            uint32_t rank = 0;
-            const uint32_t cmax = max(cnt0, cnt1);
-            for (uint32_t m = 0; m < cmax; ++m) {
-                const unsigned long long km = __shfl_sync(FULL, kq, (int)m, 16);
-                const int im = __shfl_sync(FULL, iq, (int)m, 16);
-                rank += (km < kq) || (km == kq && im < iq);  // absent entries rank last
-            }
+            __syncwarp();
+            be[lane] = make_ulonglong2(kq, (unsigned long long)(unsigned)iq);
+            __syncwarp();
+            const uint32_t rank = rank_in(be + half * 16, max(cnt0, cnt1), kq, iq);
             if (mine)
                 put_entry(x, y, w, g, s + rank, iq, kq, xs, ys, zs, ws, pos64, perm, wm);
             continue;
@@ -326,41 +334,30 @@ __global__ void __launch_bounds__(SORT_THREADS)
             const uint32_t sc = __shfl_sync(FULL, s, h * 16);
             if (cn == 0)
                 continue;
-            if (cn <= 32) {
-                const bool mine = (uint32_t)lane < cn;
-                const unsigned long long kq = mine ? tmp_key[sc + lane] : ~0ull;
-                const int iq = mine ? tmp_idx[sc + lane] : 0x7fffffff;
-                uint32_t rank = 0;
-                for (uint32_t m = 0; m < cn; ++m) {
-                    const unsigned long long km = __shfl_sync(FULL, kq, (int)m);
-                    const int im = __shfl_sync(FULL, iq, (int)m);
-                    rank += (km < kq) || (km == kq && im < iq);
-                }
-                if (mine)
-                    put_entry(x, y, w, g, sc + rank, iq, kq, xs, ys, zs, ws, pos64, perm, wm);
-                continue;
-            }
             const bool buffered = cn <= (uint32_t)SORT_BUF;
             if (buffered) {
                 __syncwarp();
-                for (uint32_t e = lane; e < cn; e += 32) {
-                    bk[e] = tmp_key[sc + e];
-                    bi[e] = tmp_idx[sc + e];
-                }
+                for (uint32_t e = lane; e < cn; e += 32)
+                    be[e] = make_ulonglong2(tmp_key[sc + e], (unsigned long long)(unsigned)tmp_idx[sc + e]);
                 __syncwarp();
             }
             for (uint32_t e0 = 0; e0 < cn; e0 += 32) {
                 const uint32_t e = e0 + lane;
                 const bool mine = e < cn;
-                const unsigned long long kq = mine ? (buffered ? bk[e] : tmp_key[sc + e]) : ~0ull;
-                const int iq = mine ? (buffered ? bi[e] : tmp_idx[sc + e]) : 0x7fffffff;
+                unsigned long long kq = ~0ull;
+                int iq = 0x7fffffff;
+                if (mine) {
+                    if (buffered) {
+                        kq = be[e].x;
+                        iq = (int)be[e].y;
+                    } else {
+                        kq = tmp_key[sc + e];
+                        iq = tmp_idx[sc + e];
+                    }
+                }
                 uint32_t rank = 0;
                 if (buffered) {
-                    for (uint32_t m = 0; m < cn; ++m) {
-                        const unsigned long long km = bk[m];
-                        const int im = bi[m];
-                        rank += (km < kq) || (km == kq && im < iq);
-                    }
+                    rank = rank_in(be, cn, kq, iq);
                 } else {
                     for (uint32_t m = 0; m < cn; ++m) {
                         const unsigned long long km = tmp_key[sc + m];
