@@ -127,14 +127,20 @@ def _is_torch(a) -> bool:
     return type(a).__module__.startswith("torch")
 
 
+_TORCH_CODES = None  # torch dtype -> cf_dtype, filled on first use (torch imported lazily)
+
+
 def _arr(a, name):
     """(pointer, dtype code, n, is_cuda, keepalive) of a 1-D contiguous array."""
+    global _TORCH_CODES
     if _is_torch(a):
-        import torch
+        if _TORCH_CODES is None:
+            import torch
+            _TORCH_CODES = {torch.float32: CF_FLOAT32, torch.float64: CF_FLOAT64}
         if a.dim() != 1 or not a.is_contiguous():
             raise ValueError(f"{name} must be a 1-D contiguous tensor")
-        code = {torch.float32: CF_FLOAT32, torch.float64: CF_FLOAT64}.get(a.dtype)
-        return a.data_ptr() if a.numel() else None, code, a.numel(), a.is_cuda, a
+        n = a.numel()
+        return a.data_ptr() if n else None, _TORCH_CODES.get(a.dtype), n, a.is_cuda, a
     a = np.ascontiguousarray(a)
     if a.ndim != 1:
         raise ValueError(f"{name} must be 1-D")
@@ -169,13 +175,18 @@ def _config(dtype, periodic, boxsize, mode, weighted, want_ravg, refine, flags, 
     shard = tuning.get("shard") or (0, 0)
     c.shard_index, c.shard_count = int(shard[0]), int(shard[1])
     c.periodic = 1 if periodic else 0
-    b = np.broadcast_to(np.asarray(boxsize if boxsize is not None else 0.0, dtype=np.float64), (3,))
-    c.boxsize[:] = [float(v) for v in b]
+    if boxsize is None:
+        boxsize = 0.0
+    if isinstance(boxsize, (int, float)):
+        c.boxsize[0] = c.boxsize[1] = c.boxsize[2] = float(boxsize)
+    else:
+        b = np.broadcast_to(np.asarray(boxsize, dtype=np.float64), (3,))
+        c.boxsize[:] = [float(v) for v in b]
     c.dtype = dtype
     c.mode = {"fp64": CF_MODE_FP64, "fp32_recheck": CF_MODE_FP32_RECHECK}[mode]
     c.weighted = 1 if weighted else 0
     c.want_ravg = 1 if want_ravg else 0
-    c.refine[:] = list(refine)
+    c.refine[0], c.refine[1], c.refine[2] = (int(v) for v in refine)
     c.flags = int(flags)
     if stream is None and cuda:
         import torch
