@@ -35,7 +35,7 @@ enum : unsigned {
 
 // Shared layout of the float32 DD(r) kernel (compile-time offsets):
 // [0,128) barrier + work item; LUT; x, y, z tiles of TILE32 + 64 floats each;
-// thresholds; squared edges; per-warp histograms ((nbins + 1) rows of 32 lanes).
+// thresholds; squared edges; histogram copies ((nbins + 2) rows of 32 lanes each).
 constexpr int XI32_LUT_OFF = 128;
 constexpr int XI32_TX_OFF = XI32_LUT_OFF + LUT_MAX;
 constexpr int XI32_TSTRIDE = (TILE32 + 64) * 4;

@@ -4,33 +4,36 @@
 // squared edges, Code 4), re-designed for GB300.
 //
 // Work unit = one (primary column a, secondary column b, periodic image) pair
-// ("column pair"); columns are z-sorted (grid.cu).  A persistent CTA pulls
-// column pairs from a global counter, drops those whose bounding boxes are at
-// least Rmax apart in (x, y) (Sec. 2.2), stages column b into shared memory
-// with 1-D TMA bulk copies (cp.async.bulk + mbarrier) in tiles, and its 8 warps
-// sweep column a in chunks of I z-consecutive points.  For each chunk and
+// ("column pair"); columns are z-sorted (grid.cu).  The work-list kernel keeps
+// the pairs whose bounding boxes are less than Rmax apart in (x, y) (Sec. 2.2)
+// with their z reach.  A persistent CTA pulls kept pairs from a global counter,
+// stages column b into shared memory with 1-D TMA bulk copies (cp.async.bulk +
+// mbarrier, bounded waits) in tiles, and its 8 warps claim chunks of
+// z-consecutive points of column a from a shared counter.  For each chunk and
 // periodic z image a warp finds, by a lane-parallel search of the staged z
 // values, the window of b points whose z can be within the reach of the chunk
 // (the paper's late entry and early exit, applied per chunk rather than per
 // particle), then sweeps it.
 //
-// Float32 kernel (k_xi32).  The staged tiles hold every coordinate twice,
-// (x,x,y,y) and (z,z,w,w) in two arrays of 16-byte elements, so one 16-byte and
-// one 8-byte conflict-free shared load give packed operands for the
-// sm_100-family f32x2 instructions: each lane evaluates two primaries against
-// one secondary with 6 packed FP32 instructions.  The squared distance's bit
-// pattern indexes (clamped, branch-free) a lookup table built on the host from
-// float32 thresholds lo_k < e_k^2 < hi_k that bracket every squared edge by a
-// proven error bound; a safe table cell gives the byte offset of the bin row
-// directly, out-of-range distances share one entry that points at a dummy row,
-// and every lane adds one to its own column of the warp's shared histogram
-// with a shared-memory atomic (no bank conflicts, no branch).  Cells that touch a band fall back to threshold
-// compares, and a distance inside a band is re-evaluated with the canonical
-// binary64 formula from the binary64 copies of the two points, so counts are
-// bit-identical to the binary64 definition.
+// Float32 DD(r) (Xi32Path; k_pipe with two tile buffers so that no CTA-wide
+// barrier separates work items).  Each lane holds PP primaries, each broadcast
+// into both halves of a 64-bit register, and evaluates them against two
+// consecutive secondaries per 8-byte shared load with the sm_100-family packed
+// f32x2 instructions.  The squared distance indexes (clamped, branch-free) a
+// byte table built on the host from float32 thresholds lo_k < e_k^2 < hi_k that
+// bracket every squared edge by a proven error bound; a safe cell gives the bin
+// row, out-of-range distances a dummy row, and every lane adds one to its own
+// column of the CTA's shared histogram with a shared-memory atomic (no bank
+// conflicts, no branch).  A pair in a flagged cell (touching a band) sets a bit
+// of the lane's mask; once per 8 steps a warp-uniform test hands the recorded
+// pairs to a resolver that compares them with the thresholds and re-evaluates a
+// distance inside a band with the canonical binary64 formula from the binary64
+// copies of the two points, so counts are bit-identical to the binary64
+// definition.  Float32 DD(rp, pi) (Rppi32PathPP) has the same structure with a
+// 2-D histogram and a pi bin from one rounding.
 //
-// Binary64 kernel (k_xi64, CF_MODE_FP64): the same loop on binary64 copies
-// with the canonical formula and exact squared-edge compares.
+// Binary64 kernels (Xi64Path, Rppi64Path, CF_MODE_FP64): the same traversal on
+// binary64 copies with the canonical formula and exact squared-edge compares.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -419,10 +422,10 @@ __device__ __forceinline__ bool stage_tile(T *tile, const T *src, int count, int
 }
 
 // ============================================================ float32 kernel
-// Shared layout of k_xi32 (compile-time offsets, so table and tile addresses
-// fold into load immediates): [0,128) barrier + item; LUT (LUT_MAX bytes);
-// two tiles of TILE32 + 32 float4 ((x,x,y,y) and (z,z,w,w)); thresholds;
-// squared edges; per-warp histograms.
+// Shared layout of the float32 DD(r) kernels (compile-time offsets, so table
+// and tile addresses fold into load immediates): [0,128) barrier + item; LUT
+// (LUT_MAX bytes); x, y, z tiles of TILE32 + 64 floats; thresholds; squared
+// edges; histogram copies (the pipelined kernel's second tile buffer follows).
 constexpr int LUT_OFF = XI32_LUT_OFF;
 constexpr int TX_OFF = XI32_TX_OFF;
 constexpr int TSTRIDE = XI32_TSTRIDE;
