@@ -99,8 +99,8 @@ typedef struct {
                             choice of the refinement); fields set explicitly
                             (refine != {0,0,0}, pair_chunk, pair_pp) are kept.   */
     int pair_chunk;      /* float32 DD(r) kernel: primary lanes per warp chunk
-                            (8, 16 or 32; with pair_pp 4 always 8); 0 = default
-                            16                                                     */
+                            (8, 16 or 32 with pair_pp 1; 8 or 16 with pair_pp 2,
+                            32 runs as 16; 8 with pair_pp 4); 0 = default 16      */
     int pair_pp;         /* float32 kernels: primaries per lane, DD(r) 1, 2 or 4,
                             DD(rp, pi) 2 (else one, with pair_chunk lanes);
                             0 = default 2                                         */
