@@ -653,6 +653,10 @@ __device__ __forceinline__ void sweep32(unsigned char *smem, const Sweep32 &S, u
     // top bit exactly for the flagged value, without carries between bytes
     const uint32_t cflag = (0x80u - (nbu + 1u)) * 0x01010101u;
     const u64 LS = pack2(S.lscale, S.lscale), LM = pack2(LIN_MAGIC, LIN_MAGIC);
+    // shared addresses of the table: fma(d2, s, 2^23) >= 2^23 (d2 >= 0, NaN larger),
+    // so bits - LIN_MAGIC_BITS never wraps and the base folds into the clamp
+    const uint32_t lutb = smem_u32(smem + LUT_OFF), lut_lo = lutb - LIN_MAGIC_BITS,
+                   lut_hi = lutb + S.lut_last;
     for (int b0 = 0; b0 < nit; b0 += 8) {
         const int jAb = jstart + 2 * jj + b0 * 2 * JS;
         const uint32_t pb = smem_u32(S.tb) + jAb * 4;
@@ -698,12 +702,12 @@ __device__ __forceinline__ void sweep32(unsigned char *smem, const Sweep32 &S, u
                     unpack2(ffma2(dA, LS, LM), t[0], t[1]);
                     unpack2(ffma2(dB, LS, LM), t[2], t[3]);
 #pragma unroll
-                    for (int r = 0; r < 4; ++r)  // below-range values wrap to huge: clamped
-                        cq[q][r] = min(__float_as_uint(t[r]) - LIN_MAGIC_BITS, S.lut_last);
+                    for (int r = 0; r < 4; ++r)  // the table byte's shared address
+                        cq[q][r] = min(__float_as_uint(t[r]) + lut_lo, lut_hi);
                 } else {
 #pragma unroll
                     for (int r = 0; r < 4; ++r)
-                        cq[q][r] = min((__float_as_uint(d[q][r]) >> S.shift) - S.u0, S.lut_last);
+                        cq[q][r] = lutb + min((__float_as_uint(d[q][r]) >> S.shift) - S.u0, S.lut_last);
                 }
             }
             const int gA = S.t0 + jA, gB = gA + JS;  // global indices of (a0, b0); a1, b1 are +1
@@ -713,7 +717,7 @@ __device__ __forceinline__ void sweep32(unsigned char *smem, const Sweep32 &S, u
                 for (int q = 0; q < PP; ++q)
 #pragma unroll
                     for (int r = 0; r < 4; ++r) {
-                        cq[q][r] = gv[r] > iv[q] ? cq[q][r] : S.lut_last;
+                        cq[q][r] = gv[r] > iv[q] ? cq[q][r] : lut_hi;
                         d[q][r] = gv[r] > iv[q] ? d[q][r] : qnan;
                     }
             }
@@ -731,7 +735,7 @@ __device__ __forceinline__ void sweep32(unsigned char *smem, const Sweep32 &S, u
                 uint32_t e[4];
 #pragma unroll
                 for (int r = 0; r < 4; ++r) {
-                    e[r] = smem[LUT_OFF + cq[q][r]];
+                    asm volatile("ld.shared.u8 %0, [%1];" : "=r"(e[r]) : "r"(cq[q][r]));  // the row
                     red_shared1(hl + e[r] * 128u);  // every entry is a row: bin, dummy or flagged
                     if (W || RV)
                         wacc_add<W, RV>(A, e[r], W ? pw[q][r] : 1.0f, d[q][r]);
@@ -1796,6 +1800,9 @@ __device__ __forceinline__ void sweep_rppi32_pp(unsigned char *smem, const Sweep
     // entries are <= nbu + 1 < 0x80: adding 0x80 - (nbu + 1) to each byte sets its
     // top bit exactly for the flagged value, without carries between bytes
     const uint32_t cflag = (0x80u - (nbu + 1u)) * 0x01010101u;
+    // shared addresses of the rp table, the base folded into the clamp (as in sweep32)
+    const uint32_t lutb = smem_u32(smem + LUT_OFF), lut_lo = lutb - LIN_MAGIC_BITS,
+                   lut_hi = lutb + S.lut_last;
     const int jstart = jlo & ~1;
     constexpr int JS = 64 / I;
     const int nit = (jhi - jstart + 2 * JS - 1) / (2 * JS);
@@ -1845,17 +1852,17 @@ __device__ __forceinline__ void sweep_rppi32_pp(unsigned char *smem, const Sweep
                     unpack2(ffma2(rA, LS, LM), c[0], c[1]);
                     unpack2(ffma2(rB, LS, LM), c[2], c[3]);
 #pragma unroll
-                    for (int k = 0; k < 4; ++k)  // below-range values wrap to huge: clamped
-                        cq[k] = min(__float_as_uint(c[k]) - LIN_MAGIC_BITS, S.lut_last);
+                    for (int k = 0; k < 4; ++k)  // the table byte's shared address
+                        cq[k] = min(__float_as_uint(c[k]) + lut_lo, lut_hi);
                 } else {
 #pragma unroll
                     for (int k = 0; k < 4; ++k)
-                        cq[k] = min((__float_as_uint(r[k]) >> S.shift) - S.u0, S.lut_last);
+                        cq[k] = lutb + min((__float_as_uint(r[k]) >> S.shift) - S.u0, S.lut_last);
                 }
                 if (TRI) {  // pairs with j <= i: the out-of-range entry, never flagged
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {
-                        cq[k] = gv[k] > iv[q] ? cq[k] : S.lut_last;
+                        cq[k] = gv[k] > iv[q] ? cq[k] : lut_hi;
                         g[k] = gv[k] > iv[q] ? g[k] : 1.0f;
                     }
                 }
@@ -1869,7 +1876,7 @@ __device__ __forceinline__ void sweep_rppi32_pp(unsigned char *smem, const Sweep
                 uint32_t e[4];
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
-                    e[k] = smem[LUT_OFF + cq[k]];
+                    asm volatile("ld.shared.u8 %0, [%1];" : "=r"(e[k]) : "r"(cq[k]));
                     const uint32_t m = min(__float_as_uint(qv[k]) - PI_MAGIC_BITS, npiu);
                     red_shared(S.hbase + min(e[k], nbu) * S.rowb + m * 4u, 1u);
                 }
