@@ -43,6 +43,11 @@
 
 namespace cf {
 
+// Rows of one float32 DD(rp, pi) histogram copy: the bins, the not-counted row,
+// and the row that pairs in a flagged rp cell land in until they are settled
+// (never read), so a table entry is a row index without a clamp.
+inline __host__ __device__ int rppi32_rows(int nb) { return nb + 2; }
+
 void plan_pairs(PairParams &P, PairLaunch &L)
 {
     const int nb = P.nbins, nr = nb + 1;
@@ -76,7 +81,7 @@ void plan_pairs(PairParams &P, PairLaunch &L)
     }
     // rp-pi: one histogram copy per warp while the CTA stays small enough for
     // three CTAs per SM, else fewer copies shared by several warps.
-    const int copy = nr * (P.npibins + 1);
+    const int copy = (L.f64 ? nr : rppi32_rows(nb)) * (P.npibins + 1);
     const int base = L.f64 ? smem64_layout(P.tile_max, nb, P.npibins, 0).hist
                            : align_up(RPPI_P_OFF + (P.npibins + 1) * 8, 128);
     const int per = copy * 4 + (P.wacc ? copy * 16 + 16 : 0);
@@ -1539,9 +1544,9 @@ __device__ void flush_rppi(uint32_t *hc, int nb, int npi, unsigned long long *gh
 
 // All copies of the CTA's histograms (and binary64 sums, if acc) -> global
 // (after the last __syncthreads).
-__device__ void merge_rppi(const PairParams &P, const uint32_t *hist, const double *acc)
+__device__ void merge_rppi(const PairParams &P, const uint32_t *hist, const double *acc, int rows)
 {
-    const int nb = P.nbins, npi = P.npibins, row = npi + 1, copy = (nb + 1) * row;
+    const int nb = P.nbins, npi = P.npibins, row = npi + 1, copy = rows * row;
     for (int s = threadIdx.x; s < nb * npi; s += THREADS) {
         const int k = s / npi, m = s - k * npi;
         long long sum = 0;
@@ -1575,7 +1580,7 @@ struct Rppi32Path {
         double *Pe = reinterpret_cast<double *>(smem + RPPI_P_OFF);
         uint32_t *hist = reinterpret_cast<uint32_t *>(smem + P.hist_off);
         double *acc = WACC ? reinterpret_cast<double *>(smem + P.acc_off) : nullptr;
-        const int copy = (nb + 1) * (npi + 1);
+        const int copy = rppi32_rows(nb) * (npi + 1);
 
         const int tid = threadIdx.x;
         for (int q = tid; q < P.lut_n; q += THREADS)
@@ -1601,7 +1606,7 @@ struct Rppi32Path {
         const float *tz = reinterpret_cast<const float *>(smem + TX_OFF + 2 * TSTRIDE);
         uint32_t *hist = reinterpret_cast<uint32_t *>(smem + P.hist_off);
         double *acc = WACC ? reinterpret_cast<double *>(smem + P.acc_off) : nullptr;
-        const int copy = (nb + 1) * (npi + 1);
+        const int copy = rppi32_rows(nb) * (npi + 1);
 
         const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
         unsigned &phase = st.phase;
@@ -1743,7 +1748,7 @@ struct Rppi32Path {
         u64 &n_viol = st.n_viol;
 
         __syncthreads();
-        merge_rppi(P, hist, acc);
+        merge_rppi(P, hist, acc, rppi32_rows(P.nbins));
         n_eval = warp_sum_u64(n_eval);
         n_rck = warp_sum_u64(n_rck);
         n_viol = warp_sum_u64(n_viol);
@@ -1776,7 +1781,7 @@ __device__ __forceinline__ int resolve_local_rppi(const unsigned char *smem, con
     const float f = __fsub_rn(t, __fsub_rn(q, PI_MAGIC));
     const uint32_t e = lut_entry<LIN>(smem, S.u0, S.shift, S.lut_last, S.lscale, rp2);
     const uint32_t m = min(__float_as_uint(q) - PI_MAGIC_BITS, (uint32_t)S.npi);
-    const uint32_t addr = S.hbase + min(e, (uint32_t)S.nb) * S.rowb + m * 4u;
+    const uint32_t addr = S.hbase + e * S.rowb + m * 4u;  // as the main path added it
     return resolve_rppi<false>(smem, S, e, rp2, m, fabsf(f) > S.pband, addr, i, S.t0 + jl, 1.0f);
 }
 
@@ -1878,7 +1883,7 @@ __device__ __forceinline__ void sweep_rppi32_pp(unsigned char *smem, const Sweep
                 for (int k = 0; k < 4; ++k) {
                     asm volatile("ld.shared.u8 %0, [%1];" : "=r"(e[k]) : "r"(cq[k]));
                     const uint32_t m = min(__float_as_uint(qv[k]) - PI_MAGIC_BITS, npiu);
-                    red_shared(S.hbase + min(e[k], nbu) * S.rowb + m * 4u, 1u);
+                    red_shared(S.hbase + e[k] * S.rowb + m * 4u, 1u);  // flagged: row nb + 1
                 }
                 const uint32_t w = __byte_perm(__byte_perm(e[0], e[1], 0x0040),
                                                __byte_perm(e[2], e[3], 0x0040), 0x5410);
@@ -1937,7 +1942,7 @@ struct Rppi32PathPP {
         uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
         const float *tz = reinterpret_cast<const float *>(smem + TX_OFF + 2 * TSTRIDE);
         uint32_t *hist = reinterpret_cast<uint32_t *>(smem + P.hist_off);
-        const int copy = (nb + 1) * (npi + 1);
+        const int copy = rppi32_rows(nb) * (npi + 1);
 
         const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
         unsigned &pending = st.pending;
@@ -2217,7 +2222,7 @@ struct Rppi64Path {
         u64 &n_eval = st.n_eval;
 
         __syncthreads();
-        merge_rppi(P, hist, acc);
+        merge_rppi(P, hist, acc, P.nbins + 1);
         n_eval = warp_sum_u64(n_eval);
         if (lane == 0 && n_eval)
             atomicAdd(&P.diag[1], n_eval);
