@@ -93,7 +93,7 @@ float bitsf(uint32_t u)
     return f;
 }
 
-// Error model of the float32 path (derivation in the design doc):
+// Error model of the float32 path:
 //   coordinates are fl32(X - O) with |X - O| <= M; the primary is shifted by
 //   fl32(S), |S| <= Ls (periodic image), then dx = fl32(x_j - x^_i).
 // Per-axis bound on |dx~ - dx_true| for a component of size <= r:
