@@ -393,7 +393,7 @@ def main():
            "diag": {"n_cellpairs": diag.n_cellpairs, "n_rechecked": diag.n_rechecked,
                     "useful_fraction": p_cnt / 2 / max(1, diag.n_evaluated)}}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rows = int(os.environ.get("CF_CPU_ROWS", "12000"))
+        rows = int(os.environ.get("CF_CPU_ROWS", "40000"))
         c, dt, cores = cpu_baseline_sample(cat, edges, rows)
         out["cpu_baseline"] = {"value": c / dt / 1e9, "unit": UNIT, "cores": cores,
                                "kind": "oracle",
