@@ -804,7 +804,7 @@ int run(Request &q)
             tmp.slot = bump.take<uint32_t>(nmax);
             tmp.tmp_idx = bump.take<int>(nmax + 3ll * g.ncols);
             tmp.tmp_key = bump.take<unsigned long long>(nmax + 3ll * g.ncols);
-            tmp.counts = bump.take<uint32_t>(g.ncells);
+            tmp.counts = bump.take<uint32_t>(g.ncells + 1);
             tmp.pad = bump.take<uint32_t>(g.ncols);
             tmp.bsum = bump.take<uint32_t>(g.ncells / 4096 + 2);
             work = bump.take<cf::WorkItem>((size_t)g.ncols * cf::MAX_STENCIL);
@@ -1528,7 +1528,7 @@ int noalloc_xi(int autocorr, const cf_catalog *d1, const cf_catalog *d2, const d
     tmp.slot = bump.take<uint32_t>(nmax);
     tmp.tmp_idx = bump.take<int>(nmax + 3ll * g.ncols);
     tmp.tmp_key = bump.take<unsigned long long>(nmax + 3ll * g.ncols);
-    tmp.counts = bump.take<uint32_t>(g.ncells);
+    tmp.counts = bump.take<uint32_t>(g.ncells + 1);
     tmp.pad = bump.take<uint32_t>(g.ncols);
     tmp.bsum = bump.take<uint32_t>(g.ncells / 4096 + 2);
     const int nstencil_max = autocorr ? ((2 * g.reach_x + 1) * (2 * g.reach_y + 1) + 1) / 2
@@ -1875,7 +1875,7 @@ int batch_plan(cf_batch *b, cudaStream_t st, const std::vector<std::array<double
             tp.slot = bump.take<uint32_t>(nm);
             tp.tmp_idx = bump.take<int>(nm + 3 * ncol);
             tp.tmp_key = bump.take<unsigned long long>(nm + 3 * ncol);
-            tp.counts = bump.take<uint32_t>(nc);
+            tp.counts = bump.take<uint32_t>(nc + 1);
             tp.pad = bump.take<uint32_t>(ncol);
             tp.bsum = bump.take<uint32_t>(nc / 4096 + 2);
         }

@@ -290,10 +290,11 @@ __device__ __forceinline__ uint32_t rank_in(const ulonglong2 *e, uint32_t n, uns
 }
 
 // Rank the cells' real entries by (z, original index) and write the sorted
-// float32 / binary64 copies.  Each warp takes two cells at a time: cells of up
-// to 16 entries are ranked by a half warp each; otherwise the whole warp ranks
-// the two cells one after the other, up to SORT_BUF entries, beyond that
-// against the cell in global memory.  The entries being ranked are copied to a
+// float32 / binary64 copies.  Each warp claims two cells at a time from a
+// counter (cell sizes vary, and a fixed split leaves a partial second wave of
+// blocks): cells of up to 16 entries are ranked by a half warp each; otherwise
+// the whole warp ranks the two cells one after the other, up to SORT_BUF
+// entries, beyond that against the cell in global memory.  The entries being ranked are copied to a
 // per-warp shared buffer as 16-byte (key, index) records: one broadcast load
 // per comparison.
 template <class T>
@@ -304,15 +305,19 @@ __global__ void __launch_bounds__(SORT_THREADS)
                  const unsigned long long *__restrict__ tmp_key, float *__restrict__ xs,
                  float *__restrict__ ys, float *__restrict__ zs, float *__restrict__ ws,
                  unsigned *__restrict__ wmax, double4_32a *__restrict__ pos64,
-                 int *__restrict__ perm)
+                 int *__restrict__ perm, unsigned *__restrict__ claim)
 {
     __shared__ ulonglong2 s_ent[SORT_THREADS / 32][SORT_BUF];
     const int lane = threadIdx.x & 31, half = lane >> 4, hl = lane & 15, wid = threadIdx.x >> 5;
     ulonglong2 *be = s_ent[wid];
     unsigned wm = 0;  // bit pattern of the largest |w| (float) this thread stored
-    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-    for (long long c0 = (((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 2; c0 < ncells;
-         c0 += 2 * nwarps) {
+    for (;;) {
+        unsigned v = 0u;
+        if (lane == 0)
+            v = atomicAdd(claim, 1u);  // the next pair of cells (zeroed with the counts)
+        const long long c0 = 2ll * __shfl_sync(FULL, v, 0);
+        if (c0 >= ncells)
+            break;
         const long long cm = c0 + half;  // this half warp's cell
         const uint32_t cnt = cm < ncells ? count[cm] : 0u;
         const uint32_t s = cm < ncells ? start[cm] : 0u;
@@ -520,7 +525,7 @@ cudaError_t build_grid_t(const void *x, const void *y, const void *z, const doub
 {
     cudaError_t e;
     const long long nc = g.ncells;
-    if ((e = cudaMemsetAsync(t.counts, 0, sizeof(uint32_t) * nc, st)))
+    if ((e = cudaMemsetAsync(t.counts, 0, sizeof(uint32_t) * (nc + 1), st)))  // + the sort's claim counter
         return e;
     const int TB = 256;
     if (n > 0) {
@@ -540,7 +545,8 @@ cudaError_t build_grid_t(const void *x, const void *y, const void *z, const doub
         const long long cwarps = std::min<long long>((nc + 1) / 2, (long long)sms * 64);
         k_sort_cells<T><<<(int)((cwarps * 32 + SORT_THREADS - 1) / SORT_THREADS), SORT_THREADS, 0, st>>>(
             (const T *)x, (const T *)y, w, nc, g, t.counts, out.cell_start, t.tmp_idx, t.tmp_key,
-            out.xs, out.ys, out.zs, out.ws, out.ws ? out.wmax : nullptr, out.pos64, out.perm);
+            out.xs, out.ys, out.zs, out.ws, out.ws ? out.wmax : nullptr, out.pos64, out.perm,
+            t.counts + nc);
     }
     k_padfill<<<(g.ncols + 255) / 256, 256, 0, st>>>(out.cell_start, t.pad, g.ncols, g.nz, out.xs,
                                                       out.ys, out.zs, out.ws, out.pos64, out.perm);

@@ -13,7 +13,7 @@ struct GridTemps {
     uint32_t *slot;      // n
     int *tmp_idx;        // n + 3 * ncols (padded index space)
     unsigned long long *tmp_key;  // n + 3 * ncols: order-preserving keys of z
-    uint32_t *counts;    // ncells
+    uint32_t *counts;    // ncells + 1 (the last: the in-cell sort's claim counter)
     uint32_t *pad;       // ncols
     uint32_t *bsum;      // ceil(ncells / 4096)
 };
