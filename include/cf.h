@@ -259,6 +259,42 @@ int cf_tune_load(const char *path);
 int cf_tune_clear(void);
 int cf_tune_count(void);
 
+/*
+ * Float32 decision tables, for diagnostics and tests (host only: no device
+ * work).  The float32 paths compute a squared separation d2~ in float32, bin
+ * it with a byte table and settle what the table cannot with thresholds, so
+ * that the counts equal the binary64 definition (bins [e_k, e_{k+1}) tested on
+ * squares, Sec. 2.2):
+ *   thr[0 .. 2 nedges): lo_0, hi_0, ..., lo_B, hi_B around E2_k = edges[k]^2
+ *     (binary64), lo_k <= E2_k <= hi_k: d2~ < lo_k proves d2 < E2_k and
+ *     d2~ >= hi_k proves d2 >= E2_k, for float32 coordinates of magnitude
+ *     <= coord_max, a periodic shift of magnitude <= shift_max added to the
+ *     primary in float32, and separations up to rmax; ncomp = 3 for 3-D
+ *     separations, 2 for projected rp.
+ *   table[0 .. lut_n): the entry of cell q is bin k when every value of the
+ *     cell lies in [hi_k, lo_{k+1}), nedges - 1 when every value is surely
+ *     not counted, nedges otherwise.  Value v >= 0 lies in cell
+ *     round(v * lscale) (lin = 1; the float32 product rounded half to even)
+ *     or ((bits(v) >> shift) - u0) mod 2^32 (lin = 0); cells past lut_n - 1
+ *     (and NaN) use entry lut_n - 1.
+ * thr holds 2 * nedges floats; table holds CF_BIN_TABLE_MAX bytes; info gets
+ * the cell parameters.  Errors: CF_EINVAL for NULL pointers, fewer than 2 or
+ * more than 65 edges, edges not finite, negative or not increasing, ncomp
+ * not 2 or 3, and bounds that are negative or not finite.
+ */
+#define CF_BIN_TABLE_MAX 16384
+typedef struct {
+    int nthr;        /* thresholds written: 2 * nedges            */
+    int lut_n;       /* table entries written                     */
+    int lin;         /* 1: linear cells, 0: float-bit cells        */
+    float lscale;    /* linear cells: cell = round(v * lscale)     */
+    int shift;       /* float-bit cells: (bits(v) >> shift) - u0   */
+    unsigned u0;
+} cf_bin_tables;
+int cf_debug_bin_tables(const double *edges, int nedges, int ncomp, double coord_max,
+                        double shift_max, double rmax, float *thr, unsigned char *table,
+                        cf_bin_tables *info);
+
 /* Text of the last non-zero status returned on the calling thread. */
 const char *cf_last_error(void);
 

@@ -36,7 +36,7 @@ _STATUS = {CF_EINVAL: "CF_EINVAL", CF_ENOMEM: "CF_ENOMEM", CF_ECUDA: "CF_ECUDA",
 EXPORTS = ("cf_countpairs_xi", "cf_countpairs_rp_pi", "cf_last_error", "cf_version",
            "cf_countpairs_xi_noalloc", "cf_tune_save", "cf_tune_load", "cf_tune_clear",
            "cf_tune_count", "cf_batch_create", "cf_batch_add_xi", "cf_batch_add_rp_pi",
-           "cf_batch_run", "cf_batch_destroy")
+           "cf_batch_run", "cf_batch_destroy", "cf_debug_bin_tables")
 
 
 class cf_catalog(ctypes.Structure):
@@ -299,6 +299,40 @@ def tune_clear() -> None:
 
 def tune_count() -> int:
     return _tune_call("cf_tune_count")
+
+
+class cf_bin_tables(ctypes.Structure):
+    _fields_ = [("nthr", ctypes.c_int), ("lut_n", ctypes.c_int), ("lin", ctypes.c_int),
+                ("lscale", ctypes.c_float), ("shift", ctypes.c_int), ("u0", ctypes.c_uint)]
+
+
+CF_BIN_TABLE_MAX = 16384
+
+
+def debug_bin_tables(edges, *, ncomp=3, coord_max, shift_max=0.0, rmax=None):
+    """Float32 thresholds and bin table for these edges (``cf_debug_bin_tables``).
+
+    Host only.  Returns (thr float32 [2 * nedges], table uint8 [lut_n], info
+    dict with lin, lscale, shift, u0); see include/cf.h for their meaning.
+    """
+    L = lib()
+    f = L.cf_debug_bin_tables
+    P = ctypes.POINTER
+    f.argtypes = [P(ctypes.c_double), ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                  ctypes.c_double, P(ctypes.c_float), P(ctypes.c_ubyte), P(cf_bin_tables)]
+    f.restype = ctypes.c_int
+    e = np.ascontiguousarray(edges, dtype=np.float64)
+    rmax = float(e[-1]) if rmax is None else float(rmax)
+    thr = np.zeros(max(2 * e.size, 1), dtype=np.float32)
+    tab = np.zeros(CF_BIN_TABLE_MAX, dtype=np.uint8)
+    info = cf_bin_tables()
+    st = f(e.ctypes.data_as(P(ctypes.c_double)), int(e.size), int(ncomp), float(coord_max),
+           float(shift_max), rmax, thr.ctypes.data_as(P(ctypes.c_float)),
+           tab.ctypes.data_as(P(ctypes.c_ubyte)), ctypes.byref(info))
+    if st < 0:
+        raise CfError(st, L.cf_last_error().decode())
+    return thr[:info.nthr].copy(), tab[:info.lut_n].copy(), {
+        "lin": info.lin, "lscale": info.lscale, "shift": info.shift, "u0": info.u0}
 
 
 def countpairs_xi_noalloc(x, y, z, edges, *, x2=None, y2=None, z2=None, autocorr=None,

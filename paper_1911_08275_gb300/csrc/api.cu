@@ -1300,6 +1300,40 @@ const char *cf_last_error(void) { return g_err.c_str(); }
 
 const char *cf_version(void) { return "cfgpu 0.1 sm_103a"; }
 
+static_assert(CF_BIN_TABLE_MAX == cf::LUT_MAX, "the header states the table size");
+
+int cf_debug_bin_tables(const double *edges, int nedges, int ncomp, double coord_max,
+                        double shift_max, double rmax, float *thr, unsigned char *table,
+                        cf_bin_tables *info)
+{
+    if (!edges || !thr || !table || !info)
+        return fail(CF_EINVAL, "NULL argument");
+    if (nedges < 2 || nedges > cf::NB_MAX + 1)
+        return fail(CF_EINVAL, "need 2 to 65 bin edges");
+    for (int k = 0; k < nedges; ++k) {
+        if (!std::isfinite(edges[k]) || edges[k] < 0.0)
+            return fail(CF_EINVAL, "edges must be finite and >= 0");
+        if (k > 0 && !(edges[k] > edges[k - 1]))
+            return fail(CF_EINVAL, "edges must be strictly increasing");
+    }
+    if (ncomp != 2 && ncomp != 3)
+        return fail(CF_EINVAL, "ncomp must be 2 or 3");
+    if (!(coord_max >= 0.0 && std::isfinite(coord_max)) ||
+        !(shift_max >= 0.0 && std::isfinite(shift_max)) || !(rmax >= 0.0 && std::isfinite(rmax)))
+        return fail(CF_EINVAL, "bounds must be finite and >= 0");
+    std::vector<double> E2(nedges);
+    for (int k = 0; k < nedges; ++k)
+        E2[k] = edges[k] * edges[k];
+    const Tables tb = build_tables(E2.data(), nedges, ncomp, coord_max, shift_max, rmax, thr, table);
+    info->nthr = tb.nthr;
+    info->lut_n = tb.lut_n;
+    info->lin = tb.lin;
+    info->lscale = tb.lscale;
+    info->shift = tb.shift;
+    info->u0 = tb.u0s;
+    return CF_OK;
+}
+
 }  // extern "C"
 
 // ============================================================================

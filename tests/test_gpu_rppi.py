@@ -167,6 +167,17 @@ def test_count_evals_and_host_inputs(cuda_device):
     assert b.n_evaluated >= a.npairs.sum() // 2
 
 
+def test_float_bit_cells_for_a_narrow_rp_range(cuda_device):
+    # rp edges over a narrow range: the rp^2 table keeps cells on float32 bit
+    # patterns (the other table shape of the kernels)
+    cat = synth.neyman_scott(1500, 20.0, 2.0, 200.0, seed=47)
+    e = np.linspace(10.0, 12.0, 5)
+    for dtype in (np.float64, np.float32):
+        r, c = gpu_rppi(cat, e, 20.0, 20, dtype, boxsize=200.0)
+        assert r.table_linear == 0
+        assert np.array_equal(r.npairs, oracle_rppi(c, e, 20.0, 20, periodic=True, box=200.0))
+
+
 @pytest.mark.parametrize("bad", ["pimax_half_box", "pimax_zero", "npibins_zero", "too_many_bins"])
 def test_invalid_arguments_rejected(cuda_device, bad):
     cat = synth.uniform_box(100, 10.0, seed=61)

@@ -213,8 +213,8 @@ def test_invalid_inputs_rejected(cuda_device, bad):
     assert r.npairs.shape == (1,)
 
 
-@pytest.mark.parametrize("edges", [synth.log_edges(1e-3, 30.0, 40),  # wide: logarithmic cells
-                                   synth.linear_edges(0.0, 25.0, 25),  # from 0: linear cells
+@pytest.mark.parametrize("edges", [synth.log_edges(1e-3, 30.0, 40),  # wide range
+                                   synth.linear_edges(0.0, 25.0, 25),  # from 0
                                    synth.log_edges(0.1, 25.0, 20)])
 def test_table_shapes_verify_band(cuda_device, edges):
     cat = synth.neyman_scott(1500, 20.0, 2.0, 200.0, seed=44)
@@ -224,6 +224,20 @@ def test_table_shapes_verify_band(cuda_device, edges):
         assert np.array_equal(r.npairs, oracle_xi(c, edges, periodic=True, box=200.0))
         r2, _ = gpu_xi(cat, edges, dtype, boxsize=200.0, pair_chunk=16, pair_pp=2)
         assert np.array_equal(r2.npairs, r.npairs)
+
+
+def test_float_bit_cells_for_a_narrow_edge_range(cuda_device):
+    # Edges over a narrow range make the host keep the table with cells on
+    # float32 bit patterns (finer there than cells linear in d2): the kernels'
+    # other table shape, in the verifying sweep and in the production shape.
+    cat = synth.neyman_scott(1500, 20.0, 2.0, 200.0, seed=46)
+    edges = np.linspace(10.0, 12.0, 9)
+    for dtype in (np.float64, np.float32):
+        for kw in (dict(flags=cf.CF_FLAG_VERIFY_BAND), dict(pair_chunk=16, pair_pp=2)):
+            r, c = gpu_xi(cat, edges, dtype, boxsize=200.0, **kw)
+            assert r.table_linear == 0
+            assert r.n_band_violations == 0
+            assert np.array_equal(r.npairs, oracle_xi(c, edges, periodic=True, box=200.0))
 
 
 @pytest.mark.parametrize("dtype", [np.float32, np.float64])
