@@ -10,7 +10,10 @@
   uniform-box counts N(N-1)/V * (4/3)pi(r_hi^3 - r_lo^3) (Sec. 1.1, analytic
   randoms for a periodic cube) within Poisson scatter;
 * invariants: auto == cross(D, D) when e_0 > 0, permutation and periodic
-  translation invariance, unit weights give wsum == npairs.
+  translation invariance, unit weights give wsum == npairs;
+* the clustered input recipe: Neyman-Scott counts equal uniform background
+  pairs plus sibling pairs whose separation follows the Maxwell law of a 3-D
+  Gaussian with sigma * sqrt(2) per axis, within a conservative scatter.
 """
 import numpy as np
 import pytest
@@ -228,6 +231,39 @@ def test_uniform_xi_closed_form_c1(orc):
     big = mean > 50
     assert np.all(np.abs(z[big]) < 5.0), z
     assert int(n[~big].sum()) <= 2 * (mean[~big].sum() + 5 * np.sqrt(mean[~big].sum()) + 4)
+
+
+def test_neyman_scott_counts_background_plus_siblings(orc):
+    # Children of one parent are offset by N(0, sigma^2) per axis, so a sibling
+    # pair's separation is Maxwell distributed with scale sigma * sqrt(2); two
+    # points of different parents are independent and uniform in the periodic
+    # box.  Given the children counts c_p (S = sum c_p (c_p - 1) ordered sibling
+    # pairs): E[DD_k] = (N (N - 1) - S) V_k / V + S P_k.
+    from scipy.special import erf
+    npar, lam, sig, box, seed = 2000, 5.0, 2.0, 100.0, 50
+    c = synth.neyman_scott(npar, lam, sig, box, seed)
+    cnt = synth.poisson(seed, 3, npar, lam)
+    S = float(np.sum(cnt * (cnt - 1.0)))
+    e = synth.log_edges(0.5, 12.0, 12)
+    n, _, _ = orc.xi(c.x, c.y, c.z, edges=e, periodic=True, box=box)
+    N, V = c.n, box ** 3
+    s = sig * np.sqrt(2.0)
+
+    def maxwell_cdf(r):
+        return erf(r / (s * np.sqrt(2.0))) - np.sqrt(2.0 / np.pi) * (r / s) * np.exp(-r * r / (2 * s * s))
+
+    vk = (4.0 / 3.0) * np.pi * (e[1:] ** 3 - e[:-1] ** 3)
+    bg = (N * (N - 1) - S) * vk / V
+    sib = S * (maxwell_cdf(e[1:]) - maxwell_cdf(e[:-1]))
+    # ordered pairs come in twos; clusters correlate both terms (a cluster pair
+    # or a cluster moves up to ~lam pairs together): a generous scatter
+    sd = np.sqrt(2 * bg * (1 + 2 * lam) + 2 * sib * (1 + lam))
+    z = (n - (bg + sib)) / sd
+    assert np.all(np.abs(z) < 5.0), z
+    # the clustering is visible: between 1 and 2.5 units the counts exceed the
+    # background by more than the scatter allowed above
+    mid = (e[:-1] >= 1.0) & (e[1:] <= 2.5)
+    assert mid.sum() == 3 and np.all((n[mid] - bg[mid]) / sd[mid] > 5.0)
 
 
 def test_uniform_rppi_closed_form(orc):
