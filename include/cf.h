@@ -295,6 +295,19 @@ int cf_debug_bin_tables(const double *edges, int nedges, int ncomp, double coord
                         double shift_max, double rmax, float *thr, unsigned char *table,
                         cf_bin_tables *info);
 
+/*
+ * The pi-bin decision of the float32 DD(rp, pi) path, for diagnostics and
+ * tests (host only).  With pscale = fl32(npibins / pimax) a pair's
+ * t' = fl32(|dz~| * pscale - 1/2) (one rounding) gives m = round(t') (half to
+ * even); the kernels trust bin m (not counted for m >= npibins) when
+ * |t' - m| <= pband and re-check the pair in binary64 otherwise (pband = -1:
+ * always).  Bounds as for cf_debug_bin_tables.  Errors: CF_EINVAL for NULL
+ * pointers, pimax not positive and finite, npibins < 1, bounds negative or not
+ * finite.
+ */
+int cf_debug_pi_band(double pimax, int npibins, double coord_max, double shift_max,
+                     float *pscale, float *pband);
+
 /* Text of the last non-zero status returned on the calling thread. */
 const char *cf_last_error(void);
 

@@ -36,7 +36,7 @@ _STATUS = {CF_EINVAL: "CF_EINVAL", CF_ENOMEM: "CF_ENOMEM", CF_ECUDA: "CF_ECUDA",
 EXPORTS = ("cf_countpairs_xi", "cf_countpairs_rp_pi", "cf_last_error", "cf_version",
            "cf_countpairs_xi_noalloc", "cf_tune_save", "cf_tune_load", "cf_tune_clear",
            "cf_tune_count", "cf_batch_create", "cf_batch_add_xi", "cf_batch_add_rp_pi",
-           "cf_batch_run", "cf_batch_destroy", "cf_debug_bin_tables")
+           "cf_batch_run", "cf_batch_destroy", "cf_debug_bin_tables", "cf_debug_pi_band")
 
 
 class cf_catalog(ctypes.Structure):
@@ -333,6 +333,22 @@ def debug_bin_tables(edges, *, ncomp=3, coord_max, shift_max=0.0, rmax=None):
         raise CfError(st, L.cf_last_error().decode())
     return thr[:info.nthr].copy(), tab[:info.lut_n].copy(), {
         "lin": info.lin, "lscale": info.lscale, "shift": info.shift, "u0": info.u0}
+
+
+def debug_pi_band(pimax, npibins, *, coord_max, shift_max=0.0):
+    """(pscale, pband) of the float32 pi-bin decision (``cf_debug_pi_band``, host only)."""
+    L = lib()
+    f = L.cf_debug_pi_band
+    P = ctypes.POINTER
+    f.argtypes = [ctypes.c_double, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                  P(ctypes.c_float), P(ctypes.c_float)]
+    f.restype = ctypes.c_int
+    ps, pb = ctypes.c_float(), ctypes.c_float()
+    st = f(float(pimax), int(npibins), float(coord_max), float(shift_max), ctypes.byref(ps),
+           ctypes.byref(pb))
+    if st < 0:
+        raise CfError(st, L.cf_last_error().decode())
+    return np.float32(ps.value), np.float32(pb.value)
 
 
 def countpairs_xi_noalloc(x, y, z, edges, *, x2=None, y2=None, z2=None, autocorr=None,

@@ -139,6 +139,21 @@ struct Tables {
     float lscale;
 };
 
+// pi bins: the kernels take t' = fl32(|dz~| * pscale - 1/2), pscale = fl32(npibins / pimax),
+// bin m = round(t') and trust it when |t' - m| <= pband.
+void pi_band(double pimax, int npibins, double M, double Ls, float &pscale, float &pband)
+{
+    const double s = (double)npibins / pimax;
+    pscale = (float)s;
+    // t = |dz| * s: float32 error in t (dz error, the scale's and the fma's
+    // roundings, the binary64 edges' own rounding), doubled for safety.
+    const double tmax = npibins + 1.0;
+    const double eps_z = eps_axis(pimax * (1.0 + 1e-6), M, Ls) + 2.0 * U64 * (M + Ls + 2.0 * pimax);
+    const double beta = 2.0 * (eps_z * s * (1.0 + 1e-6) + (2.0 * tmax + 2.0) * U32 +
+                               4.0 * tmax * U64) + 1e-30;
+    pband = 0.5 - beta > 0.0 ? f32_down(0.5 - beta) : -1.0f;  // -1: every pair re-checked
+}
+
 // Thresholds T[0..2 ne) (see above).
 void build_thresholds(const double *E2, int ne, int ncomp, double M, double Ls, double R, float *T)
 {
@@ -600,15 +615,7 @@ void base_params(const Request &q, const cf::Geom &g, const cf::Gridded &A, cons
     P.nbins = (int)q.edges.size() - 1;
     if (q.kind == 1) {
         P.npibins = q.npibins;
-        const double s = (double)q.npibins / q.pimax;
-        P.pscale = (float)s;
-        // t = |dz| * s: float32 error in t (dz error, the scale's and the fma's
-        // roundings, the binary64 edges' own rounding), doubled for safety.
-        const double tmax = q.npibins + 1.0;
-        const double eps_z = eps_axis(q.pimax * (1.0 + 1e-6), M, Ls) + 2.0 * U64 * (M + Ls + 2.0 * q.pimax);
-        const double beta = 2.0 * (eps_z * s * (1.0 + 1e-6) + (2.0 * tmax + 2.0) * U32 +
-                                   4.0 * tmax * U64) + 1e-30;
-        P.pband = 0.5 - beta > 0.0 ? f32_down(0.5 - beta) : -1.0f;  // -1: every pair re-checked
+        pi_band(q.pimax, q.npibins, M, Ls, P.pscale, P.pband);
     }
 }
 
@@ -1299,6 +1306,20 @@ int cf_tune_count(void)
 const char *cf_last_error(void) { return g_err.c_str(); }
 
 const char *cf_version(void) { return "cfgpu 0.1 sm_103a"; }
+
+int cf_debug_pi_band(double pimax, int npibins, double coord_max, double shift_max,
+                     float *pscale, float *pband)
+{
+    if (!pscale || !pband)
+        return fail(CF_EINVAL, "NULL argument");
+    if (!(pimax > 0.0 && std::isfinite(pimax)) || npibins < 1)
+        return fail(CF_EINVAL, "pimax must be positive and finite, npibins >= 1");
+    if (!(coord_max >= 0.0 && std::isfinite(coord_max)) ||
+        !(shift_max >= 0.0 && std::isfinite(shift_max)))
+        return fail(CF_EINVAL, "bounds must be finite and >= 0");
+    pi_band(pimax, npibins, coord_max, shift_max, *pscale, *pband);
+    return CF_OK;
+}
 
 static_assert(CF_BIN_TABLE_MAX == cf::LUT_MAX, "the header states the table size");
 

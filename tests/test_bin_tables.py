@@ -290,3 +290,83 @@ def test_threshold_decision_matches_binary64_near_every_edge(ncomp, periodic):
         k64 = k64 if 0 <= k64 < nb else -1
         assert k32 == k64, (xi, xj, d2f, d2)
     assert decided > len(pairs) // 10
+
+
+# ---- the pi-bin decision of the float32 DD(rp, pi) path
+
+def pi_decision(dzf, pscale, pband, npi):
+    """The kernels' float32 pi bin of one pair from its float32 dz~: the bin m,
+    -1 (not counted) or None (re-checked in binary64).  t' = fma(|dz~|, pscale,
+    -1/2) rounded once; m = round(t') half to even (t' + 1.5 * 2^23 in float32);
+    g = fl32(pband - |t' - m|) and a set sign bit sends the pair to binary64."""
+    t = f32_round(fr(abs(dzf)) * fr(pscale) - Fraction(1, 2))
+    m = round(fr(t))
+    g = f32_round(fr(pband) - abs(fr(t) - m))
+    if g < 0:
+        return None
+    return m if m < npi else -1
+
+
+def canonical_pi_bin(zi, zj, box, pimax, npi):
+    dz = np.float64(zj) - np.float64(zi)
+    if box is not None:
+        if dz > box / 2:
+            dz = dz - box
+        elif dz < -box / 2:
+            dz = dz + box
+    p = abs(dz)
+    if not p < pimax:
+        return -1
+    P = [(pimax * m) / npi for m in range(npi)]
+    return max(m for m in range(npi) if P[m] <= p)
+
+
+@pytest.mark.parametrize("periodic,pimax,npi", [(True, 40.0, 40), (False, 10.5, 7)])
+def test_pi_decision_matches_binary64_near_every_pi_edge(periodic, pimax, npi):
+    rng = np.random.default_rng(5 + npi)
+    box = 420.0
+    edges = [(pimax * m) / npi for m in range(1, npi)] + [pimax]
+    zs = []
+    for pe in edges:
+        for _ in range(40):
+            zi = rng.uniform(0.0, box)
+            dz = pe * (1.0 + rng.choice([-1.0, 1.0]) * 10.0 ** rng.uniform(-8, -3))
+            zj = zi + rng.choice([-1.0, 1.0]) * dz
+            zs.append((zi, np.mod(zj, box) if periodic else zj))
+    if periodic:
+        origin, M, Ls = 0.0, box, box
+    else:
+        allz = np.array(zs).ravel()
+        origin = float(allz.min())
+        M, Ls = float(allz.max() - origin), 0.0
+    pscale, pband = cf.debug_pi_band(pimax, npi, coord_max=M, shift_max=Ls)
+    assert pscale == F32(npi / pimax) and 0.0 < pband < 0.5
+    decided = 0
+    for zi, zj in zs:
+        if periodic:
+            kz = -box if zj - zi > box / 2 else (box if zj - zi < -box / 2 else 0.0)
+            ti, tj = F32(zi), F32(zj)
+        else:
+            kz = 0.0
+            ti, tj = F32(zi - origin), F32(zj - origin)
+        zh = f32_round(fr(ti) - fr(F32(kz)))
+        dzf = f32_round(fr(tj) - fr(zh))
+        m32 = pi_decision(dzf, pscale, pband, npi)
+        if m32 is None:
+            continue
+        decided += 1
+        assert m32 == canonical_pi_bin(zi, zj, box if periodic else None, pimax, npi), (zi, zj)
+    assert decided > len(zs) // 10
+
+
+def test_pi_band_arguments():
+    with pytest.raises(cf.CfError):
+        cf.debug_pi_band(0.0, 10, coord_max=1.0)
+    with pytest.raises(cf.CfError):
+        cf.debug_pi_band(10.0, 0, coord_max=1.0)
+    with pytest.raises(cf.CfError):
+        cf.debug_pi_band(10.0, 10, coord_max=-1.0)
+    # larger error bounds leave a narrower trusted interval
+    _, b1 = cf.debug_pi_band(40.0, 40, coord_max=420.0, shift_max=420.0)
+    _, b2 = cf.debug_pi_band(40.0, 40, coord_max=4200.0, shift_max=4200.0)
+    assert b2 < b1
