@@ -66,3 +66,18 @@ def test_cross_needs_second_catalogue():
     x = np.zeros(4)
     with pytest.raises(ValueError):
         cf.countpairs_xi(x, x, x, [0.1, 1.0], autocorr=False)
+
+
+def test_no_cpu_fallback_without_a_gpu():
+    # on a host without a usable GPU a counting call reports the CUDA error
+    # (status and message) instead of computing anything on the CPU
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    x = np.random.default_rng(0).uniform(0.0, 10.0, 100)
+    with pytest.raises(cf.CfError) as ei:
+        cf.countpairs_xi(x, x, x, [0.1, 1.0], boxsize=10.0)
+    assert ei.value.status == cf.CF_ECUDA and "CUDA" in str(ei.value)
+    with pytest.raises(cf.CfError) as ei:
+        cf.countpairs_rp_pi(x, x, x, [0.1, 1.0], 2.0, 2, boxsize=10.0)
+    assert ei.value.status == cf.CF_ECUDA
