@@ -78,6 +78,42 @@ def test_wp_closed_forms():
                        [2.0 * (pimax + 0.1 * pimax ** 2 / 2.0), -pimax])
 
 
+def test_wp_of_neyman_scott_matches_its_closed_form():
+    # Siblings (children of one parent, offsets N(0, sigma^2) per axis) are
+    # separated by a Gaussian of sigma * sqrt(2) per axis, so their projected
+    # separation falls in the annulus [a, b) with probability
+    # P = exp(-a^2 / 4 sigma^2) - exp(-b^2 / 4 sigma^2), and |dz| < pimax almost
+    # surely (pimax >> sigma); pairs of different parents are uniform.  With S
+    # ordered sibling pairs, xi(rp, pi) = DD / RR - 1 integrates to
+    #   E[wp] = S V / (N (N - 1)) * (P / (pi (b^2 - a^2)) - 2 pimax / V).
+    npar, lam, sig, box, seed = 5000, 5.0, 2.0, 100.0, 52
+    cat = synth.neyman_scott(npar, lam, sig, box, seed)
+    cnt = synth.poisson(seed, 3, npar, lam)
+    S = float(np.sum(cnt * (cnt - 1.0)))
+    N, V = cat.n, box ** 3
+    rp_e = synth.log_edges(0.5, 8.0, 8)
+    pimax, npi = 20.0, 20
+    dd = oracle.rppi(cat.x, cat.y, cat.z, rp_edges=rp_e, pimax=pimax, npibins=npi,
+                     periodic=True, box=box)[0].astype(float)
+    rr = est.rr_analytic_rppi(rp_e, pimax, npi, N, box)
+    wp = est.wp_from_xi(est.xi_natural(dd, rr), pimax, npi)
+    a, b = rp_e[:-1], rp_e[1:]
+    area = np.pi * (b * b - a * a)
+    P = np.exp(-a * a / (4 * sig * sig)) - np.exp(-b * b / (4 * sig * sig))
+    want = S * V / (N * (N - 1.0)) * (P / area - 2.0 * pimax / V)
+    # scatter of the summed counts: sibling pairs move together within a cluster,
+    # background pairs between two clusters (ordered pairs come in twos)
+    sib, bg = S * P, N * (N - 1.0) * area * 2.0 * pimax / V
+    sd = np.sqrt(2 * sib * (1 + lam) + 2 * bg * (1 + 2 * lam)) * V / (N * (N - 1.0) * area)
+    z = (wp - want) / sd
+    assert np.all(np.abs(z) < 5.0), z
+    # the check has power: a generator with sigma doubled lands several of these
+    # (deliberately generous) standard deviations away
+    P2 = np.exp(-a * a / (16 * sig * sig)) - np.exp(-b * b / (16 * sig * sig))
+    wrong = S * V / (N * (N - 1.0)) * (P2 / area - 2.0 * pimax / V)
+    assert np.max(np.abs(wp - wrong) / sd) > 4.0
+
+
 def test_landy_szalay_identities():
     nd, nr = 100, 1000
     rr = np.array([5000.0, 20000.0, 0.0])
