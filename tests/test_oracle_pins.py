@@ -366,3 +366,36 @@ def pin_cases():
             (a,) = extra
             out.extend((fn, {a: v}) for v in params[a])
     return out
+
+
+_THREADS_PROBE = r"""
+import json, sys
+sys.path.insert(0, {root!r})
+import oracle
+from paper_1911_08275_gb300 import synth
+c = synth.neyman_scott(300, 10.0, 2.0, 60.0, seed=61)
+w = synth.uniform_weights(c.n, 0.5, 1.5, seed=62)
+e = synth.log_edges(0.2, 12.0, 10)
+n, ws, rs = oracle.xi(c.x, c.y, c.z, edges=e, w1=w, periodic=True, box=60.0, want_r=True)
+print(json.dumps([oracle.num_threads(), [int(v) for v in n], [float(v).hex() for v in ws],
+                  [float(v).hex() for v in rs]]))
+"""
+
+
+def test_sums_do_not_depend_on_the_thread_count():
+    # fixed row blocks combined in block order: the binary64 sums are the same
+    # bits whatever the number of OpenMP threads
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    outs = []
+    for t in ("1", "3", "8"):
+        env = dict(os.environ, OMP_NUM_THREADS=t)
+        r = subprocess.run([sys.executable, "-c", _THREADS_PROBE.format(root=root)], env=env,
+                           capture_output=True, text=True, check=True)
+        outs.append(json.loads(r.stdout.strip().splitlines()[-1]))
+    assert [o[0] for o in outs][:2] == [1, 3]
+    assert all(o[1:] == outs[0][1:] for o in outs)
+    assert sum(outs[0][1]) > 0
