@@ -31,6 +31,7 @@ MUTANTS = {
     "weight_wrong_index": ("pw = a->w[i] * b->w[j];", "pw = a->w[i] * b->w[i];"),
     "weight_sum_not_product": ("pw = a->w[i] * b->w[j];", "pw = a->w[i] + b->w[j];"),
     "ravg_unsquared": ("const double rv = sqrt(s) * pw;", "const double rv = s * pw;"),
+    "rppi_ravg_uses_r": ("s = rp2;", "s = rp2 + dz * dz;"),
     "pi_without_abs": ("pibin_of(fabs(dz), jb->P", "pibin_of(dz, jb->P"),
     "pi_edges_shifted": ("P[m] = (pimax * (double)m) / (double)npibins;",
                          "P[m] = (pimax * (double)(m + 1)) / (double)npibins;"),

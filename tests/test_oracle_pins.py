@@ -134,6 +134,31 @@ def test_weights_and_ravg_hand_enumerated(orc):
     assert rs.tolist() == [10.0, 24.0, 26.0] and ws is None
 
 
+def test_rppi_weights_and_ravg_hand_enumerated(orc):
+    # Sec. 1.1 Code 1's weight per pair with the rp-pi separations of Eq.
+    # "separations": the mean separation of an (rp, pi) slot is the mean rp,
+    # not r.  Dyadic inputs, so every sum below is exact in binary64.
+    x, y, z = pts((0, 0, 0), (3, 4, 2.5), (6, 8, 1))
+    w = np.array([0.5, 2.0, 4.0])
+    # pairs: (0,1) rp=5 pi=2.5 w=1; (1,2) rp=5 pi=1.5 w=8; (0,2) rp=10 pi=1 w=2
+    rp, kw = [4.0, 6.0, 11.0], dict(pimax=4.0, npibins=4, periodic=False, want_r=True)
+    n, ws, rs = orc.rppi(x, y, z, w1=w, rp_edges=rp, **kw)
+    want_n = np.zeros((2, 4), dtype=np.uint64)
+    want_w, want_r = np.zeros((2, 4)), np.zeros((2, 4))
+    want_n[0, 2], want_w[0, 2], want_r[0, 2] = 2, 2.0, 10.0     # 2 x (w 1, rp 5)
+    want_n[0, 1], want_w[0, 1], want_r[0, 1] = 2, 16.0, 80.0    # 2 x (w 8, rp 5 w 8)
+    want_n[1, 1], want_w[1, 1], want_r[1, 1] = 2, 4.0, 40.0     # 2 x (w 2, rp 10 w 2)
+    assert np.array_equal(n, want_n)
+    assert ws.tolist() == want_w.tolist() and rs.tolist() == want_r.tolist()
+    n, ws, rs = orc.rppi(x, y, z, rp_edges=rp, **kw)               # unweighted: sum of rp
+    assert ws is None and rs[0, 2] == 10.0 and rs[0, 1] == 10.0 and rs[1, 1] == 20.0
+    # cross: point 0 against points 1, 2, one ordered pair each
+    n, ws, rs = orc.rppi(x[:1], y[:1], z[:1], w1=w[:1], x2=x[1:], y2=y[1:], z2=z[1:], w2=w[1:],
+                         rp_edges=rp, autocorr=False, **kw)
+    assert n[0, 2] == 1 and n[1, 1] == 1 and int(n.sum()) == 2
+    assert ws[0, 2] == 1.0 and ws[1, 1] == 2.0 and rs[0, 2] == 5.0 and rs[1, 1] == 20.0
+
+
 # ---------------------------------------------------------------- library pins (SciPy)
 
 def _kd_hist(a_xyz, b_xyz, edges, box, w=None):
