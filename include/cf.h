@@ -175,13 +175,17 @@ int cf_countpairs_rp_pi(int autocorr, const cf_catalog *d1, const cf_catalog *d2
  *   - all device scratch comes from one static device array of 32 MiB inside
  *     the library (held by every GPU that loads it until the process exits);
  *     nothing is allocated or freed by the call;
- *   - each catalogue has at most 131072 points; larger problems, or grids that
- *     do not fit the array, return CF_EINVAL with a message saying so;
+ *   - each catalogue has at most 131072 points (CF_EINVAL above that).  When
+ *     the grid the planner would choose does not fit the array (mostly the
+ *     column-pair list of fine grids), the call plans coarser columns and
+ *     z-cells until it fits; the counts do not depend on the grid;
  *   - coordinates must already be in device memory; no weights, no ravg;
  *     CF_FLAG_VERIFY_BAND is ignored; kernel_ms and total_ms are reported as 0;
- *   - the first call on each device looks up the array's device address
- *     (cudaGetSymbolAddress) while that device is current: make that first
- *     call before any stream capture;
+ *   - the first call in each CUDA context (the first call on a device, and
+ *     again after a device reset) looks up the array's device address with
+ *     cudaGetSymbolAddress while that device is current: make that first call
+ *     before any stream capture.  Every call synchronises cfg->stream (twice
+ *     for open boxes) and returns CF_EINVAL if that stream is being captured;
  *   - every call on a device reuses the same array: calls whose GPU work
  *     overlaps (concurrent streams or threads) race and must be serialised.
  */

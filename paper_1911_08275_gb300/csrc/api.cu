@@ -1396,23 +1396,76 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
 namespace {
 
 std::mutex g_noalloc_mu;
-void *g_noalloc_ptr[64] = {};
 
-// Device address of the static scratch on device `dev` (set up once per device).
+// Unique id of the calling thread's current CUDA context (cuCtxGetId, reached
+// through the runtime's driver entry points so the library does not link the
+// driver library).  A device reset or a new context gets a new id.
+typedef int (*PfnCtxGetCurrent)(void **);
+typedef int (*PfnCtxGetId)(void *, unsigned long long *);
+
+bool current_context_id(int dev, unsigned long long &id)
+{
+    static PfnCtxGetCurrent get_current = nullptr;
+    static PfnCtxGetId get_id = nullptr;
+    static bool looked_up = false;
+    if (!looked_up) {  // under g_noalloc_mu
+        looked_up = true;
+        cudaDriverEntryPointQueryResult q1, q2;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", (void **)&get_current, 12000,
+                                             cudaEnableDefault, &q1) != cudaSuccess ||
+            q1 != cudaDriverEntryPointSuccess)
+            get_current = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", (void **)&get_id, 12000,
+                                             cudaEnableDefault, &q2) != cudaSuccess ||
+            q2 != cudaDriverEntryPointSuccess)
+            get_id = nullptr;
+        cudaGetLastError();
+    }
+    if (!get_current || !get_id)
+        return false;
+    void *ctx = nullptr;
+    if (get_current(&ctx) != 0 || !ctx) {
+        // no current context yet: make the device's primary context current
+        if (cudaSetDevice(dev) != cudaSuccess || get_current(&ctx) != 0 || !ctx) {
+            cudaGetLastError();
+            return false;
+        }
+    }
+    return get_id(ctx, &id) == 0;
+}
+
+// Device address of the static scratch in the current context.  The lookup
+// (cudaGetSymbolAddress, with the device current) runs once per CUDA context:
+// the first call on a device, and again after a device reset or on another
+// context, since the address of a module's array belongs to its context.
+struct NoallocAddr {
+    unsigned long long ctx_id;
+    void *ptr;
+};
+NoallocAddr g_noalloc_addr[64] = {};
+int g_noalloc_next = 0;
+
 int noalloc_scratch(int dev, void **out)
 {
-    if (dev < 0 || dev >= 64)
-        return fail(CF_EINVAL, "device ordinal out of range for the no-alloc scratch");
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
-        void *p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p)
-            return cuda_fail(e != cudaSuccess ? e : cudaErrorInvalidSymbol,
-                             "cudaGetSymbolAddress(no-alloc scratch)");
-        g_noalloc_ptr[dev] = p;
+    unsigned long long id = 0;
+    const bool have_id = current_context_id(dev, id);
+    if (have_id)
+        for (const NoallocAddr &a : g_noalloc_addr)
+            if (a.ptr && a.ctx_id == id) {
+                *out = a.ptr;
+                return CF_OK;
+            }
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p)
+        return cuda_fail(e != cudaSuccess ? e : cudaErrorInvalidSymbol,
+                         "cudaGetSymbolAddress(no-alloc scratch)");
+    if (have_id) {  // without a context id the lookup simply runs on every call
+        g_noalloc_addr[g_noalloc_next] = NoallocAddr{id, p};
+        g_noalloc_next = (g_noalloc_next + 1) % 64;
     }
-    *out = g_noalloc_ptr[dev];
+    *out = p;
     return CF_OK;
 }
 
@@ -1421,6 +1474,15 @@ int noalloc_xi(int autocorr, const cf_catalog *d1, const cf_catalog *d2, const d
 {
     if (!c || !res || !res->npairs || !d1 || (!autocorr && !d2))
         return fail(CF_EINVAL, "NULL argument");
+    {  // first, before any other CUDA call: the call synchronises its stream
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        const cudaError_t ec = cudaStreamIsCapturing((cudaStream_t)c->stream, &cap);
+        if (ec != cudaSuccess)
+            return cuda_fail(ec, "cudaStreamIsCapturing");
+        if (cap != cudaStreamCaptureStatusNone)
+            return fail(CF_EINVAL, "no-alloc entry point: it synchronises its stream, so it "
+                                   "cannot be called while that stream is being captured");
+    }
     if (!edges || nedges < 2 || nedges - 1 > cf::NB_MAX)
         return fail(CF_EINVAL, "need 2..65 bin edges");
     if (c->dtype != CF_FLOAT32 && c->dtype != CF_FLOAT64)
@@ -1527,15 +1589,9 @@ int noalloc_xi(int autocorr, const cf_catalog *d1, const cf_catalog *d2, const d
                 hi[a] = cf::decode_dkey(h.keys[3 + a]);
             }
     }
-    int rx = c->refine[0], ry = c->refine[1], rz = c->refine[2];
-    if (rx == 0 && ry == 0 && rz == 0) {
-        rx = 2;
-        ry = 2;
-        rz = 1;
-    }
-    rx = std::max(1, std::min(rx, cf::MAX_REACH));
-    ry = std::max(1, std::min(ry, cf::MAX_REACH));
-    rz = std::max(1, rz);
+    int rr[3];
+    resolve_refine(c, rr);
+    const int rx = rr[0], ry = rr[1], rz = rr[2];
     for (int a = 0; a < 3; ++a) {
         g.origin[a] = g.periodic ? 0.0 : lo[a];
         g.extent[a] = g.periodic ? c->boxsize[a] : std::max(hi[a] - lo[a], 0.0);
@@ -1547,50 +1603,73 @@ int noalloc_xi(int autocorr, const cf_catalog *d1, const cf_catalog *d2, const d
         const double per = std::floor(ext / (R * (1.0 + delta)));
         return (int)std::max(1ll, (long long)std::max(1.0, std::min(per, 8192.0)) * r);
     };
+    // z-cells of the in-column sort for a given column count (plan_geom's rule)
+    auto zcells = [&](long long ncols) {
+        long long nz = (long long)std::floor((double)ntot / ncols * rz / 16.0);
+        nz = std::max(1ll, std::min(nz, 1ll << 16));
+        while (nz > 1 && ncols * nz > NOALLOC_MAX_CELLS)
+            nz /= 2;
+        return nz;
+    };
     g.ncx = ncol(g.extent[0], rx);
     g.ncy = ncol(g.extent[1], ry);
     while ((long long)g.ncx * g.ncy > NOALLOC_MAX_COLS) {  // wider columns stay correct
         g.ncx = std::max(1, g.ncx / 2);
         g.ncy = std::max(1, g.ncy / 2);
     }
-    g.ncols = g.ncx * g.ncy;
+    g.nz = (int)zcells((long long)g.ncx * g.ncy);
     g.reach_x = rx;
     g.reach_y = ry;
-    long long nz = (long long)std::floor((double)ntot / g.ncols * rz / 16.0);
-    nz = std::max(1ll, std::min(nz, 1ll << 16));
-    while (nz > 1 && (long long)g.ncols * nz > NOALLOC_MAX_CELLS)
-        nz /= 2;
-    g.nz = (int)nz;
-    g.ncells = (long long)g.ncols * g.nz;
+    const int nstencil_max = autocorr ? ((2 * g.reach_x + 1) * (2 * g.reach_y + 1) + 1) / 2
+                                      : (2 * g.reach_x + 1) * (2 * g.reach_y + 1);
+    cf::Gridded G[2] = {};
+    cf::GridTemps tmp = {};
+    cf::WorkItem *work = nullptr;
+    // Carve the grids, temporaries and the work list for the current geometry
+    // out of the array; if they do not fit, plan coarser (columns at least
+    // Rmax / refine wide stay correct at any width, and fewer z-cells only make
+    // the in-column sort work harder) and try again.
+    for (;;) {
+        g.ncols = g.ncx * g.ncy;
+        g.ncells = (long long)g.ncols * g.nz;
+        Bump b = bump;
+        for (int t = 0; t < ncat; ++t) {
+            const long long n = cats[t]->n + 3ll * g.ncols;  // columns padded to 4
+            G[t] = cf::Gridded{};
+            G[t].xs = b.take<float>(n);
+            G[t].ys = b.take<float>(n);
+            G[t].zs = b.take<float>(n);
+            G[t].pos64 = b.take<double4_32a>(n);
+            G[t].perm = b.take<int>(n);
+            G[t].cell_start = b.take<uint32_t>(g.ncells + 1);
+            G[t].colbox = b.take<double4_32a>(g.ncols);
+        }
+        tmp.cell_of = b.take<uint32_t>(nmax);
+        tmp.slot = b.take<uint32_t>(nmax);
+        tmp.tmp_idx = b.take<int>(nmax + 3ll * g.ncols);
+        tmp.tmp_key = b.take<unsigned long long>(nmax + 3ll * g.ncols);
+        tmp.counts = b.take<uint32_t>(g.ncells + 1);
+        tmp.pad = b.take<uint32_t>(g.ncols);
+        tmp.bsum = b.take<uint32_t>(g.ncells / 4096 + 2);
+        work = b.take<cf::WorkItem>((size_t)g.ncols * nstencil_max);
+        if (b.off <= NOALLOC_BYTES) {
+            bump = b;
+            break;
+        }
+        if (g.ncx > 1 || g.ncy > 1) {
+            g.ncx = std::max(1, g.ncx / 2);
+            g.ncy = std::max(1, g.ncy / 2);
+            g.nz = (int)zcells((long long)g.ncx * g.ncy);
+        } else if (g.nz > 1) {
+            g.nz /= 2;
+        } else {
+            return fail(CF_EINVAL, "no-alloc entry point: problem does not fit the 32 MiB static scratch");
+        }
+    }
     g.inv_w[0] = g.ncx / std::max(g.extent[0], 1e-300);
     g.inv_w[1] = g.ncy / std::max(g.extent[1], 1e-300);
     g.inv_w[2] = g.nz / std::max(g.extent[2], 1e-300);
     finish_geom(g);
-
-    cf::Gridded G[2] = {};
-    cf::GridTemps tmp = {};
-    for (int t = 0; t < ncat; ++t) {
-        const long long n = cats[t]->n + 3ll * g.ncols;  // columns padded to 4
-        G[t].xs = bump.take<float>(n);
-        G[t].ys = bump.take<float>(n);
-        G[t].zs = bump.take<float>(n);
-        G[t].pos64 = bump.take<double4_32a>(n);
-        G[t].perm = bump.take<int>(n);
-        G[t].cell_start = bump.take<uint32_t>(g.ncells + 1);
-        G[t].colbox = bump.take<double4_32a>(g.ncols);
-    }
-    tmp.cell_of = bump.take<uint32_t>(nmax);
-    tmp.slot = bump.take<uint32_t>(nmax);
-    tmp.tmp_idx = bump.take<int>(nmax + 3ll * g.ncols);
-    tmp.tmp_key = bump.take<unsigned long long>(nmax + 3ll * g.ncols);
-    tmp.counts = bump.take<uint32_t>(g.ncells + 1);
-    tmp.pad = bump.take<uint32_t>(g.ncols);
-    tmp.bsum = bump.take<uint32_t>(g.ncells / 4096 + 2);
-    const int nstencil_max = autocorr ? ((2 * g.reach_x + 1) * (2 * g.reach_y + 1) + 1) / 2
-                                      : (2 * g.reach_x + 1) * (2 * g.reach_y + 1);
-    cf::WorkItem *work = bump.take<cf::WorkItem>((size_t)g.ncols * nstencil_max);
-    if (bump.off > NOALLOC_BYTES)
-        return fail(CF_EINVAL, "no-alloc entry point: problem does not fit the 32 MiB static scratch");
 
     if ((e = cudaMemsetAsync(d_ctr, 0, 2 * sizeof(unsigned), st)) ||
         (e = cudaMemsetAsync(d_hist, 0, sizeof(unsigned long long) * nb, st)) ||

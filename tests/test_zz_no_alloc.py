@@ -2,11 +2,23 @@
 
 It serves callers that cannot allocate device memory while counting (their GPU
 memory is owned by another allocator, or they must not wait on cudaMalloc): all
-scratch lives in a static device array inside the library.  The test calls it
-through the C ABI twice in a row on different catalogues -- the second call must
-not see the first call's leftovers in the shared array -- and requires integer
-counts identical to cf_countpairs_xi (the tolerance of every count test here is
-exact equality).  This file is named to be collected last.
+scratch lives in a static device array inside the library.  The tests call it
+through the C ABI and require integer counts identical to cf_countpairs_xi (the
+tolerance of every count test here is exact equality):
+
+* twice in a row on different catalogues, so the second call must not see the
+  first call's leftovers in the shared array;
+* cross and open-box counts;
+* grids the planner must coarsen: a fine grid whose column count exceeds the
+  array's column cap, and a cross-correlation of two 131072-point catalogues
+  whose column-pair list alone would not fit the array at the planner's grid
+  (box / Rmax = 84).  With at most 131072 points per catalogue a grid of one
+  column always fits (about 16 MiB), so the coarsening loop always ends with a
+  grid that fits and its "does not fit" error stays a guard; the size limit's
+  error is what a caller can meet, and is tested;
+* a capturing stream is refused (the call synchronises its stream).
+
+This file is named to be collected last.
 """
 import numpy as np
 import pytest
@@ -47,7 +59,48 @@ def test_noalloc_cross_and_open_box(cuda_device):
         assert np.array_equal(got.npairs, want.npairs)
 
 
+def test_noalloc_fine_grid_is_coarsened(cuda_device):
+    # box 420, Rmax 2, refine 2: the planner's grid has 420 x 420 columns, more
+    # than the array's column cap; the halved grid must count the same pairs
+    cat = synth.uniform_box(100000, 420.0, seed=77)
+    e = synth.log_edges(0.05, 2.0, 8)
+    xyz = _dev(cat)
+    want = cf.countpairs_xi(*xyz, e, boxsize=420.0)
+    got = cf.countpairs_xi_noalloc(*xyz, e, boxsize=420.0)
+    assert np.array_equal(got.npairs, want.npairs) and got.npairs.sum() > 0
+
+
+@pytest.mark.parametrize("periodic", [True, False])
+def test_noalloc_cross_at_the_size_limit(cuda_device, periodic):
+    # two catalogues of 131072 points, box / Rmax = 84: the cross work list of
+    # the planner's 168 x 168 columns needs more than the 32 MiB array
+    a = synth.uniform_box(131072, 420.0, seed=78)
+    b = synth.uniform_box(131072, 420.0, seed=79)
+    e = synth.log_edges(0.1, 5.0, 10)
+    xa, xb = _dev(a), _dev(b)
+    kw = dict(x2=xb[0], y2=xb[1], z2=xb[2], periodic=periodic, boxsize=420.0)
+    want = cf.countpairs_xi(*xa, e, **kw)
+    got = cf.countpairs_xi_noalloc(*xa, e, **kw)
+    assert np.array_equal(got.npairs, want.npairs) and got.npairs.sum() > 0
+
+
 def test_noalloc_rejects_too_many_points(cuda_device):
     cat = synth.uniform_box(131073, 100.0, seed=75)
     with pytest.raises(cf.CfError, match="131072"):
         cf.countpairs_xi_noalloc(*_dev(cat), [0.1, 1.0], boxsize=100.0)
+
+
+@pytest.mark.filterwarnings("ignore:The CUDA Graph is empty")  # nothing may be captured
+def test_noalloc_rejects_a_capturing_stream(cuda_device):
+    import torch
+    cat = synth.uniform_box(2000, 50.0, seed=76)
+    xyz = _dev(cat)
+    first = cf.countpairs_xi_noalloc(*xyz, [0.5, 2.0], boxsize=50.0)  # set-up outside capture
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with pytest.raises(cf.CfError, match="captured"):
+        with torch.cuda.graph(g, stream=s):
+            cf.countpairs_xi_noalloc(*xyz, [0.5, 2.0], boxsize=50.0, stream=s.cuda_stream)
+    torch.cuda.synchronize()
+    again = cf.countpairs_xi_noalloc(*xyz, [0.5, 2.0], boxsize=50.0)  # the context is fine
+    assert np.array_equal(again.npairs, first.npairs) and first.npairs.sum() > 0
