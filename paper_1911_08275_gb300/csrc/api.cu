@@ -683,6 +683,8 @@ int run(Request &q)
     unsigned long long *bbox_keys = nullptr;
     unsigned *d_err = nullptr, *d_ctr = nullptr, *d_wcount = nullptr;
     cf::WorkItem *work = nullptr;
+    cf::Win *wins = nullptr;
+    long long win_cap = 0;
     long long *wscratch = nullptr;
     unsigned long long *d_hist = nullptr, *d_diag = nullptr;
     float *d_thr = nullptr;
@@ -815,6 +817,15 @@ int run(Request &q)
             tmp.pad = bump.take<uint32_t>(g.ncols);
             tmp.bsum = bump.take<uint32_t>(g.ncells / 4096 + 2);
             work = bump.take<cf::WorkItem>((size_t)g.ncols * cf::MAX_STENCIL);
+            if (q.kind == 0 && !f64) {  // window records of the float32 DD(r) kernels
+                const int sx = 2 * g.reach_x + 1, sy = 2 * g.reach_y + 1;
+                const int nst = q.autocorr ? (sx * sy + 1) / 2 : sx * sy;
+                const int ch = cf::xi32_chunk(c->pair_chunk ? c->pair_chunk : 16,
+                                              c->pair_pp ? c->pair_pp : 2, wacc,
+                                              (c->flags & CF_FLAG_VERIFY_BAND) != 0);
+                win_cap = cf::win_bound(cats[0]->n, g.ncols, nst, ch);
+                wins = bump.take<cf::Win>((size_t)win_cap);
+            }
             // float32 weighted DD(r): 64-bit sums per thread of at most 2 CTAs per SM
             wscratch = (wacc && !f64 && q.kind == 0) ? bump.take<long long>((size_t)sms * 2 * cf::THREADS * 3 * nb)
                                                      : nullptr;
@@ -842,6 +853,9 @@ int run(Request &q)
         double M = 0.0, Ls = 0.0;
         base_params(q, g, G[0], G[1], P, M, Ls);
         P.work = work;
+        P.win = wins;
+        P.win_cap = win_cap;
+        P.win_count = d_err + 3;  // zeroed with the result block
         P.wscratch = wscratch;
         if (q.kind == 1) {
             std::memcpy(ho->pe, Pe.data(), 8 * Pe.size());
@@ -959,7 +973,7 @@ int run(Request &q)
         for (int t = 0; t < ncat; ++t)
             res->n_kernels += cf::grid_kernels(cats[t]->n) +
                               (c->periodic ? 0 : cf::bbox_kernels(cats[t]->n));
-        res->n_kernels += P.n_items > 0 ? 2 : 0;  // work list + pair kernel
+        res->n_kernels += PL.kernels;  // work list, window pre-pass, pair kernel
     }
     rc = CF_OK;
 cleanup:
@@ -1554,7 +1568,7 @@ int noalloc_xi(int autocorr, const cf_catalog *d1, const cf_catalog *d2, const d
     bump.base = (char *)scratch;
     unsigned long long *bbox_keys = bump.take<unsigned long long>(6);
     unsigned *d_err = bump.take<unsigned>(1);
-    unsigned *d_ctr = bump.take<unsigned>(2);  // [0] item counter, [1] kept column pairs
+    unsigned *d_ctr = bump.take<unsigned>(3);  // [0] item counter, [1] kept column pairs, [2] window records
     unsigned long long *d_hist = bump.take<unsigned long long>(cf::NB_MAX);
     unsigned long long *d_diag = bump.take<unsigned long long>(4);
     float *d_thr = bump.take<float>(2 * (cf::NB_MAX + 1));
@@ -1625,6 +1639,9 @@ int noalloc_xi(int autocorr, const cf_catalog *d1, const cf_catalog *d2, const d
     cf::Gridded G[2] = {};
     cf::GridTemps tmp = {};
     cf::WorkItem *work = nullptr;
+    cf::Win *wins = nullptr;
+    long long win_cap = 0;
+    const int win_ch = cf::xi32_chunk(16, 2, false, false);  // the kernel shape of this entry point
     // Carve the grids, temporaries and the work list for the current geometry
     // out of the array; if they do not fit, plan coarser (columns at least
     // Rmax / refine wide stay correct at any width, and fewer z-cells only make
@@ -1652,6 +1669,8 @@ int noalloc_xi(int autocorr, const cf_catalog *d1, const cf_catalog *d2, const d
         tmp.pad = b.take<uint32_t>(g.ncols);
         tmp.bsum = b.take<uint32_t>(g.ncells / 4096 + 2);
         work = b.take<cf::WorkItem>((size_t)g.ncols * nstencil_max);
+        win_cap = f64 ? 0 : cf::win_bound(cats[0]->n, g.ncols, nstencil_max, win_ch);
+        wins = f64 ? nullptr : b.take<cf::Win>((size_t)win_cap);
         if (b.off <= NOALLOC_BYTES) {
             bump = b;
             break;
@@ -1671,7 +1690,7 @@ int noalloc_xi(int autocorr, const cf_catalog *d1, const cf_catalog *d2, const d
     g.inv_w[2] = g.nz / std::max(g.extent[2], 1e-300);
     finish_geom(g);
 
-    if ((e = cudaMemsetAsync(d_ctr, 0, 2 * sizeof(unsigned), st)) ||
+    if ((e = cudaMemsetAsync(d_ctr, 0, 3 * sizeof(unsigned), st)) ||
         (e = cudaMemsetAsync(d_hist, 0, sizeof(unsigned long long) * nb, st)) ||
         (e = cudaMemsetAsync(d_diag, 0, sizeof(unsigned long long) * 4, st)))
         return cuda_fail(e, "memset");
@@ -1701,6 +1720,9 @@ int noalloc_xi(int autocorr, const cf_catalog *d1, const cf_catalog *d2, const d
     P.n_items = g.ncols * P.nstencil;
     P.work = work;
     P.work_count = d_ctr + 1;
+    P.win = wins;
+    P.win_cap = win_cap;
+    P.win_count = d_ctr + 2;
     P.tile_max = 1024;
     P.flags = c->flags & (CF_FLAG_NO_PRUNE | CF_FLAG_COUNT_EVALS);
     const double M = std::max(g.extent[0], std::max(g.extent[1], g.extent[2]));
@@ -1767,7 +1789,7 @@ int noalloc_xi(int autocorr, const cf_catalog *d1, const cf_catalog *d2, const d
     res->n_rechecked = h.diag[2];
     for (int t = 0; t < ncat; ++t)
         res->n_kernels += cf::grid_kernels(cats[t]->n) + (c->periodic ? 0 : cf::bbox_kernels(cats[t]->n));
-    res->n_kernels += P.n_items > 0 ? 2 : 0;  // work list + pair kernel
+    res->n_kernels += PL.kernels;  // work list, window pre-pass, pair kernel
     return CF_OK;
 }
 

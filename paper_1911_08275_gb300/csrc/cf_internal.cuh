@@ -95,9 +95,26 @@ struct Gridded {
 struct __align__(16) WorkItem {
     int a0, a1, b0, b1;  // point ranges of columns a and b
     double dzmax;        // z reach of the pair (binary64, already widened)
-    int code;            // bits 0-1: qx + 1, bits 2-3: qy + 1 (periodic image), bit 4: self pair
-    int pad;
+    int code;            // bits 0-1: qx + 1, bits 2-3: qy + 1 (periodic image), bit 4: self pair,
+                         // bits 5-31: column b
+    int wbase;           // first window record of the pair's chunks (window pre-pass), else 0
 };
+
+// Window record of one chunk of column a against column b (window pre-pass):
+// for each periodic z image k = -1, 0, +1 the range [lo, hi) of column b (point
+// indices) whose float32 z can lie within the pair's z reach of the chunk; an
+// empty range (lo == hi) when the image does not apply.
+struct __align__(8) Win {
+    int lo[3], hi[3];
+};
+
+// Cell index along one axis from a float32 frame coordinate (monotone in it):
+// the gridding's rule, also used to locate a z value among a column's z-cells.
+__device__ __forceinline__ int cell_index_f(float t, float inv_w, int n)
+{
+    const float c = floorf(__fmul_rn(t, inv_w));
+    return (int)fminf(fmaxf(c, 0.0f), (float)(n - 1));
+}
 
 // Everything a pair kernel needs (passed by value, lives in the constant bank).
 struct PairParams {
@@ -111,6 +128,10 @@ struct PairParams {
     int shard_k, shard_n;  // keep columns whose first point lies in slice k of n (n > 1)
     WorkItem *work;     // kept column pairs (work-list kernel output)
     unsigned *work_count;  // number of kept column pairs
+    Win *win;           // window records (window pre-pass), NULL = windows found in the sweep
+    unsigned *win_count;   // window records handed out by the work-list kernel
+    long long win_cap;  // capacity of win (records)
+    int win_chunk;      // primaries per chunk the windows are computed for (0 = no pre-pass)
     int tile_max;       // points per staged tile
     uint32_t flags;
     // radii (binary64 decisions on bounding boxes)

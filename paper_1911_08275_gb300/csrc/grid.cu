@@ -42,12 +42,6 @@ __device__ __forceinline__ double key_value(unsigned long long k)
     return __longlong_as_double((long long)b);
 }
 
-// Cell index along one axis from a float32 frame coordinate (monotone in it).
-__device__ __forceinline__ int cell_index_f(float t, float inv_w, int n)
-{
-    const float c = floorf(__fmul_rn(t, inv_w));
-    return (int)fminf(fmaxf(c, 0.0f), (float)(n - 1));
-}
 
 // Validity and float32 frame coordinate of one input coordinate, without
 // binary64 arithmetic (the binary64 pipe of this GPU is narrow): range tests on

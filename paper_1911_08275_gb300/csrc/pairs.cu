@@ -36,6 +36,7 @@
 // binary64 copies with the canonical formula and exact squared-edge compares.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "cf_internal.cuh"
@@ -258,6 +259,10 @@ __device__ __forceinline__ bool plan_item(const PairParams &P, int item, WorkIte
     if (P.g.periodic) {
         qx = floor_div(bx, P.g.ncx);
         qy = floor_div(by, P.g.ncy);
+        // an image two or more boxes away holds no pair within Rmax < L/2 (every
+        // coordinate difference is below L), even when pruning is switched off
+        if (qx < -1 || qx > 1 || qy < -1 || qy > 1)
+            return false;
         bx -= qx * P.g.ncx;
         by -= qy * P.g.ncy;
     } else if (bx < 0 || bx >= P.g.ncx || by < 0 || by >= P.g.ncy) {
@@ -295,13 +300,15 @@ __device__ __forceinline__ bool plan_item(const PairParams &P, int item, WorkIte
         dzmax = sqrt(fmax(0.0, __dsub_rn(P.rxy2, __dmul_rn(g2, 1.0 - 1e-12))));
     w.dzmax = __dmul_rn(dzmax, 1.0 + 1e-9);
     const bool self = P.autocorr && o.x == 0 && o.y == 0;
-    w.code = (qx + 1) | ((qy + 1) << 2) | (self ? 16 : 0);
-    w.pad = 0;
+    w.code = (qx + 1) | ((qy + 1) << 2) | (self ? 16 : 0) | (b << 5);
+    w.wbase = 0;
     return true;
 }
 
 // Work-list kernel (a3): one thread per candidate, kept pairs appended to
-// P.work with one warp-aggregated atomic per warp.
+// P.work with one warp-aggregated atomic per warp.  With the window pre-pass
+// (P.win_chunk > 0) each kept pair also gets a run of window records,
+// one per chunk of column a, from a second warp-aggregated counter.
 __global__ void __launch_bounds__(256) k_worklist(const __grid_constant__ PairParams P)
 {
     const int item = blockIdx.x * blockDim.x + threadIdx.x;
@@ -311,12 +318,36 @@ __global__ void __launch_bounds__(256) k_worklist(const __grid_constant__ PairPa
     if (!m)
         return;
     const int lane = threadIdx.x & 31, leader = __ffs(m) - 1;
-    unsigned base = 0;
-    if (lane == leader)
+    const int ch = P.win_chunk;
+    unsigned nch = (keep && ch > 0) ? (unsigned)((w.a1 - w.a0 + ch - 1) / ch) : 0u;
+    unsigned pre = nch;  // inclusive scan of the records over the warp
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned t = __shfl_up_sync(FULL, pre, o);
+        if (lane >= o)
+            pre += t;
+    }
+    const unsigned tot = __shfl_sync(FULL, pre, 31);
+    unsigned base = 0, zb = 0;
+    if (lane == leader) {
         base = atomicAdd(P.work_count, (unsigned)__popc(m));
+        if (tot)
+            zb = atomicAdd(P.win_count, tot);
+    }
     base = __shfl_sync(FULL, base, leader);
-    if (keep)
+    zb = __shfl_sync(FULL, zb, leader);
+    if (keep) {
+        if (ch > 0) {
+            const long long first = (long long)zb + (long long)(pre - nch);
+            if (first + (long long)nch > P.win_cap) {  // never with the host's bound
+                atomicOr(P.err, ERR_INTERNAL);
+                w.wbase = -1;
+            } else {
+                w.wbase = (int)first;
+            }
+        }
         P.work[base + __popc(m & ((1u << lane) - 1u))] = w;
+    }
 }
 
 // One kept column pair, as the pair kernels use it (identical in every thread
@@ -326,6 +357,7 @@ struct Item {
     double Sx, Sy, dzmax;
     bool self;
     int kmin, kmax;
+    int wbase;  // first window record (window pre-pass); -1: none (error flagged)
 };
 
 // Per-CTA state a pair path carries from one work item to the next.
@@ -348,12 +380,90 @@ __device__ __forceinline__ void decode_record(const PairParams &P, const WorkIte
     it.self = (w.code & 16) != 0;
     it.kmin = P.g.periodic ? (it.self ? 0 : -1) : 0;
     it.kmax = P.g.periodic ? 1 : 0;
+    it.wbase = w.wbase;
 }
 
 __device__ __forceinline__ void decode_item(const PairParams &P, int item, Item &it)
 {
     const WorkItem w = P.work[item];
     decode_record(P, w, it);
+}
+
+// First index p in [b0, b1) of column b with !(z[p] < v) (upper = false) or
+// !(z[p] <= v) (upper = true); b1 if none.  The column is sorted by z (NaN
+// padding at its end compares as larger than every value) and split into nz
+// z-cells by the gridding's monotone rule cell_index_f: points of the cells
+// below v's cell are < v and points of the cells above are > v, so the answer
+// lies in v's cell and only that cell is searched.
+__device__ __forceinline__ int zbound_col(const float *__restrict__ z, const uint32_t *__restrict__ cs,
+                                          int nz, float inv_wz, int b0, int b1, float v, bool upper)
+{
+    const int c = cell_index_f(v, inv_wz, nz);
+    int lo = max((int)cs[c], b0), hi = min((int)cs[c + 1], b1);
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        const float t = z[mid];
+        if (upper ? (t <= v) : (t < v))
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+// Window pre-pass (Sec. 2.2, late entry and early exit on the sorted axis,
+// applied per chunk of primaries): for every kept column pair (one warp) and
+// every chunk of P.win_chunk z-consecutive points of column a (one lane), the
+// ranges of column b whose z lies within the pair's reach dz of the chunk's z
+// range, [z_lo - dz, z_hi + dz], per periodic z image, with the float32
+// operations the pair kernel's own search would use.  The pair kernel then
+// reads one record per chunk instead of searching its staged tile.
+__global__ void __launch_bounds__(128) k_windows(const __grid_constant__ PairParams P)
+{
+    const int n_work = (int)*P.work_count;
+    const int CH = P.win_chunk, lane = threadIdx.x & 31;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    const int nz = P.g.nz;
+    const float inv_wz = P.g.inv_wf[2];
+    for (int item = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; item < n_work; item += nw) {
+        const WorkItem w = P.work[item];
+        if (w.wbase < 0)
+            continue;
+        Item it;
+        decode_record(P, w, it);
+        const uint32_t *cs = P.B.cell_start + (long long)(w.code >> 5) * nz;
+        const float dzw = __fadd_ru(__double2float_ru(it.dzmax), P.zslack);
+        const float zb_lo = P.B.zs[it.b0];  // column b's z range (a window outside it is empty)
+        float zb_hi = P.B.zs[it.b1 - 1];
+        if (isnan(zb_hi))
+            zb_hi = INFINITY;
+        const int nch = (it.a1 - it.a0 + CH - 1) / CH;
+        for (int c = lane; c < nch; c += 32) {
+            const int ib = it.a0 + c * CH;
+            int ie = min(ib + CH, it.a1) - 1;
+            const float zlo = P.A.zs[ib];
+            float zhi = P.A.zs[ie];
+            while (ie > ib && isnan(zhi))  // column padding: the largest real z is earlier
+                zhi = P.A.zs[--ie];
+            Win wn;
+#pragma unroll
+            for (int kk = 0; kk < 3; ++kk) {
+                const int k = kk - 1;
+                int lo = 0, hi = 0;
+                if (!isnan(zlo) && k >= it.kmin && k <= it.kmax) {
+                    const float kz = (float)k * P.boxf[2];
+                    const float wlo = zlo - kz - dzw, whi = zhi - kz + dzw;
+                    if (!(whi < zb_lo || wlo > zb_hi)) {
+                        lo = zbound_col(P.B.zs, cs, nz, inv_wz, it.b0, it.b1, wlo, false);
+                        hi = zbound_col(P.B.zs, cs, nz, inv_wz, lo, it.b1, whi, true);
+                    }
+                }
+                wn.lo[kk] = lo;
+                wn.hi[kk] = hi;
+            }
+            P.win[w.wbase + c] = wn;
+        }
+    }
 }
 
 // Byte offset in the shared block of the chunk counter that the warps of a CTA
@@ -634,14 +744,21 @@ __device__ __forceinline__ u64 lds64(uint32_t a)
     return v;
 }
 
+// 16-byte shared load (four floats as two packed pairs) at a 32-bit shared
+// address plus a constant offset.
+template <int OFF>
+__device__ __forceinline__ void lds128(uint32_t a, u64 &lo, u64 &hi)
+{
+    asm volatile("ld.shared.v2.b64 {%0, %1}, [%2+%3];" : "=l"(lo), "=l"(hi) : "r"(a), "n"(OFF));
+}
+
 // Sweep one window [jlo, jhi) of the staged tile.  Lane (ii, jj) holds PP
 // primaries (each broadcast to both halves of packed registers) and evaluates
-// them against two consecutive secondaries j, j+1 (one 8-byte load per axis
-// feeds 2 PP pairs); a step covers I PP primaries x 64/I secondaries, an
-// iteration two steps.  Pairs whose table cell is flagged go to the flagged
-// row and set a bit of the lane's mask; once per block of 8 iterations a
-// warp-uniform test settles the recorded pairs (so the loop body has no
-// data-dependent branch).
+// them against four consecutive secondaries j .. j+3 (one 16-byte shared load
+// per axis feeds 4 PP pairs); a step covers I PP primaries x 128 / I
+// secondaries.  Pairs whose table cell is flagged go to the flagged row and set
+// a bit of the lane's mask; once per block of 8 steps a warp-uniform test
+// settles the recorded pairs (so the loop body has no data-dependent branch).
 template <int I, int PP, bool TRI, bool EVALS, bool VERIFY, bool LIN, bool W, bool RV>
 __device__ __forceinline__ void sweep32(unsigned char *smem, const Sweep32 &S, uint32_t hl, int jlo,
                                         int jhi, int jj, const u64 (&XH)[PP], const u64 (&YH)[PP],
@@ -650,9 +767,9 @@ __device__ __forceinline__ void sweep32(unsigned char *smem, const Sweep32 &S, u
                                         const WAcc &A, const float (&wi)[PP], unsigned &wpend)
 {
     const float qnan = __int_as_float(0x7fc00000);
-    const int jstart = jlo & ~1;  // 8-byte aligned pairs; extra j's are never counted
-    constexpr int JS = 64 / I;  // secondaries per step
-    const int nit = (jhi - jstart + 2 * JS - 1) / (2 * JS);
+    const int jstart = jlo & ~3;  // 16-byte aligned quads; extra j's are never counted
+    constexpr int JS = 128 / I;   // secondaries per step (four per lane group)
+    const int nit = (jhi - jstart + JS - 1) / JS;
     const uint32_t nbu = (uint32_t)S.nb;
     // entries are <= nbu + 1 < 0x80: adding 0x80 - (nbu + 1) to each byte sets its
     // top bit exactly for the flagged value, without carries between bytes
@@ -663,7 +780,7 @@ __device__ __forceinline__ void sweep32(unsigned char *smem, const Sweep32 &S, u
     const uint32_t lutb = smem_u32(smem + LUT_OFF), lut_lo = lutb - LIN_MAGIC_BITS,
                    lut_hi = lutb + S.lut_last;
     for (int b0 = 0; b0 < nit; b0 += 8) {
-        const int jAb = jstart + 2 * jj + b0 * 2 * JS;
+        const int jAb = jstart + 4 * jj + b0 * JS;
         const uint32_t pb = smem_u32(S.tb) + jAb * 4;
         const int tend = min(8, nit - b0);
         uint32_t fm[PP];
@@ -671,20 +788,18 @@ __device__ __forceinline__ void sweep32(unsigned char *smem, const Sweep32 &S, u
         for (int q = 0; q < PP; ++q)
             fm[q] = 0u;
         for (int t = 0; t < tend; ++t) {
-            const uint32_t p = pb + t * 8 * JS;
-            const int jA = jAb + t * 2 * JS;
-            const u64 xA = lds64<0>(p);
-            const u64 yA = lds64<TSTRIDE>(p);
-            const u64 zA = lds64<2 * TSTRIDE>(p);
-            const u64 xB = lds64<4 * JS>(p);
-            const u64 yB = lds64<4 * JS + TSTRIDE>(p);
-            const u64 zB = lds64<4 * JS + 2 * TSTRIDE>(p);
+            const uint32_t p = pb + t * 4 * JS;
+            const int jA = jAb + t * JS;
+            u64 xA, xB, yA, yB, zA, zB;  // (j, j+1) and (j+2, j+3)
+            lds128<0>(p, xA, xB);
+            lds128<TSTRIDE>(p, yA, yB);
+            lds128<2 * TSTRIDE>(p, zA, zB);
             float d[PP][4];
             float pw[PP][4];     // pair weights (weighted sums only)
             uint32_t cq[PP][4];  // table cell of each pair
-            if (W) {  // w_j of the two secondary pairs (global, 8-byte aligned)
-                const u64 wA = *reinterpret_cast<const u64 *>(A.wsj + jA);
-                const u64 wB = *reinterpret_cast<const u64 *>(A.wsj + jA + JS);
+            if (W) {  // w_j of the four secondaries (global, 16-byte aligned)
+                const float4 wv = *reinterpret_cast<const float4 *>(A.wsj + jA);
+                const u64 wA = pack2(wv.x, wv.y), wB = pack2(wv.z, wv.w);
 #pragma unroll
                 for (int q = 0; q < PP; ++q) {
                     const u64 WI = pack2(wi[q], wi[q]);
@@ -715,24 +830,22 @@ __device__ __forceinline__ void sweep32(unsigned char *smem, const Sweep32 &S, u
                         cq[q][r] = lutb + min((__float_as_uint(d[q][r]) >> S.shift) - S.u0, S.lut_last);
                 }
             }
-            const int gA = S.t0 + jA, gB = gA + JS;  // global indices of (a0, b0); a1, b1 are +1
-            const int gv[4] = {gA, gA + 1, gB, gB + 1};
+            const int gA = S.t0 + jA;  // global index of secondary r is gA + r
             if (TRI) {  // pairs with j <= i: the out-of-range entry (and NaN for the checks)
 #pragma unroll
                 for (int q = 0; q < PP; ++q)
 #pragma unroll
                     for (int r = 0; r < 4; ++r) {
-                        cq[q][r] = gv[r] > iv[q] ? cq[q][r] : lut_hi;
-                        d[q][r] = gv[r] > iv[q] ? d[q][r] : qnan;
+                        cq[q][r] = gA + r > iv[q] ? cq[q][r] : lut_hi;
+                        d[q][r] = gA + r > iv[q] ? d[q][r] : qnan;
                     }
             }
             if (EVALS) {
-                const int jv[4] = {jA, jA + 1, jA + JS, jA + JS + 1};
 #pragma unroll
                 for (int q = 0; q < PP; ++q)
 #pragma unroll
                     for (int r = 0; r < 4; ++r)
-                        n_eval += (vv[q] && jv[r] >= jlo && jv[r] < jhi && (!TRI || gv[r] > iv[q]))
+                        n_eval += (vv[q] && jA + r >= jlo && jA + r < jhi && (!TRI || gA + r > iv[q]))
                                       ? 1ull : 0ull;
             }
 #pragma unroll
@@ -761,7 +874,7 @@ __device__ __forceinline__ void sweep32(unsigned char *smem, const Sweep32 &S, u
                     for (int r = 0; r < 4; ++r)
                         if (vv[q] && !isnan(d[q][r]))
                             n_viol += verify_pair(d[q][r], T, S.nthr, S.nb, E2, S.pa, S.pb, iv[q],
-                                                  gv[r], S.Sx, S.Sy, S.Sz);
+                                                  gA + r, S.Sx, S.Sy, S.Sz);
             }
         }
         uint32_t anyf = 0u;
@@ -780,7 +893,7 @@ __device__ __forceinline__ void sweep32(unsigned char *smem, const Sweep32 &S, u
                     const int bit = __ffs(m) - 1;
                     m &= m - 1u;
                     const int t = (bit & 7) - (8 - tend), r = bit >> 3;
-                    const int jl = jAb + t * 2 * JS + ((r & 2) ? JS : 0) + (r & 1);
+                    const int jl = jAb + t * JS + r;
                     n_rck += resolve_local<W, RV>(smem, S, hl, xh, yh, zh, iv[q], jl, A, wi[q]);
                 }
             }
@@ -829,8 +942,11 @@ __device__ __forceinline__ float wmax_pair(const PairParams &P)
 }
 
 // HC histogram copies, each shared by WARPS / HC warps (red.shared is atomic);
-// the weighted rows are per warp.
-template <int I, int PP, bool EVALS, bool VERIFY, bool W = false, bool RV = false, int HC = WARPS>
+// the weighted rows are per warp.  PREWIN: chunk windows come from the window
+// pre-pass (k_windows) instead of searches of the staged tile.  LT: table
+// cells linear in d2 (1), on float bits (0), or as the launch's tables say (-1).
+template <int I, int PP, bool EVALS, bool VERIFY, bool W = false, bool RV = false, int HC = WARPS,
+          bool PREWIN = false, int LT = -1>
 struct Xi32Path {
     static_assert(HC == WARPS || !(W || RV), "weighted rows are per warp");
     static_assert(WARPS % HC == 0, "warps share copies evenly");
@@ -928,120 +1044,157 @@ struct Xi32Path {
         S.pb = P.B.pos64;
         const float qnan = __int_as_float(0x7fc00000);
 
+        // Chunk windows (late entry / early exit per chunk, Sec. 2.2): the chunk's
+        // z range widened by the column pair's reach, per periodic z image;
+        // with PREWIN read from the window pre-pass, else searched in the tile.
         const float dzw = __fadd_ru(__double2float_ru(it.dzmax), P.zslack);
         const float Sxf = __double2float_rn(it.Sx), Syf = __double2float_rn(it.Sy);
         S.Sx = it.Sx;
         S.Sy = it.Sy;
         const int nchunks = (it.a1 - it.a0 + CH - 1) / CH;
         S.tb = tb;
-        {
-            S.t0 = t0;
-            const float zt_lo = tz[0];
-            float zt_hi = tz[nt - 1];
-            if (isnan(zt_hi))  // padding at the column end: largest real z is earlier
-                zt_hi = INFINITY;
-            auto zkey = [&](int q) { return tz[q]; };
-            int lo_prev[3] = {0, 0, 0}, hi_prev[3] = {0, 0, 0};
-
-            auto next_chunk = [&]() {
-                int v = 0;
-                if (lane == 0)
-                    v = atomicAdd(claim, 1);
-                return __shfl_sync(FULL, v, 0);
-            };
-            for (int c = next_chunk(); c < nchunks; c = next_chunk()) {
-                const int ib = it.a0 + c * CH;
-                u64 XH[PP], YH[PP], ZH[PP];
-                int iv[PP];
-                bool vv[PP];
-                float zq[PP], wi[PP];
-                float zmax = qnan;
-    #pragma unroll
-                for (int q = 0; q < PP; ++q) {
-                    const int i = ib + q * I + ii;
-                    float xi = qnan, yi = qnan, zi = qnan;
-                    wi[q] = 1.0f;
-                    if (i < it.a1) {
-                        xi = P.A.xs[i];
-                        yi = P.A.ys[i];
-                        zi = P.A.zs[i];
-                        if (W)
-                            wi[q] = P.A.ws[i];
-                    }
-                    iv[q] = i;
-                    vv[q] = !isnan(xi);  // chunk tail and column padding are NaN
-                    const float xh = __fsub_rn(xi, Sxf), yh = __fsub_rn(yi, Syf);
-                    XH[q] = pack2(xh, xh);
-                    YH[q] = pack2(yh, yh);
-                    zq[q] = zi;
-                    zmax = (isnan(zmax) || zi > zmax) ? zi : zmax;
+        S.t0 = t0;
+        if (PREWIN && it.wbase < 0)
+            return;  // no window records (the work-list kernel flagged an error)
+        const float zt_lo = tz[0];
+        float zt_hi = tz[nt - 1];
+        if (isnan(zt_hi))  // padding at the column end: largest real z is earlier
+            zt_hi = INFINITY;
+        auto zkey = [&](int q) { return tz[q]; };
+        int lo_prev[3] = {0, 0, 0}, hi_prev[3] = {0, 0, 0};  // windows searched before
+        auto next_chunk = [&]() {
+            int v = 0;
+            if (lane == 0)
+                v = atomicAdd(claim, 1);
+            return __shfl_sync(FULL, v, 0);
+        };
+        const bool lin = LT < 0 ? S.lin != 0 : LT == 1;
+        for (int c = next_chunk(); c < nchunks; c = next_chunk()) {
+            const int ib = it.a0 + c * CH;
+            u64 XH[PP], YH[PP], ZH[PP];
+            int iv[PP];
+            bool vv[PP];
+            float zq[PP], wi[PP];
+            float zmax = qnan;
+            int wl0 = 0, wl1 = 0, wl2 = 0, wh0 = 0, wh1 = 0, wh2 = 0;
+            if (PREWIN) {  // this chunk's windows in column b (three 8-byte loads)
+                const int2 *wr = reinterpret_cast<const int2 *>(P.win + it.wbase + c);
+                const int2 r0 = wr[0], r1 = wr[1], r2 = wr[2];
+                wl0 = r0.x;
+                wl1 = r0.y;
+                wl2 = r1.x;
+                wh0 = r1.y;
+                wh1 = r2.x;
+                wh2 = r2.y;
+            }
+#pragma unroll
+            for (int q = 0; q < PP; ++q) {
+                const int i = ib + q * I + ii;
+                float xi = qnan, yi = qnan, zi = qnan;
+                wi[q] = 1.0f;
+                if (i < it.a1) {
+                    xi = P.A.xs[i];
+                    yi = P.A.ys[i];
+                    zi = P.A.zs[i];
+                    if (W)
+                        wi[q] = P.A.ws[i];
                 }
-                const float zlo = __shfl_sync(FULL, zq[0], 0);
-                float zhi = zmax;
-    #pragma unroll
+                iv[q] = i;
+                vv[q] = !isnan(xi);  // chunk tail and column padding are NaN
+                const float xh = __fsub_rn(xi, Sxf), yh = __fsub_rn(yi, Syf);
+                XH[q] = pack2(xh, xh);
+                YH[q] = pack2(yh, yh);
+                zq[q] = zi;
+                if (!PREWIN)
+                    zmax = (isnan(zmax) || zi > zmax) ? zi : zmax;
+            }
+            float zlo = 0.0f, zhi = 0.0f;
+            if (!PREWIN) {
+                zlo = __shfl_sync(FULL, zq[0], 0);
+                zhi = zmax;
+#pragma unroll
                 for (int o = 1; o < I; o <<= 1) {  // largest real z of the chunk
                     const float t = __shfl_xor_sync(FULL, zhi, o);
                     zhi = (isnan(zhi) || t > zhi) ? t : zhi;
                 }
                 if (isnan(zlo))
                     continue;
-
-    #pragma unroll
-                for (int kk = 0; kk < 3; ++kk) {
-                    const int k = kk - 1;
+            }
+#pragma unroll 1
+            for (int kk = 0; kk < 3; ++kk) {
+                const int k = kk - 1;
+                const float kz = (float)k * P.boxf[2];
+                int jlo, jhi;
+                if (PREWIN) {  // clip the column-b window to this tile
+                    const int lo = kk == 0 ? wl0 : (kk == 1 ? wl1 : wl2);
+                    const int hi = kk == 0 ? wh0 : (kk == 1 ? wh1 : wh2);
+                    jlo = max(lo, t0) - t0;
+                    jhi = min(hi, t0 + nt) - t0;
+                    if (jlo >= jhi)
+                        continue;
+                } else {
                     if (k < it.kmin || k > it.kmax)
                         continue;
-                    const float kz = (float)k * P.boxf[2];
                     const float wlo = zlo - kz - dzw, whi = zhi - kz + dzw;
                     if (whi < zt_lo || wlo > zt_hi)
                         continue;
-                    int jlo = warp_bound_from(zkey, lo_prev[kk], nt, wlo, false, lane);
-                    const int jhi = warp_bound_from(zkey, max(hi_prev[kk], jlo), nt, whi, true, lane);
-                    lo_prev[kk] = jlo;
-                    hi_prev[kk] = jhi;
-                    const bool tri = it.self && k == 0;
-                    if (tri)
-                        jlo = max(jlo, ib + 1 - t0);
-                    if (jlo >= jhi)
-                        continue;
-                    pending += (unsigned)((jhi - jlo) / (64 / I) + 4) * 2u * PP;
-    #pragma unroll
-                    for (int q = 0; q < PP; ++q) {
-                        const float zh = __fsub_rn(zq[q], kz);
-                        ZH[q] = pack2(zh, zh);
-                    }
-                    S.Sz = k == 0 ? 0.0 : (k > 0 ? P.g.box[2] : -P.g.box[2]);
-                    if (W)
-                        A.wsj = P.B.ws + t0;
-                    if (tri) {
-                        if (S.lin)
-                            sweep32<I, PP, true, EVALS, VERIFY, true, W, RV>(
-                                smem, S, hl, jlo, jhi, jj, XH, YH, ZH, iv, vv, n_eval, n_rck, n_viol,
-                                A, wi, st.wpend);
-                        else
-                            sweep32<I, PP, true, EVALS, VERIFY, false, W, RV>(
-                                smem, S, hl, jlo, jhi, jj, XH, YH, ZH, iv, vv, n_eval, n_rck, n_viol,
-                                A, wi, st.wpend);
+                    const int lp = kk == 0 ? lo_prev[0] : (kk == 1 ? lo_prev[1] : lo_prev[2]);
+                    const int hp = kk == 0 ? hi_prev[0] : (kk == 1 ? hi_prev[1] : hi_prev[2]);
+                    jlo = warp_bound_from(zkey, lp, nt, wlo, false, lane);
+                    jhi = warp_bound_from(zkey, max(hp, jlo), nt, whi, true, lane);
+                    if (kk == 0) {
+                        lo_prev[0] = jlo;
+                        hi_prev[0] = jhi;
+                    } else if (kk == 1) {
+                        lo_prev[1] = jlo;
+                        hi_prev[1] = jhi;
                     } else {
-                        if (S.lin)
-                            sweep32<I, PP, false, EVALS, VERIFY, true, W, RV>(
-                                smem, S, hl, jlo, jhi, jj, XH, YH, ZH, iv, vv, n_eval, n_rck, n_viol,
-                                A, wi, st.wpend);
-                        else
-                            sweep32<I, PP, false, EVALS, VERIFY, false, W, RV>(
-                                smem, S, hl, jlo, jhi, jj, XH, YH, ZH, iv, vv, n_eval, n_rck, n_viol,
-                                A, wi, st.wpend);
+                        lo_prev[2] = jlo;
+                        hi_prev[2] = jhi;
                     }
                 }
-                // keep every shared u32 count far from overflow (WARPS / HC warps add to a copy)
-                if (!(W || RV) && pending > (1u << 30) / (WARPS / HC)) {
-                    __syncwarp();
-                    if (HC == WARPS)
-                        warp_flush(hw, nb, P.hist, lane);
-                    else
-                        warp_flush_shared(hw, nb, P.hist, lane);
-                    pending = 0;
+                const bool tri = it.self && k == 0;
+                if (tri)
+                    jlo = max(jlo, ib + 1 - t0);
+                if (jlo >= jhi)
+                    continue;
+                pending += (unsigned)((jhi - jlo) / (64 / I) + 4) * 2u * PP;
+#pragma unroll
+                for (int q = 0; q < PP; ++q) {
+                    const float zh = __fsub_rn(zq[q], kz);
+                    ZH[q] = pack2(zh, zh);
                 }
+                S.Sz = k == 0 ? 0.0 : (k > 0 ? P.g.box[2] : -P.g.box[2]);
+                if (W)
+                    A.wsj = P.B.ws + t0;
+                if (tri) {
+                    if (lin)
+                        sweep32<I, PP, true, EVALS, VERIFY, true, W, RV>(
+                            smem, S, hl, jlo, jhi, jj, XH, YH, ZH, iv, vv, n_eval, n_rck, n_viol,
+                            A, wi, st.wpend);
+                    else
+                        sweep32<I, PP, true, EVALS, VERIFY, false, W, RV>(
+                            smem, S, hl, jlo, jhi, jj, XH, YH, ZH, iv, vv, n_eval, n_rck, n_viol,
+                            A, wi, st.wpend);
+                } else {
+                    if (lin)
+                        sweep32<I, PP, false, EVALS, VERIFY, true, W, RV>(
+                            smem, S, hl, jlo, jhi, jj, XH, YH, ZH, iv, vv, n_eval, n_rck, n_viol,
+                            A, wi, st.wpend);
+                    else
+                        sweep32<I, PP, false, EVALS, VERIFY, false, W, RV>(
+                            smem, S, hl, jlo, jhi, jj, XH, YH, ZH, iv, vv, n_eval, n_rck, n_viol,
+                            A, wi, st.wpend);
+                }
+            }
+            // keep every shared u32 count far from overflow (WARPS / HC warps add to a copy)
+            if (!(W || RV) && pending > (1u << 30) / (WARPS / HC)) {
+                __syncwarp();
+                if (HC == WARPS)
+                    warp_flush(hw, nb, P.hist, lane);
+                else
+                    warp_flush_shared(hw, nb, P.hist, lane);
+                pending = 0;
             }
         }
     }
@@ -2611,14 +2764,29 @@ cudaError_t launch_batch(const BatchParams &B, int smem, int sms, int &blocks, c
     return cudaGetLastError();
 }
 
-cudaError_t launch_pairs(const PairParams &P, PairLaunch &L, int sms, cudaStream_t st)
+cudaError_t launch_pairs(const PairParams &P0, PairLaunch &L, int sms, cudaStream_t st)
 {
-    if (P.n_items <= 0)
+    L.kernels = 0;
+    if (P0.n_items <= 0)
         return cudaSuccess;
+    PairParams P = P0;
+    // the float32 DD(r) kernels take their chunk windows from the window pre-pass
+    const bool xi32 = P.kind == 0 && !L.f64;
+    if (xi32 && !P.win)
+        return cudaErrorInvalidValue;  // the caller provides the window records
+    P.win_chunk = xi32 ? xi32_chunk(L.chunk, L.pp, P.wacc != 0, L.verify != 0) : 0;
     k_worklist<<<(P.n_items + 255) / 256, 256, 0, st>>>(P);
-    const cudaError_t e = cudaGetLastError();
+    cudaError_t e = cudaGetLastError();
     if (e)
         return e;
+    L.kernels = 2;
+    if (xi32) {
+        const int wblocks = std::max(1, std::min((P.n_items + 3) / 4, sms * 16));
+        k_windows<<<wblocks, 128, 0, st>>>(P);
+        if ((e = cudaGetLastError()))
+            return e;
+        L.kernels = 3;
+    }
     if (P.kind == 1) {
         if (L.f64) {
             if (P.wacc)
@@ -2656,46 +2824,48 @@ cudaError_t launch_pairs(const PairParams &P, PairLaunch &L, int sms, cudaStream
         return L.evals ? launch_persistent(k_path<Xi64Path<8, true, false>, 1>, P, L, sms, st)
                        : launch_persistent(k_path<Xi64Path<8, false, false>, 1>, P, L, sms, st);
     }
+    constexpr int HW = WARPS;
+    constexpr bool PW = true;
     if (P.wacc) {  // pair weights and / or mean separation: integer sums in the same sweep
         if (P.weighted && P.want_r)
-            return L.evals ? launch_persistent(k_path<Xi32Path<16, 1, true, false, true, true>, 2>, P, L, sms, st)
-                           : launch_persistent(k_path<Xi32Path<16, 1, false, false, true, true>, 2>, P, L, sms, st);
+            return L.evals ? launch_persistent(k_path<Xi32Path<16, 1, true, false, true, true, HW, PW>, 2>, P, L, sms, st)
+                           : launch_persistent(k_path<Xi32Path<16, 1, false, false, true, true, HW, PW>, 2>, P, L, sms, st);
         if (P.weighted)
-            return L.evals ? launch_persistent(k_path<Xi32Path<16, 1, true, false, true, false>, 2>, P, L, sms, st)
-                           : launch_persistent(k_path<Xi32Path<16, 1, false, false, true, false>, 2>, P, L, sms, st);
-        return L.evals ? launch_persistent(k_path<Xi32Path<16, 1, true, false, false, true>, 2>, P, L, sms, st)
-                       : launch_persistent(k_path<Xi32Path<16, 1, false, false, false, true>, 2>, P, L, sms, st);
+            return L.evals ? launch_persistent(k_path<Xi32Path<16, 1, true, false, true, false, HW, PW>, 2>, P, L, sms, st)
+                           : launch_persistent(k_path<Xi32Path<16, 1, false, false, true, false, HW, PW>, 2>, P, L, sms, st);
+        return L.evals ? launch_persistent(k_path<Xi32Path<16, 1, true, false, false, true, HW, PW>, 2>, P, L, sms, st)
+                       : launch_persistent(k_path<Xi32Path<16, 1, false, false, false, true, HW, PW>, 2>, P, L, sms, st);
     }
     if (!L.pipe) {  // single tile buffer, one histogram copy per warp
         if (L.verify)
-            return launch_persistent(k_path<Xi32Path<8, 1, true, true>, 3>, P, L, sms, st);
-        return L.evals ? launch_persistent(k_path<Xi32Path<16, 2, true, false>, 3>, P, L, sms, st)
-                       : launch_persistent(k_path<Xi32Path<16, 2, false, false>, 3>, P, L, sms, st);
+            return launch_persistent(k_path<Xi32Path<8, 1, true, true, false, false, HW, PW>, 3>, P, L, sms, st);
+        return L.evals ? launch_persistent(k_path<Xi32Path<16, 2, true, false, false, false, HW, PW>, 3>, P, L, sms, st)
+                       : launch_persistent(k_path<Xi32Path<16, 2, false, false, false, false, HW, PW>, 3>, P, L, sms, st);
     }
     // two tile buffers, one shared histogram copy
     constexpr int H1 = 1;
     if (L.verify)
-        return launch_persistent(k_pipe<Xi32Path<8, 1, true, true, false, false, H1>, 3>, P, L, sms, st);
+        return launch_persistent(k_pipe<Xi32Path<8, 1, true, true, false, false, H1, PW>, 3>, P, L, sms, st);
     if (L.pp == 4)
-        return L.evals ? launch_persistent(k_pipe<Xi32Path<8, 4, true, false, false, false, H1>, 2>, P, L, sms, st)
-                       : launch_persistent(k_pipe<Xi32Path<8, 4, false, false, false, false, H1>, 2>, P, L, sms, st);
+        return L.evals ? launch_persistent(k_pipe<Xi32Path<8, 4, true, false, false, false, H1, PW>, 2>, P, L, sms, st)
+                       : launch_persistent(k_pipe<Xi32Path<8, 4, false, false, false, false, H1, PW>, 2>, P, L, sms, st);
     if (L.pp == 2) {
         if (L.chunk == 8)
-            return L.evals ? launch_persistent(k_pipe<Xi32Path<8, 2, true, false, false, false, H1>, 3>, P, L, sms, st)
-                           : launch_persistent(k_pipe<Xi32Path<8, 2, false, false, false, false, H1>, 3>, P, L, sms, st);
-        return L.evals ? launch_persistent(k_pipe<Xi32Path<16, 2, true, false, false, false, H1>, 3>, P, L, sms, st)
-                       : launch_persistent(k_pipe<Xi32Path<16, 2, false, false, false, false, H1>, 3>, P, L, sms, st);
+            return L.evals ? launch_persistent(k_pipe<Xi32Path<8, 2, true, false, false, false, H1, PW>, 3>, P, L, sms, st)
+                           : launch_persistent(k_pipe<Xi32Path<8, 2, false, false, false, false, H1, PW>, 3>, P, L, sms, st);
+        return L.evals ? launch_persistent(k_pipe<Xi32Path<16, 2, true, false, false, false, H1, PW>, 3>, P, L, sms, st)
+                       : launch_persistent(k_pipe<Xi32Path<16, 2, false, false, false, false, H1, PW>, 3>, P, L, sms, st);
     }
     switch (L.chunk) {
     case 16:
-        return L.evals ? launch_persistent(k_pipe<Xi32Path<16, 1, true, false, false, false, H1>, 3>, P, L, sms, st)
-                       : launch_persistent(k_pipe<Xi32Path<16, 1, false, false, false, false, H1>, 3>, P, L, sms, st);
+        return L.evals ? launch_persistent(k_pipe<Xi32Path<16, 1, true, false, false, false, H1, PW>, 3>, P, L, sms, st)
+                       : launch_persistent(k_pipe<Xi32Path<16, 1, false, false, false, false, H1, PW>, 3>, P, L, sms, st);
     case 32:
-        return L.evals ? launch_persistent(k_pipe<Xi32Path<32, 1, true, false, false, false, H1>, 3>, P, L, sms, st)
-                       : launch_persistent(k_pipe<Xi32Path<32, 1, false, false, false, false, H1>, 3>, P, L, sms, st);
+        return L.evals ? launch_persistent(k_pipe<Xi32Path<32, 1, true, false, false, false, H1, PW>, 3>, P, L, sms, st)
+                       : launch_persistent(k_pipe<Xi32Path<32, 1, false, false, false, false, H1, PW>, 3>, P, L, sms, st);
     default:
-        return L.evals ? launch_persistent(k_pipe<Xi32Path<8, 1, true, false, false, false, H1>, 3>, P, L, sms, st)
-                       : launch_persistent(k_pipe<Xi32Path<8, 1, false, false, false, false, H1>, 3>, P, L, sms, st);
+        return L.evals ? launch_persistent(k_pipe<Xi32Path<8, 1, true, false, false, false, H1, PW>, 3>, P, L, sms, st)
+                       : launch_persistent(k_pipe<Xi32Path<8, 1, false, false, false, false, H1, PW>, 3>, P, L, sms, st);
     }
 }
 

@@ -43,7 +43,32 @@ struct PairLaunch {
     int hist_words;  // shared histogram words
     int max_blocks;  // upper bound on the persistent grid (0 = none)
     int pipe;        // float32 DD(r) without sums: two tile buffers (no CTA barrier per item)
+    int kernels;     // kernels the launch issued (work list, window pre-pass, pair kernel)
 };
+
+// Primaries per chunk of the float32 DD(r) kernel for a requested shape (chunk
+// lanes x primaries per lane; the weighted sweep runs 16 x 1, the verifying
+// one 8 x 1); the window pre-pass writes one record per chunk of this size.
+inline int xi32_chunk(int chunk, int pp, bool weighted, bool verify)
+{
+    if (verify)
+        return 8;
+    if (weighted)
+        return 16;
+    if (pp == 4)
+        return 32;
+    if (pp == 2)
+        return chunk == 8 ? 16 : 32;
+    return chunk == 16 || chunk == 32 ? chunk : 8;
+}
+
+// Upper bound on the window records of one launch: every kept column pair
+// (at most nstencil per column of d1) has one record per chunk of its column a,
+// and the columns of d1 hold n1 points plus at most 3 padding points each.
+inline long long win_bound(long long n1, int ncols, int nstencil, int chunk)
+{
+    return (long long)nstencil * ((n1 + 3ll * ncols) / chunk + ncols + 1);
+}
 
 // Fill the shared-memory plan of a launch: L.smem, L.hist_words and, for
 // rp-pi, P.hcopies and P.hist_off.  Needs P.kind, P.nbins, P.npibins,
