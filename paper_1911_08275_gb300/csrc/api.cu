@@ -794,6 +794,10 @@ int run(Request &q)
     plan_geom(q, lo, hi, ntot, g);
 
     {  // grid workspace
+        // float32 DD(r) with mean separations: the coordinates' float32 rounding
+        // residuals, unless the inputs are float32 in a periodic box (exact)
+        const bool resid = q.kind == 0 && !f64 && c->want_ravg &&
+                           !(c->dtype == CF_FLOAT32 && c->periodic);
         for (int pass = 0; pass < 2; ++pass) {
             bump.base = pass ? (char *)ws2 : nullptr;
             bump.off = 0;
@@ -803,6 +807,11 @@ int run(Request &q)
                 G[t].ys = bump.take<float>(n);
                 G[t].zs = bump.take<float>(n);
                 G[t].ws = c->weighted ? bump.take<float>(n + 64) : nullptr;  // + slack for tile reads
+                if (resid) {  // float32 mean separation from inputs float32 cannot hold exactly
+                    G[t].xl = bump.take<float>(n + 64);
+                    G[t].yl = bump.take<float>(n + 64);
+                    G[t].zl = bump.take<float>(n + 64);
+                }
                 G[t].wmax = c->weighted ? reinterpret_cast<unsigned *>(d_hist + nslots + 6) + t : nullptr;
                 G[t].pos64 = bump.take<double4_32a>(n);
                 G[t].perm = bump.take<int>(n);
@@ -885,6 +894,7 @@ int run(Request &q)
         P.weighted = c->weighted ? 1 : 0;
         P.want_r = c->want_ravg ? 1 : 0;
         P.wacc = wacc ? 1 : 0;
+        P.rlo = resid ? 1 : 0;
         P.wsum = wacc ? reinterpret_cast<double *>(d_hist + nslots + 7) : nullptr;
         P.rsum = wacc ? P.wsum + nslots : nullptr;
         P.diag = d_diag;
@@ -971,7 +981,7 @@ int run(Request &q)
         res->n_rechecked = ho->diag[2];
         res->n_band_violations = ho->diag[3];
         for (int t = 0; t < ncat; ++t)
-            res->n_kernels += cf::grid_kernels(cats[t]->n) +
+            res->n_kernels += cf::grid_kernels(cats[t]->n, G[t].xl != nullptr) +
                               (c->periodic ? 0 : cf::bbox_kernels(cats[t]->n));
         res->n_kernels += PL.kernels;  // work list, window pre-pass, pair kernel
     }

@@ -85,6 +85,8 @@ struct Gridded {
     float *xs, *ys, *zs;  // float32 coordinates in the grid frame (padded columns)
     float *ws;            // float32 weights (padded columns, 64 floats of slack; NULL without weights)
     unsigned *wmax;       // bit pattern of max |w| as float (written by gridding; NULL without weights)
+    float *xl, *yl, *zl;  // rounding residuals fl32((X - O) - xs) of the float32 coordinates
+                          // (float32 mean separations from float64 inputs; else NULL)
     double4_32a *pos64;       // (x, y, z, w) binary64, exact inputs
     int *perm;            // original index of each sorted point
     uint32_t *cell_start; // ncells + 1
@@ -156,6 +158,7 @@ struct PairParams {
     int weighted;       // pair weight w_i * w_j (else 1)
     int want_r;         // accumulate r (xi) or rp (rp-pi) times the pair weight
     int wacc;           // weighted || want_r
+    int rlo;            // float32 mean separation corrected with the coordinates' residuals
     int acc_off;        // byte offset of the binary64 accumulators in shared memory
     long long *wscratch;  // float32 weighted DD(r): per-thread [bin][count, w, r w] int64 sums
     const float *thr;        // nthr

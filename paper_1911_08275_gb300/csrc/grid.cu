@@ -512,6 +512,33 @@ inline int grid_blocks(long long n, int threads, int sms)
     return (int)(b < 1 ? 1 : b);
 }
 
+// Rounding residuals of the float32 frame coordinates, from the sorted binary64
+// copies: r = fl32((X - O) - x~) with (X - O) evaluated as the frame conversion
+// does (binary64; X itself in a periodic box, whose origin is 0).  The float32
+// mean separation uses them to restore the coordinates' lost bits.  Padding
+// entries get 0.
+__global__ void k_residual(const double4_32a *__restrict__ pos64, const float *__restrict__ xs,
+                           const float *__restrict__ ys, const float *__restrict__ zs,
+                           const uint32_t *__restrict__ cell_start, Geom g, float *__restrict__ xl,
+                           float *__restrict__ yl, float *__restrict__ zl)
+{
+    const long long n = cell_start[g.ncells];  // padded length of the gridded catalogue
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long d = (long long)blockIdx.x * blockDim.x + threadIdx.x; d < n; d += stride) {
+        const double4_32a p = pos64[d];
+        if (isnan(p.x)) {
+            xl[d] = yl[d] = zl[d] = 0.0f;
+            continue;
+        }
+        const double X = g.periodic ? p.x : __dsub_rn(p.x, g.origin[0]);
+        const double Y = g.periodic ? p.y : __dsub_rn(p.y, g.origin[1]);
+        const double Z = g.periodic ? p.z : __dsub_rn(p.z, g.origin[2]);
+        xl[d] = __double2float_rn(__dsub_rn(X, (double)xs[d]));
+        yl[d] = __double2float_rn(__dsub_rn(Y, (double)ys[d]));
+        zl[d] = __double2float_rn(__dsub_rn(Z, (double)zs[d]));
+    }
+}
+
 template <class T>
 cudaError_t build_grid_t(const void *x, const void *y, const void *z, const double *w, long long n,
                          const Geom &g, const GridTemps &t, Gridded &out, int sms, unsigned *err,
@@ -546,6 +573,12 @@ cudaError_t build_grid_t(const void *x, const void *y, const void *z, const doub
                                                       out.ys, out.zs, out.ws, out.pos64, out.perm);
     k_colbox<<<std::min(g.ncols, sms * 8), 256, 0, st>>>(out.pos64, out.cell_start, g.ncols, g.nz,
                                                           out.colbox);
+    if (out.xl) {
+        const long long np = n + 3ll * g.ncols;  // padded length (an upper bound)
+        k_residual<<<grid_blocks(np, TB, sms), TB, 0, st>>>(out.pos64, out.xs, out.ys, out.zs,
+                                                            out.cell_start, g, out.xl, out.yl,
+                                                            out.zl);
+    }
     return cudaGetLastError();
 }
 

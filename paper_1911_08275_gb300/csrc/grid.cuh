@@ -31,7 +31,10 @@ cudaError_t launch_bbox(cf_dtype dt, const void *x, const void *y, const void *z
 double decode_dkey(unsigned long long k);
 
 // Kernels launched by build_grid / launch_bbox for a catalogue of n points.
-inline int grid_kernels(long long n) { return n > 0 ? 9 : 6; }
+inline int grid_kernels(long long n, bool residuals = false)
+{
+    return (n > 0 ? 9 : 6) + (residuals ? 1 : 0);
+}
 inline int bbox_kernels(long long n) { return n > 0 ? 1 : 0; }
 
 }  // namespace cf

@@ -659,6 +659,7 @@ struct WAcc {
     const float *sr;       // per-row scale of r w (shared; 0 for the two dummy rows)
     float sw;              // scale of w
     const float *wsj;      // secondary weights of the staged tile (global, from tile element 0)
+    const float *xlj, *ylj, *zlj;  // secondaries' coordinate residuals (global, from tile element 0)
     uint32_t *cnt, *wq, *rq;  // this lane's rows (generic pointers, stride 32 words)
     long long *g;          // this thread's [bin][count, w, r w] 64-bit sums (global)
     int nb;
@@ -706,16 +707,22 @@ __device__ __noinline__ void wacc_flush(const WAcc &A)
 // A flagged pair recorded by sweep32: recompute its float32 d2 from the
 // staged tile (the same IEEE operations as the packed main path), settle it
 // with the thresholds (binary64 inside a band) and add it to its true row.
-template <bool W, bool RV>
+template <bool W, bool RV, bool RL = false>
 __device__ __forceinline__ int resolve_local(const unsigned char *smem, const Sweep32 &S, uint32_t hl,
                                           float xh, float yh, float zh, int i, int jl,
-                                          const WAcc &A, float wi)
+                                          const WAcc &A, float wi, float lx = 0.0f, float ly = 0.0f,
+                                          float lz = 0.0f)
 {
     const float *tx = reinterpret_cast<const float *>(S.tb);
     const float dx = __fsub_rn(tx[jl], xh);
     const float dy = __fsub_rn(tx[jl + TSTRIDE / 4], yh);
     const float dz = __fsub_rn(tx[jl + TSTRIDE / 2], zh);
     const float d2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+    // the mean separation's squared distance with the coordinates' residuals
+    const float dc = RL ? __fmaf_rn(2.0f, __fmaf_rn(dz, A.zlj[jl] - lz, __fmaf_rn(dy, A.ylj[jl] - ly,
+                                                                                 dx * (A.xlj[jl] - lx))),
+                                    d2)
+                        : d2;
     if (!W && !RV)
         return resolve_pair(smem, S, hl, d2, i, S.t0 + jl);
     const float *T = reinterpret_cast<const float *>(smem + THR_OFF);
@@ -730,7 +737,7 @@ __device__ __forceinline__ int resolve_local(const unsigned char *smem, const Sw
     }
     if (row >= 0) {
         red_shared1(hl + (uint32_t)row * 128u);
-        wacc_add<W, RV>(A, (uint32_t)row, W ? __fmul_rn(A.wsj[jl], wi) : 1.0f, d2);
+        wacc_add<W, RV>(A, (uint32_t)row, W ? __fmul_rn(A.wsj[jl], wi) : 1.0f, dc);
     }
     return re;
 }
@@ -759,13 +766,20 @@ __device__ __forceinline__ void lds128(uint32_t a, u64 &lo, u64 &hi)
 // secondaries.  Pairs whose table cell is flagged go to the flagged row and set
 // a bit of the lane's mask; once per block of 8 steps a warp-uniform test
 // settles the recorded pairs (so the loop body has no data-dependent branch).
-template <int I, int PP, bool TRI, bool EVALS, bool VERIFY, bool LIN, bool W, bool RV>
+// RL: the mean separation's r comes from the squared distance corrected with
+// the coordinates' float32 rounding residuals (secondaries' from the residual
+// tiles, primaries' in LX, LY, LZ, shift roundings included):
+// d2 = d2~ + 2 (dx~ ex + dy~ ey + dz~ ez) up to the square of the residuals.
+template <int I, int PP, bool TRI, bool EVALS, bool VERIFY, bool LIN, bool W, bool RV, bool RL = false>
 __device__ __forceinline__ void sweep32(unsigned char *smem, const Sweep32 &S, uint32_t hl, int jlo,
                                         int jhi, int jj, const u64 (&XH)[PP], const u64 (&YH)[PP],
                                         const u64 (&ZH)[PP], const int (&iv)[PP],
                                         const bool (&vv)[PP], u64 &n_eval, u64 &n_rck, u64 &n_viol,
-                                        const WAcc &A, const float (&wi)[PP], unsigned &wpend)
+                                        const WAcc &A, const float (&wi)[PP], unsigned &wpend,
+                                        u64 LX, u64 LY, u64 LZ)
 {
+    static_assert(!RL || PP == 1, "residual-corrected separations take one primary per lane");
+    const u64 TWO = pack2(2.0f, 2.0f);
     const float qnan = __int_as_float(0x7fc00000);
     const int jstart = jlo & ~3;  // 16-byte aligned quads; extra j's are never counted
     constexpr int JS = 128 / I;   // secondaries per step (four per lane group)
@@ -795,8 +809,21 @@ __device__ __forceinline__ void sweep32(unsigned char *smem, const Sweep32 &S, u
             lds128<TSTRIDE>(p, yA, yB);
             lds128<2 * TSTRIDE>(p, zA, zB);
             float d[PP][4];
+            float dr[PP][4];     // residual-corrected squared separations (RL only)
             float pw[PP][4];     // pair weights (weighted sums only)
             uint32_t cq[PP][4];  // table cell of each pair
+            u64 lxA = 0, lxB = 0, lyA = 0, lyB = 0, lzA = 0, lzB = 0;
+            if (RL) {  // residuals of the four secondaries (global, 16-byte aligned)
+                const float4 rx = *reinterpret_cast<const float4 *>(A.xlj + jA);
+                const float4 ry = *reinterpret_cast<const float4 *>(A.ylj + jA);
+                const float4 rz = *reinterpret_cast<const float4 *>(A.zlj + jA);
+                lxA = pack2(rx.x, rx.y);
+                lxB = pack2(rx.z, rx.w);
+                lyA = pack2(ry.x, ry.y);
+                lyB = pack2(ry.z, ry.w);
+                lzA = pack2(rz.x, rz.y);
+                lzB = pack2(rz.z, rz.w);
+            }
             if (W) {  // w_j of the four secondaries (global, 16-byte aligned)
                 const float4 wv = *reinterpret_cast<const float4 *>(A.wsj + jA);
                 const u64 wA = pack2(wv.x, wv.y), wB = pack2(wv.z, wv.w);
@@ -811,10 +838,18 @@ __device__ __forceinline__ void sweep32(unsigned char *smem, const Sweep32 &S, u
             for (int q = 0; q < PP; ++q) {
                 u64 dx = fsub2(xA, XH[q]), dy = fsub2(yA, YH[q]), dz = fsub2(zA, ZH[q]);
                 const u64 dA = ffma2(dz, dz, ffma2(dy, dy, fmul2(dx, dx)));
+                if (RL) {
+                    const u64 c = ffma2(dz, fsub2(lzA, LZ), ffma2(dy, fsub2(lyA, LY), fmul2(dx, fsub2(lxA, LX))));
+                    unpack2(ffma2(TWO, c, dA), dr[q][0], dr[q][1]);
+                }
                 dx = fsub2(xB, XH[q]);
                 dy = fsub2(yB, YH[q]);
                 dz = fsub2(zB, ZH[q]);
                 const u64 dB = ffma2(dz, dz, ffma2(dy, dy, fmul2(dx, dx)));
+                if (RL) {
+                    const u64 c = ffma2(dz, fsub2(lzB, LZ), ffma2(dy, fsub2(lyB, LY), fmul2(dx, fsub2(lxB, LX))));
+                    unpack2(ffma2(TWO, c, dB), dr[q][2], dr[q][3]);
+                }
                 unpack2(dA, d[q][0], d[q][1]);
                 unpack2(dB, d[q][2], d[q][3]);
                 if (LIN) {  // one packed fma gives two cells
@@ -856,7 +891,7 @@ __device__ __forceinline__ void sweep32(unsigned char *smem, const Sweep32 &S, u
                     asm volatile("ld.shared.u8 %0, [%1];" : "=r"(e[r]) : "r"(cq[q][r]));  // the row
                     red_shared1(hl + e[r] * 128u);  // every entry is a row: bin, dummy or flagged
                     if (W || RV)
-                        wacc_add<W, RV>(A, e[r], W ? pw[q][r] : 1.0f, d[q][r]);
+                        wacc_add<W, RV>(A, e[r], W ? pw[q][r] : 1.0f, RL ? dr[q][r] : d[q][r]);
                 }
                 const uint32_t w = __byte_perm(__byte_perm(e[0], e[1], 0x0040),
                                                __byte_perm(e[2], e[3], 0x0040), 0x5410);
@@ -884,17 +919,23 @@ __device__ __forceinline__ void sweep32(unsigned char *smem, const Sweep32 &S, u
         if (__any_sync(FULL, anyf != 0u)) {
 #pragma unroll
             for (int q = 0; q < PP; ++q) {
-                float xh, yh, zh, tmp;
+                float xh, yh, zh, lx = 0.0f, ly = 0.0f, lz = 0.0f, tmp;
                 unpack2(XH[q], xh, tmp);
                 unpack2(YH[q], yh, tmp);
                 unpack2(ZH[q], zh, tmp);
+                if (RL) {
+                    unpack2(LX, lx, tmp);
+                    unpack2(LY, ly, tmp);
+                    unpack2(LZ, lz, tmp);
+                }
                 uint32_t m = fm[q];
                 while (m) {
                     const int bit = __ffs(m) - 1;
                     m &= m - 1u;
                     const int t = (bit & 7) - (8 - tend), r = bit >> 3;
                     const int jl = jAb + t * JS + r;
-                    n_rck += resolve_local<W, RV>(smem, S, hl, xh, yh, zh, iv[q], jl, A, wi[q]);
+                    n_rck += resolve_local<W, RV, RL>(smem, S, hl, xh, yh, zh, iv[q], jl, A, wi[q],
+                                                      lx, ly, lz);
                 }
             }
         }
@@ -941,12 +982,20 @@ __device__ __forceinline__ float wmax_pair(const PairParams &P)
     return __uint_as_float(*P.A.wmax) * __uint_as_float(*P.B.wmax);
 }
 
+// Rounding error of s = fl(a + b), i.e. a + b - s exactly (Knuth's TwoSum).
+__device__ __forceinline__ float two_sum_err(float a, float b, float s)
+{
+    const float bb = __fsub_rn(s, a);
+    return __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
 // HC histogram copies, each shared by WARPS / HC warps (red.shared is atomic);
 // the weighted rows are per warp.  PREWIN: chunk windows come from the window
 // pre-pass (k_windows) instead of searches of the staged tile.  LT: table
 // cells linear in d2 (1), on float bits (0), or as the launch's tables say (-1).
+// RL: mean separations from residual-corrected squared distances (sweep32).
 template <int I, int PP, bool EVALS, bool VERIFY, bool W = false, bool RV = false, int HC = WARPS,
-          bool PREWIN = false, int LT = -1>
+          bool PREWIN = false, int LT = -1, bool RL = false>
 struct Xi32Path {
     static_assert(HC == WARPS || !(W || RV), "weighted rows are per warp");
     static_assert(WARPS % HC == 0, "warps share copies evenly");
@@ -1049,6 +1098,15 @@ struct Xi32Path {
         // with PREWIN read from the window pre-pass, else searched in the tile.
         const float dzw = __fadd_ru(__double2float_ru(it.dzmax), P.zslack);
         const float Sxf = __double2float_rn(it.Sx), Syf = __double2float_rn(it.Sy);
+        // RL: the roundings of the periodic shifts, S - fl32(S) and L_z - fl32(L_z)
+        const float dSx = RL ? __double2float_rn(__dsub_rn(it.Sx, (double)Sxf)) : 0.0f;
+        const float dSy = RL ? __double2float_rn(__dsub_rn(it.Sy, (double)Syf)) : 0.0f;
+        const float dLz = RL ? __double2float_rn(__dsub_rn(P.g.box[2], (double)P.boxf[2])) : 0.0f;
+        if (RL) {
+            A.xlj = P.B.xl + t0;
+            A.ylj = P.B.yl + t0;
+            A.zlj = P.B.zl + t0;
+        }
         S.Sx = it.Sx;
         S.Sy = it.Sy;
         const int nchunks = (it.a1 - it.a0 + CH - 1) / CH;
@@ -1072,9 +1130,11 @@ struct Xi32Path {
         for (int c = next_chunk(); c < nchunks; c = next_chunk()) {
             const int ib = it.a0 + c * CH;
             u64 XH[PP], YH[PP], ZH[PP];
+            u64 LX = 0, LY = 0, LZ = 0;  // the primary's shifted residuals (RL, one primary per lane)
             int iv[PP];
             bool vv[PP];
             float zq[PP], wi[PP];
+            float lzq = 0.0f;
             float zmax = qnan;
             int wl0 = 0, wl1 = 0, wl2 = 0, wh0 = 0, wh1 = 0, wh2 = 0;
             if (PREWIN) {  // this chunk's windows in column b (three 8-byte loads)
@@ -1105,6 +1165,18 @@ struct Xi32Path {
                 XH[q] = pack2(xh, xh);
                 YH[q] = pack2(yh, yh);
                 zq[q] = zi;
+                if (RL) {  // the primary's residuals after the shift: r_i + (x~ - S~ - x^) - (S - S~)
+                    float rx = 0.0f, ry = 0.0f;
+                    if (i < it.a1) {
+                        rx = P.A.xl[i];
+                        ry = P.A.yl[i];
+                        lzq = P.A.zl[i];
+                    }
+                    const float lx = __fsub_rn(__fadd_rn(rx, two_sum_err(xi, -Sxf, xh)), dSx);
+                    const float ly = __fsub_rn(__fadd_rn(ry, two_sum_err(yi, -Syf, yh)), dSy);
+                    LX = pack2(lx, lx);
+                    LY = pack2(ly, ly);
+                }
                 if (!PREWIN)
                     zmax = (isnan(zmax) || zi > zmax) ? zi : zmax;
             }
@@ -1163,28 +1235,33 @@ struct Xi32Path {
                 for (int q = 0; q < PP; ++q) {
                     const float zh = __fsub_rn(zq[q], kz);
                     ZH[q] = pack2(zh, zh);
+                    if (RL) {
+                        const float lz = __fsub_rn(__fadd_rn(lzq, two_sum_err(zq[q], -kz, zh)),
+                                                   (float)k * dLz);
+                        LZ = pack2(lz, lz);
+                    }
                 }
                 S.Sz = k == 0 ? 0.0 : (k > 0 ? P.g.box[2] : -P.g.box[2]);
                 if (W)
                     A.wsj = P.B.ws + t0;
                 if (tri) {
                     if (lin)
-                        sweep32<I, PP, true, EVALS, VERIFY, true, W, RV>(
+                        sweep32<I, PP, true, EVALS, VERIFY, true, W, RV, RL>(
                             smem, S, hl, jlo, jhi, jj, XH, YH, ZH, iv, vv, n_eval, n_rck, n_viol,
-                            A, wi, st.wpend);
+                            A, wi, st.wpend, LX, LY, LZ);
                     else
-                        sweep32<I, PP, true, EVALS, VERIFY, false, W, RV>(
+                        sweep32<I, PP, true, EVALS, VERIFY, false, W, RV, RL>(
                             smem, S, hl, jlo, jhi, jj, XH, YH, ZH, iv, vv, n_eval, n_rck, n_viol,
-                            A, wi, st.wpend);
+                            A, wi, st.wpend, LX, LY, LZ);
                 } else {
                     if (lin)
-                        sweep32<I, PP, false, EVALS, VERIFY, true, W, RV>(
+                        sweep32<I, PP, false, EVALS, VERIFY, true, W, RV, RL>(
                             smem, S, hl, jlo, jhi, jj, XH, YH, ZH, iv, vv, n_eval, n_rck, n_viol,
-                            A, wi, st.wpend);
+                            A, wi, st.wpend, LX, LY, LZ);
                     else
-                        sweep32<I, PP, false, EVALS, VERIFY, false, W, RV>(
+                        sweep32<I, PP, false, EVALS, VERIFY, false, W, RV, RL>(
                             smem, S, hl, jlo, jhi, jj, XH, YH, ZH, iv, vv, n_eval, n_rck, n_viol,
-                            A, wi, st.wpend);
+                            A, wi, st.wpend, LX, LY, LZ);
                 }
             }
             // keep every shared u32 count far from overflow (WARPS / HC warps add to a copy)
@@ -2827,6 +2904,13 @@ cudaError_t launch_pairs(const PairParams &P0, PairLaunch &L, int sms, cudaStrea
     constexpr int HW = WARPS;
     constexpr bool PW = true;
     if (P.wacc) {  // pair weights and / or mean separation: integer sums in the same sweep
+        if (P.want_r && P.rlo) {  // r from residual-corrected squared distances
+            if (P.weighted)
+                return L.evals ? launch_persistent(k_path<Xi32Path<16, 1, true, false, true, true, HW, PW, -1, true>, 2>, P, L, sms, st)
+                               : launch_persistent(k_path<Xi32Path<16, 1, false, false, true, true, HW, PW, -1, true>, 2>, P, L, sms, st);
+            return L.evals ? launch_persistent(k_path<Xi32Path<16, 1, true, false, false, true, HW, PW, -1, true>, 2>, P, L, sms, st)
+                           : launch_persistent(k_path<Xi32Path<16, 1, false, false, false, true, HW, PW, -1, true>, 2>, P, L, sms, st);
+        }
         if (P.weighted && P.want_r)
             return L.evals ? launch_persistent(k_path<Xi32Path<16, 1, true, false, true, true, HW, PW>, 2>, P, L, sms, st)
                            : launch_persistent(k_path<Xi32Path<16, 1, false, false, true, true, HW, PW>, 2>, P, L, sms, st);

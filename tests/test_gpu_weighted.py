@@ -7,10 +7,9 @@ order and, in float32 mode, by float32 arithmetic:
   - float32 mode: weights are rounded to float32 (product error <= 3 u32) and
     each term to a power-of-two fixed-point grid, then summed exactly in
     integers (error <= 2^-22 max|w w| / |w w| per term), so wsum agrees to
-    1e-5 relative; r comes from float32 coordinates, so ravg agrees to 1e-5
-    relative when those coordinates are the caller's float32 inputs (periodic
-    box) and otherwise within 1e-5 plus the coordinate-rounding bound
-    2 * sqrt(3) * u32 * (extent + box) of |r32 - r|.
+    1e-5 relative; DD(r)'s r comes from the float32 squared distance corrected
+    to first order with the coordinates' float32 rounding residuals, so ravg
+    agrees to 1e-5 relative as well, for float64 inputs in an open box too.
 """
 import json
 import os
@@ -24,7 +23,6 @@ from paper_1911_08275_gb300 import synth
 
 pytestmark = pytest.mark.gpu
 
-U32 = 2.0 ** -24
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 
 
@@ -44,7 +42,7 @@ def ravg_of(rsum, den):
     return np.where(den != 0, rsum / np.where(den != 0, den, 1.0), 0.0)
 
 
-def check(r, n_ref, w_ref, rs_ref, mode, weighted, coord_bound=0.0):
+def check(r, n_ref, w_ref, rs_ref, mode, weighted):
     assert np.array_equal(r.npairs, n_ref)
     tol = 1e-12 if mode == "fp64" else 1e-5
     if weighted:
@@ -52,7 +50,7 @@ def check(r, n_ref, w_ref, rs_ref, mode, weighted, coord_bound=0.0):
         assert ok, f"wsum rel err {worst}"
     if rs_ref is not None:
         den = w_ref if weighted else n_ref
-        ok, worst = close(r.ravg, ravg_of(rs_ref, den), tol, coord_bound)
+        ok, worst = close(r.ravg, ravg_of(rs_ref, den), tol)
         assert ok, f"ravg rel err {worst}"
 
 
@@ -96,8 +94,21 @@ def test_xi_weighted_dr_open_box_float64_inputs(cuda_device, mode):
                          mode=mode, want_ravg=True)
     n, ws, rs = oracle.xi(d.x, d.y, d.z, w1=wd, x2=rnd.x, y2=rnd.y, z2=rnd.z, w2=wr, edges=e,
                           autocorr=False, periodic=False, want_r=True)
-    bound = 0.0 if mode == "fp64" else 2.0 * np.sqrt(3.0) * U32 * 150.0 * 2
-    check(r, n, ws, rs, mode, True, coord_bound=bound)
+    check(r, n, ws, rs, mode, True)
+
+
+@pytest.mark.parametrize("periodic", [True, False])
+def test_xi_ravg_float64_inputs_fp32_mode(cuda_device, periodic):
+    # float64 coordinates the float32 path cannot hold exactly: the residual-
+    # corrected mean separation agrees to 1e-5 relative in every bin, down to
+    # the smallest separations (clusters of sigma 2 fill the bins near 0.1)
+    cat = synth.neyman_scott(1500, 20.0, 2.0, 300.0, seed=86)
+    e = synth.log_edges(0.1, 25.0, 20)
+    x, y, z = tdev(cat.x, cat.y, cat.z)
+    r = cf.countpairs_xi(x, y, z, e, boxsize=300.0, periodic=periodic, want_ravg=True)
+    n, _, rs = oracle.xi(cat.x, cat.y, cat.z, edges=e, periodic=periodic, box=300.0, want_r=True)
+    assert n[0] > 0
+    check(r, n, None, rs, "fp32_recheck", False)
 
 
 @pytest.mark.parametrize("mode", ["fp32_recheck", "fp64"])
@@ -159,5 +170,4 @@ def test_dr_slice_full_randoms_matches_stored_oracle(cuda_device, mode):
                          mode=mode, want_ravg=True)
     ws = np.array([float.fromhex(h) for h in g["wsum_hex"]])
     rs = np.array([float.fromhex(h) for h in g["rsum_hex"]])
-    bound = 0.0 if mode == "fp64" else 2.0 * np.sqrt(3.0) * U32 * 420.0 * 2
-    check(r, np.array(g["npairs"], dtype=np.uint64), ws, rs, mode, True, coord_bound=bound)
+    check(r, np.array(g["npairs"], dtype=np.uint64), ws, rs, mode, True)
