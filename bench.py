@@ -21,9 +21,13 @@ ordered pairs the histogram holds (P_cnt) per second.
          14 x 40, the weighted DR count with ravg (1.2M x 12M, open box), and the
          48-job batched launch (graph replay vs 48 single calls).
 
---impl reference times the CPU oracle (brute force, canonical binary64) on a
-bounded sample of the same workload: each step counts the pairs of a slice of
-primary points against the whole catalogue.
+cpu_baseline is the plain gridded CPU counter (oracle/gridded.c: cell lists of
+Sec. 1.2 / 2.1 / 2.2 with refine (2, 2, 1), scalar canonical binary64, OpenMP
+on all host cores, counts equal to the oracle's bit for bit) on the whole
+workload; cpu_oracle is the brute-force oracle on a slice of primary points.
+--impl reference times the gridded CPU counter on the whole workload each step
+(the oracle is the brute-force definition; the gridded counter is the paper's
+method on the CPU, pinned to it).
 
 Multi-GPU (torchrun): each rank counts its own replica (independent problems,
 no collective on the data path); value = total pairs over the max time.
@@ -156,6 +160,21 @@ def cpu_baseline_sample(cat, edges, rows, reps=1):
     return cnt, dt, oracle.num_threads()
 
 
+def gridded_run(cat, edges):
+    """One gridded CPU count of the whole workload: (pairs, seconds, threads)."""
+    import oracle
+    oracle.build_gridded()
+    t0 = time.perf_counter()
+    n = oracle.gridded_xi(cat.x, cat.y, cat.z, edges=edges, periodic=True, box=cat.box)
+    dt = time.perf_counter() - t0
+    return n, dt, oracle.gridded_num_threads()
+
+
+GRIDDED_SAMPLE = ("whole workload per step: plain gridded CPU count (oracle/gridded.c: cell "
+                  "lists, refine (2,2,1), scalar canonical binary64, OpenMP), counts equal to "
+                  "the GPU's")
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -163,23 +182,28 @@ def run_reference(args):
     from paper_1911_08275_gb300 import synth
     cat = synth.c2_clustered()
     edges = synth.log_edges(RMIN, RMAX, NBINS)
-    rows = int(os.environ.get("CF_REF_ROWS", "2000"))
+    small = cat.take(np.arange(min(cat.n, 100000)))
     for _ in range(args.warmup):
-        cpu_baseline_sample(cat, edges, max(50, rows // 10))
+        gridded_run(small, edges)
     times, counts, cores = [], [], 1
     for _ in range(args.steps):
-        c, dt, cores = cpu_baseline_sample(cat, edges, rows)
+        n, dt, cores = gridded_run(cat, edges)
         times.append(dt)
-        counts.append(c)
+        counts.append(int(n.sum()))
+    if len(set(counts)) != 1:
+        raise RuntimeError("gridded CPU counts changed between steps")
     value = sum(counts) / sum(times) / 1e9
-    sample = (f"{rows} primary points x all {cat.n} points per step (cross count of a slice; "
-              f"{rows * cat.n:.3g} pair evaluations)")
+    rows = int(os.environ.get("CF_REF_ROWS", "2000"))
+    oc, odt, ocores = cpu_baseline_sample(cat, edges, rows)
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-           "data": "synthetic", "config": workload_config(cat.n),
-           "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                            "sample": sample},
+           "data": "synthetic", "config": workload_config(cat.n), "p_cnt": counts[0],
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "gridded",
+                            "sample": GRIDDED_SAMPLE},
+           "cpu_oracle": {"value": oc / odt / 1e9, "unit": UNIT, "cores": ocores, "kind": "oracle",
+                          "sample": f"brute force, {rows} primary points x all {cat.n} points "
+                                    f"({rows * cat.n:.3g} pair evaluations, {odt:.1f} s)"},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
@@ -393,12 +417,17 @@ def main():
            "diag": {"n_cellpairs": diag.n_cellpairs, "n_rechecked": diag.n_rechecked,
                     "useful_fraction": p_cnt / 2 / max(1, diag.n_evaluated)}}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        gridded_run(cat.take(np.arange(min(cat.n, 100000))), edges)  # build, warm caches
+        gn, gdt, gcores = gridded_run(cat, edges)
+        out["cpu_baseline"] = {"value": float(gn.sum()) / gdt / 1e9, "unit": UNIT, "cores": gcores,
+                               "kind": "gridded", "sample": GRIDDED_SAMPLE + f" ({gdt:.2f} s)",
+                               "counts_equal_gpu": bool(np.array_equal(gn, diag.npairs))}
         rows = int(os.environ.get("CF_CPU_ROWS", "40000"))
         c, dt, cores = cpu_baseline_sample(cat, edges, rows)
-        out["cpu_baseline"] = {"value": c / dt / 1e9, "unit": UNIT, "cores": cores,
-                               "kind": "oracle",
-                               "sample": f"{rows} primary points x all {cat.n} points "
-                                         f"({rows * cat.n:.3g} pair evaluations, {dt:.1f} s)"}
+        out["cpu_oracle"] = {"value": c / dt / 1e9, "unit": UNIT, "cores": cores,
+                             "kind": "oracle",
+                             "sample": f"brute force, {rows} primary points x all {cat.n} points "
+                                       f"({rows * cat.n:.3g} pair evaluations, {dt:.1f} s)"}
     if args.mode == "fp32_recheck" and rank == 0:
         # the plain binary64 path on the same workload, for the FP32/FP64 ratio
         r64 = [call(xyz, mode="fp64") for _ in range(3)]

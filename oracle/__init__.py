@@ -1,17 +1,21 @@
-"""Brute-force CPU oracle (test infrastructure only).
+"""Brute-force CPU oracle and the gridded CPU baseline (test infrastructure only).
 
-Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
-``bench.py`` may import this package.  It compiles ``oracle.c`` with gcc
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU legs of ``bench.py``
+may import this package.  It compiles ``oracle.c`` (and ``gridded.c``) with gcc
 (``-ffp-contract=off``: no fused multiply-add, so every operation is one
-correctly rounded binary64 operation) and wraps it with ctypes.
+correctly rounded binary64 operation) and wraps them with ctypes.
 
 Functions (all inputs are numpy arrays; float32 positions are promoted exactly
 to float64 before the call):
 
-* ``xi(...)``    DD(r) of Sec. 1.1 (Code 1, Eq. "separations");
-* ``rppi(...)``  DD(rp, pi), rp-major 2-D histogram, line of sight = z.
+* ``xi(...)``    DD(r) of Sec. 1.1 (Code 1, Eq. "separations"), brute force;
+* ``rppi(...)``  DD(rp, pi), rp-major 2-D histogram, line of sight = z, brute force;
+* ``gridded_xi(...)``  DD(r) by cell lists (Sec. 1.2 / 2.1 / 2.2, scalar, OpenMP):
+  the plain gridded CPU count the benchmark reports as its CPU baseline; the
+  tests pin it to ``xi`` bit for bit.
 
-Both return ``(npairs[uint64], wsum[float64] or None, rsum[float64] or None)``.
+``xi`` and ``rppi`` return ``(npairs[uint64], wsum[float64] or None, rsum[float64]
+or None)``; ``gridded_xi`` returns ``npairs``.
 """
 from __future__ import annotations
 
@@ -25,24 +29,32 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
 _OUT = os.path.join(_HERE, "_build", "liboracle.so")
+_GSRC = os.path.join(_HERE, "gridded.c")
+_GOUT = os.path.join(_HERE, "_build", "libgridded.so")
 _lock = threading.Lock()
 _lib = None
+_glib = None
 
 _D = ctypes.POINTER(ctypes.c_double)
 _U = ctypes.POINTER(ctypes.c_uint64)
 
 
-def build(force: bool = False, src: str = _SRC, out: str = _OUT) -> str:
+def build(force: bool = False, src: str = _SRC, out: str = _OUT, opt: str = "-O2") -> str:
     """Compile the oracle shared library (gcc, OpenMP, no FP contraction)."""
     os.makedirs(os.path.dirname(out), exist_ok=True)
     if not force and os.path.exists(out) and os.path.getmtime(out) >= os.path.getmtime(src):
         return out
     tmp = out + f".{os.getpid()}.tmp"
-    cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-ffp-contract=off", "-fno-fast-math",
+    cmd = ["gcc", opt, "-std=c11", "-fopenmp", "-ffp-contract=off", "-fno-fast-math",
            "-fPIC", "-shared", src, "-o", tmp, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, out)
     return out
+
+
+def build_gridded(force: bool = False) -> str:
+    """Compile the gridded CPU counter (gcc -O3, OpenMP, no FP contraction)."""
+    return build(force=force, src=_GSRC, out=_GOUT, opt="-O3")
 
 
 def _bind(path: str):
@@ -146,3 +158,39 @@ def rppi(*args, **kw):
 
 xi.__doc__ = Oracle.xi.__doc__
 rppi.__doc__ = Oracle.rppi.__doc__
+
+
+def _load_gridded():
+    global _glib
+    with _lock:
+        if _glib is None:
+            lib = ctypes.CDLL(build_gridded())
+            lib.gridded_xi.argtypes = [ctypes.c_int, ctypes.c_int64, _D, _D, _D, ctypes.c_int64, _D,
+                                       _D, _D, ctypes.c_int, _D, _D, ctypes.c_int,
+                                       ctypes.POINTER(ctypes.c_int), _U]
+            lib.gridded_xi.restype = ctypes.c_int
+            lib.gridded_num_threads.restype = ctypes.c_int
+            _glib = lib
+    return _glib
+
+
+def gridded_num_threads() -> int:
+    return int(_load_gridded().gridded_num_threads())
+
+
+def gridded_xi(x1, y1, z1, *, edges, x2=None, y2=None, z2=None, autocorr=True, periodic=True,
+               box=None, refine=(2, 2, 1)):
+    """DD(r) histogram (ordered pairs) by cell lists, see ``gridded.c``."""
+    lib = _load_gridded()
+    n1, a1 = _cat(x1, y1, z1, None)
+    n2, a2 = (0, (None, None, None, None)) if autocorr else _cat(x2, y2, z2, None)
+    edges = _f64(edges)
+    boxa = None if box is None else _f64(np.broadcast_to(np.asarray(box, dtype=np.float64), (3,)))
+    ref = (ctypes.c_int * 3)(*[int(v) for v in refine])
+    npairs = np.zeros(edges.size - 1, dtype=np.uint64)
+    st = lib.gridded_xi(int(autocorr), n1, *map(_ptr, a1[:3]), n2, *map(_ptr, a2[:3]),
+                        int(periodic), _ptr(boxa), _ptr(edges), int(edges.size), ref,
+                        npairs.ctypes.data_as(_U))
+    if st != 0:
+        raise ValueError(f"gridded counter returned status {st}")
+    return npairs
