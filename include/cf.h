@@ -54,7 +54,8 @@ extern "C" {
 #define CF_EINVAL (-1)    /* invalid argument (see cf_last_error)               */
 #define CF_ENOMEM (-2)    /* device or host allocation failed                   */
 #define CF_ECUDA (-3)     /* a CUDA runtime call failed                         */
-#define CF_ETIMEOUT (-4)  /* a bounded device-side wait gave up                 */
+#define CF_ETIMEOUT (-4)  /* a bounded device-side wait gave up (after ~2 s;
+                             the kernel returns, the context stays usable)      */
 #define CF_EDEVICE (-5)   /* a kernel reported an inconsistency (error word)    */
 
 typedef enum { CF_FLOAT32 = 0, CF_FLOAT64 = 1 } cf_dtype;
@@ -70,6 +71,12 @@ typedef enum {
 #define CF_FLAG_VERIFY_BAND (1u << 2) /* FP32 mode: also evaluate every pair in
                                          binary64 and count float32 decisions that
                                          disagree into n_band_violations (debug)  */
+#define CF_FLAG_DEBUG_STALL (1u << 3) /* diagnostic (float32 DD(r) without sums):
+                                         each CTA's first tile barrier is armed for
+                                         a copy that is never issued, and the waits
+                                         give up after 1 ms, so the call returns
+                                         CF_ETIMEOUT; tests the bounded waits.
+                                         Ignored by the other kernels.          */
 
 /* One catalogue: n points with coordinates x[i], y[i], z[i] of type
  * cf_config.dtype, contiguous, in device or host memory, and optional float64

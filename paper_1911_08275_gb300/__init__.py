@@ -28,6 +28,7 @@ CF_MODE_FP64, CF_MODE_FP32_RECHECK = 0, 1
 CF_FLAG_COUNT_EVALS = 1 << 0
 CF_FLAG_NO_PRUNE = 1 << 1
 CF_FLAG_VERIFY_BAND = 1 << 2
+CF_FLAG_DEBUG_STALL = 1 << 3
 
 _STATUS = {CF_EINVAL: "CF_EINVAL", CF_ENOMEM: "CF_ENOMEM", CF_ECUDA: "CF_ECUDA",
            CF_ETIMEOUT: "CF_ETIMEOUT", CF_EDEVICE: "CF_EDEVICE"}

@@ -575,6 +575,13 @@ int plan_geom(const Request &q, const double lo[3], const double hi[3], long lon
     return CF_OK;
 }
 
+// Limit of a kernel's tile-barrier waits: 2 s (a tile copy of a few tens of KB
+// that has not landed by then never will), 1 ms under CF_FLAG_DEBUG_STALL.
+uint64_t wait_limit_ns(uint32_t flags)
+{
+    return (flags & CF_FLAG_DEBUG_STALL) ? 1000000ull : 2000000000ull;
+}
+
 // Pair-kernel parameters that depend only on the request and the geometry:
 // stencil (Sec. 2.1: half stencil for auto), pruning radius and z reach
 // (Sec. 2.2), float32 slacks, bins and the pi-bin error band.  M and Ls return
@@ -602,6 +609,7 @@ void base_params(const Request &q, const cf::Geom &g, const cf::Gridded &A, cons
     P.shard_k = c->shard_count > 1 ? c->shard_index : 0;
     P.tile_max = 1024;
     P.flags = c->flags;
+    P.wait_ns = wait_limit_ns(c->flags);
     M = std::max(g.extent[0], std::max(g.extent[1], g.extent[2]));
     Ls = g.periodic ? std::max(g.box[0], std::max(g.box[1], g.box[2])) : 0.0;
     const double Rp = R * (1.0 + 1e-9) + 8.0 * U64 * (M + Ls);
@@ -1735,6 +1743,7 @@ int noalloc_xi(int autocorr, const cf_catalog *d1, const cf_catalog *d2, const d
     P.win_count = d_ctr + 2;
     P.tile_max = 1024;
     P.flags = c->flags & (CF_FLAG_NO_PRUNE | CF_FLAG_COUNT_EVALS);
+    P.wait_ns = wait_limit_ns(P.flags);
     const double M = std::max(g.extent[0], std::max(g.extent[1], g.extent[2]));
     const double Ls = g.periodic ? std::max(g.box[0], std::max(g.box[1], g.box[2])) : 0.0;
     const double Rp = R * (1.0 + 1e-9) + 8.0 * U64 * (M + Ls);

@@ -136,6 +136,7 @@ struct PairParams {
     int win_chunk;      // primaries per chunk the windows are computed for (0 = no pre-pass)
     int tile_max;       // points per staged tile
     uint32_t flags;
+    uint64_t wait_ns;   // limit of every tile-barrier wait (then the error word gets ERR_TIMEOUT)
     // radii (binary64 decisions on bounding boxes)
     double prune_r2;    // prune a column pair if its xy gap^2 >= prune_r2
     double rz;          // z reach: Rmax (xi) or pimax (rp-pi)
@@ -198,11 +199,21 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-// One bounded wait on phase `parity`; returns false if the limit was reached.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity, unsigned limit)
+// Nanoseconds of the GPU's global timer.
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// One bounded wait on phase `parity`: true once the phase completed, false
+// after limit_ns nanoseconds (or 2^26 tries, whichever comes first).
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity, uint64_t limit_ns)
 {
     const uint32_t a = smem_u32(bar);
-    for (unsigned it = 0; it < limit; ++it) {
+    uint64_t t0 = 0;
+    for (unsigned it = 0; it < (1u << 26); ++it) {
         uint32_t done;
         asm volatile(
             "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
@@ -212,6 +223,13 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity, unsign
             : "memory");
         if (done)
             return true;
+        if ((it & 31u) == 0u) {
+            const uint64_t t = global_ns();
+            if (it == 0u)
+                t0 = t;
+            else if (t - t0 > limit_ns)
+                return false;
+        }
     }
     return false;
 }

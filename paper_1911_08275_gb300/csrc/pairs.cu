@@ -101,7 +101,6 @@ void plan_pairs(PairParams &P, PairLaunch &L)
 
 namespace {
 
-constexpr unsigned WAIT_LIMIT = 1u << 22;
 typedef unsigned long long u64;
 
 __device__ __forceinline__ int floor_div(int a, int n)
@@ -477,7 +476,7 @@ constexpr int CLAIM_OFF = 16;
 // thread if the wait gave up.
 __device__ __forceinline__ bool stage_tiles32(unsigned char *smem, const Gridded &B, int t0,
                                               int count, uint64_t *bar, unsigned &phase,
-                                              unsigned *err, bool with_w = false)
+                                              unsigned *err, uint64_t wait_ns, bool with_w = false)
 {
     __syncthreads();  // previous tile fully consumed
     const unsigned bytes = (unsigned)count * 4u;
@@ -497,13 +496,17 @@ __device__ __forceinline__ bool stage_tiles32(unsigned char *smem, const Gridded
     if (with_w)
         for (int s = threadIdx.x; s < 64; s += THREADS)
             reinterpret_cast<float *>(smem + XIW_W_OFF)[count + s] = 0.0f;
-    const bool ok = mbar_wait(bar, phase, WAIT_LIMIT);
-    phase ^= 1u;
+    const bool ok = mbar_wait(bar, phase, wait_ns);
     if (__syncthreads_or(!ok)) {
-        if (threadIdx.x == 0)
+        if (threadIdx.x == 0) {
             atomicOr(err, ERR_TIMEOUT);
+            mbar_wait(bar, phase, wait_ns);  // a copy still in flight lands before the CTA exits
+        }
+        __syncthreads();
+        phase ^= 1u;
         return false;
     }
+    phase ^= 1u;
     return true;
 }
 
@@ -511,7 +514,8 @@ __device__ __forceinline__ bool stage_tiles32(unsigned char *smem, const Gridded
 // Returns false (in every thread) if the wait gave up.
 template <class T>
 __device__ __forceinline__ bool stage_tile(T *tile, const T *src, int count, int pad_elems,
-                                           uint64_t *bar, unsigned &phase, unsigned *err)
+                                           uint64_t *bar, unsigned &phase, unsigned *err,
+                                           uint64_t wait_ns)
 {
     __syncthreads();  // previous tile fully consumed
     if (threadIdx.x == 0) {
@@ -526,13 +530,17 @@ __device__ __forceinline__ bool stage_tile(T *tile, const T *src, int count, int
         nanv.x = nanv.y = nanv.z = nanv.w = q;
         tile[count + s] = nanv;  // sentinels after the copied range: never counted
     }
-    const bool ok = mbar_wait(bar, phase, WAIT_LIMIT);
-    phase ^= 1u;
+    const bool ok = mbar_wait(bar, phase, wait_ns);
     if (__syncthreads_or(!ok)) {
-        if (threadIdx.x == 0)
+        if (threadIdx.x == 0) {
             atomicOr(err, ERR_TIMEOUT);
+            mbar_wait(bar, phase, wait_ns);  // a copy still in flight lands before the CTA exits
+        }
+        __syncthreads();
+        phase ^= 1u;
         return false;
     }
+    phase ^= 1u;
     return true;
 }
 
@@ -1038,7 +1046,7 @@ struct Xi32Path {
         uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
         for (int t0 = it.b0; t0 < it.b1; t0 += TILE32) {
             const int nt = min(TILE32, it.b1 - t0);
-            if (!stage_tiles32(smem, P.B, t0, nt, bar, st.phase, P.err))
+            if (!stage_tiles32(smem, P.B, t0, nt, bar, st.phase, P.err, P.wait_ns))
                 return false;
             tile(P, it, t0, nt, smem + TX_OFF, reinterpret_cast<int *>(smem + CLAIM_OFF), smem, st);
         }
@@ -1398,7 +1406,7 @@ struct Xi64Path {
 
         for (int t0 = it.b0; t0 < it.b1; t0 += P.tile_max) {
             const int nt = min(P.tile_max, it.b1 - t0);
-            if (!stage_tile(tile, P.B.pos64 + t0, nt, 32, bar, phase, P.err)) {
+            if (!stage_tile(tile, P.B.pos64 + t0, nt, 32, bar, phase, P.err, P.wait_ns)) {
                 return false;
             }
             const double zt_lo = tile[0].z, zt_hi = tile[nt - 1].z;
@@ -1876,7 +1884,7 @@ struct Rppi32Path {
 
         for (int t0 = it.b0; t0 < it.b1; t0 += TILE32) {
             const int nt = min(TILE32, it.b1 - t0);
-            if (!stage_tiles32(smem, P.B, t0, nt, bar, phase, P.err, S.weighted)) {
+            if (!stage_tiles32(smem, P.B, t0, nt, bar, phase, P.err, P.wait_ns, S.weighted)) {
                 return false;
             }
             S.t0 = t0;
@@ -2208,7 +2216,7 @@ struct Rppi32PathPP {
 
         for (int t0 = it.b0; t0 < it.b1; t0 += TILE32) {
             const int nt = min(TILE32, it.b1 - t0);
-            if (!stage_tiles32(smem, P.B, t0, nt, bar, st.phase, P.err))
+            if (!stage_tiles32(smem, P.B, t0, nt, bar, st.phase, P.err, P.wait_ns))
                 return false;
             S.t0 = t0;
             const float zt_lo = tz[0];
@@ -2361,7 +2369,7 @@ struct Rppi64Path {
 
         for (int t0 = it.b0; t0 < it.b1; t0 += P.tile_max) {
             const int nt = min(P.tile_max, it.b1 - t0);
-            if (!stage_tile(tile, P.B.pos64 + t0, nt, 32, bar, phase, P.err)) {
+            if (!stage_tile(tile, P.B.pos64 + t0, nt, 32, bar, phase, P.err, P.wait_ns)) {
                 return false;
             }
             double zt_hi = tile[nt - 1].z;
@@ -2514,7 +2522,7 @@ static_assert(sizeof(PipeHdr) <= XI32_LUT_OFF, "pipeline header fits before the 
 // Fill buffer s with the next unit (called by one whole warp; lane 0 claims,
 // every lane pads, lane 0 issues the copies and arrives on the barrier).
 __device__ __forceinline__ void pipe_issue(const PairParams &P, PipeHdr *H, int s, int n_work,
-                                           unsigned char *buf, int lane)
+                                           unsigned char *buf, int lane, bool stall = false)
 {
     int item = -1, t0 = 0, nt = 0;
     if (lane == 0) {
@@ -2560,9 +2568,11 @@ __device__ __forceinline__ void pipe_issue(const PairParams &P, PipeHdr *H, int 
             const unsigned bytes = (unsigned)nt * 4u;
             fence_proxy_async_smem();
             mbar_arrive_expect_tx(&H->full[s], 3u * bytes);
-            bulk_g2s(buf, P.B.xs + t0, bytes, &H->full[s]);
-            bulk_g2s(buf + XI32_TSTRIDE, P.B.ys + t0, bytes, &H->full[s]);
-            bulk_g2s(buf + 2 * XI32_TSTRIDE, P.B.zs + t0, bytes, &H->full[s]);
+            if (!stall) {  // diagnostic stall: the armed copy is never issued
+                bulk_g2s(buf, P.B.xs + t0, bytes, &H->full[s]);
+                bulk_g2s(buf + XI32_TSTRIDE, P.B.ys + t0, bytes, &H->full[s]);
+                bulk_g2s(buf + 2 * XI32_TSTRIDE, P.B.zs + t0, bytes, &H->full[s]);
+            }
         } else {
             mbar_arrive(&H->full[s]);
         }
@@ -2590,17 +2600,19 @@ __global__ void __launch_bounds__(THREADS, MINB) k_pipe(const __grid_constant__ 
     __syncthreads();
     const int n_work = (int)*P.work_count;
     if (warp == 0) {
-        pipe_issue(P, H, 0, n_work, buf0, lane);
+        pipe_issue(P, H, 0, n_work, buf0, lane, (P.flags & CF_FLAG_DEBUG_STALL) != 0);
         pipe_issue(P, H, 1, n_work, buf1, lane);
     }
     PathState st = {0ull, 0ull, 0ull, 0u, 0u, 0u};
     unsigned par = 0u;  // bit s: parity of buffer s's next phase
+    bool timed_out = false;
     for (int u = 0;; ++u) {
         const int s = u & 1;
         unsigned char *buf = s ? buf1 : buf0;
-        if (!mbar_wait(&H->full[s], (par >> s) & 1u, WAIT_LIMIT)) {
+        if (!mbar_wait(&H->full[s], (par >> s) & 1u, P.wait_ns)) {
             if (lane == 0)
                 atomicOr(P.err, ERR_TIMEOUT);
+            timed_out = true;
             break;
         }
         par ^= 1u << s;
@@ -2626,7 +2638,16 @@ __global__ void __launch_bounds__(THREADS, MINB) k_pipe(const __grid_constant__ 
             pipe_issue(P, H, s, n_work, buf, lane);
         }
     }
-    __syncthreads();
+    if (__syncthreads_or(timed_out)) {
+        // every warp gave up at the same unit: let the copies still in flight (the
+        // other buffer's, and a late one of the stuck buffer) land before the CTA
+        // exits, each wait bounded again
+        if (threadIdx.x == 0) {
+            mbar_wait(&H->full[0], par & 1u, P.wait_ns);
+            mbar_wait(&H->full[1], (par >> 1) & 1u, P.wait_ns);
+        }
+        __syncthreads();
+    }
     Path::fini(P, smem, st);
 }
 
