@@ -219,7 +219,25 @@ def _median_call(fn, flush, reps=3):
     return res[-1], ms, kms
 
 
-def other_workloads(cf, synth, torch, cat, xyz, dev, stream, flush):
+def _timed_row(cf, fn, flush, peak_evals, fp32=True):
+    """One secondary workload: evaluation count (a separate run with
+    CF_FLAG_COUNT_EVALS), then the median of three timed calls; the roofline
+    fraction of the pair kernel is evaluations / kernel time / R1 (the same
+    7-instructions-per-evaluation roofline as the headline)."""
+    diag = fn(cf.CF_FLAG_COUNT_EVALS)
+    r, ms, kms = _median_call(lambda: fn(0), flush)
+    if not np.array_equal(r.npairs, diag.npairs):
+        raise RuntimeError("counts differ between the counting and the timed runs")
+    row = {"ms": ms, "kernel_ms": kms, "Gpairs_s": float(r.npairs.sum()) / (ms * 1e-3) / 1e9,
+           "evaluations": int(diag.n_evaluated)}
+    if fp32:
+        achieved = diag.n_evaluated / (kms * 1e-3) / 1e9
+        row["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak_evals,
+                           "unit": "Gevals/s", "frac": achieved / peak_evals}
+    return row
+
+
+def other_workloads(cf, synth, torch, cat, xyz, dev, stream, flush, peak_evals):
     """Secondary measurements (a few calls each; not the headline)."""
     out = {}
     st = stream.cuda_stream
@@ -227,18 +245,16 @@ def other_workloads(cf, synth, torch, cat, xyz, dev, stream, flush):
         e = synth.log_edges(RMIN, rmax, NBINS)
         row = {}
         for mode in ("fp32_recheck", "fp64"):
-            r, ms, kms = _median_call(lambda: cf.countpairs_xi(*xyz, e, boxsize=synth.BOX, mode=mode,
-                                                               stream=st), flush)
-            row[mode] = {"ms": ms, "kernel_ms": kms,
-                         "Gpairs_s": float(r.npairs.sum()) / (ms * 1e-3) / 1e9}
+            row[mode] = _timed_row(cf, lambda fl: cf.countpairs_xi(*xyz, e, boxsize=synth.BOX,
+                                                                   mode=mode, flags=fl, stream=st),
+                                   flush, peak_evals, mode == "fp32_recheck")
         out[f"xi_auto_rmax{rmax:g}"] = row
     e = synth.log_edges(RMIN, RMAX, 14)
     row = {}
     for mode in ("fp32_recheck", "fp64"):
-        r, ms, kms = _median_call(lambda: cf.countpairs_rp_pi(*xyz, e, 40.0, 40, boxsize=synth.BOX,
-                                                              mode=mode, stream=st), flush)
-        row[mode] = {"ms": ms, "kernel_ms": kms,
-                     "Gpairs_s": float(r.npairs.sum()) / (ms * 1e-3) / 1e9}
+        row[mode] = _timed_row(cf, lambda fl: cf.countpairs_rp_pi(*xyz, e, 40.0, 40, boxsize=synth.BOX,
+                                                                  mode=mode, flags=fl, stream=st),
+                               flush, peak_evals, mode == "fp32_recheck")
     out["rppi_auto_14x40_pimax40"] = row
     # weighted DR with ravg: 1.2M clustered data x 12M uniform randoms, open box
     wd = synth.uniform_weights(cat.n, 0.5, 1.5, seed=4)
@@ -246,62 +262,106 @@ def other_workloads(cf, synth, torch, cat, xyz, dev, stream, flush):
     wr = synth.uniform_weights(rnd.n, 0.5, 1.5, seed=5)
     a_w = torch.from_numpy(wd).to(dev)
     b = [torch.from_numpy(v).to(dev) for v in (rnd.x, rnd.y, rnd.z, wr)]
-    r, ms, kms = _median_call(lambda: cf.countpairs_xi(
-        *xyz, synth.log_edges(RMIN, RMAX, NBINS), w=a_w, x2=b[0], y2=b[1], z2=b[2], w2=b[3],
-        periodic=False, mode="fp32_recheck", want_ravg=True, stream=st), flush)
-    out["dr_weighted_ravg_1.2Mx12M_open"] = {
-        "fp32_recheck": {"ms": ms, "kernel_ms": kms,
-                         "Gpairs_s": float(r.npairs.sum()) / (ms * 1e-3) / 1e9}}
+    ed = synth.log_edges(RMIN, RMAX, NBINS)
+    out["dr_weighted_ravg_1.2Mx12M_open"] = {"fp32_recheck": _timed_row(
+        cf, lambda fl: cf.countpairs_xi(*xyz, ed, w=a_w, x2=b[0], y2=b[1], z2=b[2], w2=b[3],
+                                        periodic=False, mode="fp32_recheck", want_ravg=True,
+                                        flags=fl, stream=st), flush, peak_evals)}
+    out["dr_weighted_1.2Mx12M_open"] = {"fp32_recheck": _timed_row(
+        cf, lambda fl: cf.countpairs_xi(*xyz, ed, w=a_w, x2=b[0], y2=b[1], z2=b[2], w2=b[3],
+                                        periodic=False, mode="fp32_recheck", flags=fl,
+                                        stream=st), flush, peak_evals)}
     del b, a_w
     out["batch_48_jobs"] = batch_workload(cf, synth, torch, dev, flush)
     return out
 
 
-def batch_workload(cf, synth, torch, dev, flush):
-    """48 independent DD(r) / DD(rp, pi) jobs (synth.batch_job) in one batched
-    persistent launch replayed from a CUDA graph, against the same jobs as 48
-    single calls; per-job counts must be identical."""
-    jobs = [synth.batch_job(j) for j in range(48)]
-    xyz = [[torch.from_numpy(v).to(dev) for v in (jb["cat"].x, jb["cat"].y, jb["cat"].z)]
-           for jb in jobs]
+def _batch(cf, jobs, xyz, autotune):
     b = cf.Batch()
     res = []
     for jb, x in zip(jobs, xyz):
+        kw = dict(boxsize=jb["box"], mode=jb["mode"], autotune=autotune)
         if jb["kind"] == "xi":
-            res.append(b.add_xi(*x, jb["edges"], boxsize=jb["box"], mode=jb["mode"]))
+            res.append(b.add_xi(*x, jb["edges"], **kw))
         else:
-            res.append(b.add_rp_pi(*x, jb["edges"], jb["pimax"], jb["npibins"], boxsize=jb["box"],
-                                   mode=jb["mode"]))
-    first = b.run(use_graph=True)  # plan + capture
+            res.append(b.add_rp_pi(*x, jb["edges"], jb["pimax"], jb["npibins"], **kw))
+    return b, res
+
+
+def _time_batch(b, flush, reps=3, use_graph=True):
     runs = []
-    for _ in range(3):
+    for _ in range(reps):
         flush.zero_()
-        runs.append(b.run(use_graph=True))
-    direct = []
-    for _ in range(2):
-        flush.zero_()
-        direct.append(b.run(use_graph=False))
-    ms = statistics.median(r["total_ms"] for r in runs)
+        runs.append(b.run(use_graph=use_graph))
+    return statistics.median(r["total_ms"] for r in runs), runs[-1]
+
+
+def batch_workload(cf, synth, torch, dev, flush):
+    """48 independent DD(r) / DD(rp, pi) jobs (synth.batch_job) in one batched
+    persistent launch replayed from a CUDA graph, each job with the tuner's
+    refinement and float32 DD(r) kernel shape for its signature (tuned while the
+    first run plans the batch), against the same jobs as 48 single calls
+    (per-job counts must be identical); the float32 and the binary64 jobs as
+    batches of their own; and 480 small jobs (launch-bound) with and without
+    the graph."""
+    jobs = [synth.batch_job(j) for j in range(48)]
+    xyz = [[torch.from_numpy(v).to(dev) for v in (jb["cat"].x, jb["cat"].y, jb["cat"].z)]
+           for jb in jobs]
+    b, res = _batch(cf, jobs, xyz, autotune=True)
+    t0 = time.perf_counter()
+    first = b.run(use_graph=True)  # plan (tuning every new signature) + capture
+    first_wall_s = time.perf_counter() - t0
+    ms, last = _time_batch(b, flush)
+    direct_ms, direct = _time_batch(b, flush, reps=2, use_graph=False)
     single_ms, exact = 0.0, 0
     for jb, x, r in zip(jobs, xyz, res):
         flush.zero_()
+        kw = dict(boxsize=jb["box"], mode=jb["mode"], autotune=True)
         if jb["kind"] == "xi":
-            s = cf.countpairs_xi(*x, jb["edges"], boxsize=jb["box"], mode=jb["mode"])
+            sc = cf.countpairs_xi(*x, jb["edges"], **kw)
         else:
-            s = cf.countpairs_rp_pi(*x, jb["edges"], jb["pimax"], jb["npibins"], boxsize=jb["box"],
-                                    mode=jb["mode"])
-        single_ms += s.total_ms
-        exact += int(np.array_equal(s.npairs, r.npairs))
-    pairs = runs[-1]["pairs"]
+            sc = cf.countpairs_rp_pi(*x, jb["edges"], jb["pimax"], jb["npibins"], **kw)
+        single_ms += sc.total_ms
+        exact += int(np.array_equal(sc.npairs, r.npairs))
+    pairs = last["pairs"]
+    shapes = {}
+    for jb, r in zip(jobs, res):
+        key = f"{jb['kind']} {jb['mode']} refine {r.refine_used[0]}" + (
+            f" shape {r.chunk_used}x{r.pp_used}" if jb["kind"] == "xi" and jb["mode"] == "fp32_recheck"
+            else "")
+        shapes[key] = shapes.get(key, 0) + 1
     out = {"jobs": 48, "points": int(sum(jb["cat"].n for jb in jobs)), "pairs": int(pairs),
-           "ms": ms, "kernel_ms": statistics.median(r["kernel_ms"] for r in direct),
-           "ms_without_graph": statistics.median(r["total_ms"] for r in direct),
+           "ms": ms, "kernel_ms": direct["kernel_ms"], "ms_without_graph": direct_ms,
            "Gpairs_s": pairs / (ms * 1e-3) / 1e9, "graph": True,
-           "kernels_per_run": int(runs[-1]["n_kernels"]), "blocks": int(runs[-1]["blocks"]),
-           "first_run_ms_plan_and_capture": first["total_ms"],
+           "kernels_per_run": int(last["n_kernels"]), "blocks": int(last["blocks"]),
+           "first_run_wall_s_plan_tune_capture": first_wall_s,
+           "tuned_choices": shapes,
            "single_calls_ms": single_ms, "single_calls_Gpairs_s": pairs / (single_ms * 1e-3) / 1e9,
            "jobs_exact_vs_single_calls": exact}
     b.close()
+    # per mode: the float32 + re-check jobs and the binary64 jobs as batches of their own
+    for mode in ("fp32_recheck", "fp64"):
+        sel = [k for k, jb in enumerate(jobs) if jb["mode"] == mode]
+        bm, rm = _batch(cf, [jobs[k] for k in sel], [xyz[k] for k in sel], autotune=True)
+        bm.run(use_graph=True)
+        mms, ml = _time_batch(bm, flush)
+        out[f"by_mode_{mode}"] = {"jobs": len(sel), "pairs": int(ml["pairs"]), "ms": mms,
+                                  "Gpairs_s": ml["pairs"] / (mms * 1e-3) / 1e9}
+        bm.close()
+    del xyz
+    # launch-bound: 480 small jobs (about 2,000-8,000 points each), graph vs direct issue
+    small = [synth.batch_job(j % 48, scale=0.004) for j in range(480)]
+    sx = [[torch.from_numpy(v).to(dev) for v in (jb["cat"].x, jb["cat"].y, jb["cat"].z)]
+          for jb in small]
+    bs, _ = _batch(cf, small, sx, autotune=False)
+    bs.run(use_graph=True)
+    g_ms, gl = _time_batch(bs, flush)
+    d_ms, _ = _time_batch(bs, flush, use_graph=False)
+    out["small_480_jobs"] = {"jobs": 480, "points": int(sum(jb["cat"].n for jb in small)),
+                             "pairs": int(gl["pairs"]), "kernels_per_run": int(gl["n_kernels"]),
+                             "ms_graph": g_ms, "ms_without_graph": d_ms,
+                             "graph_gain": d_ms / g_ms}
+    bs.close()
     return out
 
 
@@ -437,7 +497,8 @@ def main():
         out["fp64_path"]["value"] = p_cnt / (out["fp64_path"]["ms_per_step"] * 1e-3) / 1e9
         out["fp32_over_fp64"] = out["fp64_path"]["ms_per_step"] / t_mean
     if rank == 0 and world == 1 and not args.no_extra:
-        out["other_workloads"] = other_workloads(cf, synth, torch, cat, xyz, dev, stream, flush)
+        out["other_workloads"] = other_workloads(cf, synth, torch, cat, xyz, dev, stream, flush,
+                                                 peak_evals)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if dist:

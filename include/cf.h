@@ -211,12 +211,18 @@ int cf_countpairs_xi_noalloc(int autocorr, const cf_catalog *d1, const cf_catalo
  * by later runs.
  *   cf_batch_add_xi / cf_batch_add_rp_pi: arguments as cf_countpairs_xi /
  *     cf_countpairs_rp_pi, validated at once.  Batched jobs count unweighted
- *     pairs (cfg->weighted and cfg->want_ravg must be 0), take coordinates in
- *     DEVICE memory, and use the float32 kernel shape 16 x 2; flags other than
- *     CF_FLAG_NO_PRUNE are ignored; with cfg->autotune a cached refinement is
- *     used when the tuning cache has one (a batch never times candidates).
+ *     pairs (cfg->weighted and cfg->want_ravg must be 0) and take coordinates
+ *     in DEVICE memory; flags other than CF_FLAG_NO_PRUNE are ignored.  With
+ *     cfg->autotune a job uses the tuner's refinement and, for float32 DD(r),
+ *     kernel shape (16 x 2, 8 x 2, 16 x 1 or 32 x 1) for its signature; a
+ *     signature the cache does not hold is tuned when the batch is planned, by
+ *     timing the candidates with single calls as cf_countpairs_xi does (res
+ *     reports refine_used, chunk_used, pp_used and tuned).  Without autotune a
+ *     job uses its own refinement and the shape 16 x 2.
  *     The catalogues and res stay borrowed until cf_batch_destroy; their
- *     contents may change between runs.
+ *     contents may change between runs.  A job's results are written to its
+ *     res by every cf_batch_run (res takes the place of a separate result
+ *     query).
  *   cf_batch_run: plans the jobs on the first run (open boxes: one bounding-box
  *     pass with a host synchronisation), counts every job and writes each
  *     job's res before returning (one synchronisation of the stream).  Later

@@ -479,6 +479,7 @@ class Batch:
             r.refine_used = tuple(res.refine_used)
             r.chunk_used = int(res.chunk_used)
             r.pp_used = int(res.pp_used)
+            r.tuned = int(res.tuned)
         return {f: getattr(stats, f) for f, _ in cf_batch_stats._fields_}
 
     def close(self) -> None:

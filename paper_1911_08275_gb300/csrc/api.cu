@@ -1840,6 +1840,8 @@ struct BatchJob {
     cf::Gridded G[2] = {};
     cf::PairParams P;
     int path = 0, nslots = 0, smem = 0;
+    int chunk = 16, pp = 2;  // float32 DD(r) kernel shape (tuned or the default 16 x 2)
+    int tuned = 0;           // as cf_result.tuned: 1 tuned at plan time, 2 cached choice used
     size_t out_off = 0;  // u64 words into the output block: [hist | diag(4) | err, - | kept, -]
     uint64_t n_kernels = 0;
 };
@@ -1989,7 +1991,9 @@ int batch_plan(cf_batch *b, cudaStream_t st, const std::vector<std::array<double
 {
     batch_free_plan(b);
     const int nj = (int)b->jobs.size();
-    // refinement: a cached autotuner choice, else the job's own
+    // refinement and float32 DD(r) kernel shape: with autotune the tuner's choice
+    // for the job's signature (Sec. 3.1), timed now with single calls when the
+    // cache has none; else the job's own refinement and the default shape
     for (int k = 0; k < nj; ++k) {
         BatchJob &j = b->jobs[k];
         batch_bind(j);
@@ -1997,16 +2001,51 @@ int batch_plan(cf_batch *b, cudaStream_t st, const std::vector<std::array<double
             j.lo[a] = box[k][a];
             j.hi[a] = box[k][3 + a];
         }
-        if (j.cfg.autotune && !(j.cfg.refine[0] || j.cfg.refine[1] || j.cfg.refine[2])) {
+        j.chunk = 16;
+        j.pp = 2;
+        j.tuned = 0;
+        if (j.cfg.autotune) {
+            const bool fixed_refine = j.cfg.refine[0] || j.cfg.refine[1] || j.cfg.refine[2];
             double vol = 1.0;
             for (int a = 0; a < 3; ++a)
                 vol *= j.cfg.periodic ? j.cfg.boxsize[a] : std::max(j.hi[a] - j.lo[a], j.edges.back());
-            std::lock_guard<std::mutex> lock(g_tune.mu);
-            tune_env_load_locked();
-            auto it = g_tune.m.find(tune_key(j.q, vol));
-            if (it != g_tune.m.end())
-                for (int a = 0; a < 3; ++a)
-                    j.cfg.refine[a] = it->second.refine[a];
+            const std::string key = tune_key(j.q, vol);
+            TuneChoice ch;
+            bool have = false;
+            auto lookup = [&]() {
+                std::lock_guard<std::mutex> lock(g_tune.mu);
+                tune_env_load_locked();
+                auto it = g_tune.m.find(key);
+                if (it != g_tune.m.end()) {
+                    ch = it->second;
+                    have = true;
+                }
+            };
+            lookup();
+            j.tuned = have ? 2 : 1;
+            if (!have) {  // time the candidates with single calls, as cf_countpairs_xi does
+                const int ns = j.q.kind == 0 ? (int)j.edges.size() - 1
+                                              : ((int)j.edges.size() - 1) * j.q.npibins;
+                std::vector<uint64_t> scratch(ns);
+                cf_result tr;
+                std::memset(&tr, 0, sizeof(tr));
+                tr.npairs = scratch.data();
+                Request r = j.q;
+                r.res = &tr;
+                const int rc = run_tuned(r);
+                if (rc)
+                    return fail(rc, "batch job " + std::to_string(k) + " autotuning: " + g_err);
+                lookup();
+            }
+            if (have) {
+                if (!fixed_refine)
+                    for (int a = 0; a < 3; ++a)
+                        j.cfg.refine[a] = ch.refine[a];
+                if (j.q.kind == 0 && j.cfg.mode == CF_MODE_FP32_RECHECK) {
+                    j.chunk = ch.chunk;
+                    j.pp = ch.pp;
+                }
+            }
         }
         long long ntot = 0;
         for (int t = 0; t < j.ncat; ++t)
@@ -2138,11 +2177,11 @@ int batch_plan(cf_batch *b, cudaStream_t st, const std::vector<std::array<double
         cf::PairLaunch PL;
         std::memset(&PL, 0, sizeof(PL));
         PL.f64 = f64;
-        PL.chunk = 16;
-        PL.pp = 2;
+        PL.chunk = j.chunk;
+        PL.pp = j.pp;
         cf::plan_pairs(j.P, PL);
         j.smem = PL.smem;
-        j.path = cf::batch_path(j.P, f64);
+        j.path = cf::batch_path(j.P, f64, j.chunk, j.pp);
         b->smem_max = std::max(b->smem_max, PL.smem);
         hp[k] = j.P;
         hpath[k] = j.path;
@@ -2315,9 +2354,9 @@ int batch_run(cf_batch *b, cudaStream_t user, int use_graph, cf_batch_stats *sta
         int rr[3];
         resolve_refine(&j.cfg, rr);
         res->refine_used[2] = rr[2];
-        res->chunk_used = 16;
-        res->pp_used = 2;
-        res->tuned = 0;
+        res->chunk_used = j.chunk;
+        res->pp_used = j.pp;
+        res->tuned = j.tuned;
         res->table_linear = j.P.lut_lin;
     }
     if (stats) {

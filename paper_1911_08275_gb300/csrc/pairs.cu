@@ -2657,6 +2657,9 @@ __global__ void __launch_bounds__(THREADS, MINB) k_pipe(const __grid_constant__ 
 // kept column pairs; a CTA that moves on to another job merges its histograms
 // into the previous job's output and loads the next job's tables.
 using XiF32 = Xi32Path<16, 2, false, false>;
+using XiF32_8x2 = Xi32Path<8, 2, false, false>;
+using XiF32_16x1 = Xi32Path<16, 1, false, false>;
+using XiF32_32x1 = Xi32Path<32, 1, false, false>;
 using XiF64 = Xi64Path<8, false, false>;
 using RpF32 = Rppi32PathPP<16, 2, false>;
 using RpF64 = Rppi64Path<8, false, false>;
@@ -2664,7 +2667,10 @@ using RpF64 = Rppi64Path<8, false, false>;
 __device__ __forceinline__ void batch_init(int path, const PairParams &P, unsigned char *smem)
 {
     switch (path) {
-    case BATCH_XI32: XiF32::init(P, smem); break;
+    case BATCH_XI32:
+    case BATCH_XI32_8x2:
+    case BATCH_XI32_16x1:
+    case BATCH_XI32_32x1: XiF32::init(P, smem); break;  // shape-independent
     case BATCH_XI64: XiF64::init(P, smem); break;
     case BATCH_RPPI32: RpF32::init(P, smem); break;
     default: RpF64::init(P, smem); break;
@@ -2676,6 +2682,9 @@ __device__ __forceinline__ bool batch_item(int path, const PairParams &P, const 
 {
     switch (path) {
     case BATCH_XI32: return XiF32::item(P, it, smem, st);
+    case BATCH_XI32_8x2: return XiF32_8x2::item(P, it, smem, st);
+    case BATCH_XI32_16x1: return XiF32_16x1::item(P, it, smem, st);
+    case BATCH_XI32_32x1: return XiF32_32x1::item(P, it, smem, st);
     case BATCH_XI64: return XiF64::item(P, it, smem, st);
     case BATCH_RPPI32: return RpF32::item(P, it, smem, st);
     default: return RpF64::item(P, it, smem, st);
@@ -2686,7 +2695,10 @@ __device__ __forceinline__ void batch_fini(int path, const PairParams &P, unsign
                                            PathState &st)
 {
     switch (path) {
-    case BATCH_XI32: XiF32::fini(P, smem, st); break;
+    case BATCH_XI32:
+    case BATCH_XI32_8x2:
+    case BATCH_XI32_16x1:
+    case BATCH_XI32_32x1: XiF32::fini(P, smem, st); break;  // shape-independent
     case BATCH_XI64: XiF64::fini(P, smem, st); break;
     case BATCH_RPPI32: RpF32::fini(P, smem, st); break;
     default: RpF64::fini(P, smem, st); break;
@@ -2829,10 +2841,19 @@ cudaError_t launch_persistent(K kern, const PairParams &P, PairLaunch &L, int sm
 
 }  // namespace
 
-int batch_path(const PairParams &P, int f64)
+int batch_path(const PairParams &P, int f64, int chunk, int pp)
 {
-    if (P.kind == 0)
-        return f64 ? BATCH_XI64 : BATCH_XI32;
+    if (P.kind == 0) {
+        if (f64)
+            return BATCH_XI64;
+        if (pp == 2 && chunk == 8)
+            return BATCH_XI32_8x2;
+        if (pp == 1 && chunk == 16)
+            return BATCH_XI32_16x1;
+        if (pp == 1 && chunk == 32)
+            return BATCH_XI32_32x1;
+        return BATCH_XI32;
+    }
     return f64 ? BATCH_RPPI64 : BATCH_RPPI32;
 }
 

@@ -80,7 +80,15 @@ void plan_pairs(PairParams &P, PairLaunch &L);
 cudaError_t launch_pairs(const PairParams &P, PairLaunch &L, int sms, cudaStream_t st);
 
 // ---- batched launch: jobs of these paths share one persistent kernel
-enum : int { BATCH_XI32 = 0, BATCH_XI64 = 1, BATCH_RPPI32 = 2, BATCH_RPPI64 = 3 };
+enum : int {
+    BATCH_XI32 = 0,       // float32 DD(r), chunks of 16 lanes x 2 primaries
+    BATCH_XI64 = 1,
+    BATCH_RPPI32 = 2,
+    BATCH_RPPI64 = 3,
+    BATCH_XI32_8x2 = 4,   // float32 DD(r) with the other tuned shapes
+    BATCH_XI32_16x1 = 5,
+    BATCH_XI32_32x1 = 6,
+};
 constexpr int BATCH_MAX = 1024;  // jobs per batched launch
 
 struct BatchParams {
@@ -91,9 +99,10 @@ struct BatchParams {
     unsigned *item_counter;  // device, zeroed before the launch
 };
 
-// Path of a job: float32 (kernel shape 16 x 2) or binary64, DD(r) or DD(rp, pi);
+// Path of a job: float32 (float32 DD(r) in the kernel shape chunk x pp: 16 x 2,
+// 8 x 2, 16 x 1 or 32 x 1, else 16 x 2) or binary64, DD(r) or DD(rp, pi);
 // unweighted only.
-int batch_path(const PairParams &P, int f64);
+int batch_path(const PairParams &P, int f64, int chunk = 16, int pp = 2);
 
 // The work-list kernel of one job (kept column pairs into P.work, count into
 // *P.work_count, which must be zero).

@@ -122,3 +122,57 @@ def test_batch_rejects_host_inputs_and_empty_runs(cuda_device):
     with pytest.raises(cf.CfError):
         b.run()
     b.close()
+
+
+def test_batch_autotune_tunes_at_plan_time_and_forced_shapes_are_exact(cuda_device, tmp_path):
+    import json
+    cf.tune_clear()
+    jobs = []
+    for k, (n_par, box) in enumerate(((150, 80.0), (600, 120.0), (2400, 200.0), (9000, 300.0))):
+        jobs.append(dict(kind="xi", mode="fp32_recheck", box=box,
+                         edges=synth.log_edges(0.1, 12.0 + 3 * k, 12),
+                         cat=synth.neyman_scott(n_par, 20.0, 2.0, box, seed=420 + k)))
+    jobs.append(dict(kind="rppi", mode="fp32_recheck", box=150.0, edges=synth.log_edges(0.2, 10.0, 8),
+                     pimax=10.0, npibins=10, cat=synth.uniform_box(20000, 150.0, seed=430)))
+    jobs.append(dict(kind="xi", mode="fp64", box=100.0, edges=synth.log_edges(0.2, 10.0, 8),
+                     cat=synth.uniform_box(8000, 100.0, seed=431)))
+    xyz = [dev(jb["cat"]) for jb in jobs]
+
+    def run_batch():
+        b = cf.Batch()
+        res = []
+        for jb, x in zip(jobs, xyz):
+            kw = dict(boxsize=jb["box"], mode=jb["mode"], autotune=True)
+            if jb["kind"] == "xi":
+                res.append(b.add_xi(*x, jb["edges"], **kw))
+            else:
+                res.append(b.add_rp_pi(*x, jb["edges"], jb["pimax"], jb["npibins"], **kw))
+        b.run(use_graph=True)
+        for jb, x, r in zip(jobs, xyz, res):
+            assert np.array_equal(r.npairs, single(jb, x))
+        b.close()
+        return res
+
+    # first batch: every signature is tuned while the batch is planned
+    first = run_batch()
+    assert cf.tune_count() >= 4
+    assert all(r.refine_used[0] in (1, 2, 3) for r in first)
+    # force each float32 DD(r) kernel shape through the tuning cache file
+    path = str(tmp_path / "tune.json")
+    cf.tune_save(path)
+    with open(path) as f:
+        cache = json.load(f)
+    shapes = [(16, 2), (8, 2), (16, 1), (32, 1)]
+    forced = {}
+    for i, entry in enumerate(e for e in cache["entries"] if e["key"].startswith("k0 m1")):
+        entry["chunk"], entry["pp"] = shapes[i % 4]
+        forced[entry["key"]] = shapes[i % 4]
+    with open(path, "w") as f:
+        json.dump(cache, f)
+    cf.tune_clear()
+    cf.tune_load(path)
+    second = run_batch()
+    used = {(r.chunk_used, r.pp_used) for jb, r in zip(jobs, second)
+            if jb["kind"] == "xi" and jb["mode"] == "fp32_recheck"}
+    assert len(used) == min(4, len(forced)) and all(r.tuned == 2 for r in second)
+    cf.tune_clear()
