@@ -365,6 +365,37 @@ def batch_workload(cf, synth, torch, dev, flush):
     return out
 
 
+def run_profile_case(args):
+    """A few calls of one workload for an ncu capture (no L2 flush, no JSON line):
+    xi (C2, Rmax 25), rppi (C2, 14 x 40, pimax 40), dr_small (the C2 data, weighted,
+    against the first 1.2M weighted randoms, open box, with ravg)."""
+    import torch
+    import paper_1911_08275_gb300 as cf
+    from paper_1911_08275_gb300 import synth
+    cf.lib()
+    cat = synth.c2_clustered()
+    dev = torch.device("cuda", 0)
+    xyz = [torch.from_numpy(v).to(dev) for v in (cat.x, cat.y, cat.z)]
+    e = synth.log_edges(RMIN, RMAX, NBINS)
+    if args.profile == "dr_small":
+        wd = torch.from_numpy(synth.uniform_weights(cat.n, 0.5, 1.5, seed=4)).to(dev)
+        rnd = synth.c4_randoms().take(np.arange(1200000))
+        wr = synth.uniform_weights(12000000, 0.5, 1.5, seed=5)[:1200000]
+        b = [torch.from_numpy(np.ascontiguousarray(v)).to(dev) for v in (rnd.x, rnd.y, rnd.z, wr)]
+    ms = []
+    for _ in range(args.steps):
+        if args.profile == "xi":
+            r = cf.countpairs_xi(*xyz, e, boxsize=synth.BOX)
+        elif args.profile == "rppi":
+            r = cf.countpairs_rp_pi(*xyz, synth.log_edges(RMIN, RMAX, 14), 40.0, 40, boxsize=synth.BOX)
+        else:
+            r = cf.countpairs_xi(*xyz, e, w=wd, x2=b[0], y2=b[1], z2=b[2], w2=b[3], periodic=False,
+                                 want_ravg=True)
+        ms.append(round(r.kernel_ms, 4))
+    torch.cuda.synchronize()
+    print(f"profile case {args.profile}: kernel_ms {ms}, pairs {int(r.npairs.sum())}", flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -375,7 +406,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the secondary workloads (Rmax sweep, DD(rp,pi), weighted DR)")
+    ap.add_argument("--profile", choices=["xi", "rppi", "dr_small"],
+                    help="run --steps calls of one workload for a profiler capture, then exit")
     args = ap.parse_args()
+    if args.profile:
+        return run_profile_case(args)
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
