@@ -290,7 +290,7 @@ int cf_tune_count(void);
  *     separations, 2 for projected rp.
  *   table[0 .. lut_n): the entry of cell q is bin k when every value of the
  *     cell lies in [hi_k, lo_{k+1}), nedges - 1 when every value is surely
- *     not counted, nedges otherwise.  Value v >= 0 lies in cell
+ *     not counted, 255 otherwise.  Value v >= 0 lies in cell
  *     round(v * lscale) (lin = 1; the float32 product rounded half to even)
  *     or ((bits(v) >> shift) - u0) mod 2^32 (lin = 0); cells past lut_n - 1
  *     (and NaN) use entry lut_n - 1.

@@ -130,7 +130,7 @@ double band_sq(double S, int ncomp, double M, double Ls, double R)
 //     patterns u with (u >> shift) == u0s + q; tab[lut_n - 1] is the entry that
 //     every out-of-range distance (below lo_0, at or above hi_n, NaN) uses.
 //     Entries: bin k if every value of the cell lies in [hi_k, lo_{k+1});
-//     nbins if every value is surely not counted; nbins + 1 otherwise (the
+//     nbins if every value is surely not counted; TAB_FLAGGED otherwise (the
 //     cell contains a threshold or lies inside a band).
 struct Tables {
     int nthr, lut_n, shift;
@@ -181,7 +181,7 @@ template <class Bounds>
 double classify_cells(const float *T, int nthr, int nbins, int n, int ncomp, Bounds bounds,
                       uint8_t *tab)
 {
-    const uint8_t dummy = (uint8_t)nbins, flagged = (uint8_t)(nbins + 1);
+    const uint8_t dummy = (uint8_t)nbins, flagged = cf::TAB_FLAGGED;
     auto mass = [&](double a, double b) {
         a = std::max(a, 0.0);
         b = std::max(b, a);

@@ -28,14 +28,18 @@ enum : unsigned {
 };
 
 // Lookup-table entry (one byte): 0..nbins-1 -> the bin (the cell lies wholly
-// between hi_k and lo_{k+1}); nbins -> surely not counted; nbins + 1 -> the
-// cell touches a threshold or a band (settled by the thresholds, maybe a
-// binary64 re-check).  The float32 DD(r) kernel keeps a histogram row for each
-// of the nbins + 2 values, so an entry is a row index without a clamp.
+// between hi_k and lo_{k+1}); nbins -> surely not counted; TAB_FLAGGED (0xff)
+// -> the cell touches a threshold or a band (settled by the thresholds, maybe
+// a binary64 re-check).  Loaded sign-extended the flagged entry is -1, so its
+// sign bit marks the pair: the float32 kernels keep a histogram row for each
+// of the values -1 .. nbins (the row of -1 just before bin 0, never read) and
+// an entry is a row index without a clamp.
+constexpr unsigned char TAB_FLAGGED = 0xff;
 
 // Shared layout of the float32 DD(r) kernel (compile-time offsets):
 // [0,128) barrier + work item; LUT; x, y, z tiles of TILE32 + 64 floats each;
-// thresholds; squared edges; histogram copies ((nbins + 2) rows of 32 lanes each).
+// thresholds; squared edges; histogram copies ((nbins + 2) rows of 32 lanes each:
+// the flagged row, the bins, the not-counted row).
 constexpr int XI32_LUT_OFF = 128;
 constexpr int XI32_TX_OFF = XI32_LUT_OFF + LUT_MAX;
 constexpr int XI32_TSTRIDE = (TILE32 + 64) * 4;

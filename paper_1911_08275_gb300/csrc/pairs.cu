@@ -44,9 +44,10 @@
 
 namespace cf {
 
-// Rows of one float32 DD(rp, pi) histogram copy: the bins, the not-counted row,
-// and the row that pairs in a flagged rp cell land in until they are settled
-// (never read), so a table entry is a row index without a clamp.
+// Rows of one float32 DD(rp, pi) histogram copy: the row that pairs in a flagged
+// rp cell land in until they are settled (row -1, never read), the bins and the
+// not-counted row, so a sign-extended table entry is a row index without a
+// clamp.  Row 0 is the copy's second row.
 inline __host__ __device__ int rppi32_rows(int nb) { return nb + 2; }
 
 void plan_pairs(PairParams &P, PairLaunch &L)
@@ -627,6 +628,22 @@ __device__ __forceinline__ void red_shared1(uint32_t addr)
     asm volatile("red.shared.add.u32 [%0], 1;" ::"r"(addr));
 }
 
+// Table byte at a shared address, sign-extended: the flagged entry gives -1.
+__device__ __forceinline__ uint32_t lds_entry(uint32_t addr)
+{
+    uint32_t e;
+    asm volatile("ld.shared.s8 %0, [%1];" : "=r"(e) : "r"(addr));
+    return e;
+}
+
+// (m << 1) | (v >> 31): one funnel shift appends v's sign bit to the mask m.
+__device__ __forceinline__ uint32_t push_sign(uint32_t m, uint32_t v)
+{
+    uint32_t r;
+    asm("shf.l.wrap.b32 %0, %1, %2, 1;" : "=r"(r) : "r"(v), "r"(m));
+    return r;
+}
+
 // Flagged table cell: count the thresholds <= d2; inside a band re-evaluate in
 // binary64.  Adds the pair to its true bin (the main path has already put it in
 // the flagged row, which is never read).  Returns 1 if re-evaluated.
@@ -687,7 +704,7 @@ __device__ __forceinline__ void wacc_add(const WAcc &A, uint32_t e, float pw, fl
         float r;
         asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(d2));
         const float rw = W ? r * pw : r;
-        red_shared_u32(A.hlr + e * 128u, __float_as_uint(__fmaf_rn(rw, A.sr[e], QMAGIC)));
+        red_shared_u32(A.hlr + e * 128u, __float_as_uint(__fmaf_rn(rw, A.sr[(int)e], QMAGIC)));
     }
 }
 
@@ -792,10 +809,6 @@ __device__ __forceinline__ void sweep32(unsigned char *smem, const Sweep32 &S, u
     const int jstart = jlo & ~3;  // 16-byte aligned quads; extra j's are never counted
     constexpr int JS = 128 / I;   // secondaries per step (four per lane group)
     const int nit = (jhi - jstart + JS - 1) / JS;
-    const uint32_t nbu = (uint32_t)S.nb;
-    // entries are <= nbu + 1 < 0x80: adding 0x80 - (nbu + 1) to each byte sets its
-    // top bit exactly for the flagged value, without carries between bytes
-    const uint32_t cflag = (0x80u - (nbu + 1u)) * 0x01010101u;
     const u64 LS = pack2(S.lscale, S.lscale), LM = pack2(LIN_MAGIC, LIN_MAGIC);
     // shared addresses of the table: fma(d2, s, 2^23) >= 2^23 (d2 >= 0, NaN larger),
     // so bits - LIN_MAGIC_BITS never wraps and the base folds into the clamp
@@ -893,19 +906,15 @@ __device__ __forceinline__ void sweep32(unsigned char *smem, const Sweep32 &S, u
             }
 #pragma unroll
             for (int q = 0; q < PP; ++q) {
-                uint32_t e[4];
 #pragma unroll
                 for (int r = 0; r < 4; ++r) {
-                    asm volatile("ld.shared.u8 %0, [%1];" : "=r"(e[r]) : "r"(cq[q][r]));  // the row
-                    red_shared1(hl + e[r] * 128u);  // every entry is a row: bin, dummy or flagged
+                    const uint32_t e = lds_entry(cq[q][r]);  // the row: bin, dummy or flagged (-1)
+                    red_shared1(hl + e * 128u);
                     if (W || RV)
-                        wacc_add<W, RV>(A, e[r], W ? pw[q][r] : 1.0f, RL ? dr[q][r] : d[q][r]);
+                        wacc_add<W, RV>(A, e, W ? pw[q][r] : 1.0f, RL ? dr[q][r] : d[q][r]);
+                    // pair (t, r) ends at bit 4 tend - 1 - (4 t + r) of the mask
+                    fm[q] = push_sign(fm[q], e);
                 }
-                const uint32_t w = __byte_perm(__byte_perm(e[0], e[1], 0x0040),
-                                               __byte_perm(e[2], e[3], 0x0040), 0x5410);
-                // shift the mask one step down and add this step's bits at 8 r + 7: after
-                // tend steps, step t sits at bit 8 r + 8 - tend + t
-                fm[q] = (fm[q] >> 1) | ((w + cflag) & 0x80808080u);
             }
             if (VERIFY) {
                 const float *T = reinterpret_cast<const float *>(smem + THR_OFF);
@@ -940,8 +949,8 @@ __device__ __forceinline__ void sweep32(unsigned char *smem, const Sweep32 &S, u
                 while (m) {
                     const int bit = __ffs(m) - 1;
                     m &= m - 1u;
-                    const int t = (bit & 7) - (8 - tend), r = bit >> 3;
-                    const int jl = jAb + t * JS + r;
+                    const int k = 4 * tend - 1 - bit;  // = 4 t + r
+                    const int jl = jAb + (k >> 2) * JS + (k & 3);
                     n_rck += resolve_local<W, RV, RL>(smem, S, hl, xh, yh, zh, iv[q], jl, A, wi[q],
                                                       lx, ly, lz);
                 }
@@ -1030,8 +1039,8 @@ struct Xi32Path {
         if (W || RV) {
             float *sr = reinterpret_cast<float *>(hist + planes * WARPS * (nb + 2) * 32);
             const float mw = W ? wmax_pair(P) : 1.0f;
-            for (int k = tid; k < nb + 2; k += THREADS)  // r w < 2^20 scale in bin k (headroom 2)
-                sr[k] = k < nb ? pow2_floor(1048576.0f / (sqrtf((float)E2[k + 1]) * mw)) : 0.0f;
+            for (int k = tid; k < nb + 2; k += THREADS)  // r w < 2^20 scale in bin k - 1 (headroom 2)
+                sr[k] = (k >= 1 && k <= nb) ? pow2_floor(1048576.0f / (sqrtf((float)E2[k]) * mw)) : 0.0f;
             long long *g = P.wscratch + ((long long)blockIdx.x * THREADS + tid) * 3 * nb;
             for (int k = 0; k < 3 * nb; ++k)
                 g[k] = 0;
@@ -1072,7 +1081,8 @@ struct Xi32Path {
         u64 &n_viol = st.n_viol;
         unsigned &pending = st.pending;
 
-        uint32_t *hw = hist + (warp % HC) * (nb + 2) * 32;  // rows: bins, not counted, flagged
+        // row 0 of the warp's copy (rows: flagged at -1, the bins, not counted)
+        uint32_t *hw = hist + ((warp % HC) * (nb + 2) + 1) * 32;
         const uint32_t hl = smem_u32(hw + lane);  // this lane's histogram column (shared address)
         const int ii = lane % I, jj = lane / I;
         WAcc A;
@@ -1083,7 +1093,7 @@ struct Xi32Path {
             A.rq = A.cnt + (W ? 2 : 1) * plane;
             A.hlw = smem_u32(A.wq);
             A.hlr = smem_u32(A.rq);
-            A.sr = reinterpret_cast<const float *>(hist + (1 + (W ? 1 : 0) + (RV ? 1 : 0)) * plane);
+            A.sr = reinterpret_cast<const float *>(hist + (1 + (W ? 1 : 0) + (RV ? 1 : 0)) * plane) + 1;
             A.sw = W ? pow2_floor(2097152.0f / wmax_pair(P)) : 1.0f;
             A.wsj = P.B.ws;
             A.g = P.wscratch + ((long long)blockIdx.x * THREADS + tid) * 3 * nb;
@@ -1300,7 +1310,7 @@ struct Xi32Path {
             // the lane's last rows, then the CTA's 64-bit sums -> global
             const int plane = WARPS * (nb + 2) * 32, warp = tid >> 5;
             WAcc A;
-            A.cnt = hist + warp * (nb + 2) * 32 + lane;
+            A.cnt = hist + (warp * (nb + 2) + 1) * 32 + lane;
             A.wq = A.cnt + plane;
             A.rq = A.cnt + (W ? 2 : 1) * plane;
             A.g = P.wscratch + ((long long)blockIdx.x * THREADS + tid) * 3 * nb;
@@ -1308,7 +1318,7 @@ struct Xi32Path {
             wacc_flush<W, RV>(A);
             __threadfence_block();
             __syncthreads();
-            const float *sr = reinterpret_cast<const float *>(hist + (1 + (W ? 1 : 0) + (RV ? 1 : 0)) * plane);
+            const float *sr = reinterpret_cast<const float *>(hist + (1 + (W ? 1 : 0) + (RV ? 1 : 0)) * plane) + 1;
             const float sw = W ? pow2_floor(2097152.0f / wmax_pair(P)) : 1.0f;
             const long long *gb = P.wscratch + (long long)blockIdx.x * THREADS * 3 * nb;
             for (int bn = tid; bn < nb; bn += THREADS) {
@@ -1332,7 +1342,7 @@ struct Xi32Path {
                 u64 sum = 0;
                 for (int w = 0; w < HC; ++w)
                     for (int l = 0; l < 32; ++l)
-                        sum += hist[(w * (nb + 2) + bn) * 32 + l];
+                        sum += hist[(w * (nb + 2) + 1 + bn) * 32 + l];
                 if (sum)
                     atomicAdd(&P.hist[bn], sum);
             }
@@ -1782,7 +1792,8 @@ __device__ void flush_rppi(uint32_t *hc, int nb, int npi, unsigned long long *gh
 
 // All copies of the CTA's histograms (and binary64 sums, if acc) -> global
 // (after the last __syncthreads).
-__device__ void merge_rppi(const PairParams &P, const uint32_t *hist, const double *acc, int rows)
+__device__ void merge_rppi(const PairParams &P, const uint32_t *hist, const double *acc, int rows,
+                           int row0 = 0)
 {
     const int nb = P.nbins, npi = P.npibins, row = npi + 1, copy = rows * row;
     for (int s = threadIdx.x; s < nb * npi; s += THREADS) {
@@ -1790,8 +1801,8 @@ __device__ void merge_rppi(const PairParams &P, const uint32_t *hist, const doub
         long long sum = 0;
         double ws = 0.0, rs = 0.0;
         for (int c = 0; c < P.hcopies; ++c) {
-            const int q = c * copy + k * row + m;
-            sum += (int)hist[q];
+            const int q = c * copy + k * row + m;  // binary64 sums have no row -1
+            sum += (int)hist[q + row0 * row];
             if (acc) {
                 ws += acc[2 * q];
                 rs += acc[2 * q + 1];
@@ -1853,7 +1864,7 @@ struct Rppi32Path {
         u64 &n_viol = st.n_viol;
         unsigned &pending = st.pending;
 
-        uint32_t *hc = hist + (warp % P.hcopies) * copy;
+        uint32_t *hc = hist + (warp % P.hcopies) * copy + (npi + 1);  // row 0 of the warp's copy
         const int ii = lane % I, jj = lane / I;
         SweepRP S;
         S.nb = nb;
@@ -1986,7 +1997,7 @@ struct Rppi32Path {
         u64 &n_viol = st.n_viol;
 
         __syncthreads();
-        merge_rppi(P, hist, acc, rppi32_rows(P.nbins));
+        merge_rppi(P, hist, acc, rppi32_rows(P.nbins), 1);
         n_eval = warp_sum_u64(n_eval);
         n_rck = warp_sum_u64(n_rck);
         n_viol = warp_sum_u64(n_viol);
@@ -2017,7 +2028,9 @@ __device__ __forceinline__ int resolve_local_rppi(const unsigned char *smem, con
     const float t = __fmaf_rn(fabsf(dz), s, -0.5f);
     const float q = __fadd_rn(t, PI_MAGIC);
     const float f = __fsub_rn(t, __fsub_rn(q, PI_MAGIC));
-    const uint32_t e = lut_entry<LIN>(smem, S.u0, S.shift, S.lut_last, S.lscale, rp2);
+    // the entry as the main path loaded it (sign-extended: flagged = -1)
+    const uint32_t e = (uint32_t)(int)(signed char)lut_entry<LIN>(smem, S.u0, S.shift, S.lut_last,
+                                                                  S.lscale, rp2);
     const uint32_t m = min(__float_as_uint(q) - PI_MAGIC_BITS, (uint32_t)S.npi);
     const uint32_t addr = S.hbase + e * S.rowb + m * 4u;  // as the main path added it
     return resolve_rppi<false>(smem, S, e, rp2, m, fabsf(f) > S.pband, addr, i, S.t0 + jl, 1.0f);
@@ -2039,10 +2052,7 @@ __device__ __forceinline__ void sweep_rppi32_pp(unsigned char *smem, const Sweep
     const u64 MH = pack2(-0.5f, -0.5f), MG = pack2(PI_MAGIC, PI_MAGIC);
     const u64 PB = pack2(S.pband, S.pband);
     const u64 LS = pack2(S.lscale, S.lscale), LM = pack2(LIN_MAGIC, LIN_MAGIC);
-    const uint32_t npiu = (uint32_t)S.npi, nbu = (uint32_t)S.nb;
-    // entries are <= nbu + 1 < 0x80: adding 0x80 - (nbu + 1) to each byte sets its
-    // top bit exactly for the flagged value, without carries between bytes
-    const uint32_t cflag = (0x80u - (nbu + 1u)) * 0x01010101u;
+    const uint32_t npiu = (uint32_t)S.npi;
     // shared addresses of the rp table, the base folded into the clamp (as in sweep32)
     const uint32_t lutb = smem_u32(smem + LUT_OFF), lut_lo = lutb - LIN_MAGIC_BITS,
                    lut_hi = lutb + S.lut_last;
@@ -2116,21 +2126,15 @@ __device__ __forceinline__ void sweep_rppi32_pp(unsigned char *smem, const Sweep
                         n_eval += (vv[q] && jv[k] >= jlo && jv[k] < jhi && (!TRI || gv[k] > iv[q]))
                                       ? 1ull : 0ull;
                 }
-                uint32_t e[4];
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
-                    asm volatile("ld.shared.u8 %0, [%1];" : "=r"(e[k]) : "r"(cq[k]));
+                    const uint32_t e = lds_entry(cq[k]);  // flagged: -1, the row before bin 0
                     const uint32_t m = min(__float_as_uint(qv[k]) - PI_MAGIC_BITS, npiu);
-                    red_shared(S.hbase + e[k] * S.rowb + m * 4u, 1u);  // flagged: row nb + 1
+                    red_shared(S.hbase + e * S.rowb + m * 4u, 1u);
+                    // pair (t, k) ends at bit 4 tend - 1 - (4 t + k): flagged rp cell or
+                    // near a pi edge (sign of g)
+                    fm[q] = push_sign(fm[q], e | __float_as_uint(g[k]));
                 }
-                const uint32_t w = __byte_perm(__byte_perm(e[0], e[1], 0x0040),
-                                               __byte_perm(e[2], e[3], 0x0040), 0x5410);
-                // top bytes of g: bit 7 of byte k is the sign of g[k]
-                const uint32_t sg = __byte_perm(__byte_perm(__float_as_uint(g[0]), __float_as_uint(g[1]), 0x0073),
-                                                __byte_perm(__float_as_uint(g[2]), __float_as_uint(g[3]), 0x0073),
-                                                0x5410);
-                // shift the mask one step down, add this step's bits at 8 k + 7
-                fm[q] = (fm[q] >> 1) | (((w + cflag) | sg) & 0x80808080u);
             }
         }
         uint32_t anyf = 0u;
@@ -2148,7 +2152,7 @@ __device__ __forceinline__ void sweep_rppi32_pp(unsigned char *smem, const Sweep
                 while (m) {
                     const int bit = __ffs(m) - 1;
                     m &= m - 1u;
-                    const int t = (bit & 7) - (8 - tend), k = bit >> 3;
+                    const int tk = 4 * tend - 1 - bit, t = tk >> 2, k = tk & 3;
                     const int jl = jAb + t * 2 * JS + ((k & 2) ? JS : 0) + (k & 1);
                     n_rck += resolve_local_rppi<LIN>(smem, S, xh, yh, zh, sc, iv[q], jl);
                 }
@@ -2185,7 +2189,7 @@ struct Rppi32PathPP {
         const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
         unsigned &pending = st.pending;
 
-        uint32_t *hc = hist + (warp % P.hcopies) * copy;
+        uint32_t *hc = hist + (warp % P.hcopies) * copy + (npi + 1);  // row 0 of the warp's copy
         const int ii = lane % I, jj = lane / I;
         SweepRP S;
         S.nb = nb;
