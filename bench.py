@@ -229,7 +229,7 @@ def _timed_row(cf, fn, flush, peak_evals, fp32=True):
     if not np.array_equal(r.npairs, diag.npairs):
         raise RuntimeError("counts differ between the counting and the timed runs")
     row = {"ms": ms, "kernel_ms": kms, "Gpairs_s": float(r.npairs.sum()) / (ms * 1e-3) / 1e9,
-           "evaluations": int(diag.n_evaluated)}
+           "evaluations": int(diag.n_evaluated), "refine": list(r.refine_used)}
     if fp32:
         achieved = diag.n_evaluated / (kms * 1e-3) / 1e9
         row["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak_evals,

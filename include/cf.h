@@ -94,14 +94,18 @@ typedef struct {
     cf_mode mode;        /* arithmetic path                                       */
     int weighted;        /* 1: accumulate w_i * w_j per bin (weights required)   */
     int want_ravg;       /* 1: accumulate the mean separation per bin             */
-    int refine[3];       /* cell refinement (rx, ry, rz); {0,0,0} = automatic.
-                            Columns in x, y are >= Rmax/rx wide (Sec. 3.1: the
-                            paper's default is (2, 2, 1)); rz sets the z-cell
-                            granularity of the in-column sort.                   */
+    int refine[3];       /* cell refinement (rx, ry, rz); {0,0,0} = automatic:
+                            (r, r, 1) with r = round(Rmax / s) in [1, 4], s the
+                            column side over which the smaller catalogue holds
+                            about 1024 points.  Columns in
+                            x, y are >= Rmax/rx wide (Sec. 3.1 names (2, 2, 1)
+                            as a good start); rz sets the z-cell granularity of
+                            the in-column sort.                                  */
     uint32_t flags;      /* CF_FLAG_*                                             */
     void *stream;        /* cudaStream_t to run on; NULL = legacy default stream  */
     int autotune;        /* 1: choose refine (and the float32 DD(r) kernel shape)
-                            by timing candidates once per problem signature and
+                            by timing candidates (the automatic r and r +- 1,
+                            then the kernel shapes) once per problem signature and
                             caching the winner (Sec. 3.1 asks for an automatic
                             choice of the refinement); fields set explicitly
                             (refine != {0,0,0}, pair_chunk, pair_pp) are kept.   */

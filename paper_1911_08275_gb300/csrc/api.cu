@@ -502,16 +502,38 @@ void finish_geom(cf::Geom &g)
     }
 }
 
-// The refinement a call uses: {0,0,0} -> the paper's default (2, 2, 1);
-// x, y clamped to [1, MAX_REACH], z to >= 1.
-void resolve_refine(const cf_config *c, int r[3])
+// Points per column the default refinement aims at: fewer make the per-work-item
+// and per-chunk costs (window records, claims, tile copies) dominate, more make
+// the columns' square cross-section a poorer fit to the sphere (more pairs
+// evaluated beyond Rmax).
+constexpr double DEFAULT_COL_POINTS = 1024.0;
+
+// Default x, y refinement (Sec. 3.1 leaves the choice to the user and names
+// (2, 2, 1) as a good start): the column side s over which the smaller
+// catalogue holds DEFAULT_COL_POINTS points on average (an ex x ey
+// cross-section), and r = round(Rxy / s) in [1, MAX_REACH].  The smaller one
+// decides because a work item's tile copies of the secondaries are spread over
+// its primaries and its per-chunk costs over the secondaries in the windows;
+// both want enough points per column.  Degenerate extents give 2.
+int default_reach(double R, double ex, double ey, double na, double nb)
+{
+    const double area = ex * ey, n = std::max(std::min(na, nb), 1.0);
+    if (!(area > 0.0) || !(R > 0.0) || !std::isfinite(area))
+        return 2;
+    const double side = std::sqrt(area * DEFAULT_COL_POINTS / n);
+    return (int)std::max(1.0, std::min((double)cf::MAX_REACH, std::round(R / side)));
+}
+
+// The refinement a call uses: {0,0,0} -> (dxy, dxy, 1) with dxy the default
+// x, y reach for the geometry; x, y clamped to [1, MAX_REACH], z to >= 1.
+void resolve_refine(const cf_config *c, int dxy, int r[3])
 {
     r[0] = c->refine[0];
     r[1] = c->refine[1];
     r[2] = c->refine[2];
     if (r[0] == 0 && r[1] == 0 && r[2] == 0) {
-        r[0] = 2;
-        r[1] = 2;
+        r[0] = dxy;
+        r[1] = dxy;
         r[2] = 1;
     }
     r[0] = std::max(1, std::min(r[0], cf::MAX_REACH));
@@ -519,14 +541,18 @@ void resolve_refine(const cf_config *c, int r[3])
     r[2] = std::max(1, r[2]);
 }
 
+// Catalogue sizes of a request (primaries, secondaries).
+void cat_sizes(const Request &q, double &na, double &nb)
+{
+    na = (double)q.d1->n;
+    nb = (double)(q.autocorr ? q.d1->n : q.d2->n);
+}
+
 // Grid geometry: columns of side >= Rxy / refine in x, y; z-cells for the sort.
 int plan_geom(const Request &q, const double lo[3], const double hi[3], long long ntot, cf::Geom &g)
 {
     const cf_config *c = q.cfg;
     const double R = q.edges.back();
-    int rr[3];
-    resolve_refine(c, rr);
-    const int rx = rr[0], ry = rr[1], rz = rr[2];
     std::memset(&g, 0, sizeof(g));
     g.periodic = c->periodic ? 1 : 0;
     for (int a = 0; a < 3; ++a) {
@@ -540,6 +566,12 @@ int plan_geom(const Request &q, const double lo[3], const double hi[3], long lon
             g.box[a] = 0.0;
         }
     }
+    double na, nb;
+    cat_sizes(q, na, nb);
+    int rr[3];
+    resolve_refine(c, default_reach(R, g.extent[0], g.extent[1], na, nb), rr);
+    const int rx = rr[0], ry = rr[1], rz = rr[2];
+    g.reach_z = rz;
     auto ncol = [&](double ext, int r) {
         // Cell indices are computed in float32 (relative error <= 4 u32 per index
         // coordinate t in [0, n)): widen cells by delta >= 16 u32 n so two points
@@ -665,7 +697,7 @@ int run(Request &q)
     res->n_cellpairs = res->n_evaluated = res->n_rechecked = res->n_band_violations = 0;
     res->kernel_ms = res->total_ms = 0.0;
     res->n_kernels = 0;
-    resolve_refine(c, res->refine_used);
+    res->refine_used[0] = res->refine_used[1] = res->refine_used[2] = 0;  // set with the grid
     res->chunk_used = c->pair_chunk ? c->pair_chunk : 16;
     res->pp_used = c->pair_pp ? c->pair_pp : 2;
     res->tuned = 0;
@@ -800,6 +832,9 @@ int run(Request &q)
     }
     trace.point("setup");
     plan_geom(q, lo, hi, ntot, g);
+    res->refine_used[0] = g.reach_x;
+    res->refine_used[1] = g.reach_y;
+    res->refine_used[2] = g.reach_z;
 
     {  // grid workspace
         // float32 DD(r) with mean separations: the coordinates' float32 rounding
@@ -1188,8 +1223,13 @@ int run_tuned(Request &q)
     double vol = 1.0;
     if ((rc = tune_volume(q, vol)))
         return rc;
-    const std::string key = tune_key(q, vol);
     const bool fixed_refine = c0->refine[0] || c0->refine[1] || c0->refine[2];
+    std::string key = tune_key(q, vol);
+    if (fixed_refine) {  // a separate entry: its choice must not reach calls that leave it open
+        char buf[48];
+        std::snprintf(buf, sizeof(buf), " f%d,%d,%d", c0->refine[0], c0->refine[1], c0->refine[2]);
+        key += buf;
+    }
     const bool shape = q.kind == 0 && c0->mode == CF_MODE_FP32_RECHECK && !c0->weighted &&
                        !c0->want_ravg && !c0->pair_chunk && !c0->pair_pp;
     TuneChoice best;
@@ -1217,10 +1257,19 @@ int run_tuned(Request &q)
         }
     };
     if (!have) {
+        // candidates: the default reach for this geometry and its neighbours
         std::vector<TuneChoice> cand;
-        const int refs[3] = {1, 2, 3};
-        for (int k = 0; k < (fixed_refine ? 1 : 3); ++k)
-            cand.push_back(TuneChoice{{refs[k], refs[k], 1}, 16, 2, 0.0});
+        double na, nb;
+        cat_sizes(q, na, nb);
+        const double ex = std::cbrt(vol), ey = ex;  // the signature's volume as a cube
+        const int d = fixed_refine ? 0 : default_reach(q.edges.back(), ex, ey, na, nb);
+        if (fixed_refine)  // recorded as given (clamped as the grid clamps it)
+            cand.push_back(TuneChoice{{std::max(1, std::min(c0->refine[0], cf::MAX_REACH)),
+                                       std::max(1, std::min(c0->refine[1], cf::MAX_REACH)),
+                                       std::max(1, c0->refine[2])}, 16, 2, 0.0});
+        else
+            for (int rf = std::max(1, d - 1); rf <= std::min(cf::MAX_REACH, d + 1); ++rf)
+                cand.push_back(TuneChoice{{rf, rf, 1}, 16, 2, 0.0});
         auto time_one = [&](TuneChoice &t, int reps) -> int {
             apply(t);
             t.ms = INFINITY;
@@ -1557,7 +1606,7 @@ int noalloc_xi(int autocorr, const cf_catalog *d1, const cf_catalog *d2, const d
     res->n_cellpairs = res->n_evaluated = res->n_rechecked = res->n_band_violations = 0;
     res->kernel_ms = res->total_ms = 0.0;
     res->n_kernels = 0;
-    resolve_refine(c, res->refine_used);
+    res->refine_used[0] = res->refine_used[1] = res->refine_used[2] = 0;  // set with the grid
     res->chunk_used = 16;
     res->pp_used = 2;
     res->tuned = 0;
@@ -1621,14 +1670,16 @@ int noalloc_xi(int autocorr, const cf_catalog *d1, const cf_catalog *d2, const d
                 hi[a] = cf::decode_dkey(h.keys[3 + a]);
             }
     }
-    int rr[3];
-    resolve_refine(c, rr);
-    const int rx = rr[0], ry = rr[1], rz = rr[2];
     for (int a = 0; a < 3; ++a) {
         g.origin[a] = g.periodic ? 0.0 : lo[a];
         g.extent[a] = g.periodic ? c->boxsize[a] : std::max(hi[a] - lo[a], 0.0);
         g.box[a] = g.periodic ? c->boxsize[a] : 0.0;
     }
+    int rr[3];
+    resolve_refine(c, default_reach(R, g.extent[0], g.extent[1], (double)d1->n,
+                                    (double)(autocorr ? d1->n : d2->n)), rr);
+    const int rx = rr[0], ry = rr[1], rz = rr[2];
+    g.reach_z = rz;
     auto ncol = [&](double ext, int r) {  // same rule as plan_geom
         const double nmax = std::max(1.0, std::floor(ext / R)) * r;
         const double delta = 16.0 * U32 * nmax + 1e-9;
@@ -1652,6 +1703,9 @@ int noalloc_xi(int autocorr, const cf_catalog *d1, const cf_catalog *d2, const d
     g.nz = (int)zcells((long long)g.ncx * g.ncy);
     g.reach_x = rx;
     g.reach_y = ry;
+    res->refine_used[0] = rx;
+    res->refine_used[1] = ry;
+    res->refine_used[2] = rz;
     const int nstencil_max = autocorr ? ((2 * g.reach_x + 1) * (2 * g.reach_y + 1) + 1) / 2
                                       : (2 * g.reach_x + 1) * (2 * g.reach_y + 1);
     cf::Gridded G[2] = {};
@@ -2351,9 +2405,7 @@ int batch_run(cf_batch *b, cudaStream_t user, int use_graph, cf_batch_stats *sta
         res->n_kernels = j.n_kernels;
         res->refine_used[0] = j.g.reach_x;
         res->refine_used[1] = j.g.reach_y;
-        int rr[3];
-        resolve_refine(&j.cfg, rr);
-        res->refine_used[2] = rr[2];
+        res->refine_used[2] = j.g.reach_z;
         res->chunk_used = j.chunk;
         res->pp_used = j.pp;
         res->tuned = j.tuned;

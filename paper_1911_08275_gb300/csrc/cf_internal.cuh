@@ -73,6 +73,7 @@ struct Geom {
     int ncols;
     long long ncells;
     int reach_x, reach_y;
+    int reach_z;            // z refinement (z-cells of the in-column sort per Rmax)
     double origin[3];   // grid frame origin (0 in periodic mode)
     double extent[3];   // grid extent (= box in periodic mode)
     double inv_w[3];    // cells per unit length along each axis

@@ -156,7 +156,7 @@ def test_batch_autotune_tunes_at_plan_time_and_forced_shapes_are_exact(cuda_devi
     # first batch: every signature is tuned while the batch is planned
     first = run_batch()
     assert cf.tune_count() >= 4
-    assert all(r.refine_used[0] in (1, 2, 3) for r in first)
+    assert all(r.refine_used[0] in (1, 2, 3, 4) for r in first)
     # force each float32 DD(r) kernel shape through the tuning cache file
     path = str(tmp_path / "tune.json")
     cf.tune_save(path)

@@ -65,8 +65,8 @@ def test_noalloc_fine_grid_is_coarsened(cuda_device):
     cat = synth.uniform_box(100000, 420.0, seed=77)
     e = synth.log_edges(0.05, 2.0, 8)
     xyz = _dev(cat)
-    want = cf.countpairs_xi(*xyz, e, boxsize=420.0)
-    got = cf.countpairs_xi_noalloc(*xyz, e, boxsize=420.0)
+    want = cf.countpairs_xi(*xyz, e, boxsize=420.0, refine=(2, 2, 1))
+    got = cf.countpairs_xi_noalloc(*xyz, e, boxsize=420.0, refine=(2, 2, 1))
     assert np.array_equal(got.npairs, want.npairs) and got.npairs.sum() > 0
 
 
@@ -78,7 +78,7 @@ def test_noalloc_cross_at_the_size_limit(cuda_device, periodic):
     b = synth.uniform_box(131072, 420.0, seed=79)
     e = synth.log_edges(0.1, 5.0, 10)
     xa, xb = _dev(a), _dev(b)
-    kw = dict(x2=xb[0], y2=xb[1], z2=xb[2], periodic=periodic, boxsize=420.0)
+    kw = dict(x2=xb[0], y2=xb[1], z2=xb[2], periodic=periodic, boxsize=420.0, refine=(2, 2, 1))
     want = cf.countpairs_xi(*xa, e, **kw)
     got = cf.countpairs_xi_noalloc(*xa, e, **kw)
     assert np.array_equal(got.npairs, want.npairs) and got.npairs.sum() > 0
