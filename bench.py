@@ -302,8 +302,9 @@ def batch_workload(cf, synth, torch, dev, flush):
     refinement and float32 DD(r) kernel shape for its signature (tuned while the
     first run plans the batch), against the same jobs as 48 single calls
     (per-job counts must be identical); the float32 and the binary64 jobs as
-    batches of their own; and 480 small jobs (launch-bound) with and without
-    the graph."""
+    batches of their own; and 480 small jobs (launch-bound: every gridding
+    stage and the work lists of all jobs run as one launch each) with and
+    without the graph, and as 480 single calls."""
     jobs = [synth.batch_job(j) for j in range(48)]
     xyz = [[torch.from_numpy(v).to(dev) for v in (jb["cat"].x, jb["cat"].y, jb["cat"].z)]
            for jb in jobs]
@@ -353,14 +354,28 @@ def batch_workload(cf, synth, torch, dev, flush):
     small = [synth.batch_job(j % 48, scale=0.004) for j in range(480)]
     sx = [[torch.from_numpy(v).to(dev) for v in (jb["cat"].x, jb["cat"].y, jb["cat"].z)]
           for jb in small]
-    bs, _ = _batch(cf, small, sx, autotune=False)
+    bs, sres = _batch(cf, small, sx, autotune=False)
     bs.run(use_graph=True)
     g_ms, gl = _time_batch(bs, flush)
     d_ms, _ = _time_batch(bs, flush, use_graph=False)
+    # the same jobs as 480 single calls (each call's own device time, summed)
+    s_ms, s_kernels, s_exact = 0.0, 0, 0
+    for jb, x, r in zip(small, sx, sres):
+        kw = dict(boxsize=jb["box"], mode=jb["mode"])
+        if jb["kind"] == "xi":
+            sc = cf.countpairs_xi(*x, jb["edges"], **kw)
+        else:
+            sc = cf.countpairs_rp_pi(*x, jb["edges"], jb["pimax"], jb["npibins"], **kw)
+        s_ms += sc.total_ms
+        s_kernels += sc.n_kernels
+        s_exact += int(np.array_equal(sc.npairs, r.npairs))
     out["small_480_jobs"] = {"jobs": 480, "points": int(sum(jb["cat"].n for jb in small)),
                              "pairs": int(gl["pairs"]), "kernels_per_run": int(gl["n_kernels"]),
                              "ms_graph": g_ms, "ms_without_graph": d_ms,
-                             "graph_gain": d_ms / g_ms}
+                             "graph_gain": d_ms / g_ms,
+                             "single_calls_ms": s_ms, "single_calls_kernels": s_kernels,
+                             "batch_gain_vs_single_calls": s_ms / g_ms,
+                             "jobs_exact_vs_single_calls": s_exact}
     bs.close()
     return out
 

@@ -207,12 +207,15 @@ int cf_countpairs_xi_noalloc(int autocorr, const cf_catalog *d1, const cf_catalo
 /*
  * Batched counting (a persistent launch over many jobs).  Jobs -- catalogues
  * of uneven sizes, DD(r) or DD(rp, pi), float32+re-check or binary64, auto or
- * cross, periodic or open -- are added to a batch and then run together: their
- * gridding and work lists run on a few side streams, and one persistent kernel
- * pulls column pairs from a single queue over all jobs' work lists (the GPU
- * analogue of the paper's OpenMP loop over cell pairs, Sec. 2.1).  With
+ * cross, periodic or open -- are added to a batch and then run together: every
+ * gridding stage runs once for all catalogues of all jobs (each catalogue a
+ * segment of the launch), the work lists of all jobs in one more launch, and
+ * one persistent kernel pulls column pairs from a single queue over all jobs'
+ * work lists (the GPU analogue of the paper's OpenMP loop over cell pairs,
+ * Sec. 2.1): a run is 16 launches whatever the number of jobs.  With
  * use_graph the whole sequence is captured once into a CUDA graph and replayed
- * by later runs.
+ * by later runs.  A job's res->n_kernels is 0 (the launches are shared; the
+ * batch's count is in cf_batch_stats).
  *   cf_batch_add_xi / cf_batch_add_rp_pi: arguments as cf_countpairs_xi /
  *     cf_countpairs_rp_pi, validated at once.  Batched jobs count unweighted
  *     pairs (cfg->weighted and cfg->want_ravg must be 0) and take coordinates
@@ -235,7 +238,7 @@ int cf_countpairs_xi_noalloc(int autocorr, const cf_catalog *d1, const cf_catalo
  *     again.  stream NULL runs on a stream owned by the batch.  stats may be
  *     NULL.  Errors name the job index in cf_last_error(); a failed job leaves
  *     every res of that run undefined.
- *   cf_batch_destroy: frees the batch's device memory, streams and graph.
+ *   cf_batch_destroy: frees the batch's device memory, stream and graph.
  */
 typedef struct cf_batch cf_batch;
 

@@ -1880,7 +1880,6 @@ extern "C" int cf_countpairs_xi_noalloc(int autocorr, const cf_catalog *d1, cons
 // ============================================================================
 namespace {
 
-constexpr int BATCH_STREAMS = 4;  // side streams for the jobs' gridding and work lists
 
 struct BatchJob {
     Request q;
@@ -1914,10 +1913,11 @@ struct cf_batch {
     int *d_path = nullptr;
     unsigned *d_offsets = nullptr, *d_counter = nullptr;
     unsigned long long *d_bbox = nullptr;
-    cf::GridTemps tmp[BATCH_STREAMS] = {};
-    cudaStream_t side[BATCH_STREAMS] = {};
+    cf::GridBatch grid = {};             // every catalogue of every job, gridded in one pass
+    unsigned *d_wpre = nullptr;          // work-list blocks: prefix over the jobs
+    unsigned wblocks = 0;
     cudaStream_t own = nullptr;
-    cudaEvent_t fork = nullptr, join[BATCH_STREAMS] = {}, ev[4] = {};
+    cudaEvent_t ev[4] = {};
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
     uint64_t n_kernels = 0;
@@ -2117,14 +2117,32 @@ int batch_plan(cf_batch *b, cudaStream_t st, const std::vector<std::array<double
         b->jobs[k].out_off = out_words;
         out_words += (size_t)b->jobs[k].nslots + 8;
     }
-    long long tmax_n[BATCH_STREAMS] = {0}, tmax_cells[BATCH_STREAMS] = {0}, tmax_cols[BATCH_STREAMS] = {0};
+    // one gridding segment per catalogue of every job; its entries in the
+    // concatenated per-cell arrays start at c0 (ncells + 1 each)
+    std::vector<cf::GridSeg> seg;
+    long long ctot = 0;
     for (int k = 0; k < nj; ++k) {
         const BatchJob &j = b->jobs[k];
-        const int s = k % BATCH_STREAMS;
-        for (int t = 0; t < j.ncat; ++t)
-            tmax_n[s] = std::max<long long>(tmax_n[s], j.cat[t].n);
-        tmax_cells[s] = std::max<long long>(tmax_cells[s], j.g.ncells);
-        tmax_cols[s] = std::max<long long>(tmax_cols[s], j.g.ncols);
+        for (int t = 0; t < j.ncat; ++t) {
+            cf::GridSeg sg;
+            std::memset(&sg, 0, sizeof(sg));
+            sg.x = j.cat[t].x;
+            sg.y = j.cat[t].y;
+            sg.z = j.cat[t].z;
+            sg.f32 = j.cfg.dtype == CF_FLOAT32 ? 1 : 0;
+            sg.job = k;
+            sg.n = j.cat[t].n;
+            sg.c0 = ctot;
+            ctot += j.g.ncells + 1;
+            seg.push_back(sg);
+        }
+    }
+    const int nseg = (int)seg.size();
+    std::vector<unsigned> pre[cf::GB_SHAPES], wpre(nj + 1, 0u);
+    for (int k = 0; k < cf::GB_SHAPES; ++k) {
+        pre[k].assign(nseg + 1, 0u);
+        for (int q = 0; q < nseg; ++q)
+            pre[k][q + 1] = pre[k][q] + cf::grid_batch_blocks(k, seg[q].n, b->jobs[seg[q].job].g);
     }
     Bump bump;
     cudaError_t e;
@@ -2136,22 +2154,26 @@ int batch_plan(cf_batch *b, cudaStream_t st, const std::vector<std::array<double
         b->d_path = bump.take<int>(nj);
         b->d_offsets = bump.take<unsigned>(nj + 1);
         b->d_counter = bump.take<unsigned>(1);
-        for (int s = 0; s < BATCH_STREAMS; ++s) {
-            cf::GridTemps &tp = b->tmp[s];
-            const long long nm = tmax_n[s], nc = tmax_cells[s], ncol = tmax_cols[s];
-            tp.cell_of = bump.take<uint32_t>(nm);
-            tp.slot = bump.take<uint32_t>(nm);
-            tp.tmp_idx = bump.take<int>(nm + 3 * ncol);
-            tp.tmp_key = bump.take<unsigned long long>(nm + 3 * ncol);
-            tp.counts = bump.take<uint32_t>(nc + 1);
-            tp.pad = bump.take<uint32_t>(ncol);
-            tp.bsum = bump.take<uint32_t>(nc / 4096 + 2);
+        cf::GridBatch &gb = b->grid;
+        gb.seg = bump.take<cf::GridSeg>(nseg);
+        gb.geom = bump.take<cf::Geom>(nj);
+        gb.nseg = nseg;
+        gb.ctot = ctot;
+        gb.counts = bump.take<uint32_t>(ctot + 1);
+        gb.scan = bump.take<uint32_t>(ctot);
+        gb.bsum = bump.take<uint32_t>(cf::scan_block_sums(ctot));
+        for (int k = 0; k < cf::GB_SHAPES; ++k) {
+            gb.pre[k] = bump.take<unsigned>(nseg + 1);
+            gb.blocks[k] = pre[k][nseg];
         }
+        b->d_wpre = bump.take<unsigned>(nj + 1);
+        int q = 0;
         for (int k = 0; k < nj; ++k) {
             BatchJob &j = b->jobs[k];
-            for (int t = 0; t < j.ncat; ++t) {
+            for (int t = 0; t < j.ncat; ++t, ++q) {
                 const long long n = j.cat[t].n + 3ll * j.g.ncols;
                 cf::Gridded &G = j.G[t];
+                G.n = j.cat[t].n;
                 G.xs = bump.take<float>(n);
                 G.ys = bump.take<float>(n);
                 G.zs = bump.take<float>(n);
@@ -2160,6 +2182,13 @@ int batch_plan(cf_batch *b, cudaStream_t st, const std::vector<std::array<double
                 G.perm = bump.take<int>(n);
                 G.cell_start = bump.take<uint32_t>(j.g.ncells + 1);
                 G.colbox = bump.take<double4_32a>(j.g.ncols);
+                cf::GridSeg &sg = seg[q];
+                sg.out = G;
+                sg.cell_of = bump.take<uint32_t>(j.cat[t].n);
+                sg.slot = bump.take<uint32_t>(j.cat[t].n);
+                sg.tmp_idx = bump.take<int>(n);
+                sg.tmp_key = bump.take<unsigned long long>(n);
+                sg.pad = bump.take<uint32_t>(j.g.ncols);
             }
             if (j.ncat == 1)
                 j.G[1] = j.G[0];
@@ -2239,17 +2268,27 @@ int batch_plan(cf_batch *b, cudaStream_t st, const std::vector<std::array<double
         b->smem_max = std::max(b->smem_max, PL.smem);
         hp[k] = j.P;
         hpath[k] = j.path;
-        j.n_kernels = 0;
-        for (int t = 0; t < j.ncat; ++t)
-            j.n_kernels += cf::grid_kernels(j.cat[t].n);
-        j.n_kernels += j.P.n_items > 0 ? 1 : 0;
+        j.n_kernels = 0;  // the batch's launches are shared by all jobs (batch statistics)
+        wpre[k + 1] = wpre[k] + (unsigned)((std::max(j.P.n_items, 0) + 255) / 256);
     }
+    for (auto &sg : seg)
+        sg.err = b->jobs[sg.job].P.err;
+    std::vector<cf::Geom> geom(nj);
+    for (int k = 0; k < nj; ++k)
+        geom[k] = b->jobs[k].g;
+    b->wblocks = wpre[nj];
     if ((e = cudaMemcpy(b->d_jobs, hp.data(), sizeof(cf::PairParams) * nj, cudaMemcpyHostToDevice)) ||
-        (e = cudaMemcpy(b->d_path, hpath.data(), sizeof(int) * nj, cudaMemcpyHostToDevice)))
+        (e = cudaMemcpy(b->d_path, hpath.data(), sizeof(int) * nj, cudaMemcpyHostToDevice)) ||
+        (e = cudaMemcpy((void *)b->grid.seg, seg.data(), sizeof(cf::GridSeg) * nseg, cudaMemcpyHostToDevice)) ||
+        (e = cudaMemcpy((void *)b->grid.geom, geom.data(), sizeof(cf::Geom) * nj, cudaMemcpyHostToDevice)) ||
+        (e = cudaMemcpy(b->d_wpre, wpre.data(), sizeof(unsigned) * (nj + 1), cudaMemcpyHostToDevice)))
         return cuda_fail(e, "H2D batch jobs");
-    b->n_kernels = 2;  // offsets + batched kernel
-    for (auto &j : b->jobs)
-        b->n_kernels += j.n_kernels;
+    for (int k = 0; k < cf::GB_SHAPES; ++k)
+        if ((e = cudaMemcpy((void *)b->grid.pre[k], pre[k].data(), sizeof(unsigned) * (nseg + 1),
+                            cudaMemcpyHostToDevice)))
+            return cuda_fail(e, "H2D batch gridding plan");
+    // two memsets, the batched gridding, the work lists, offsets + batched pair kernel
+    b->n_kernels = 2 + cf::grid_batch_kernels() + 1 + 2;
     b->planned = true;
     (void)st;
     return CF_OK;
@@ -2263,25 +2302,13 @@ int batch_issue(cf_batch *b, cudaStream_t st, bool capturing)
     const int nj = (int)b->jobs.size();
     if ((!capturing && (e = cudaEventRecord(b->ev[0], st))) ||
         (e = cudaMemsetAsync(b->d_out, 0, b->out_words * 8, st)) ||
-        (e = cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned), st)) ||
-        (e = cudaEventRecord(b->fork, st)))
+        (e = cudaMemsetAsync(b->d_counter, 0, sizeof(unsigned), st)))
         return cuda_fail(e, "batch start");
-    for (int s = 0; s < BATCH_STREAMS; ++s)
-        if ((e = cudaStreamWaitEvent(b->side[s], b->fork, 0)))
-            return cuda_fail(e, "batch fork");
-    for (int k = 0; k < nj; ++k) {
-        BatchJob &j = b->jobs[k];
-        const int s = k % BATCH_STREAMS;
-        for (int t = 0; t < j.ncat; ++t)
-            if ((e = cf::build_grid(j.cfg.dtype, j.cat[t].x, j.cat[t].y, j.cat[t].z, nullptr,
-                                    j.cat[t].n, j.g, b->tmp[s], j.G[t], b->sms, j.P.err, b->side[s])))
-                return cuda_fail(e, ("batch job " + std::to_string(k) + " gridding").c_str());
-        if ((e = cf::launch_worklist(j.P, b->side[s])))
-            return cuda_fail(e, ("batch job " + std::to_string(k) + " work list").c_str());
-    }
-    for (int s = 0; s < BATCH_STREAMS; ++s)
-        if ((e = cudaEventRecord(b->join[s], b->side[s])) || (e = cudaStreamWaitEvent(st, b->join[s], 0)))
-            return cuda_fail(e, "batch join");
+    // every catalogue of every job gridded stage by stage, then every work list
+    if ((e = cf::build_grid_batch(b->grid, b->sms, st)))
+        return cuda_fail(e, "batched gridding");
+    if ((e = cf::launch_worklist_batch(b->d_jobs, b->d_wpre, nj, b->wblocks, st)))
+        return cuda_fail(e, "batched work lists");
     cf::BatchParams B;
     B.jobs = b->d_jobs;
     B.path = b->d_path;
@@ -2313,13 +2340,8 @@ int batch_run(cf_batch *b, cudaStream_t user, int use_graph, cf_batch_stats *sta
         b->dev = dev;
         if ((e = cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev)))
             return cuda_fail(e, "device attribute");
-        for (int s = 0; s < BATCH_STREAMS; ++s)
-            if ((e = cudaStreamCreateWithFlags(&b->side[s], cudaStreamNonBlocking)) ||
-                (e = cudaEventCreateWithFlags(&b->join[s], cudaEventDisableTiming)))
-                return cuda_fail(e, "batch streams");
-        if ((e = cudaStreamCreateWithFlags(&b->own, cudaStreamNonBlocking)) ||
-            (e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming)))
-            return cuda_fail(e, "batch streams");
+        if ((e = cudaStreamCreateWithFlags(&b->own, cudaStreamNonBlocking)))
+            return cuda_fail(e, "batch stream");
         for (auto &ev : b->ev)
             if ((e = cudaEventCreate(&ev)))
                 return cuda_fail(e, "batch events");
@@ -2483,16 +2505,8 @@ int cf_batch_destroy(cf_batch *b)
     if (!b)
         return CF_OK;
     batch_free_plan(b);
-    for (int s = 0; s < BATCH_STREAMS; ++s) {
-        if (b->side[s])
-            cudaStreamDestroy(b->side[s]);
-        if (b->join[s])
-            cudaEventDestroy(b->join[s]);
-    }
     if (b->own)
         cudaStreamDestroy(b->own);
-    if (b->fork)
-        cudaEventDestroy(b->fork);
     for (auto &ev : b->ev)
         if (ev)
             cudaEventDestroy(ev);

@@ -309,9 +309,8 @@ __device__ __forceinline__ bool plan_item(const PairParams &P, int item, WorkIte
 // P.work with one warp-aggregated atomic per warp.  With the window pre-pass
 // (P.win_chunk > 0) each kept pair also gets a run of window records,
 // one per chunk of column a, from a second warp-aggregated counter.
-__global__ void __launch_bounds__(256) k_worklist(const __grid_constant__ PairParams P)
+__device__ __forceinline__ void worklist_body(const PairParams &P, int item)
 {
-    const int item = blockIdx.x * blockDim.x + threadIdx.x;
     WorkItem w;
     const bool keep = item < P.n_items && plan_item(P, item, w);
     const unsigned m = __ballot_sync(FULL, keep);
@@ -348,6 +347,33 @@ __global__ void __launch_bounds__(256) k_worklist(const __grid_constant__ PairPa
         }
         P.work[base + __popc(m & ((1u << lane) - 1u))] = w;
     }
+}
+
+__global__ void __launch_bounds__(256) k_worklist(const __grid_constant__ PairParams P)
+{
+    worklist_body(P, blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+// The work lists of every job of a batch in one launch: job j owns blocks
+// [pre[j], pre[j + 1]) (one thread per candidate, as k_worklist).
+__global__ void __launch_bounds__(256) k_worklist_batch(const PairParams *__restrict__ jobs,
+                                                        const unsigned *__restrict__ pre, int njobs)
+{
+    __shared__ int s_job;
+    if (threadIdx.x == 0) {
+        int lo = 0, hi = njobs - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (pre[mid] <= blockIdx.x)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        s_job = lo;
+    }
+    __syncthreads();
+    const int j = s_job;
+    worklist_body(jobs[j], (int)(blockIdx.x - pre[j]) * blockDim.x + threadIdx.x);
 }
 
 // One kept column pair, as the pair kernels use it (identical in every thread
@@ -2866,6 +2892,15 @@ cudaError_t launch_worklist(const PairParams &P, cudaStream_t st)
     if (P.n_items <= 0)
         return cudaSuccess;
     k_worklist<<<(P.n_items + 255) / 256, 256, 0, st>>>(P);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_worklist_batch(const PairParams *jobs, const unsigned *pre, int njobs,
+                                  unsigned blocks, cudaStream_t st)
+{
+    if (blocks == 0 || njobs < 1)
+        return cudaSuccess;
+    k_worklist_batch<<<blocks, 256, 0, st>>>(jobs, pre, njobs);
     return cudaGetLastError();
 }
 

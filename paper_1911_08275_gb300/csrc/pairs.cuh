@@ -108,6 +108,11 @@ int batch_path(const PairParams &P, int f64, int chunk = 16, int pp = 2);
 // *P.work_count, which must be zero).
 cudaError_t launch_worklist(const PairParams &P, cudaStream_t st);
 
+// The work lists of njobs jobs (device parameter array) in one launch; job j
+// owns blocks [pre[j], pre[j + 1]) of 256 candidates, blocks = pre[njobs].
+cudaError_t launch_worklist_batch(const PairParams *jobs, const unsigned *pre, int njobs,
+                                  unsigned blocks, cudaStream_t st);
+
 // Offsets over the jobs' kept pairs, then the batched persistent kernel with
 // smem bytes of dynamic shared memory (the largest job's plan); blocks returns
 // the grid size.

@@ -176,3 +176,33 @@ def test_batch_autotune_tunes_at_plan_time_and_forced_shapes_are_exact(cuda_devi
             if jb["kind"] == "xi" and jb["mode"] == "fp32_recheck"}
     assert len(used) == min(4, len(forced)) and all(r.tuned == 2 for r in second)
     cf.tune_clear()
+
+
+def test_batch_mixed_dtypes_empty_catalogues_and_many_segments(cuda_device):
+    # 120 jobs gridded together: float32 and float64 inputs side by side, empty
+    # catalogues (auto and as the secondary of a cross job), sizes from 0 to
+    # 2000, clustered and uniform, DD(r) and DD(rp, pi), both modes
+    b = cf.Batch()
+    cases = []
+    for k in range(120):
+        n = [0, 1, 5, 37, 300, 2000][k % 6]
+        c = synth.uniform_box(n, 100.0, seed=600 + k)
+        if k % 5 == 4:
+            c = synth.neyman_scott(max(n // 20, 1), 20.0, 2.0, 100.0, seed=600 + k)
+        dtype = np.float32 if k % 3 == 0 else np.float64
+        c = c.astype(dtype)
+        c2 = None
+        if k % 4 == 3:
+            c2 = synth.uniform_box([0, 17, 900][k % 3], 100.0, seed=900 + k).astype(dtype)
+        job = dict(kind="xi" if k % 2 == 0 else "rppi", mode="fp64" if k % 7 == 0 else "fp32_recheck",
+                   box=100.0, periodic=(k % 8 != 5), edges=synth.log_edges(0.3, 12.0, 9),
+                   pimax=10.0, npibins=10)
+        x = dev(c)
+        x2 = dev(c2) if c2 is not None else None
+        cases.append((k, job, x, x2, add(b, job, x, x2)))
+    for use_graph in (False, True):
+        stats = b.run(use_graph=use_graph)
+        assert stats["n_jobs"] == 120
+        for k, job, x, x2, r in cases:
+            assert np.array_equal(r.npairs, single(job, x, x2)), k
+    b.close()
