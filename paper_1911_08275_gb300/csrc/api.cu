@@ -508,6 +508,22 @@ void finish_geom(cf::Geom &g)
 // evaluated beyond Rmax).
 constexpr double DEFAULT_COL_POINTS = 1024.0;
 
+// Fewest points per column (both catalogues) the grid keeps: a sparse catalogue
+// in a large box would otherwise get more columns than points, and the
+// gridding and work-list costs grow with the columns.
+constexpr double MIN_COL_POINTS = 32.0;
+
+// Halve the columns on both axes until there are at most max(1, ntot /
+// MIN_COL_POINTS); columns wider than Rxy / refine stay correct at any width.
+void cap_columns(long long ntot, int &ncx, int &ncy)
+{
+    const long long cap = std::max(1ll, (long long)((double)ntot / MIN_COL_POINTS));
+    while ((long long)ncx * ncy > cap && (ncx > 1 || ncy > 1)) {
+        ncx = std::max(1, ncx / 2);
+        ncy = std::max(1, ncy / 2);
+    }
+}
+
 // Default x, y refinement (Sec. 3.1 leaves the choice to the user and names
 // (2, 2, 1) as a good start): the column side s over which the smaller
 // catalogue holds DEFAULT_COL_POINTS points on average (an ex x ey
@@ -588,6 +604,7 @@ int plan_geom(const Request &q, const double lo[3], const double hi[3], long lon
         g.ncx = std::max(1, g.ncx / 2);
         g.ncy = std::max(1, g.ncy / 2);
     }
+    cap_columns(ntot, g.ncx, g.ncy);
     g.ncols = g.ncx * g.ncy;
     g.reach_x = rx;
     g.reach_y = ry;
@@ -1696,6 +1713,7 @@ int noalloc_xi(int autocorr, const cf_catalog *d1, const cf_catalog *d2, const d
     };
     g.ncx = ncol(g.extent[0], rx);
     g.ncy = ncol(g.extent[1], ry);
+    cap_columns(ntot, g.ncx, g.ncy);
     while ((long long)g.ncx * g.ncy > NOALLOC_MAX_COLS) {  // wider columns stay correct
         g.ncx = std::max(1, g.ncx / 2);
         g.ncy = std::max(1, g.ncy / 2);

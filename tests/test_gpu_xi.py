@@ -260,3 +260,25 @@ def test_pinned_host_inputs(cuda_device, dtype):
     views = [b[1:] for b in big]
     r2 = cf.countpairs_xi(*views, e, boxsize=150.0)
     assert np.array_equal(r2.npairs, ref_n)
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("periodic", [True, False])
+def test_sparse_catalogues_get_wide_columns(cuda_device, mode, periodic):
+    # 100 and 400 points in a box of 1000 with Rmax 40: the planner keeps at
+    # least 32 points per column, so the grid shrinks to 1 x 1 and 3 x 3
+    # columns, fewer than the stencil's 2 r + 1 per axis (refine 2): the same
+    # column then appears under several periodic images
+    e = synth.log_edges(1.0, 40.0, 8)
+    for n, refine in ((100, (2, 2, 1)), (400, (2, 2, 1)), (400, (0, 0, 0))):
+        cat = synth.neyman_scott(n // 10, 10.0, 15.0, 1000.0, seed=44 + n)
+        r, c = gpu_xi(cat, e, boxsize=1000.0, mode=mode, periodic=periodic, refine=refine)
+        assert np.array_equal(r.npairs, oracle_xi(c, e, periodic=periodic, box=1000.0)), (n, refine)
+        u = synth.uniform_box(n, 1000.0, seed=45 + n)
+        (ux, uy, uz), _ = dev(u)
+        (cx, cy, cz), _ = dev(c)
+        rc = cf.countpairs_xi(cx, cy, cz, e, x2=ux, y2=uy, z2=uz, boxsize=1000.0, mode=mode,
+                              periodic=periodic, refine=refine)
+        want = oracle.xi(c.x, c.y, c.z, edges=e, x2=u.x, y2=u.y, z2=u.z, autocorr=False,
+                         periodic=periodic, box=1000.0)[0]
+        assert np.array_equal(rc.npairs, want), (n, refine)

@@ -60,8 +60,9 @@ def test_noalloc_cross_and_open_box(cuda_device):
 
 
 def test_noalloc_fine_grid_is_coarsened(cuda_device):
-    # box 420, Rmax 2, refine 2: the planner's grid has 420 x 420 columns, more
-    # than the array's column cap; the halved grid must count the same pairs
+    # box 420, Rmax 2, refine 2: 420 x 420 base columns for 100k points; the
+    # planner halves them to at most one column per 32 points, and the halved
+    # grid must count the same pairs
     cat = synth.uniform_box(100000, 420.0, seed=77)
     e = synth.log_edges(0.05, 2.0, 8)
     xyz = _dev(cat)
@@ -72,13 +73,15 @@ def test_noalloc_fine_grid_is_coarsened(cuda_device):
 
 @pytest.mark.parametrize("periodic", [True, False])
 def test_noalloc_cross_at_the_size_limit(cuda_device, periodic):
-    # two catalogues of 131072 points, box / Rmax = 84: the cross work list of
-    # the planner's 168 x 168 columns needs more than the 32 MiB array
+    # two catalogues of 131072 points, box / Rmax = 84, refine 4: over the
+    # 83 x 83 columns the point cap leaves, the 81-offset cross work list and
+    # the window records need about 57 MB, so the planner coarsens further to
+    # fit the 32 MiB array
     a = synth.uniform_box(131072, 420.0, seed=78)
     b = synth.uniform_box(131072, 420.0, seed=79)
     e = synth.log_edges(0.1, 5.0, 10)
     xa, xb = _dev(a), _dev(b)
-    kw = dict(x2=xb[0], y2=xb[1], z2=xb[2], periodic=periodic, boxsize=420.0, refine=(2, 2, 1))
+    kw = dict(x2=xb[0], y2=xb[1], z2=xb[2], periodic=periodic, boxsize=420.0, refine=(4, 4, 1))
     want = cf.countpairs_xi(*xa, e, **kw)
     got = cf.countpairs_xi_noalloc(*xa, e, **kw)
     assert np.array_equal(got.npairs, want.npairs) and got.npairs.sum() > 0
