@@ -193,6 +193,16 @@ __device__ __forceinline__ double canon_r2(const double4_32a &p, const double4_3
     return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
 }
 
+// The same for an image whose shifts are all zero (canon_comp's adds are then
+// skipped, so the value is bit-identical).  The binary64 sweeps choose between
+// the two once per window: a shift test inside the pair loop is compiled into
+// adds issued under a predicate, which still occupy the narrow binary64 pipe.
+__device__ __forceinline__ double plain_r2(const double4_32a &p, const double4_32a &q)
+{
+    const double dx = __dsub_rn(q.x, p.x), dy = __dsub_rn(q.y, p.y), dz = __dsub_rn(q.z, p.z);
+    return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+}
+
 // Binary64 re-evaluation of one pair inside an error band: bin row or -1.
 __device__ __noinline__ int recheck64(const double *E2, int nb, const double4_32a *pa,
                                       const double4_32a *pb, int i, int j, double Sx, double Sy,
@@ -1483,13 +1493,18 @@ struct Xi64Path {
                     if (jlo >= jhi)
                         continue;
                     pending += (unsigned)((jhi - jlo + J - 1) / J);
+                    const bool noshift = it.Sx == 0.0 && it.Sy == 0.0 && kz == 0.0;
                     for (int jb = jlo; jb < jhi; jb += J) {
                         const int j = jb + jj;
                         const double4_32a pj = tile[j];
                         const bool live = !tri || (t0 + j > i);
                         if (EVALS)
                             n_eval += (vi && j < jhi && live) ? 1ull : 0ull;
-                        double r2 = canon_r2(pi, pj, it.Sx, it.Sy, kz);
+                        double r2;
+                        if (noshift)
+                            r2 = plain_r2(pi, pj);
+                        else
+                            r2 = canon_r2(pi, pj, it.Sx, it.Sy, kz);
                         if (!live)
                             r2 = qnan;
                         const int kb = bin_f64(r2, E2, nb);
@@ -2443,15 +2458,23 @@ struct Rppi64Path {
                     if (jlo >= jhi)
                         continue;
                     pending += (unsigned)((jhi - jlo + J - 1) / J) * 32u;
+                    const bool noshift = it.Sx == 0.0 && it.Sy == 0.0 && kz == 0.0;  // as in Xi64Path
                     for (int jb = jlo; jb < jhi; jb += J) {
                         const int j = jb + jj;
                         const double4_32a pj = tile[j];
                         const bool live = !tri || (t0 + j > i);
                         if (EVALS)
                             n_eval += (vi && j < jhi && live) ? 1ull : 0ull;
-                        const double dx = canon_comp(pi.x, pj.x, it.Sx);
-                        const double dy = canon_comp(pi.y, pj.y, it.Sy);
-                        const double dz = canon_comp(pi.z, pj.z, kz);
+                        double dx, dy, dz;
+                        if (noshift) {
+                            dx = __dsub_rn(pj.x, pi.x);
+                            dy = __dsub_rn(pj.y, pi.y);
+                            dz = __dsub_rn(pj.z, pi.z);
+                        } else {
+                            dx = canon_comp(pi.x, pj.x, it.Sx);
+                            dy = canon_comp(pi.y, pj.y, it.Sy);
+                            dz = canon_comp(pi.z, pj.z, kz);
+                        }
                         double rp2 = __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy));
                         if (!live)
                             rp2 = qnan;
