@@ -382,8 +382,9 @@ def batch_workload(cf, synth, torch, dev, flush):
 
 def run_profile_case(args):
     """A few calls of one workload for an ncu capture (no L2 flush, no JSON line):
-    xi (C2, Rmax 25), rppi (C2, 14 x 40, pimax 40), dr_small (the C2 data, weighted,
-    against the first 1.2M weighted randoms, open box, with ravg)."""
+    xi (C2, Rmax 25), xi64 (the same in binary64), rppi (C2, 14 x 40, pimax 40),
+    dr_small (the C2 data, weighted, against the first 1.2M weighted randoms, open
+    box, with ravg)."""
     import torch
     import paper_1911_08275_gb300 as cf
     from paper_1911_08275_gb300 import synth
@@ -401,6 +402,8 @@ def run_profile_case(args):
     for _ in range(args.steps):
         if args.profile == "xi":
             r = cf.countpairs_xi(*xyz, e, boxsize=synth.BOX)
+        elif args.profile == "xi64":
+            r = cf.countpairs_xi(*xyz, e, boxsize=synth.BOX, mode="fp64")
         elif args.profile == "rppi":
             r = cf.countpairs_rp_pi(*xyz, synth.log_edges(RMIN, RMAX, 14), 40.0, 40, boxsize=synth.BOX)
         else:
@@ -421,7 +424,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the secondary workloads (Rmax sweep, DD(rp,pi), weighted DR)")
-    ap.add_argument("--profile", choices=["xi", "rppi", "dr_small"],
+    ap.add_argument("--profile", choices=["xi", "xi64", "rppi", "dr_small"],
                     help="run --steps calls of one workload for a profiler capture, then exit")
     args = ap.parse_args()
     if args.profile:
