@@ -854,10 +854,9 @@ int run(Request &q)
     res->refine_used[2] = g.reach_z;
 
     {  // grid workspace
-        // float32 DD(r) with mean separations: the coordinates' float32 rounding
-        // residuals, unless the inputs are float32 in a periodic box (exact)
-        const bool resid = q.kind == 0 && !f64 && c->want_ravg &&
-                           !(c->dtype == CF_FLOAT32 && c->periodic);
+        // float32 mean separations: the coordinates' float32 rounding residuals,
+        // unless the inputs are float32 in a periodic box (exact)
+        const bool resid = !f64 && c->want_ravg && !(c->dtype == CF_FLOAT32 && c->periodic);
         for (int pass = 0; pass < 2; ++pass) {
             bump.base = pass ? (char *)ws2 : nullptr;
             bump.off = 0;

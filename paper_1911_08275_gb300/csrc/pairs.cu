@@ -1639,6 +1639,7 @@ struct SweepRP {
     float pband;
     double *acc;           // weighted sums: this copy's binary64 [slot][w, r w] (or NULL)
     bool weighted, want_r;
+    const float *xlj, *ylj;  // secondaries' coordinate residuals from tile element 0 (or NULL)
     const double4_32a *pa, *pb;
     double Sx, Sy, Sz;
 };
@@ -1646,18 +1647,36 @@ struct SweepRP {
 // A pair whose rp table cell is flagged or whose t is near a pi edge: settle
 // both decisions exactly, undo the main path's increment (at addr_main) and
 // add the pair to its true slot.  Returns 1 if binary64 was needed.
-// Binary64 accumulation of one counted pair's weight and rp * weight.
-__device__ __forceinline__ void acc_rppi(const SweepRP &S, int slot, float pw, float rp2)
+// The primary's side of a pair for the residual correction of its rp: the
+// primary's shifted float32 coordinates and its residuals after the shift.
+struct PrimRL {
+    float xh, yh, lx, ly;
+};
+
+// Binary64 accumulation of one counted pair's weight and rp * weight.  With the
+// coordinates' float32 rounding residuals (gridding stores them for float64
+// inputs or an open box) rp^2 is corrected to first order, as the float32 DD(r)
+// path corrects r^2: rp^2 = rp2~ + 2 (dx~ (r_xj - r_xi') + dy~ (r_yj - r_yi')),
+// dx~ the float32 difference of the main path recomputed from the staged tile.
+__device__ __forceinline__ void acc_rppi(const unsigned char *smem, const SweepRP &S, int slot,
+                                         float pw, float rp2, int jl, const PrimRL &R)
 {
     atomicAdd(S.acc + 2 * slot, (double)pw);
-    if (S.want_r)
+    if (S.want_r) {
+        if (S.xlj) {
+            const float *tx = reinterpret_cast<const float *>(smem + TX_OFF);
+            const float dx = __fsub_rn(tx[jl], R.xh), dy = __fsub_rn(tx[jl + TSTRIDE / 4], R.yh);
+            rp2 = __fmaf_rn(2.0f, __fmaf_rn(dy, S.ylj[jl] - R.ly, dx * (S.xlj[jl] - R.lx)), rp2);
+        }
         atomicAdd(S.acc + 2 * slot + 1, (double)(sqrt_approx(rp2) * pw));
+    }
 }
 
 template <bool WACC>
 __device__ __forceinline__ int resolve_rppi(const unsigned char *smem, const SweepRP &S, uint32_t e,
                                             float rp2, uint32_t m_main, bool pflag,
-                                            uint32_t addr_main, int i, int jg, float pw)
+                                            uint32_t addr_main, int i, int jg, float pw,
+                                            const PrimRL &R = PrimRL{0.0f, 0.0f, 0.0f, 0.0f})
 {
     int k, re = 0;
     if (e > (uint32_t)S.nb) {
@@ -1687,7 +1706,7 @@ __device__ __forceinline__ int resolve_rppi(const unsigned char *smem, const Swe
     if (m >= 0) {
         red_shared(S.hbase + (uint32_t)k * S.rowb + (uint32_t)m * 4u, 1u);
         if (WACC)
-            acc_rppi(S, k * (S.npi + 1) + m, pw, rp2);
+            acc_rppi(smem, S, k * (S.npi + 1) + m, pw, rp2, jg - S.t0, R);
     }
     return re;
 }
@@ -1699,7 +1718,8 @@ __device__ __forceinline__ int resolve_rppi(const unsigned char *smem, const Swe
 template <int I, bool TRI, bool EVALS, bool VERIFY, bool WACC, bool LIN>
 __device__ __forceinline__ void sweep_rppi32(unsigned char *smem, const SweepRP &S, int jlo, int jhi,
                                              int jj, u64 XH, u64 YH, u64 ZH, u64 SC, u64 WH, int i,
-                                             bool vi, u64 &n_eval, u64 &n_rck, u64 &n_viol)
+                                             bool vi, u64 &n_eval, u64 &n_rck, u64 &n_viol,
+                                             const PrimRL &R)
 {
     const float qnan = __int_as_float(0x7fc00000);
     const u64 MH = pack2(-0.5f, -0.5f), MG = pack2(PI_MAGIC, PI_MAGIC);
@@ -1778,25 +1798,25 @@ __device__ __forceinline__ void sweep_rppi32(unsigned char *smem, const SweepRP 
             }
             // pairs settled by the float32 path; flagged ones are added when resolved
             if (!pa0 && ea0 < nbu && ma0 < npiu)
-                acc_rppi(S, (int)(ea0 * (npiu + 1) + ma0), wa0, a0);
+                acc_rppi(smem, S, (int)(ea0 * (npiu + 1) + ma0), wa0, a0, jA, R);
             if (!pa1 && ea1 < nbu && ma1 < npiu)
-                acc_rppi(S, (int)(ea1 * (npiu + 1) + ma1), wa1, a1);
+                acc_rppi(smem, S, (int)(ea1 * (npiu + 1) + ma1), wa1, a1, jA + 1, R);
             if (!pb0 && eb0 < nbu && mb0 < npiu)
-                acc_rppi(S, (int)(eb0 * (npiu + 1) + mb0), wb0, b0);
+                acc_rppi(smem, S, (int)(eb0 * (npiu + 1) + mb0), wb0, b0, jA + JS, R);
             if (!pb1 && eb1 < nbu && mb1 < npiu)
-                acc_rppi(S, (int)(eb1 * (npiu + 1) + mb1), wb1, b1);
+                acc_rppi(smem, S, (int)(eb1 * (npiu + 1) + mb1), wb1, b1, jA + JS + 1, R);
         }
         const bool ga0 = ea0 > nbu || pa0, ga1 = ea1 > nbu || pa1;
         const bool gb0 = eb0 > nbu || pb0, gb1 = eb1 > nbu || pb1;
         if (__any_sync(FULL, ga0 || ga1 || gb0 || gb1)) {
             if (ga0)
-                n_rck += resolve_rppi<WACC>(smem, S, ea0, a0, ma0, pa0, ha0, i, gA, wa0);
+                n_rck += resolve_rppi<WACC>(smem, S, ea0, a0, ma0, pa0, ha0, i, gA, wa0, R);
             if (ga1)
-                n_rck += resolve_rppi<WACC>(smem, S, ea1, a1, ma1, pa1, ha1, i, gA + 1, wa1);
+                n_rck += resolve_rppi<WACC>(smem, S, ea1, a1, ma1, pa1, ha1, i, gA + 1, wa1, R);
             if (gb0)
-                n_rck += resolve_rppi<WACC>(smem, S, eb0, b0, mb0, pb0, hb0, i, gB, wb0);
+                n_rck += resolve_rppi<WACC>(smem, S, eb0, b0, mb0, pb0, hb0, i, gB, wb0, R);
             if (gb1)
-                n_rck += resolve_rppi<WACC>(smem, S, eb1, b1, mb1, pb1, hb1, i, gB + 1, wb1);
+                n_rck += resolve_rppi<WACC>(smem, S, eb1, b1, mb1, pb1, hb1, i, gB + 1, wb1, R);
         }
         if (VERIFY) {
             const float *T = reinterpret_cast<const float *>(smem + THR_OFF);
@@ -1924,12 +1944,18 @@ struct Rppi32Path {
         S.acc = WACC ? acc + 2 * (warp % P.hcopies) * copy : nullptr;
         S.weighted = WACC && P.weighted;
         S.want_r = WACC && P.want_r;
+        // rp of the mean separations from residual-corrected rp^2 when the gridding
+        // stored the coordinates' float32 rounding residuals
+        const bool rl = S.want_r && P.B.xl != nullptr;
         const u64 SC = pack2(P.pscale, P.pscale);
         const unsigned flush_at = (1u << 30) / (unsigned)(WARPS / P.hcopies);
         const float qnan = __int_as_float(0x7fc00000);
 
         const float dzw = __fadd_ru(__double2float_ru(it.dzmax), P.zslack);
         const float Sxf = __double2float_rn(it.Sx), Syf = __double2float_rn(it.Sy);
+        // the roundings of the periodic shifts, S - fl32(S)
+        const float dSx = rl ? __double2float_rn(__dsub_rn(it.Sx, (double)Sxf)) : 0.0f;
+        const float dSy = rl ? __double2float_rn(__dsub_rn(it.Sy, (double)Syf)) : 0.0f;
         S.Sx = it.Sx;
         S.Sy = it.Sy;
         const int nchunks = (it.a1 - it.a0 + I - 1) / I;
@@ -1940,6 +1966,8 @@ struct Rppi32Path {
                 return false;
             }
             S.t0 = t0;
+            S.xlj = rl ? P.B.xl + t0 : nullptr;
+            S.ylj = rl ? P.B.yl + t0 : nullptr;
             const float zt_lo = tz[0];
             float zt_hi = tz[nt - 1];
             if (isnan(zt_hi))
@@ -1957,17 +1985,27 @@ struct Rppi32Path {
                 const int ib = it.a0 + c * I;
                 const int nvi = min(I, it.a1 - ib);
                 const int i = ib + ii;
-                float xi = qnan, yi = qnan, zi = qnan, wi = 1.0f;
+                float xi = qnan, yi = qnan, zi = qnan, wi = 1.0f, rx = 0.0f, ry = 0.0f;
                 if (ii < nvi) {
                     xi = P.A.xs[i];
                     yi = P.A.ys[i];
                     zi = P.A.zs[i];
                     if (S.weighted)
                         wi = P.A.ws[i];
+                    if (rl) {
+                        rx = P.A.xl[i];
+                        ry = P.A.yl[i];
+                    }
                 }
                 const bool vi = !isnan(xi);
                 const float xh = __fsub_rn(xi, Sxf), yh = __fsub_rn(yi, Syf);
                 const u64 XH = pack2(xh, xh), YH = pack2(yh, yh), WH = pack2(wi, wi);
+                // the primary's residuals after the shift: r_i + (x~ - S~ - x^) - (S - S~)
+                PrimRL R{xh, yh, 0.0f, 0.0f};
+                if (rl) {
+                    R.lx = __fsub_rn(__fadd_rn(rx, two_sum_err(xi, -Sxf, xh)), dSx);
+                    R.ly = __fsub_rn(__fadd_rn(ry, two_sum_err(yi, -Syf, yh)), dSy);
+                }
                 const float zlo = __shfl_sync(FULL, zi, 0);
                 float zhi = zi;
     #pragma unroll
@@ -2003,17 +2041,17 @@ struct Rppi32Path {
                     if (tri) {
                         if (S.lin)
                             sweep_rppi32<I, true, EVALS, VERIFY, WACC, true>(
-                                smem, S, jlo, jhi, jj, XH, YH, ZH, SC, WH, i, vi, n_eval, n_rck, n_viol);
+                                smem, S, jlo, jhi, jj, XH, YH, ZH, SC, WH, i, vi, n_eval, n_rck, n_viol, R);
                         else
                             sweep_rppi32<I, true, EVALS, VERIFY, WACC, false>(
-                                smem, S, jlo, jhi, jj, XH, YH, ZH, SC, WH, i, vi, n_eval, n_rck, n_viol);
+                                smem, S, jlo, jhi, jj, XH, YH, ZH, SC, WH, i, vi, n_eval, n_rck, n_viol, R);
                     } else {
                         if (S.lin)
                             sweep_rppi32<I, false, EVALS, VERIFY, WACC, true>(
-                                smem, S, jlo, jhi, jj, XH, YH, ZH, SC, WH, i, vi, n_eval, n_rck, n_viol);
+                                smem, S, jlo, jhi, jj, XH, YH, ZH, SC, WH, i, vi, n_eval, n_rck, n_viol, R);
                         else
                             sweep_rppi32<I, false, EVALS, VERIFY, WACC, false>(
-                                smem, S, jlo, jhi, jj, XH, YH, ZH, SC, WH, i, vi, n_eval, n_rck, n_viol);
+                                smem, S, jlo, jhi, jj, XH, YH, ZH, SC, WH, i, vi, n_eval, n_rck, n_viol, R);
                     }
                 }
                 if (pending > flush_at) {  // keep every shared u32 count far from overflow
@@ -2249,6 +2287,7 @@ struct Rppi32PathPP {
         S.acc = nullptr;
         S.weighted = false;
         S.want_r = false;
+        S.xlj = S.ylj = nullptr;
         const u64 SC = pack2(P.pscale, P.pscale);
         const unsigned flush_at = (1u << 30) / (unsigned)(WARPS / P.hcopies);
         const float qnan = __int_as_float(0x7fc00000);

@@ -7,9 +7,10 @@ order and, in float32 mode, by float32 arithmetic:
   - float32 mode: weights are rounded to float32 (product error <= 3 u32) and
     each term to a power-of-two fixed-point grid, then summed exactly in
     integers (error <= 2^-22 max|w w| / |w w| per term), so wsum agrees to
-    1e-5 relative; DD(r)'s r comes from the float32 squared distance corrected
-    to first order with the coordinates' float32 rounding residuals, so ravg
-    agrees to 1e-5 relative as well, for float64 inputs in an open box too.
+    1e-5 relative; r (DD(r)) and rp (DD(rp, pi)) come from the float32 squared
+    distance corrected to first order with the coordinates' float32 rounding
+    residuals, so ravg agrees to 1e-5 relative as well, for float64 inputs in
+    an open box too.
 """
 import json
 import os
@@ -109,6 +110,35 @@ def test_xi_ravg_float64_inputs_fp32_mode(cuda_device, periodic):
     n, _, rs = oracle.xi(cat.x, cat.y, cat.z, edges=e, periodic=periodic, box=300.0, want_r=True)
     assert n[0] > 0
     check(r, n, None, rs, "fp32_recheck", False)
+
+
+@pytest.mark.parametrize("periodic", [True, False])
+@pytest.mark.parametrize("weighted", [False, True])
+def test_rppi_ravg_float64_inputs_fp32_mode(cuda_device, periodic, weighted):
+    # the same for DD(rp, pi): rp from residual-corrected rp^2, 1e-5 relative in
+    # every (rp, pi) slot down to the 0.1-0.14 rp bin, auto and cross
+    cat = synth.neyman_scott(1000, 20.0, 2.0, 300.0, seed=87)
+    u = synth.uniform_box(4000, 300.0, seed=88)
+    w = synth.uniform_weights(cat.n, 0.5, 1.5, seed=89) if weighted else None
+    wu = synth.uniform_weights(u.n, 0.5, 1.5, seed=90) if weighted else None
+    e = synth.log_edges(0.1, 20.0, 12)
+    x, y, z = tdev(cat.x, cat.y, cat.z)
+    kw = dict(boxsize=300.0, periodic=periodic, want_ravg=True)
+    if weighted:
+        kw["w"] = tdev(w)[0]
+    r = cf.countpairs_rp_pi(x, y, z, e, 30.0, 30, **kw)
+    n, ws, rs = oracle.rppi(cat.x, cat.y, cat.z, w1=w, rp_edges=e, pimax=30.0, npibins=30,
+                            periodic=periodic, box=300.0, want_r=True)
+    assert n[0].sum() > 0
+    check(r, n, ws, rs, "fp32_recheck", weighted)
+    ux, uy, uz = tdev(u.x, u.y, u.z)
+    if weighted:
+        kw["w2"] = tdev(wu)[0]
+    rc = cf.countpairs_rp_pi(x, y, z, e, 30.0, 30, x2=ux, y2=uy, z2=uz, **kw)
+    n, ws, rs = oracle.rppi(cat.x, cat.y, cat.z, w1=w, x2=u.x, y2=u.y, z2=u.z, w2=wu, rp_edges=e,
+                            pimax=30.0, npibins=30, autocorr=False, periodic=periodic, box=300.0,
+                            want_r=True)
+    check(rc, n, ws, rs, "fp32_recheck", weighted)
 
 
 @pytest.mark.parametrize("mode", ["fp32_recheck", "fp64"])
