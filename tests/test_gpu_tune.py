@@ -68,3 +68,24 @@ def test_invalid_kernel_shapes_rejected(cuda_device, chunk, pp):
     with pytest.raises(cf.CfError) as ei:
         cf.countpairs_xi(*dev(cat), [0.1, 1.0], boxsize=10.0, pair_chunk=chunk, pair_pp=pp)
     assert ei.value.status == cf.CF_EINVAL
+
+
+def test_default_refinement_follows_the_points_per_column(cuda_device):
+    # refine (0, 0, 0): r = round(Rmax / s) in [1, 4], s the column side over
+    # which the smaller catalogue holds 1024 points: 200k uniform points in a
+    # box of 200 give s = 14.3, so Rmax 5, 30, 60 -> r = 1 (clamped), 2, 4; a
+    # cross count against a 20k-point catalogue (s = 45.3) at Rmax 60 -> 1
+    big = synth.uniform_box(200000, 200.0, seed=95)
+    small = synth.uniform_box(20000, 200.0, seed=96)
+    xb, xs = dev(big), dev(small)
+    for rmax, want in ((5.0, 1), (30.0, 2), (60.0, 4)):
+        e = synth.log_edges(0.5, rmax, 8)
+        r = cf.countpairs_xi(*xb, e, boxsize=200.0)
+        assert r.refine_used == (want, want, 1), (rmax, r.refine_used)
+        fixed = cf.countpairs_xi(*xb, e, boxsize=200.0, refine=(2, 2, 1))
+        assert np.array_equal(r.npairs, fixed.npairs)
+    e = synth.log_edges(0.5, 60.0, 8)
+    rc = cf.countpairs_xi(*xs, e, x2=xb[0], y2=xb[1], z2=xb[2], boxsize=200.0)
+    assert rc.refine_used == (1, 1, 1)
+    fixed = cf.countpairs_xi(*xs, e, x2=xb[0], y2=xb[1], z2=xb[2], boxsize=200.0, refine=(3, 3, 1))
+    assert np.array_equal(rc.npairs, fixed.npairs)
