@@ -146,6 +146,23 @@ def profile_traffic():
     return int(fields["traffic_bytes_per_launch"]), "ncu capture " + os.path.basename(PROFILE)
 
 
+def counts_equal_oracle(name, cat, npairs):
+    """Counts against the brute-force oracle's stored histogram of the same
+    catalogue (tests/golden/<name>.json, written by tests/golden/make_golden.py,
+    which calls only the oracle); None when the file or its catalogue digest
+    does not match."""
+    path = os.path.join(ROOT, "tests", "golden", name + ".json")
+    try:
+        with open(path) as f:
+            g = json.load(f)
+    except OSError:
+        return None
+    if g.get("catalog_digest") != cat.digest():
+        return None
+    return bool(np.array_equal(np.asarray(g["npairs"], dtype=np.uint64).ravel(),
+                               np.asarray(npairs, dtype=np.uint64).ravel()))
+
+
 def cpu_baseline_sample(cat, edges, rows, reps=1):
     """Time the oracle on primary rows [0, rows) against the whole catalogue."""
     import oracle
@@ -219,7 +236,7 @@ def _median_call(fn, flush, reps=3):
     return res[-1], ms, kms
 
 
-def _timed_row(cf, fn, flush, peak_evals, fp32=True):
+def _timed_row(cf, fn, flush, peak_evals, fp32=True, golden=None):
     """One secondary workload: evaluation count (a separate run with
     CF_FLAG_COUNT_EVALS), then the median of three timed calls; the roofline
     fraction of the pair kernel is evaluations / kernel time / R1 (the same
@@ -230,6 +247,8 @@ def _timed_row(cf, fn, flush, peak_evals, fp32=True):
         raise RuntimeError("counts differ between the counting and the timed runs")
     row = {"ms": ms, "kernel_ms": kms, "Gpairs_s": float(r.npairs.sum()) / (ms * 1e-3) / 1e9,
            "evaluations": int(diag.n_evaluated), "refine": list(r.refine_used)}
+    if golden is not None:
+        row["counts_equal_oracle"] = counts_equal_oracle(golden[0], golden[1], r.npairs)
     if fp32:
         achieved = diag.n_evaluated / (kms * 1e-3) / 1e9
         row["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak_evals,
@@ -247,7 +266,8 @@ def other_workloads(cf, synth, torch, cat, xyz, dev, stream, flush, peak_evals):
         for mode in ("fp32_recheck", "fp64"):
             row[mode] = _timed_row(cf, lambda fl: cf.countpairs_xi(*xyz, e, boxsize=synth.BOX,
                                                                    mode=mode, flags=fl, stream=st),
-                                   flush, peak_evals, mode == "fp32_recheck")
+                                   flush, peak_evals, mode == "fp32_recheck",
+                                   golden=(f"c2_xi_r{rmax:g}_f64", cat))
         out[f"xi_auto_rmax{rmax:g}"] = row
     e = synth.log_edges(RMIN, RMAX, 14)
     row = {}
@@ -522,7 +542,9 @@ def main():
            "warmup": args.warmup, "ms_per_step": t_mean, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64recheck" if args.mode ==
            "fp32_recheck" else "f64", "data": "synthetic", "config": workload_config(cat.n),
-           "p_cnt": p_cnt, "clocks": clk.summary(), "roofline": roofline,
+           "p_cnt": p_cnt, "counts_equal_oracle": counts_equal_oracle("c2_xi_r25_f64", cat,
+                                                                      diag.npairs),
+           "clocks": clk.summary(), "roofline": roofline,
            "e2e": {"value": e2e_value, "unit": UNIT, "ms_per_step": e_mean,
                    "h2d_bytes_per_step": int(3 * 8 * cat.n),
                    "d2h_bytes_per_step": int(8 * NBINS + 8 * 4 + 4)},

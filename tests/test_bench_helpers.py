@@ -74,3 +74,24 @@ def test_clock_summary_without_samples(tmp_path):
     s = bench.ClockSampler(0)
     s.path = str(tmp_path / "none.csv")
     assert s.summary()["reasons"] == ["unsampled"]
+
+
+def test_counts_equal_oracle_checks_the_stored_histogram_and_its_catalogue():
+    import json
+
+    import numpy as np
+
+    from paper_1911_08275_gb300 import synth
+    path = os.path.join(bench.ROOT, "tests", "golden", "c2_xi_r10_f64.json")
+    with open(path) as f:
+        g = json.load(f)
+    cat = synth.c2_clustered()
+    ref = np.asarray(g["npairs"], dtype=np.uint64)
+    assert bench.counts_equal_oracle("c2_xi_r10_f64", cat, ref) is True
+    bad = ref.copy()
+    bad[-1] += 2
+    assert bench.counts_equal_oracle("c2_xi_r10_f64", cat, bad) is False
+    # another catalogue, or no stored histogram: no claim either way
+    other = synth.uniform_box(1000, 420.0, seed=1)
+    assert bench.counts_equal_oracle("c2_xi_r10_f64", other, ref) is None
+    assert bench.counts_equal_oracle("no_such_golden", cat, ref) is None
