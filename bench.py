@@ -274,7 +274,7 @@ def other_workloads(cf, synth, torch, cat, xyz, dev, stream, flush, peak_evals):
     for mode in ("fp32_recheck", "fp64"):
         row[mode] = _timed_row(cf, lambda fl: cf.countpairs_rp_pi(*xyz, e, 40.0, 40, boxsize=synth.BOX,
                                                                   mode=mode, flags=fl, stream=st),
-                               flush, peak_evals, mode == "fp32_recheck")
+                               flush, peak_evals, mode == "fp32_recheck", golden=("c3_rppi_f64", cat))
     out["rppi_auto_14x40_pimax40"] = row
     # weighted DR with ravg: 1.2M clustered data x 12M uniform randoms, open box
     wd = synth.uniform_weights(cat.n, 0.5, 1.5, seed=4)

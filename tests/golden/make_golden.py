@@ -39,6 +39,8 @@ CASES = {
     # DD(rp, pi): 14 log rp bins 0.1 -> 25, pimax 40 in 40 unit bins, LOS = z.
     "c3_rppi_f32": dict(kind="rppi", cat=("c2", "f32"), rmin=0.1, rmax=25.0, nbins=14,
                         pimax=40.0, npibins=40),
+    "c3_rppi_f64": dict(kind="rppi", cat=("c2", "f64"), rmin=0.1, rmax=25.0, nbins=14,
+                        pimax=40.0, npibins=40),
     # DR with weights and ravg, open box: a slice of the weighted data (the first
     # 8000 points of the clustered catalogue, weights U(0.5,1.5) seed 4) against
     # all 12M weighted randoms (seed 3, weights seed 5); 20 log bins 0.1 -> 25.

@@ -53,9 +53,13 @@ def test_xi_full_size_matches_stored_oracle(cuda_device, c2, path, mode):
     assert r.npairs.tolist() == g["npairs"]
 
 
+RPPI_FILES = sorted(glob.glob(os.path.join(GOLDEN, "c3_rppi_*.json")))
+
+
+@pytest.mark.parametrize("path", RPPI_FILES, ids=[os.path.basename(p) for p in RPPI_FILES])
 @pytest.mark.parametrize("mode", ["fp32_recheck", "fp64"])
-def test_rppi_full_size_matches_stored_oracle(cuda_device, c2, mode):
-    g = _load(os.path.join(GOLDEN, "c3_rppi_f32.json"))
+def test_rppi_full_size_matches_stored_oracle(cuda_device, c2, path, mode):
+    g = _load(path)
     cat = _cat(c2, g["workload"]["cat"][1])
     assert cat.digest() == g["catalog_digest"], "catalogue differs from the stored one"
     edges = np.array([float.fromhex(h) for h in g["edges_hex"]])
