@@ -407,13 +407,24 @@ def run_profile_case(args):
     """A few calls of one workload for an ncu capture (no L2 flush, no JSON line):
     xi (C2, Rmax 25), xi64 (the same in binary64), rppi (C2, 14 x 40, pimax 40),
     dr_small (the C2 data, weighted, against the first 1.2M weighted randoms, open
-    box, with ravg)."""
+    box, with ravg), batch_small (the 480 small jobs of the batch workload, one run
+    per step without the graph, so every launch is visible)."""
     import torch
     import paper_1911_08275_gb300 as cf
     from paper_1911_08275_gb300 import synth
     cf.lib()
-    cat = synth.c2_clustered()
     dev = torch.device("cuda", 0)
+    if args.profile == "batch_small":
+        small = [synth.batch_job(j % 48, scale=0.004) for j in range(480)]
+        sx = [[torch.from_numpy(v).to(dev) for v in (jb["cat"].x, jb["cat"].y, jb["cat"].z)]
+              for jb in small]
+        b, _ = _batch(cf, small, sx, autotune=False)
+        runs = [b.run(use_graph=False) for _ in range(args.steps)]
+        b.close()
+        print(f"profile case batch_small: run ms {[round(r['total_ms'], 3) for r in runs]}, "
+              f"pair kernel ms {[round(r['kernel_ms'], 3) for r in runs]}", flush=True)
+        return
+    cat = synth.c2_clustered()
     xyz = [torch.from_numpy(v).to(dev) for v in (cat.x, cat.y, cat.z)]
     e = synth.log_edges(RMIN, RMAX, NBINS)
     if args.profile == "dr_small":
@@ -447,7 +458,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the secondary workloads (Rmax sweep, DD(rp,pi), weighted DR)")
-    ap.add_argument("--profile", choices=["xi", "xi64", "rppi", "dr_small"],
+    ap.add_argument("--profile", choices=["xi", "xi64", "rppi", "dr_small", "batch_small"],
                     help="run --steps calls of one workload for a profiler capture, then exit")
     args = ap.parse_args()
     if args.profile:

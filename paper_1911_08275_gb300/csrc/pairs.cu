@@ -2798,17 +2798,35 @@ __device__ __forceinline__ void batch_fini(int path, const PairParams &P, unsign
 }
 
 // offsets[j] = kept column pairs of jobs 0..j-1 (one thread; a few thousand jobs at most).
+// Exclusive scan of the jobs' kept-item counts (one warp: each lane loads its
+// jobs' counts in parallel, 32 jobs per round).
 __global__ void k_batch_offsets(const __grid_constant__ BatchParams B)
 {
-    if (threadIdx.x != 0 || blockIdx.x != 0)
+    if (blockIdx.x != 0)
         return;
-    unsigned acc = 0;
-    for (int j = 0; j < B.njobs; ++j) {
-        B.offsets[j] = acc;
-        acc += *B.jobs[j].work_count;
+    const int lane = threadIdx.x & 31;
+    unsigned carry = 0;
+    for (int j0 = 0; j0 < B.njobs; j0 += 32) {
+        const int j = j0 + lane;
+        const unsigned v = j < B.njobs ? *B.jobs[j].work_count : 0u;
+        unsigned incl = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned t = __shfl_up_sync(FULL, incl, o);
+            if (lane >= o)
+                incl += t;
+        }
+        if (j < B.njobs)
+            B.offsets[j] = carry + incl - v;
+        carry += __shfl_sync(FULL, incl, 31);
     }
-    B.offsets[B.njobs] = acc;
+    if (lane == 0)
+        B.offsets[B.njobs] = carry;
 }
+
+// Candidate pairs of a work item below which the batch kernel claims items in
+// groups (see k_batch).
+constexpr long long GROUP_PAIRS = 1ll << 16;
 
 __global__ void __launch_bounds__(THREADS, 2) k_batch(const __grid_constant__ BatchParams B)
 {
@@ -2824,40 +2842,58 @@ __global__ void __launch_bounds__(THREADS, 2) k_batch(const __grid_constant__ Ba
     }
     __syncthreads();
     const unsigned total = s_off[B.njobs];
+    // Small items (column pairs of fewer than GROUP_PAIRS candidate pairs) are
+    // claimed in groups of consecutive items (up to 16, together about
+    // GROUP_PAIRS), so that a CTA stays on a small job for a while instead of
+    // every CTA switching to it for one item (each switch loads the job's table
+    // and merges its histogram); larger items are claimed one by one, which keeps
+    // the load balanced.  The size of the next group comes from the last item
+    // decoded (the next one is most often of the same job), so a claim stays one
+    // atomic.
     PathState st = {0ull, 0ull, 0ull, 0u, 0u, 0u};
     int cur = -1;
-    for (;;) {
+    unsigned group = 1;
+    bool ok = true;
+    while (ok) {
         if (threadIdx.x == 0)
-            *s_item = (int)atomicAdd(B.item_counter, 1u);
+            *s_item = (int)atomicAdd(B.item_counter, group);
         __syncthreads();
-        const unsigned item = (unsigned)*s_item;
+        const unsigned base = (unsigned)*s_item;
         __syncthreads();
-        if (item >= total)
+        if (base >= total)
             break;
-        int lo = 0, hi = B.njobs;  // largest job with s_off[job] <= item
-        while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
-            if (s_off[mid] <= item)
-                lo = mid;
-            else
-                hi = mid;
+        const unsigned stop = min(base + group, total);
+#pragma unroll 1
+        for (unsigned item = base; item < stop; ++item) {
+            int lo = 0, hi = B.njobs;  // largest job with s_off[job] <= item
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (s_off[mid] <= item)
+                    lo = mid;
+                else
+                    hi = mid;
+            }
+            const int job = lo;
+            if (job != cur) {  // CTA-uniform: every thread holds the same item
+                if (cur >= 0)
+                    batch_fini(B.path[cur], B.jobs[cur], smem, st);
+                __syncthreads();
+                batch_init(B.path[job], B.jobs[job], smem);
+                st.n_eval = st.n_rck = st.n_viol = 0ull;
+                st.pending = 0u;
+                __syncthreads();
+                cur = job;
+            }
+            const PairParams &P = B.jobs[job];
+            Item it;
+            decode_item(P, (int)(item - s_off[job]), it);
+            const long long pairs = (long long)max(it.a1 - it.a0, 1) * max(it.b1 - it.b0, 1);
+            group = pairs < GROUP_PAIRS ? (unsigned)min(16ll, GROUP_PAIRS / pairs) : 1u;
+            if (!batch_item(B.path[job], P, it, smem, st)) {
+                ok = false;
+                break;
+            }
         }
-        const int job = lo;
-        if (job != cur) {  // CTA-uniform: every thread holds the same item
-            if (cur >= 0)
-                batch_fini(B.path[cur], B.jobs[cur], smem, st);
-            __syncthreads();
-            batch_init(B.path[job], B.jobs[job], smem);
-            st.n_eval = st.n_rck = st.n_viol = 0ull;
-            st.pending = 0u;
-            __syncthreads();
-            cur = job;
-        }
-        const PairParams &P = B.jobs[job];
-        Item it;
-        decode_item(P, (int)(item - s_off[job]), it);
-        if (!batch_item(B.path[job], P, it, smem, st))
-            break;
     }
     if (cur >= 0)
         batch_fini(B.path[cur], B.jobs[cur], smem, st);
