@@ -127,7 +127,11 @@ typedef struct {
     uint64_t *npairs;    /* [nbins] (xi) or [n_rp_bins * npibins] rp-major      */
     double *wsum;        /* same shape: sum of w_i*w_j (weighted) else unused     */
     double *ravg;        /* same shape: mean separation (r or rp), weighted by
-                            w_i*w_j when weighted; 0 for empty bins               */
+                            w_i*w_j when weighted; 0 for empty bins.  Binary64
+                            mode: within 1e-12 relative of the binary64
+                            definition; float32 mode: within 1e-5 relative (r
+                            from the float32 squared distance corrected with the
+                            coordinates' float32 rounding residuals)             */
     uint64_t n_cellpairs;       /* column pairs kept after pruning                */
     uint64_t n_evaluated;       /* pair evaluations (CF_FLAG_COUNT_EVALS)        */
     uint64_t n_rechecked;       /* pairs re-evaluated in binary64 (FP32 mode)    */
