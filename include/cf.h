@@ -128,10 +128,15 @@ typedef struct {
     double *wsum;        /* same shape: sum of w_i*w_j (weighted) else unused     */
     double *ravg;        /* same shape: mean separation (r or rp), weighted by
                             w_i*w_j when weighted; 0 for empty bins.  Binary64
-                            mode: within 1e-12 relative of the binary64
-                            definition; float32 mode: within 1e-5 relative (r
-                            from the float32 squared distance corrected with the
-                            coordinates' float32 rounding residuals)             */
+                            mode: exact per-pair terms, sums within 1e-12
+                            relative (summation order).  Float32 mode: r from
+                            the float32 squared distance corrected with the
+                            coordinates' float32 rounding residuals (~3e-7
+                            relative per pair); DD(r) terms rounded to a fixed-
+                            point grid scaled by the largest weights (2^-22
+                            max|w w| / |w w| relative per term), so wsum and
+                            ravg agree to 1e-5 relative for weights within a
+                            factor 3 of each other                              */
     uint64_t n_cellpairs;       /* column pairs kept after pruning                */
     uint64_t n_evaluated;       /* pair evaluations (CF_FLAG_COUNT_EVALS)        */
     uint64_t n_rechecked;       /* pairs re-evaluated in binary64 (FP32 mode)    */
