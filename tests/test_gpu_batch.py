@@ -206,3 +206,19 @@ def test_batch_mixed_dtypes_empty_catalogues_and_many_segments(cuda_device):
         for k, job, x, x2, r in cases:
             assert np.array_equal(r.npairs, single(job, x, x2)), k
     b.close()
+
+
+def test_batch_reports_a_coordinate_outside_the_box_by_job(cuda_device):
+    # the batched gridding checks every segment's coordinates and flags the
+    # job that owns a bad one (periodic: x must lie in [0, boxsize))
+    good = synth.uniform_box(500, 50.0, seed=501)
+    bad = synth.uniform_box(500, 50.0, seed=502)
+    bad.x[17] = 50.0
+    e = synth.log_edges(0.5, 10.0, 6)
+    b = cf.Batch()
+    b.add_xi(*dev(good), e, boxsize=50.0)
+    b.add_xi(*dev(bad), e, boxsize=50.0)
+    with pytest.raises(cf.CfError) as ei:
+        b.run(use_graph=False)
+    assert ei.value.status == cf.CF_EINVAL and "batch job 1" in str(ei.value)
+    b.close()
